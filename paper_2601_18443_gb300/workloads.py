@@ -1,0 +1,109 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module holds no arithmetic of the method: it only generates wall polylines
+(analytic NACA 4-digit sections, rectangles, channels) and the solver
+configurations of the workloads.  Both the CUDA library and the CPU oracle
+receive the same arrays from here.
+
+The paper's own geometries (the NASA TMR NACA 0012 coordinates and the HLPW
+MD-30P30N) are not available; analytic NACA sections stand in for them.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def naca4(m: float, p: float, t: float, n: int) -> np.ndarray:
+    """Closed NACA 4-digit section of unit chord, leading edge at the origin.
+
+    Standard analytic thickness and mean-line formulas with the closed
+    trailing-edge coefficient; cosine spacing with ``n`` intervals per surface.
+    The loop runs trailing edge -> upper surface -> leading edge -> lower
+    surface (counter-clockwise); the first vertex is not repeated.
+    """
+    beta = np.linspace(math.pi, 0.0, n + 1)
+    x = 0.5 * (1.0 - np.cos(beta))                      # 1 -> 0
+    yt = np.maximum(5.0 * t * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x**2 + 0.2843 * x**3 - 0.1036 * x**4), 0.0)
+    if m > 0.0 and p > 0.0:
+        yc = np.where(x < p, m / p**2 * (2 * p * x - x**2), m / (1 - p)**2 * ((1 - 2 * p) + 2 * p * x - x**2))
+        dyc = np.where(x < p, 2 * m / p**2 * (p - x), 2 * m / (1 - p)**2 * (p - x))
+    else:
+        yc = np.zeros_like(x)
+        dyc = np.zeros_like(x)
+    th = np.arctan(dyc)
+    xu, yu = x - yt * np.sin(th), yc + yt * np.cos(th)
+    xl, yl = x + yt * np.sin(th), yc - yt * np.cos(th)
+    upper = np.stack([xu, yu], axis=1)                  # TE .. LE (n+1 points)
+    lower = np.stack([xl, yl], axis=1)[::-1][1:-1]      # after LE .. before TE
+    return np.concatenate([upper, lower], axis=0)
+
+
+def transform(loop: np.ndarray, chord=1.0, alpha_deg=0.0, pivot=(0.25, 0.0), offset=(0.0, 0.0)) -> np.ndarray:
+    """Scale by chord, rotate nose-up by alpha about the pivot (freestream +x), translate."""
+    a = -math.radians(alpha_deg)
+    R = np.array([[math.cos(a), -math.sin(a)], [math.sin(a), math.cos(a)]])
+    pv = np.asarray(pivot, dtype=np.float64) * chord
+    out = (loop * chord - pv) @ R.T + pv
+    return out + np.asarray(offset, dtype=np.float64)
+
+
+def naca_loop(code: str, h_finest: float, chord=1.0, alpha_deg=0.0, pivot=(0.25, 0.0), offset=(0.0, 0.0),
+              max_seg_frac=0.5) -> np.ndarray:
+    """NACA section with every segment shorter than max_seg_frac * h_finest."""
+    m, p, t = int(code[0]) / 100.0, int(code[1]) / 10.0, int(code[2:]) / 100.0
+    n = max(16, int(math.ceil(math.pi * chord / (max_seg_frac * h_finest))))
+    while True:
+        loop = naca4(m, p, t, n)
+        seg = np.linalg.norm(np.diff(np.vstack([loop, loop[:1]]), axis=0), axis=1) * chord
+        if seg.max() <= max_seg_frac * h_finest:
+            break
+        n = int(n * 1.25) + 1
+    return transform(loop, chord, alpha_deg, pivot, offset)
+
+
+def rectangle(x0, y0, x1, y1) -> np.ndarray:
+    return np.array([[x0, y0], [x1, y0], [x1, y1], [x0, y1]], dtype=np.float64)
+
+
+def l_shape(x0, y0, x1, y1, xm, ym) -> np.ndarray:
+    """L-shaped loop: the rectangle [x0,x1]x[y0,y1] minus the corner (xm,x1]x(ym,y1]."""
+    return np.array([[x0, y0], [x1, y0], [x1, ym], [xm, ym], [xm, y1], [x0, y1]], dtype=np.float64)
+
+
+def base_config(**kw) -> dict:
+    cfg = dict(levels=1, nx0=64, ny0=64, x0=0.0, y0=0.0, h0=1.0, layers=8, chord=1.0, Re=1000.0, Ma=0.1,
+               chi_inf=3.0, d_wr=2.0, d_wv=1.0, turbulence=0, wall_model=3, periodic=0, solid_walls=1)
+    cfg.update(kw)
+    return cfg
+
+
+# --- named workloads ----------------------------------------------------------
+
+def naca0012_small(levels=6):
+    """NACA 0012, alpha 0, Re 1e6, Ma 0.1; coarse 128 x 64 over a 16c x 8c box
+    (h0 = c/8), six 2:1 levels to h = c/256; SA-neg with nu_t~ = 3 nu."""
+    h0 = 1.0 / 8.0
+    cfg = base_config(levels=levels, nx0=128, ny0=64, x0=-5.5, y0=-4.0, h0=h0, layers=8, chord=1.0, Re=1.0e6,
+                      Ma=0.1, turbulence=1, wall_model=0, periodic=0, solid_walls=1)
+    hf = h0 / 2 ** (levels - 1)
+    return cfg, [naca_loop("0012", hf, alpha_deg=0.0)]
+
+
+def naca0012_large(box=(8.0, 4.0), layers=12):
+    """NACA 0012, alpha 10 deg, Re 6e6, Ma 0.15; six 2:1 levels with the finest
+    spacing c/4096 (h0 = c/128); box chosen for about 1.5M nodes."""
+    h0 = 1.0 / 128.0
+    nx0, ny0 = int(round(box[0] / h0)), int(round(box[1] / h0))
+    cfg = base_config(levels=6, nx0=nx0, ny0=ny0, x0=-0.375 * box[0] + 0.25, y0=-0.5 * box[1], h0=h0,
+                      layers=layers, chord=1.0, Re=6.0e6, Ma=0.15, turbulence=1, wall_model=0, periodic=0,
+                      solid_walls=1)
+    hf = h0 / 32.0
+    return cfg, [naca_loop("0012", hf, alpha_deg=10.0)]
+
+
+def noise_field(shape, amplitude, seed):
+    """Seeded uniform noise in [-amplitude, amplitude]."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-amplitude, amplitude, size=shape)

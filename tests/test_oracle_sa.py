@@ -1,0 +1,114 @@
+"""Pins of the oracle's SA-neg model (Sec 2.2, eqs 11-17) and its explicit
+finite-difference update (Lax-Wendroff convection, centred diffusion, LSQ vorticity)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+KAPPA, CB1, CB2, SIGMA, CV1 = 0.41, 0.1355, 0.622, 2.0 / 3.0, 7.1
+CX = np.array([0, 1, -1, 0, 0, 1, -1, 1, -1])
+CY = np.array([0, 0, 0, 1, -1, 1, -1, -1, 1])
+FAR = 1e12
+
+
+def eq21(yp):
+    k3 = (KAPPA * yp) ** 3
+    return (CV1**3 + k3) / (CV1**3 + k3 * (1.0 + KAPPA * yp))
+
+
+@pytest.mark.parametrize("yp", [0.1, 1.0, 4.0, 10.0, 30.0, 100.0, 1e3, 1e4])
+def test_law_of_the_wall_balance(yp):
+    # With chi = kappa y+ and du/dy from eq 21 (eq 20 solution), production - destruction must
+    # balance the diffusion term (1/sigma)[d/dy((nu+nt)dnt/dy) + cb2 (dnt/dy)^2] = kappa^2 ut^2 (1+cb2)/sigma
+    # exactly, at every y+ (pins fv1, fv2, the S_bar reading, S_tilde, r, g, fw and cw1).
+    nu, ut = 1.5e-5, 0.05
+    y = yp * nu / ut
+    vort = ut * ut / nu * eq21(yp)
+    P, D = oracle.sa_source(KAPPA * yp, nu, vort, y)
+    diff = KAPPA**2 * ut**2 * (1 + CB2) / SIGMA
+    assert (P - D + diff) / diff == pytest.approx(0.0, abs=1e-12)
+
+
+def test_modified_vorticity_stays_positive_and_continuous():
+    # eq 14 second branch (S_bar < -cv2 Omega) must keep S_tilde positive ("defined to be positive")
+    # and meet the first branch continuously at S_bar = -cv2 Omega (reading cv3 = 0.9)
+    nu, chi = 1e-3, 5.0                       # fv2 < 0 at chi = 5
+    vort = 1.0
+    fv1 = chi**3 / (chi**3 + CV1**3)
+    fv2 = 1 - chi / (1 + chi * fv1)
+    st_prev = None
+    for ratio in np.linspace(-0.05, -3.0, 300):      # S_bar / Omega
+        d = math.sqrt(chi * nu * fv2 / (KAPPA**2 * ratio * vort))
+        P, _ = oracle.sa_source(chi, nu, vort, d)
+        st = P / (CB1 * chi * nu)
+        assert st > 0
+        assert st < vort * 1.000001
+        if st_prev is not None:
+            assert abs(st - st_prev) < 0.05 * vort
+        st_prev = st
+    # continuity at the switch point
+    for eps in (1e-7, -1e-7):
+        r = -0.7 + eps
+        d = math.sqrt(chi * nu * fv2 / (KAPPA**2 * r * vort))
+        P, _ = oracle.sa_source(chi, nu, vort, d)
+        assert P / (CB1 * chi * nu) == pytest.approx(0.3 * vort, abs=1e-5)
+
+
+def test_negative_branch_continuous_at_zero():
+    nu, vort, d = 1e-5, 0.3, 2.0
+    for eps in (1e-12, -1e-12):
+        P, D = oracle.sa_source(eps, nu, vort, d)
+        assert abs(P - D) < 1e-15
+    # SA-neg production is positive for negative nu_t~ (drives it back towards zero), eq 17
+    P, D = oracle.sa_source(-0.5, nu, vort, d)
+    assert P > 0 and D < 0
+
+
+def _stencil(fun):
+    return np.array([fun(CX[k], CY[k]) for k in range(9)], dtype=np.float64)
+
+
+@pytest.mark.parametrize("u,v", [(0.3, 0.0), (0.0, -0.2), (0.25, 0.15), (-0.4, 0.3)])
+def test_lax_wendroff_translates_quadratics_exactly(u, v):
+    # a second-order Taylor (Lax-Wendroff) step advects any quadratic field exactly; nu -> 0 removes
+    # diffusion (it scales as nu^2 against nu for convection) and d -> inf removes the sources
+    c = [1.3, 0.2, -0.35, 0.07, -0.04, 0.11]
+    q = lambda x, y: c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * x * y + c[5] * y * y
+    chi = _stencil(q)
+    new = oracle.sa_update_point(chi, np.full(9, u), np.full(9, v), FAR, 1e-14)
+    assert new == pytest.approx(q(-u, -v), rel=1e-9)
+
+
+@pytest.mark.parametrize("grad", [(0.01, -0.02, 0.03, 0.005), (0.0, 0.05, -0.02, 0.0), (-0.03, 0.0, 0.0, 0.04)])
+def test_lsq_vorticity_exact_for_linear_velocity(grad):
+    # uniform chi: no convection or diffusion; the update is cb1 * Omega * chi with Omega = |dv/dx - du/dy|
+    a, b, c, e = grad
+    ux = _stencil(lambda x, y: 0.1 + a * x + b * y)
+    uy = _stencil(lambda x, y: -0.05 + c * x + e * y)
+    # constant velocity offset is removed from convection because chi is uniform
+    chi0 = 2.0
+    new = oracle.sa_update_point(np.full(9, chi0), ux, uy, FAR, 1e-6)
+    assert (new - chi0) / (CB1 * chi0) == pytest.approx(abs(c - b), rel=1e-9, abs=1e-15)
+
+
+def test_diffusion_second_order():
+    # u = 0, d -> inf: the update equals (1/sigma)[div((nu+nt) grad nt) + cb2 |grad nt|^2] up to O(h^2)
+    nu = 1.0
+    errs = []
+    for h in (0.2, 0.1, 0.05):
+        f = lambda x, y: 1.0 + 0.5 * math.sin(0.7 + x) * math.cos(0.3 + 2 * y)
+        chi = _stencil(lambda i, j: f(i * h, j * h))
+        new = oracle.sa_update_point(chi, np.zeros(9), np.zeros(9), FAR, nu)
+        # analytic right-hand side in physical units, scaled by h^2 for the unit lattice
+        x, y = 0.0, 0.0
+        nt = f(x, y)
+        fx = 0.5 * math.cos(0.7 + x) * math.cos(0.3 + 2 * y)
+        fy = -1.0 * math.sin(0.7 + x) * math.sin(0.3 + 2 * y)
+        fxx = -0.5 * math.sin(0.7 + x) * math.cos(0.3 + 2 * y)
+        fyy = -2.0 * math.sin(0.7 + x) * math.cos(0.3 + 2 * y)
+        rhs = ((1 + nt) * (fxx + fyy) + (fx * fx + fy * fy) + CB2 * (fx * fx + fy * fy)) / SIGMA
+        errs.append(abs((new - chi[0]) / h**2 - rhs))
+    assert math.log2(errs[0] / errs[1]) > 1.8
+    assert math.log2(errs[1] / errs[2]) > 1.8
