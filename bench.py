@@ -1,0 +1,332 @@
+"""Throughput benchmark of the GB300 LBM-RANS step.
+
+Workload: NACA 0012 at alpha = 10 deg, Re = 6e6, Ma = 0.15, six 2:1 levels with the
+finest spacing c/4096 (coarse h0 = c/128 over an 8c x 4c box, about 1.5M nodes),
+FP32 populations and nu_tilde, SA-neg, virtual-node wall function.  One step is one
+coarse time step: 2^l sub-steps of every level l, each with its wall function (finest
+level), SA-neg update, stream-collide with the cut-link bounce-back and the Rohde
+transfers.  The geometry is built once; inputs are synthetic (analytic NACA section).
+
+Metric: MLUPS = sum_l (active nodes of level l) * 2^l per coarse step / time.
+
+Arms:
+  default            the CUDA library (one replica per rank under torchrun, no collective)
+  --impl reference   the FP64 CPU oracle on the host cores (rank 0 only)
+
+Timing: W untimed warm-up steps, then K steps timed with CUDA events on the solver's
+stream; a 512 MB buffer is written between timed steps to flush L2 (the flush is
+outside the events).  The dominant kernel's roofline comes from a per-launch event
+pass over the same workload right after the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2601_18443_gb300 import workloads as W  # noqa: E402
+
+METRIC = "MLUPS"
+WORKLOAD = "naca0012_a10_re6e6_ma015_6lvl_c4096"
+CPU_SAMPLE = "naca0012_a0_re1e6_ma01_6lvl_c256"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of the SM clock and throttle reasons."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- oracle arm
+
+def run_oracle_sample(steps, warmup):
+    """Times the FP64 oracle on the host cores; returns (MLUPS, cores, sample text)."""
+    import oracle
+
+    cfg, loops = W.naca0012_small()
+    s = oracle.Solver(cfg)
+    s.set_geometry(loops)
+    nu = 0
+    for l in range(cfg["levels"]):
+        m = s.get_fields(l)["mask"]
+        nu += int(((m == 1) | (m == 2)).sum()) << l
+    s.step(warmup)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    s.close()
+    mlups = nu * steps / dt / 1e6
+    sample = (f"{CPU_SAMPLE}: NACA 0012 6 levels to c/256 (coarse 128x64 over 16c x 8c), "
+              f"{nu} node updates per coarse step, {steps} coarse steps after {warmup} warm-up, FP64 oracle, "
+              f"{dt:.2f} s")
+    return mlups, oracle.threads(), sample, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    steps = max(1, args.steps)
+    mlups, cores, sample, dt = run_oracle_sample(steps, max(0, min(args.warmup, 3)))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": 0,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": CPU_SAMPLE, "arm": "FP64 CPU oracle on host cores (bounded sample)"},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def gpu_arm(args, rank, world, dist):
+    import torch
+
+    import paper_2601_18443_gb300 as pkg
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.library()
+    stream = torch.cuda.current_stream(dev)
+    cfg, loops = W.naca0012_large()
+    s = pkg.Solver(cfg, stream=stream)
+    s.set_geometry(loops)
+    info = s.info()
+    nu_step = info["node_updates_per_step"]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.5)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        s.step_async(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    s.synchronize()          # status word: non-finite fields raise here
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nu_step * K * world / (ms * 1e-3) / 1e6
+
+    # dominant kernel: per-launch CUDA events on the solver stream over the same workload
+    kt = s.time_kernels(max(2, min(10, K)))
+    fin = kt["stream_collide_finest"]
+    avg_ms = fin["ms"] / max(fin["launches"], 1)
+    act_fin = info["cells_active"][-1]
+    bpn = info["bytes_per_node_update"]
+    achieved = act_fin * bpn / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    total_kt = sum(v["ms"] for v in kt.values())
+    loads = s.get_loads()
+
+    # end to end through the public API: host polyline -> grid build + upload -> K steps -> loads to host
+    e2e = None
+    if rank == 0 or world > 1:
+        xy_bytes = sum(np.asarray(p).nbytes for p in loops) + 4 * (len(loops) + 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = pkg.Solver(cfg, stream=stream)
+        s2.set_geometry(loops)
+        s2.step(K)
+        l2 = s2.get_loads()
+        t1 = time.perf_counter()
+        dev_b = s2.info()["device_bytes"]
+        s2.close()
+        n_seg = len(l2["cp"])
+        e2e = {"value": round(nu_step * K / (t1 - t0) / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": int((xy_bytes + dev_b) / K),
+               "d2h_bytes_per_step": int((56 + 16 * n_seg) / K),
+               "what": f"lbm_create + lbm_set_geometry (host grid build, table upload) + lbm_step({K}) + "
+                       f"lbm_get_loads, wall clock; h2d counts the polyline plus the uploaded tables "
+                       f"(upper bound: device bytes held) spread over the K steps"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups_c, cores, sample, _ = run_oracle_sample(args.cpu_steps, 2)
+        cpu = {"value": round(mlups_c, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample}
+
+    hbm = None
+    if rank == 0 and not args.no_hbm_grid:
+        hbm = hbm_grid_roofline(pkg, stream, peak, peak_kind)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms / K, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": int(sum(info["cells_active"])),
+                       "node_updates_per_step": int(nu_step), "levels": info["levels"],
+                       "cells_active_per_level": [int(x) for x in info["cells_active"]],
+                       "l2": "512 MB buffer written between timed steps (outside the events)",
+                       "replicas": world, "parallelism": f"replicas{world}"},
+            "gbs_full_step_algorithmic": round(value * 1e6 * (bpn + (20.0 if cfg["turbulence"] else 0.0)) / 1e9, 1),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "k_stream_collide (finest level)", "peak_kind": peak_kind,
+                         "bytes_per_launch": int(act_fin * bpn), "avg_launch_ms": round(avg_ms, 5),
+                         "share_of_step": round(fin["ms"] / total_kt, 3) if total_kt > 0 else None},
+            "kernel_times": {k: {"ms_per_step": round(v["ms"] / max(2, min(10, K)), 4), "launches": v["launches"]}
+                             for k, v in kt.items()},
+            "gpu_launches": int(info["kernels_per_step"] * K),
+            "clocks": clk,
+            "loads": {"CL": loads["CL"], "CD": loads["CD"], "step": loads["step"]},
+            "e2e": e2e,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        if hbm is not None:
+            line["roofline_hbm_grid"] = hbm
+        print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
+def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096):
+    """Stream-collide on one periodic 4096 x 4096 level (1.5 GB of traffic per launch,
+    far beyond L2): the kernel's HBM roofline without multilevel effects."""
+    cfg = W.base_config(levels=1, nx0=n, ny0=n, h0=1.0, Re=1000.0, Ma=0.1, periodic=1, solid_walls=0,
+                        turbulence=1, wall_model=3)
+    s = pkg.Solver(cfg, stream=stream)
+    s.set_geometry([])
+    s.step(3)
+    kt = s.time_kernels(5)
+    info = s.info()
+    sc = kt["stream_collide_finest"]
+    avg = sc["ms"] / sc["launches"]
+    bpl = info["cells_active"][0] * info["bytes_per_node_update"]
+    s.close()
+    ach = bpl / (avg * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "kernel": "k_stream_collide", "grid": f"{n}x{n} periodic, 1 level, SA on", "bytes_per_launch": int(bpl),
+            "avg_launch_ms": round(avg, 4), "mlups": round(info["cells_active"][0] / avg / 1e3, 1),
+            "peak_kind": peak_kind}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hbm-grid", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        td.init_process_group("nccl")
+        dist = td
+    rc = gpu_arm(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) LBM-RANS library.
+ *
+ * One time step of the lattice Boltzmann RANS method of Ponsin & Lozano,
+ * "Enhanced Wall Boundary Modeling for Turbulent Flows Using the Lattice
+ * Boltzmann Method with Adaptive Cartesian Grids" (arXiv 2601.18443):
+ * D2Q9 central-moment stream-collide relaxing with nu + nu_t (Sec 2.1, eqs 1-10),
+ * virtual-node slip-velocity interpolated bounce-back on cut wall links
+ * (Sec 2.3, eqs 24-28), SA-neg finite-difference update of nu_tilde (Sec 2.2,
+ * eqs 11-17), Rohde explosion/coalescence between 2:1 levels with level
+ * sub-cycling (Sec 2.1), and surface loads (Sec 3.1.3, eqs 29-30).
+ *
+ * Conventions (every entry point):
+ *  - Status codes, never exceptions or aborts.  After an error the handle stays
+ *    valid for lbm_get_* / lbm_last_error / lbm_destroy.
+ *  - All pointer arguments are HOST pointers owned by the caller; inputs are
+ *    copied during the call, outputs are written into caller-allocated buffers
+ *    whose capacity is passed in.  The handle owns all device memory.
+ *  - Coordinates returned for geometry are in finest-level lattice units
+ *    measured from the box origin (x0, y0): x_lat = (x - x0) / h_finest.  Level-l
+ *    cell (i, j) has its centre at ((i + 0.5) 2^(L-1-l), (j + 0.5) 2^(L-1-l)).
+ *  - Field arrays are row-major over the level's present-cell box returned by
+ *    lbm_get_level_box: element (j - j0) * nx + (i - i0).
+ *  - Every call runs on the solver's CUDA stream (cfg->cuda_stream or a stream
+ *    the library creates) and is synchronous unless its name ends in _async.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_solver lbm_solver;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = -1,
+    LBM_ERR_OOM = -2,
+    LBM_ERR_CUDA = -3,
+    LBM_ERR_NO_GEOMETRY = -4,
+    LBM_ERR_GEOMETRY = -5,
+    LBM_ERR_DIVERGED = -6,
+    LBM_ERR_TIMEOUT = -7
+} lbm_status;
+
+typedef struct {
+    int levels;             /* L >= 1 levels of 2:1 refinement, level 0 coarsest (Sec 2.1)          */
+    int nx0, ny0;           /* level-0 cells                                                         */
+    double x0, y0, h0;      /* box origin and level-0 cell size, chord units                         */
+    int layers;             /* refinement band width in cells of each level (Sec 2.1), >= 3          */
+    double chord, Re, Ma;   /* reference chord, Reynolds number on the chord, Mach number            */
+    double chi_inf;         /* inlet and initial nu_tilde / nu (Sec 3.1.1: 3)                        */
+    double d_wr, d_wv;      /* reference / virtual node wall distances in finest cells (Sec 2.3: 2, 1) */
+    int turbulence;         /* 0 laminar, 1 SA-neg                                                   */
+    int wall_model;         /* 0 virtual-node slip (Sec 2.3), 2 prescribed slip per loop, 3 no-slip  */
+    int periodic;           /* 1: periodic level-0 box without domain BCs (nx0 % 32 == 0, ny0 % 8 == 0) */
+    int solid_walls;        /* 1: loops are walls; 0: loops only drive the refinement                */
+    int store;              /* population storage: 0 FP32 shifted (f - w_i); 1 FP16 and 2 BF16 reserved */
+    void *cuda_stream;      /* cudaStream_t to run on, or NULL for a library-owned stream            */
+    void *(*dev_alloc)(size_t bytes, void *stream, void *ctx); /* optional device allocator          */
+    void (*dev_free)(void *ptr, void *stream, void *ctx);      /* its matching free                  */
+    void *alloc_ctx;        /* passed back to dev_alloc / dev_free                                   */
+} lbm_config;
+
+typedef struct {
+    double CL, CD, CDp, CDf; /* eq 30: lift, drag, pressure and friction drag                        */
+    double mass;             /* sum over levels of h_l^2 sum_active rho (finest-cell area units)     */
+    double dCL;              /* CL minus the CL of the previous lbm_get_loads call (0 on the first)  */
+    long long step;          /* coarse steps taken since lbm_set_geometry                            */
+} lbm_loads;
+
+typedef struct {
+    int levels;
+    long long cells_active[16];   /* active fluid cells per level                                    */
+    long long cells_present[16];  /* present cells (active, covered, ghost, solid) per level         */
+    long long slots[16];          /* device cell slots per level (tiles x 256)                       */
+    long long node_updates_per_step; /* sum_l active_l * 2^l per coarse step                         */
+    long long wall_records, cut_links, surface_segments;
+    long long kernels_per_step;   /* kernel launches issued per coarse step                          */
+    double bytes_per_node_update; /* algorithmic bytes of the stream-collide per node update         */
+    double device_bytes;          /* device memory held by the handle                                */
+} lbm_info;
+
+/* Per-kernel-class timing of eagerly launched steps (CUDA events on the solver stream). */
+typedef struct {
+    int n_classes;
+    char name[8][32];
+    double total_ms[8];
+    long long launches[8];
+    long long cells[8];           /* cell slots processed by all launches of the class               */
+} lbm_kernel_times;
+
+/* Create a solver from a level/box specification (Sec 2.1, Sec 3.1.1).  No device work
+ * beyond creating the stream.  Errors: LBM_ERR_INVALID_ARG for a bad spec, LBM_ERR_CUDA. */
+lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out);
+
+/* Build the multilevel grid, cut links and wall records from closed wall polylines
+ * (Sec 2.1 pre-processor, Sec 2.3 preprocessing), upload them and initialise the state
+ * to the equilibrium of rho = 1, u = (U, 0), chi = chi_inf.  xy: 2 * n_points doubles
+ * (x, y) in chord units; loop_offsets: n_loops + 1 ints, loop k = points
+ * [loop_offsets[k], loop_offsets[k+1]), first vertex not repeated, any orientation.
+ * Errors: LBM_ERR_GEOMETRY (refinement breaks 2:1 nesting or reaches the box edge, a
+ * wall touches a non-finest cell, a reference stencil leaves the finest level),
+ * LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_offsets, int n_loops);
+
+/* Prescribed wall slip velocity per loop for wall_model 2 (lattice units): uw_xy holds
+ * 2 * n_loops doubles.  Errors: LBM_ERR_INVALID_ARG, LBM_ERR_NO_GEOMETRY. */
+lbm_status lbm_set_wall_slip(lbm_solver *s, const double *uw_xy, int n_loops);
+
+/* Advance n_coarse_steps level-0 steps (each: 2^l sub-steps of level l, Sec 2.1).
+ * Synchronous: returns after the work completes; checks the device status word and
+ * the non-finite flag.  Errors: LBM_ERR_NO_GEOMETRY, LBM_ERR_DIVERGED, LBM_ERR_CUDA. */
+lbm_status lbm_step(lbm_solver *s, int n_coarse_steps);
+
+/* Enqueue n_coarse_steps on the solver stream without waiting (no status check);
+ * pair with lbm_synchronize. */
+lbm_status lbm_step_async(lbm_solver *s, int n_coarse_steps);
+
+/* Wait for enqueued work and check the status word (as lbm_step). */
+lbm_status lbm_synchronize(lbm_solver *s);
+
+/* Present-cell box of a level: cells i in [i0, i0 + nx), j in [j0, j0 + ny). */
+lbm_status lbm_get_level_box(lbm_solver *s, int level, int *i0, int *j0, int *nx, int *ny);
+
+/* Copy a level's macroscopic fields to the host (any pointer may be NULL).  cap is the
+ * element capacity of each array (>= nx * ny).  rho, ux, uy in lattice units; nu_tilde_ratio
+ * is nu_tilde / nu (chi).  Cells without values hold NaN.  mask: 0 absent, 1 active fluid,
+ * 2 boundary node B, 3 covered, 4 ghost, 5 solid. */
+lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, double *uy,
+                          double *nu_tilde_ratio, unsigned char *mask, int cap);
+
+/* Set the macroscopic fields of the active fluid cells of a level (NULL = keep) and
+ * reset their populations to the equilibrium of eq 4; the interfaces are re-synchronised
+ * (restriction, explosion, ghost reconstruction).  Arrays as in lbm_get_fields. */
+lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const double *ux,
+                          const double *uy, const double *nu_tilde_ratio);
+
+/* Surface loads (eqs 29-30) from the wall function evaluated on the current state.
+ * cp_seg / cf_seg (may be NULL) receive per-segment C_p and signed C_f, n_seg_cap their
+ * capacity; *n_seg the number of surface segments. */
+lbm_status lbm_get_loads(lbm_solver *s, lbm_loads *out, double *cp_seg, double *cf_seg,
+                         int n_seg_cap, int *n_seg);
+
+/* Geometry tables (host copies, for inspection and bit-exact comparison).
+ * cut links (finest level, ordered by (j, i, dir)): ij_dir[3k] = i, j, pulled direction
+ * 1..8 (paper index 2..9), q[k] = wall fraction of eq 27.  Wall records (ordered by
+ * (j, i)): ij[2r]; geo[9r] = IW x, IW y, n x, n y, d_WB, R x, R y, loop, segment;
+ * nstencil[r] = reference-stencil size.  Wall state (wall function on the current
+ * state): st[8r] = rho_W, u_W x, u_W y, u_tau, chi_B, t x, t y, |u_Rt|.  Any pointer
+ * may be NULL to query the count. */
+lbm_status lbm_get_cut_links(lbm_solver *s, int *ij_dir, double *q, int cap, int *n);
+lbm_status lbm_get_wall_records(lbm_solver *s, int *ij, double *geo, int *nstencil, int cap, int *n);
+lbm_status lbm_get_wall_state(lbm_solver *s, double *st, int cap, int *n);
+
+/* Wall distance of the active fluid cells of a level (level lattice units, NaN elsewhere). */
+lbm_status lbm_get_wall_distance(lbm_solver *s, int level, double *d, int cap);
+
+/* Sizes, counts and the algorithmic bytes per node update. */
+lbm_status lbm_get_info(lbm_solver *s, lbm_info *out);
+
+/* Run n_coarse_steps with every kernel launched eagerly and bracketed by CUDA events on
+ * the solver stream; accumulate device time per kernel class.  Same results as lbm_step. */
+lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times *out);
+
+/* Per-handle message of the last error. */
+const char *lbm_last_error(const lbm_solver *s);
+
+/* Free everything the handle owns.  NULL-safe. */
+void lbm_destroy(lbm_solver *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,1 +1,260 @@
-"""GB300-native LBM-RANS hot path (arXiv 2601.18443)."""
+"""GB300-native (sm_103a) LBM-RANS hot path of Ponsin & Lozano (arXiv 2601.18443).
+
+Thin ctypes binding over the C ABI in ``include/lbm.h`` (``liblbm.so`` built
+in-tree from ``csrc/``).  Argument marshalling only: every step of the path runs
+in the library's CUDA kernels.  There is no CPU fallback; if the library is not
+built the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build_ext
+
+__all__ = ["Solver", "LBMError", "library", "build"]
+
+_lib = None
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbm status {code}: {msg}")
+        self.code = code
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class lbm_config(C.Structure):
+    _fields_ = [
+        ("levels", C.c_int), ("nx0", C.c_int), ("ny0", C.c_int),
+        ("x0", C.c_double), ("y0", C.c_double), ("h0", C.c_double),
+        ("layers", C.c_int),
+        ("chord", C.c_double), ("Re", C.c_double), ("Ma", C.c_double),
+        ("chi_inf", C.c_double), ("d_wr", C.c_double), ("d_wv", C.c_double),
+        ("turbulence", C.c_int), ("wall_model", C.c_int), ("periodic", C.c_int),
+        ("solid_walls", C.c_int), ("store", C.c_int),
+        ("cuda_stream", C.c_void_p),
+        ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
+    ]
+
+
+class lbm_loads(C.Structure):
+    _fields_ = [("CL", C.c_double), ("CD", C.c_double), ("CDp", C.c_double), ("CDf", C.c_double),
+                ("mass", C.c_double), ("dCL", C.c_double), ("step", C.c_longlong)]
+
+
+class lbm_info(C.Structure):
+    _fields_ = [("levels", C.c_int), ("cells_active", C.c_longlong * 16), ("cells_present", C.c_longlong * 16),
+                ("slots", C.c_longlong * 16), ("node_updates_per_step", C.c_longlong),
+                ("wall_records", C.c_longlong), ("cut_links", C.c_longlong), ("surface_segments", C.c_longlong),
+                ("kernels_per_step", C.c_longlong), ("bytes_per_node_update", C.c_double),
+                ("device_bytes", C.c_double)]
+
+
+class lbm_kernel_times(C.Structure):
+    _fields_ = [("n_classes", C.c_int), ("name", (C.c_char * 32) * 8), ("total_ms", C.c_double * 8),
+                ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    return _build_ext.build(force=force, verbose=verbose)
+
+
+def library():
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build_ext.SO):
+        raise RuntimeError("liblbm.so is not built: run __graft_entry__.build() (the CUDA library is required)")
+    L = C.CDLL(_build_ext.SO)
+    vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+    sig = {
+        "lbm_create": ([C.POINTER(lbm_config), C.POINTER(vp)], C.c_int),
+        "lbm_set_geometry": ([vp, dp, ip, C.c_int], C.c_int),
+        "lbm_set_wall_slip": ([vp, dp, C.c_int], C.c_int),
+        "lbm_step": ([vp, C.c_int], C.c_int),
+        "lbm_step_async": ([vp, C.c_int], C.c_int),
+        "lbm_synchronize": ([vp], C.c_int),
+        "lbm_get_level_box": ([vp, C.c_int, ip, ip, ip, ip], C.c_int),
+        "lbm_get_fields": ([vp, C.c_int, dp, dp, dp, dp, vp, C.c_int], C.c_int),
+        "lbm_set_fields": ([vp, C.c_int, dp, dp, dp, dp], C.c_int),
+        "lbm_get_loads": ([vp, C.POINTER(lbm_loads), dp, dp, C.c_int, ip], C.c_int),
+        "lbm_get_cut_links": ([vp, ip, dp, C.c_int, ip], C.c_int),
+        "lbm_get_wall_records": ([vp, ip, dp, ip, C.c_int, ip], C.c_int),
+        "lbm_get_wall_state": ([vp, dp, C.c_int, ip], C.c_int),
+        "lbm_get_wall_distance": ([vp, C.c_int, dp, C.c_int], C.c_int),
+        "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
+        "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
+        "lbm_last_error": ([vp], C.c_char_p),
+        "lbm_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+class Solver:
+    """One LBM-RANS solve on the current CUDA device (see include/lbm.h)."""
+
+    def __init__(self, cfg: dict, stream=None, torch_allocator: bool = False):
+        self._lib = library()
+        c = lbm_config()
+        for name, _ in lbm_config._fields_:
+            if name in ("cuda_stream", "dev_alloc", "dev_free", "alloc_ctx"):
+                continue
+            setattr(c, name, cfg.get(name, 0))
+        self.cfg = dict(cfg)
+        self._keep = []
+        if stream is not None:
+            c.cuda_stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        if torch_allocator:
+            import torch
+            blocks = {}
+
+            def _alloc(nbytes, stream_, ctx):
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+                blocks[t.data_ptr()] = t
+                return t.data_ptr()
+
+            def _free(ptr, stream_, ctx):
+                blocks.pop(int(ptr), None)
+
+            a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._keep += [a, f, blocks]
+            c.dev_alloc, c.dev_free = a, f
+        h = C.c_void_p()
+        rc = self._lib.lbm_create(C.byref(c), C.byref(h))
+        if rc != 0:
+            raise LBMError(rc, "lbm_create rejected the configuration")
+        self._h = h
+        self._cfg_struct = c
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LBMError(rc, self._lib.lbm_last_error(self._h).decode())
+
+    # -- API
+    def set_geometry(self, loops):
+        xy = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64) for p in loops])
+                                  if loops else np.zeros((0, 2)))
+        off = np.zeros(len(loops) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([len(p) for p in loops])
+        self._check(self._lib.lbm_set_geometry(self._h, _dp(xy), _ip(off), len(loops)))
+        self.n_loops = len(loops)
+
+    def set_wall_slip(self, uw):
+        uw = np.ascontiguousarray(uw, dtype=np.float64).reshape(-1)
+        self._check(self._lib.lbm_set_wall_slip(self._h, _dp(uw), len(uw) // 2))
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_step(self._h, int(n)))
+
+    def step_async(self, n=1):
+        self._check(self._lib.lbm_step_async(self._h, int(n)))
+
+    def synchronize(self):
+        self._check(self._lib.lbm_synchronize(self._h))
+
+    def level_box(self, level):
+        v = [C.c_int() for _ in range(4)]
+        self._check(self._lib.lbm_get_level_box(self._h, level, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def get_fields(self, level):
+        i0, j0, nx, ny = self.level_box(level)
+        rho, ux, uy, chi = (np.zeros((ny, nx)) for _ in range(4))
+        mask = np.zeros((ny, nx), dtype=np.uint8)
+        self._check(self._lib.lbm_get_fields(self._h, level, _dp(rho), _dp(ux), _dp(uy), _dp(chi),
+                                             mask.ctypes.data_as(C.c_void_p), nx * ny))
+        return dict(rho=rho, ux=ux, uy=uy, chi=chi, mask=mask, i0=i0, j0=j0)
+
+    def set_fields(self, level, rho=None, ux=None, uy=None, chi=None):
+        i0, j0, nx, ny = self.level_box(level)
+        arrs = [None if a is None else np.ascontiguousarray(np.broadcast_to(a, (ny, nx)), dtype=np.float64)
+                for a in (rho, ux, uy, chi)]
+        self._check(self._lib.lbm_set_fields(self._h, level, *[None if a is None else _dp(a) for a in arrs]))
+
+    def get_loads(self):
+        out = lbm_loads()
+        n = C.c_int()
+        self._check(self._lib.lbm_get_loads(self._h, C.byref(out), None, None, 0, C.byref(n)))
+        cap = n.value
+        cp, cf = np.zeros(max(cap, 1)), np.zeros(max(cap, 1))
+        self._check(self._lib.lbm_get_loads(self._h, C.byref(out), _dp(cp), _dp(cf), cap, C.byref(n)))
+        d = {k: getattr(out, k) for k, _ in lbm_loads._fields_}
+        d["cp"], d["cf"] = cp[:cap], cf[:cap]
+        return d
+
+    def cut_links(self):
+        n = C.c_int()
+        self._check(self._lib.lbm_get_cut_links(self._h, None, None, 0, C.byref(n)))
+        ijd = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+        q = np.zeros(max(n.value, 1))
+        self._check(self._lib.lbm_get_cut_links(self._h, _ip(ijd), _dp(q), n.value, C.byref(n)))
+        return ijd[:n.value], q[:n.value]
+
+    def wall_records(self):
+        n = C.c_int()
+        self._check(self._lib.lbm_get_wall_records(self._h, None, None, None, 0, C.byref(n)))
+        m = max(n.value, 1)
+        ij, geo, ns = np.zeros((m, 2), dtype=np.int32), np.zeros((m, 9)), np.zeros(m, dtype=np.int32)
+        self._check(self._lib.lbm_get_wall_records(self._h, _ip(ij), _dp(geo), _ip(ns), n.value, C.byref(n)))
+        return ij[:n.value], geo[:n.value], ns[:n.value]
+
+    def wall_state(self):
+        n = C.c_int()
+        self._check(self._lib.lbm_get_wall_state(self._h, None, 0, C.byref(n)))
+        st = np.zeros((max(n.value, 1), 8))
+        self._check(self._lib.lbm_get_wall_state(self._h, _dp(st), n.value, C.byref(n)))
+        return st[:n.value]
+
+    def wall_distance(self, level):
+        i0, j0, nx, ny = self.level_box(level)
+        d = np.zeros((ny, nx))
+        self._check(self._lib.lbm_get_wall_distance(self._h, level, _dp(d), nx * ny))
+        return d
+
+    def info(self):
+        out = lbm_info()
+        self._check(self._lib.lbm_get_info(self._h, C.byref(out)))
+        L = out.levels
+        return dict(levels=L, cells_active=list(out.cells_active[:L]), cells_present=list(out.cells_present[:L]),
+                    slots=list(out.slots[:L]), node_updates_per_step=out.node_updates_per_step,
+                    wall_records=out.wall_records, cut_links=out.cut_links,
+                    surface_segments=out.surface_segments, kernels_per_step=out.kernels_per_step,
+                    bytes_per_node_update=out.bytes_per_node_update, device_bytes=out.device_bytes)
+
+    def time_kernels(self, n=1):
+        out = lbm_kernel_times()
+        self._check(self._lib.lbm_time_kernels(self._h, int(n), C.byref(out)))
+        return {out.name[i].value.decode(): dict(ms=out.total_ms[i], launches=out.launches[i], cells=out.cells[i])
+                for i in range(out.n_classes)}

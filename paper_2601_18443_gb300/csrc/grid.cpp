@@ -1,0 +1,562 @@
+// grid.cpp -- host builder of the sparse tiled 2:1 multilevel grid.
+//
+// Reading of the paper's pre-processor (Sec 2.1; its octree/ADT/advancing-front
+// generator is not specified): level l >= 1 holds the children of level l-1
+// cells whose centre lies within R_l of a wall, R_{L-1} = layers h_{L-1},
+// R_l = R_{l+1} + layers h_l.  Active cells with a covered D2Q9 neighbour form the
+// band whose children are ghost cells of the next level (Rohde transfers).  A cell
+// is solid iff its centre lies inside or on a wall loop.  All yes/no decisions use
+// exact integer arithmetic on vertices snapped to 1/4096 of the finest cell, so
+// that the tables are bit-exact and reproducible.
+//
+// Algorithms: per-segment candidate boxes for the refinement bands, a row scanline
+// with exact rational crossings for the solid painting, a bounding-volume tree over
+// the wall segments for distances, feet of perpendiculars and link crossings.
+#include "grid.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace lbmgrid {
+
+typedef __int128 i128;
+static const int CX[9] = LBM_CX_INIT;
+static const int CY[9] = LBM_CY_INIT;
+static const long long FIXU = 4096;   // fixed-point units per finest cell
+static const double DCAP = 1.0e12;
+
+static inline long long fdiv(i128 a, i128 b)
+{   // floor(a / b), b > 0
+    i128 q = a / b;
+    if ((a % b) != 0 && (a < 0)) q -= 1;
+    return (long long)q;
+}
+static inline long long cdiv(i128 a, i128 b) { return -fdiv(-a, b); }
+
+long Level::slot(long long i, long long j) const
+{
+    long long tx = fdiv(i, LBM_TX), ty = fdiv(j, LBM_TY);
+    if (tx < tx0 || ty < ty0 || tx >= tx0 + ntx || ty >= ty0 + nty) return -1;
+    int t = tile_of[(size_t)(ty - ty0) * ntx + (tx - tx0)];
+    if (t < 0) return -1;
+    return (long)t * LBM_TILE + (long)(j - ty * LBM_TY) * LBM_TX + (long)(i - tx * LBM_TX);
+}
+
+// ---------------------------------------------------------------- exact tests
+static bool within_r(IPt a, IPt b, IPt p, long long R)
+{
+    i128 ex = b.x - a.x, ey = b.y - a.y, px = p.x - a.x, py = p.y - a.y;
+    i128 l2 = ex * ex + ey * ey, dot = px * ex + py * ey, R2 = (i128)R * R;
+    if (l2 == 0 || dot <= 0) return px * px + py * py <= R2;
+    if (dot >= l2) {
+        i128 qx = p.x - b.x, qy = p.y - b.y;
+        return qx * qx + qy * qy <= R2;
+    }
+    i128 c = ex * py - ey * px;
+    return c * c <= R2 * l2;
+}
+
+static bool on_seg(IPt a, IPt b, IPt p)
+{
+    i128 ex = b.x - a.x, ey = b.y - a.y, px = p.x - a.x, py = p.y - a.y;
+    if (ex * py - ey * px != 0) return false;
+    i128 dot = px * ex + py * ey;
+    return dot >= 0 && dot <= ex * ex + ey * ey;
+}
+
+// ---------------------------------------------------------------- segment tree
+struct SegTree {
+    struct Node { double x0, y0, x1, y1; int lo, hi, left, right; };
+    std::vector<Node> nodes;
+    std::vector<double> ax, ay, bx, by;   // finest lattice units
+    int root = -1;
+
+    int make(int lo, int hi)
+    {
+        Node nd;
+        nd.lo = lo; nd.hi = hi; nd.left = nd.right = -1;
+        nd.x0 = nd.y0 = std::numeric_limits<double>::infinity();
+        nd.x1 = nd.y1 = -std::numeric_limits<double>::infinity();
+        for (int k = lo; k < hi; k++) {
+            nd.x0 = std::min(nd.x0, std::min(ax[k], bx[k])); nd.x1 = std::max(nd.x1, std::max(ax[k], bx[k]));
+            nd.y0 = std::min(nd.y0, std::min(ay[k], by[k])); nd.y1 = std::max(nd.y1, std::max(ay[k], by[k]));
+        }
+        int id = (int)nodes.size();
+        nodes.push_back(nd);
+        if (hi - lo > 8) {
+            int mid = (lo + hi) / 2;
+            int l = make(lo, mid), r = make(mid, hi);
+            nodes[id].left = l; nodes[id].right = r;
+        }
+        return id;
+    }
+    void init(const Grid &g)
+    {
+        size_t n = g.sa.size();
+        ax.resize(n); ay.resize(n); bx.resize(n); by.resize(n);
+        for (size_t k = 0; k < n; k++) {
+            ax[k] = (double)g.v[g.sa[k]].x / FIXU; ay[k] = (double)g.v[g.sa[k]].y / FIXU;
+            bx[k] = (double)g.v[g.sb[k]].x / FIXU; by[k] = (double)g.v[g.sb[k]].y / FIXU;
+        }
+        nodes.clear();
+        root = n ? make(0, (int)n) : -1;
+    }
+    // distance from p to segment k and the foot of the perpendicular
+    double seg_dist(int k, double px, double py, double &qx, double &qy) const
+    {
+        double dx = bx[k] - ax[k], dy = by[k] - ay[k];
+        double len2 = dx * dx + dy * dy;
+        double t = len2 > 0 ? ((px - ax[k]) * dx + (py - ay[k]) * dy) / len2 : 0.0;
+        if (t < 0) t = 0;
+        if (t > 1) t = 1;
+        qx = ax[k] + t * dx; qy = ay[k] + t * dy;
+        return std::sqrt((px - qx) * (px - qx) + (py - qy) * (py - qy));
+    }
+    static double box_dist(const Node &nd, double px, double py)
+    {
+        double dx = std::max(0.0, std::max(nd.x0 - px, px - nd.x1));
+        double dy = std::max(0.0, std::max(nd.y0 - py, py - nd.y1));
+        return std::sqrt(dx * dx + dy * dy);
+    }
+    // nearest segment; ties go to the lowest segment index
+    double nearest(double px, double py, int &kbest, double &cx, double &cy) const
+    {
+        double best = std::numeric_limits<double>::infinity();
+        kbest = -1; cx = cy = 0;
+        if (root < 0) return best;
+        int stack[128];
+        int sp = 0;
+        stack[sp++] = root;
+        while (sp) {
+            const Node &nd = nodes[stack[--sp]];
+            if (box_dist(nd, px, py) > best) continue;
+            if (nd.left < 0) {
+                for (int k = nd.lo; k < nd.hi; k++) {
+                    double qx, qy, d = seg_dist(k, px, py, qx, qy);
+                    if (d < best || (d == best && k < kbest)) { best = d; kbest = k; cx = qx; cy = qy; }
+                }
+            } else {
+                double dl = box_dist(nodes[nd.left], px, py), dr = box_dist(nodes[nd.right], px, py);
+                if (dl <= dr) { stack[sp++] = nd.right; stack[sp++] = nd.left; }
+                else { stack[sp++] = nd.left; stack[sp++] = nd.right; }
+            }
+        }
+        return best;
+    }
+    void overlapping(double x0, double y0, double x1, double y1, std::vector<int> &out) const
+    {
+        out.clear();
+        if (root < 0) return;
+        int stack[128];
+        int sp = 0;
+        stack[sp++] = root;
+        while (sp) {
+            const Node &nd = nodes[stack[--sp]];
+            if (nd.x1 < x0 || nd.x0 > x1 || nd.y1 < y0 || nd.y0 > y1) continue;
+            if (nd.left < 0) {
+                for (int k = nd.lo; k < nd.hi; k++) out.push_back(k);
+            } else {
+                stack[sp++] = nd.left; stack[sp++] = nd.right;
+            }
+        }
+        std::sort(out.begin(), out.end());
+    }
+};
+
+// first wall crossing along the link p -> p + d (fraction in (0, 1]), exact tests
+static double link_q(const Grid &g, const SegTree &T, IPt p, IPt d)
+{
+    std::vector<int> cand;
+    double x0 = (double)std::min(p.x, p.x + d.x) / FIXU - 1e-9, x1 = (double)std::max(p.x, p.x + d.x) / FIXU + 1e-9;
+    double y0 = (double)std::min(p.y, p.y + d.y) / FIXU - 1e-9, y1 = (double)std::max(p.y, p.y + d.y) / FIXU + 1e-9;
+    T.overlapping(x0, y0, x1, y1, cand);
+    double best = 2.0;
+    for (int k : cand) {
+        IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
+        i128 ex = b.x - a.x, ey = b.y - a.y;
+        i128 den = (i128)d.x * ey - (i128)d.y * ex;
+        i128 rx = a.x - p.x, ry = a.y - p.y;
+        i128 tn = rx * ey - ry * ex;          // parameter along the link (x den)
+        i128 un = rx * d.y - ry * d.x;        // parameter along the segment (x den)
+        if (den != 0) {
+            if (den < 0) { den = -den; tn = -tn; un = -un; }
+            if (tn >= 0 && tn <= den && un >= 0 && un <= den) best = std::min(best, (double)tn / (double)den);
+        } else if (tn == 0) {
+            double dd = (double)((i128)d.x * d.x + (i128)d.y * d.y);
+            double ta = (double)(rx * d.x + ry * d.y) / dd;
+            double tb = (double)((i128)(b.x - p.x) * d.x + (i128)(b.y - p.y) * d.y) / dd;
+            double lo = std::min(ta, tb), hi = std::max(ta, tb);
+            if (hi >= 0 && lo <= 1) best = std::min(best, std::max(lo, 0.0));
+        }
+    }
+    return best;
+}
+
+// ---------------------------------------------------------------- build
+static int failmsg(std::string &msg, const char *m)
+{
+    msg = m;
+    return -5;
+}
+
+static void alloc_level(Level &Lv, int i0, int j0, int nx, int ny)
+{
+    Lv.bi0 = i0; Lv.bj0 = j0; Lv.bnx = nx; Lv.bny = ny;
+    size_t n = (size_t)nx * ny;
+    Lv.kind.assign(n, KIND_ABSENT); Lv.solid.assign(n, 0); Lv.band.assign(n, 0); Lv.bnode.assign(n, 0);
+    Lv.coal.assign(n, 0); Lv.cut.assign(n, 0); Lv.dist.assign(n, 0.f); Lv.rec.assign(n, -1);
+}
+
+// centre of level cell (i, j) in fixed units
+static inline IPt centre(const Level &Lv, long long i, long long j)
+{
+    long long hh = Lv.scale * FIXU / 2;
+    return IPt{(2 * i + 1) * hh, (2 * j + 1) * hh};
+}
+
+// solid painting of one level by exact row scanlines
+static void paint_solid(const Grid &g, Level &Lv)
+{
+    const long long hh = Lv.scale * FIXU / 2;     // half cell
+    const size_t nseg = g.sa.size();
+    // rows crossed by each segment (half-open rule ymin <= Y < ymax)
+    std::vector<std::vector<int>> rows(Lv.bny);
+    for (size_t k = 0; k < nseg; k++) {
+        IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
+        if (a.y == b.y) continue;
+        long long ymin = std::min(a.y, b.y), ymax = std::max(a.y, b.y);
+        long long jl = cdiv((i128)ymin - hh, 2 * (i128)hh), jh = cdiv((i128)ymax - hh, 2 * (i128)hh);
+        jl = std::max<long long>(jl, Lv.bj0);
+        jh = std::min<long long>(jh, (long long)Lv.bj0 + Lv.bny);
+        for (long long j = jl; j < jh; j++) rows[j - Lv.bj0].push_back((int)k);
+    }
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int r = 0; r < Lv.bny; r++) {
+        long long j = Lv.bj0 + r;
+        long long Y = (2 * j + 1) * hh;
+        std::vector<uint8_t> diff(Lv.bnx + 1, 0);
+        for (int k : rows[r]) {
+            IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
+            if (a.y > b.y) std::swap(a, b);
+            i128 den = (i128)(b.y - a.y);
+            i128 num = (i128)a.x * den + (i128)(Y - a.y) * (b.x - a.x);   // crossing x = num / den
+            i128 M = (i128)hh * den;
+            long long imax = fdiv((i128)cdiv(num, M) - 2, 2);             // last centre strictly left
+            long long hi = std::min<long long>(imax, (long long)Lv.bi0 + Lv.bnx - 1);
+            if (hi < Lv.bi0) continue;
+            diff[0] ^= 1;
+            diff[hi - Lv.bi0 + 1] ^= 1;
+        }
+        uint8_t par = 0;
+        for (int c = 0; c < Lv.bnx; c++) {
+            par ^= diff[c];
+            Lv.solid[(size_t)r * Lv.bnx + c] = par;
+        }
+    }
+    // centres lying exactly on a segment are solid
+    for (size_t k = 0; k < nseg; k++) {
+        IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
+        long long il = cdiv((i128)std::min(a.x, b.x) - hh, 2 * (i128)hh), ih = fdiv((i128)std::max(a.x, b.x) - hh, 2 * (i128)hh);
+        long long jl = cdiv((i128)std::min(a.y, b.y) - hh, 2 * (i128)hh), jh = fdiv((i128)std::max(a.y, b.y) - hh, 2 * (i128)hh);
+        for (long long j = jl; j <= jh; j++)
+            for (long long i = il; i <= ih; i++) {
+                long c = Lv.idx(i, j);
+                if (c >= 0 && on_seg(a, b, centre(Lv, i, j))) Lv.solid[c] = 1;
+            }
+    }
+    for (size_t c = 0; c < Lv.solid.size(); c++)
+        if (Lv.kind[c] == KIND_ABSENT) Lv.solid[c] = 0;
+}
+
+int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Grid &g, std::string &msg)
+{
+    g = Grid();
+    g.spec = sp;
+    const int L = sp.levels;
+    g.L = L;
+    const double hf = sp.h0 / (double)(1LL << (L - 1));
+    int nv = n_loops > 0 ? loop_off[n_loops] : 0;
+    g.v.resize(nv);
+    for (int k = 0; k < nv; k++) {
+        g.v[k].x = llround((xy[2 * k] - sp.x0) / hf * (double)FIXU);
+        g.v[k].y = llround((xy[2 * k + 1] - sp.y0) / hf * (double)FIXU);
+    }
+    g.loop_ccw.assign(std::max(n_loops, 1), 1);
+    for (int lp = 0; lp < n_loops; lp++) {
+        int a = loop_off[lp], b = loop_off[lp + 1];
+        if (b - a < 3) return failmsg(msg, "loop with fewer than 3 vertices");
+        i128 area2 = 0;
+        for (int k = a; k < b; k++) {
+            int k2 = (k + 1 < b) ? k + 1 : a;
+            g.sa.push_back(k); g.sb.push_back(k2); g.sloop.push_back(lp);
+            area2 += (i128)g.v[k].x * g.v[k2].y - (i128)g.v[k2].x * g.v[k].y;
+            if (std::llabs(g.v[k2].x - g.v[k].x) > (1LL << 30) || std::llabs(g.v[k2].y - g.v[k].y) > (1LL << 30))
+                return failmsg(msg, "wall segment longer than 2^18 finest cells");
+        }
+        if (area2 == 0) return failmsg(msg, "degenerate loop");
+        g.loop_ccw[lp] = area2 > 0;
+    }
+    if (!sp.solid_walls) g.loop_ccw.assign(std::max(n_loops, 1), 1);
+    SegTree T;
+    T.init(g);
+
+    g.lv.resize(L);
+    for (int l = 0; l < L; l++) { g.lv[l].l = l; g.lv[l].scale = 1LL << (L - 1 - l); }
+    alloc_level(g.lv[0], 0, 0, sp.nx0, sp.ny0);
+    std::fill(g.lv[0].kind.begin(), g.lv[0].kind.end(), (uint8_t)KIND_ACTIVE);
+
+    std::vector<long long> R(L, 0);
+    R[L - 1] = (long long)sp.layers * FIXU;
+    for (int l = L - 2; l >= 1; l--) R[l] = R[l + 1] + (long long)sp.layers * g.lv[l].scale * FIXU;
+
+    for (int l = 1; l < L; l++) {
+        Level &P = g.lv[l - 1];
+        const long long hh = P.scale * FIXU / 2;
+        // refinement: candidate cells around each segment, exact distance test
+        for (size_t k = 0; k < g.sa.size(); k++) {
+            IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
+            long long il = cdiv((i128)std::min(a.x, b.x) - R[l] - hh, 2 * (i128)hh);
+            long long ih = fdiv((i128)std::max(a.x, b.x) + R[l] - hh, 2 * (i128)hh);
+            long long jl = cdiv((i128)std::min(a.y, b.y) - R[l] - hh, 2 * (i128)hh);
+            long long jh = fdiv((i128)std::max(a.y, b.y) + R[l] - hh, 2 * (i128)hh);
+            il = std::max<long long>(il, P.bi0); jl = std::max<long long>(jl, P.bj0);
+            ih = std::min<long long>(ih, (long long)P.bi0 + P.bnx - 1);
+            jh = std::min<long long>(jh, (long long)P.bj0 + P.bny - 1);
+            for (long long j = jl; j <= jh; j++)
+                for (long long i = il; i <= ih; i++) {
+                    long c = P.idx(i, j);
+                    if (P.kind[c] == KIND_ACTIVE && within_r(a, b, centre(P, i, j), R[l])) P.kind[c] = KIND_COVERED;
+                }
+        }
+        // nesting checks, band, child box
+        long long ci0 = (1LL << 40), cj0 = (1LL << 40), ci1 = -(1LL << 40), cj1 = -(1LL << 40);
+        for (int r = 0; r < P.bny; r++)
+            for (int q = 0; q < P.bnx; q++) {
+                if (P.kind[(size_t)r * P.bnx + q] != KIND_COVERED) continue;
+                long long i = P.bi0 + q, j = P.bj0 + r;
+                if (l == 1 && (i < 2 || j < 2 || i >= sp.nx0 - 2 || j >= sp.ny0 - 2))
+                    return failmsg(msg, "refinement reaches the level-0 box edge");
+                for (int d = 1; d < 9; d++) {
+                    long c = P.idx(i + CX[d], j + CY[d]);
+                    if (c < 0 || (P.kind[c] != KIND_ACTIVE && P.kind[c] != KIND_COVERED))
+                        return failmsg(msg, "refinement band violates 2:1 nesting (increase layers)");
+                    if (P.kind[c] == KIND_ACTIVE) P.band[c] = 1;
+                }
+                ci0 = std::min(ci0, i - 1); cj0 = std::min(cj0, j - 1);
+                ci1 = std::max(ci1, i + 1); cj1 = std::max(cj1, j + 1);
+            }
+        if (ci1 < ci0) return failmsg(msg, "level has no cells (wall far from the box?)");
+        Level &F = g.lv[l];
+        alloc_level(F, (int)(2 * ci0 - 1), (int)(2 * cj0 - 1), (int)(2 * (ci1 - ci0 + 1) + 2), (int)(2 * (cj1 - cj0 + 1) + 2));
+        for (long long j = cj0; j <= cj1; j++)
+            for (long long i = ci0; i <= ci1; i++) {
+                long c = P.idx(i, j);
+                uint8_t kd = P.kind[c] == KIND_COVERED ? KIND_ACTIVE : (P.band[c] ? KIND_GHOST : KIND_ABSENT);
+                if (kd == KIND_ABSENT) continue;
+                for (int b = 0; b < 2; b++)
+                    for (int a = 0; a < 2; a++) F.kind[F.idx(2 * i + a, 2 * j + b)] = kd;
+            }
+    }
+    // coalescence: pulled direction d of band cell c comes from the fine ghosts iff
+    // c - c_d, c - (c_dx, 0) or c - (0, c_dy) is covered
+    for (int l = 0; l < L - 1; l++) {
+        Level &P = g.lv[l];
+        for (int r = 0; r < P.bny; r++)
+            for (int q = 0; q < P.bnx; q++) {
+                size_t c = (size_t)r * P.bnx + q;
+                if (!P.band[c]) continue;
+                long long i = P.bi0 + q, j = P.bj0 + r;
+                uint16_t m = 0;
+                for (int d = 1; d < 9; d++) {
+                    long n3[3] = {P.idx(i - CX[d], j - CY[d]), P.idx(i - CX[d], j), P.idx(i, j - CY[d])};
+                    for (long cc : n3)
+                        if (cc >= 0 && P.kind[cc] == KIND_COVERED) { m |= (uint16_t)(1u << d); break; }
+                }
+                P.coal[c] = m;
+            }
+    }
+    // solid painting
+    if (sp.solid_walls && !g.sa.empty())
+        for (int l = 0; l < L; l++) paint_solid(g, g.lv[l]);
+    // cut links; walls may only touch active cells of the finest level
+    for (int l = 0; l < L; l++) {
+        Level &P = g.lv[l];
+        for (int r = 0; r < P.bny; r++)
+            for (int q = 0; q < P.bnx; q++) {
+                size_t c = (size_t)r * P.bnx + q;
+                if (P.kind[c] == KIND_ABSENT || P.kind[c] == KIND_COVERED || P.solid[c]) continue;
+                long long i = P.bi0 + q, j = P.bj0 + r;
+                uint16_t m = 0;
+                for (int d = 1; d < 9; d++) {
+                    long long si = i - CX[d], sj = j - CY[d];
+                    if (l == 0 && sp.periodic) { si = (si + sp.nx0) % sp.nx0; sj = (sj + sp.ny0) % sp.ny0; }
+                    long cc = P.idx(si, sj);
+                    if (cc >= 0 && P.kind[cc] != KIND_ABSENT && P.solid[cc]) m |= (uint16_t)(1u << d);
+                }
+                if (!m) continue;
+                if (l != L - 1 || P.kind[c] != KIND_ACTIVE)
+                    return failmsg(msg, "wall reaches a cell that is not on the finest active level");
+                P.cut[c] = m;
+                P.bnode[c] = 1;
+            }
+    }
+    // wall distance of active fluid cells
+    for (int l = 0; l < L; l++) {
+        Level &P = g.lv[l];
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int r = 0; r < P.bny; r++)
+            for (int q = 0; q < P.bnx; q++) {
+                size_t c = (size_t)r * P.bnx + q;
+                if (P.kind[c] != KIND_ACTIVE || P.solid[c]) continue;
+                double dd = DCAP;
+                if (sp.solid_walls && !g.sa.empty()) {
+                    int kb;
+                    double cx, cy;
+                    double px = (P.bi0 + q + 0.5) * (double)P.scale, py = (P.bj0 + r + 0.5) * (double)P.scale;
+                    dd = T.nearest(px, py, kb, cx, cy) / (double)P.scale;
+                    if (dd > DCAP) dd = DCAP;
+                }
+                P.dist[c] = (float)dd;
+            }
+    }
+    // wall records in (j, i) order at the finest level
+    Level &Fn = g.lv[L - 1];
+    for (int r = 0; r < Fn.bny; r++)
+        for (int q = 0; q < Fn.bnx; q++) {
+            size_t c = (size_t)r * Fn.bnx + q;
+            if (!Fn.bnode[c]) continue;
+            Record rc;
+            std::memset(&rc, 0, sizeof rc);
+            rc.i = Fn.bi0 + q; rc.j = Fn.bj0 + r;
+            double bx = rc.i + 0.5, by = rc.j + 0.5, cx, cy;
+            int kb;
+            double dwb = T.nearest(bx, by, kb, cx, cy);
+            rc.seg = kb; rc.loop = g.sloop[kb];
+            rc.iw[0] = cx; rc.iw[1] = cy; rc.dwb = dwb;
+            rc.n[0] = (bx - cx) / dwb; rc.n[1] = (by - cy) / dwb;
+            rc.r[0] = cx + sp.d_wr * rc.n[0]; rc.r[1] = cy + sp.d_wr * rc.n[1];
+            IPt pb = centre(Fn, rc.i, rc.j);
+            for (int d = 1; d < 9; d++) {
+                if (!(Fn.cut[c] >> d & 1)) continue;
+                double t = link_q(g, T, pb, IPt{-CX[d] * FIXU, -CY[d] * FIXU});
+                if (t > 1.0) return failmsg(msg, "cut link without a wall crossing");
+                rc.q[d] = t;
+                g.n_cut++;
+            }
+            int ic = (int)std::floor(rc.r[0] - 0.5), jc = (int)std::floor(rc.r[1] - 0.5);
+            rc.ns = 0;
+            for (int b = -1; b <= 2; b++)
+                for (int a = -1; a <= 2; a++) {
+                    long cc = Fn.idx(ic + a, jc + b);
+                    bool act = cc >= 0 && Fn.kind[cc] == KIND_ACTIVE;
+                    if (sp.wall_model == 0 && !act) return failmsg(msg, "reference point stencil leaves the finest active level");
+                    if (!act || Fn.solid[cc] || Fn.bnode[cc]) continue;
+                    rc.si[rc.ns] = ic + a; rc.sj[rc.ns] = jc + b; rc.ns++;
+                }
+            if (sp.wall_model == 0 && rc.ns == 0) return failmsg(msg, "empty reference stencil");
+            Fn.rec[c] = (int)g.recs.size();
+            g.recs.push_back(rc);
+        }
+    // surface element centroid -> two nearest boundary nodes (ties: lower record index)
+    size_t nseg = g.sa.size();
+    g.seg_b1.assign(nseg, -1); g.seg_b2.assign(nseg, -1); g.seg_w1.assign(nseg, 0); g.seg_w2.assign(nseg, 0);
+    if (!g.recs.empty()) {
+        const int BK = 4;
+        int mi = 1 << 30, mj = 1 << 30, Mi = -(1 << 30), Mj = -(1 << 30);
+        for (auto &rc : g.recs) { mi = std::min(mi, rc.i); mj = std::min(mj, rc.j); Mi = std::max(Mi, rc.i); Mj = std::max(Mj, rc.j); }
+        int gbx0 = (int)fdiv(mi, BK), gby0 = (int)fdiv(mj, BK);
+        int gnx = (int)fdiv(Mi, BK) - gbx0 + 1, gny = (int)fdiv(Mj, BK) - gby0 + 1;
+        std::vector<std::vector<int>> bucket((size_t)gnx * gny);
+        for (size_t k = 0; k < g.recs.size(); k++)
+            bucket[(size_t)(fdiv(g.recs[k].j, BK) - gby0) * gnx + (fdiv(g.recs[k].i, BK) - gbx0)].push_back((int)k);
+#pragma omp parallel for schedule(dynamic, 16)
+        for (long k = 0; k < (long)nseg; k++) {
+            double mx = 0.5 * (double)(g.v[g.sa[k]].x + g.v[g.sb[k]].x) / FIXU;
+            double my = 0.5 * (double)(g.v[g.sa[k]].y + g.v[g.sb[k]].y) / FIXU;
+            int cbx = (int)std::floor(mx / BK) - gbx0, cby = (int)std::floor(my / BK) - gby0;
+            double d1 = INFINITY, d2 = INFINITY;
+            int b1 = -1, b2 = -1;
+            for (int ring = 0;; ring++) {
+                for (int by = cby - ring; by <= cby + ring; by++)
+                    for (int bx = cbx - ring; bx <= cbx + ring; bx++) {
+                        if (std::max(std::abs(bx - cbx), std::abs(by - cby)) != ring) continue;
+                        if (bx < 0 || by < 0 || bx >= gnx || by >= gny) continue;
+                        for (int rr : bucket[(size_t)by * gnx + bx]) {
+                            double dx = g.recs[rr].i + 0.5 - mx, dy = g.recs[rr].j + 0.5 - my;
+                            double dd = dx * dx + dy * dy;
+                            if (dd < d1 || (dd == d1 && rr < b1)) { d2 = d1; b2 = b1; d1 = dd; b1 = rr; }
+                            else if (dd < d2 || (dd == d2 && rr < b2)) { d2 = dd; b2 = rr; }
+                        }
+                    }
+                double reach = (double)ring * BK;
+                bool all_out = (cbx - ring <= 0 && cby - ring <= 0 && cbx + ring >= gnx - 1 && cby + ring >= gny - 1);
+                if ((b2 >= 0 && d2 <= reach * reach) || all_out) break;
+            }
+            g.seg_b1[k] = b1; g.seg_b2[k] = b2;
+            g.seg_w1[k] = b1 >= 0 ? 1.0 / (d1 > 1e-300 ? d1 : 1e-300) : 0.0;
+            g.seg_w2[k] = b2 >= 0 ? 1.0 / (d2 > 1e-300 ? d2 : 1e-300) : 0.0;
+        }
+    }
+    // tiles
+    for (int l = 0; l < L; l++) {
+        Level &P = g.lv[l];
+        int a0 = 1 << 30, b0 = 1 << 30, a1 = -(1 << 30), b1 = -(1 << 30);
+        for (int r = 0; r < P.bny; r++)
+            for (int q = 0; q < P.bnx; q++)
+                if (P.kind[(size_t)r * P.bnx + q] != KIND_ABSENT) {
+                    a0 = std::min(a0, P.bi0 + q); a1 = std::max(a1, P.bi0 + q);
+                    b0 = std::min(b0, P.bj0 + r); b1 = std::max(b1, P.bj0 + r);
+                }
+        P.pi0 = a0; P.pj0 = b0; P.pnx = a1 - a0 + 1; P.pny = b1 - b0 + 1;
+        P.tx0 = (int)fdiv(a0, LBM_TX); P.ty0 = (int)fdiv(b0, LBM_TY);
+        P.ntx = (int)fdiv(a1, LBM_TX) - P.tx0 + 1; P.nty = (int)fdiv(b1, LBM_TY) - P.ty0 + 1;
+        P.tile_of.assign((size_t)P.ntx * P.nty, -1);
+        P.tile_x.clear(); P.tile_y.clear();
+        for (int ty = 0; ty < P.nty; ty++)
+            for (int tx = 0; tx < P.ntx; tx++) {
+                bool any = false;
+                int gx = (P.tx0 + tx) * LBM_TX, gy = (P.ty0 + ty) * LBM_TY;
+                for (int y = 0; y < LBM_TY && !any; y++)
+                    for (int x = 0; x < LBM_TX && !any; x++) {
+                        long c = P.idx(gx + x, gy + y);
+                        any = c >= 0 && P.kind[c] != KIND_ABSENT;
+                    }
+                if (!any) continue;
+                P.tile_of[(size_t)ty * P.ntx + tx] = (int)P.tile_x.size();
+                P.tile_x.push_back(P.tx0 + tx); P.tile_y.push_back(P.ty0 + ty);
+            }
+        P.ntiles = (int)P.tile_x.size();
+        P.nbr.assign((size_t)P.ntiles * 9, -1);
+        const bool wrap = (l == 0 && sp.periodic);
+        const int wtx = sp.nx0 / LBM_TX, wty = sp.ny0 / LBM_TY;
+        for (int t = 0; t < P.ntiles; t++)
+            for (int d = 0; d < 9; d++) {
+                int tx = P.tile_x[t] + CX[d], ty = P.tile_y[t] + CY[d];
+                if (wrap) { tx = (tx % wtx + wtx) % wtx; ty = (ty % wty + wty) % wty; }
+                if (tx < P.tx0 || ty < P.ty0 || tx >= P.tx0 + P.ntx || ty >= P.ty0 + P.nty) continue;
+                P.nbr[(size_t)t * 9 + d] = P.tile_of[(size_t)(ty - P.ty0) * P.ntx + (tx - P.tx0)];
+            }
+    }
+    for (int l = 0; l < L; l++) {
+        Level &P = g.lv[l];
+        P.child.assign((size_t)P.ntiles * 4, -1);
+        if (l == L - 1) continue;
+        Level &F = g.lv[l + 1];
+        for (int t = 0; t < P.ntiles; t++)
+            for (int b = 0; b < 2; b++)
+                for (int a = 0; a < 2; a++) {
+                    int tx = 2 * P.tile_x[t] + a, ty = 2 * P.tile_y[t] + b;
+                    if (tx < F.tx0 || ty < F.ty0 || tx >= F.tx0 + F.ntx || ty >= F.ty0 + F.nty) continue;
+                    P.child[(size_t)t * 4 + b * 2 + a] = F.tile_of[(size_t)(ty - F.ty0) * F.ntx + (tx - F.tx0)];
+                }
+    }
+    return 0;
+}
+
+}  // namespace lbmgrid

@@ -1,0 +1,74 @@
+// grid.hpp -- host-side builder of the sparse tiled multilevel grid (Sec 2.1
+// pre-processor: 2:1 distance-band refinement, cell-centred solid painting,
+// inter-level connectivity; Sec 2.3 preprocessing: cut links, wall records).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "layout.hpp"
+
+namespace lbmgrid {
+
+struct Spec {
+    int levels, nx0, ny0, layers;
+    double x0, y0, h0;
+    double d_wr, d_wv;
+    int periodic, solid_walls, wall_model;
+};
+
+struct IPt { long long x, y; };
+
+struct Level {
+    int l = 0;
+    long long scale = 1;            // finest cells per cell edge: 2^(L-1-l)
+    // dense build-time box (global level indices)
+    int bi0 = 0, bj0 = 0, bnx = 0, bny = 0;
+    std::vector<uint8_t> kind;      // KIND_* over the box
+    std::vector<uint8_t> solid, band, bnode;
+    std::vector<uint16_t> coal, cut;
+    std::vector<float> dist;        // wall distance, level lattice units
+    std::vector<int> rec;           // wall record of a B node
+    // present-cell box
+    int pi0 = 0, pj0 = 0, pnx = 0, pny = 0;
+    // tiles
+    int tx0 = 0, ty0 = 0, ntx = 0, nty = 0;
+    std::vector<int> tile_of;       // ntx * nty -> tile index or -1
+    std::vector<int> tile_x, tile_y;
+    std::vector<int> nbr;           // 9 per tile (D2Q9 order), -1 absent
+    std::vector<int> child;         // 4 per tile: level l+1 tiles (b * 2 + a)
+    int ntiles = 0;
+
+    long idx(long long i, long long j) const {
+        if (i < bi0 || j < bj0 || i >= bi0 + bnx || j >= bj0 + bny) return -1;
+        return (long)(j - bj0) * bnx + (long)(i - bi0);
+    }
+    // device slot of a cell (tile * 256 + ly * 32 + lx), or -1
+    long slot(long long i, long long j) const;
+};
+
+struct Record {
+    int i, j, seg, loop;
+    double iw[2], n[2], dwb, r[2];
+    int ns;
+    int si[16], sj[16];
+    double q[9];
+};
+
+struct Grid {
+    Spec spec;
+    int L = 0;
+    std::vector<IPt> v;
+    std::vector<int> sa, sb, sloop, loop_ccw;
+    std::vector<Level> lv;
+    std::vector<Record> recs;
+    std::vector<int> seg_b1, seg_b2;
+    std::vector<double> seg_w1, seg_w2;
+    long long n_cut = 0;
+};
+
+// Returns 0 on success, otherwise an LBM status code with msg filled in.
+int build(const Spec &spec, const double *xy, const int *loop_off, int n_loops, Grid &g, std::string &msg);
+
+}  // namespace lbmgrid

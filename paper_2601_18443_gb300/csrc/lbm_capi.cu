@@ -1,0 +1,751 @@
+// lbm_capi.cu -- C ABI of the library (include/lbm.h): solver object, upload of
+// the tiled grid, the recursive level scheduler (Sec 2.1: each finer level takes
+// two sub-steps per parent step) captured into CUDA graphs, and host queries.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "device.cuh"
+#include "grid.hpp"
+
+using lbmdev::LevelView;
+using lbmdev::LoadsView;
+using lbmdev::RecView;
+using lbmdev::StepConsts;
+
+namespace {
+
+const int CXh[9] = LBM_CX_INIT;
+const int CYh[9] = LBM_CY_INIT;
+const double WQh[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+// shifted equilibrium g_q = f_q^eq - w_q as the product of two one-dimensional
+// three-velocity equilibria (equal to the fourth-order Hermite form of eq 4)
+void feq_shifted(double rho, double ux, double uy, float *g)
+{
+    auto h = [](int c, double u) { return c == 0 ? 2.0 / 3.0 - u * u : 0.5 * (u * u + 1.0 / 3.0 + c * u); };
+    for (int q = 0; q < 9; q++) g[q] = (float)(rho * h(CXh[q], ux) * h(CYh[q], uy) - WQh[q]);
+}
+
+struct HostLevelDev {
+    LevelView v;
+    std::vector<uint32_t> flags;   // host copy
+};
+
+}  // namespace
+
+struct lbm_solver {
+    lbm_config cfg;
+    std::string err;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    int device = 0;
+    int L = 0;
+    double U = 0;
+    bool geometry = false;
+    lbmgrid::Grid g;
+    HostLevelDev lv[LBM_MAXL];
+    RecView rec;
+    LoadsView segs;
+    StepConsts k;
+    int parity[LBM_MAXL];
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::vector<void *> allocs;
+    double device_bytes = 0;
+    int *d_status = nullptr;
+    double *d_acc = nullptr;
+    float *d_slip = nullptr;
+    long long step = 0;
+    double last_cl = 0;
+    bool have_cl = false;
+    long long kernels_per_step = 0;
+    int n_loops = 0;
+    // eager timing (lbm_time_kernels)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_marks;   // (class, event index pair start)
+    std::vector<long long> ev_cells;
+    int ev_used = 0;
+};
+
+static lbm_status fail(lbm_solver *s, lbm_status code, const std::string &m)
+{
+    if (s) s->err = m;
+    return code;
+}
+
+static lbm_status cuda_fail(lbm_solver *s, cudaError_t e, const char *where)
+{
+    return fail(s, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t _e = (call);                                     \
+        if (_e != cudaSuccess) return cuda_fail(s, _e, #call);       \
+    } while (0)
+
+static void *dalloc(lbm_solver *s, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (s->cfg.dev_alloc) {
+        p = s->cfg.dev_alloc(bytes, (void *)s->stream, s->cfg.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p) { s->allocs.push_back(p); s->device_bytes += (double)bytes; }
+    return p;
+}
+
+static void free_all(lbm_solver *s)
+{
+    for (int b = 0; b < 2; b++)
+        if (s->graph[b]) { cudaGraphExecDestroy(s->graph[b]); s->graph[b] = nullptr; }
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (void *p : s->allocs) {
+        if (s->cfg.dev_free) s->cfg.dev_free(p, (void *)s->stream, s->cfg.alloc_ctx);
+        else cudaFree(p);
+    }
+    s->allocs.clear();
+    s->device_bytes = 0;
+    s->geometry = false;
+    for (auto &e : s->ev_pool) cudaEventDestroy(e);
+    s->ev_pool.clear();
+}
+
+template <class T>
+static T *upload(lbm_solver *s, const std::vector<T> &h, bool &ok)
+{
+    T *d = (T *)dalloc(s, h.size() * sizeof(T));
+    if (!d) { ok = false; return nullptr; }
+    if (!h.empty() && cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        ok = false;
+    return d;
+}
+
+// ---------------------------------------------------------------- scheduler
+// Kernel classes for lbm_time_kernels.
+enum { KC_SC_FINEST = 0, KC_SC_COARSE = 1, KC_SA = 2, KC_WALLFN = 3, KC_N = 4 };
+static const char *KC_NAME[KC_N] = {"stream_collide_finest", "stream_collide_coarse", "sa_neg", "wall_function"};
+
+static void mark_begin(lbm_solver *s)
+{
+    if (!s->timing) return;
+    if (s->ev_used + 2 > (int)s->ev_pool.size()) {
+        for (int i = 0; i < 256; i++) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            s->ev_pool.push_back(e);
+        }
+    }
+    cudaEventRecord(s->ev_pool[s->ev_used], s->stream);
+}
+
+static void mark_end(lbm_solver *s, int cls, long long cells)
+{
+    if (!s->timing) return;
+    cudaEventRecord(s->ev_pool[s->ev_used + 1], s->stream);
+    s->ev_marks.push_back({cls, s->ev_used});
+    s->ev_cells.push_back(cells);
+    s->ev_used += 2;
+}
+
+static void advance(lbm_solver *s, cudaStream_t st, int l, long long &nk)
+{
+    const int L = s->L;
+    LevelView &P = s->lv[l].v;
+    const LevelView *F = (l < L - 1) ? &s->lv[l + 1].v : nullptr;
+    if (l == L - 1 && s->rec.n > 0) {
+        mark_begin(s);
+        lbmdev::launch_wallfn(st, P, s->rec, s->k);
+        mark_end(s, KC_WALLFN, (long long)s->rec.n * 16);
+        nk++;
+    }
+    if (s->cfg.turbulence) {
+        mark_begin(s);
+        lbmdev::launch_sa(st, P, F, s->parity[l], s->rec, s->k, l == 0);
+        mark_end(s, KC_SA, P.ns);
+        nk++;
+    }
+    if (l < L - 1) {
+        advance(s, st, l + 1, nk);
+        advance(s, st, l + 1, nk);
+    }
+    mark_begin(s);
+    lbmdev::launch_stream_collide(st, P, F, s->parity[l], F ? s->parity[l + 1] : 0, F ? s->parity[l + 1] : 0, s->rec,
+                                  s->k, l == 0);
+    mark_end(s, l == L - 1 ? KC_SC_FINEST : KC_SC_COARSE, P.ns);
+    nk++;
+    s->parity[l] ^= 1;
+}
+
+static lbm_status capture_graphs(lbm_solver *s)
+{
+    for (int b = 0; b < 2; b++) {
+        if (s->parity[0] != b) return fail(s, LBM_ERR_CUDA, "internal: parity mismatch at capture");
+        cudaGraph_t gr;
+        long long nk = 0;
+        CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+        advance(s, s->cap_stream, 0, nk);
+        CK(cudaStreamEndCapture(s->cap_stream, &gr));
+        CK(cudaGraphInstantiate(&s->graph[b], gr, 0));
+        cudaGraphDestroy(gr);
+        s->kernels_per_step = nk;
+    }
+    return LBM_OK;
+}
+
+static lbm_status enqueue_steps(lbm_solver *s, int n)
+{
+    for (int it = 0; it < n; it++) {
+        CK(cudaGraphLaunch(s->graph[s->parity[0]], s->stream));
+        s->parity[0] ^= 1;
+        s->step++;
+    }
+    return LBM_OK;
+}
+
+// non-finite check and FP64 mass into d_acc[4]
+static lbm_status enqueue_mass(lbm_solver *s)
+{
+    CK(cudaMemsetAsync(s->d_acc + 4, 0, sizeof(double), s->stream));
+    for (int l = 0; l < s->L; l++) {
+        double area = (double)(1LL << (s->L - 1 - l));
+        lbmdev::launch_mass(s->stream, s->lv[l].v, area * area, s->d_acc + 4, s->d_status);
+    }
+    return LBM_OK;
+}
+
+static lbm_status check_status(lbm_solver *s)
+{
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (st & 1) return fail(s, LBM_ERR_DIVERGED, "diverged (non-finite field)");
+    if (st) return fail(s, LBM_ERR_CUDA, "device status word set");
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------- API
+extern "C" {
+
+lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
+{
+    if (!cfg || !out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cfg->levels < 1 || cfg->levels > LBM_MAXL || cfg->nx0 < 4 || cfg->ny0 < 4 || !(cfg->h0 > 0) ||
+        cfg->layers < 3 || !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->chord > 0) || cfg->store != 0 ||
+        (cfg->periodic && (cfg->nx0 % LBM_TX || cfg->ny0 % LBM_TY)) || (!cfg->periodic && (cfg->nx0 < 8)) ||
+        (cfg->wall_model != 0 && cfg->wall_model != 2 && cfg->wall_model != 3) || (!cfg->dev_alloc != !cfg->dev_free))
+        return LBM_ERR_INVALID_ARG;
+    lbm_solver *s = new (std::nothrow) lbm_solver();
+    if (!s) return LBM_ERR_OOM;
+    s->cfg = *cfg;
+    s->L = cfg->levels;
+    s->U = cfg->Ma * std::sqrt(1.0 / 3.0);
+    for (int l = 0; l < LBM_MAXL; l++) s->parity[l] = 0;
+    if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LBM_ERR_CUDA; }
+    if (cfg->cuda_stream) {
+        s->stream = (cudaStream_t)cfg->cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) { delete s; return LBM_ERR_CUDA; }
+        s->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return LBM_ERR_CUDA;
+    }
+    *out = s;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_solver *s)
+{
+    if (!s) return;
+    free_all(s);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+const char *lbm_last_error(const lbm_solver *s) { return s ? s->err.c_str() : "null handle"; }
+
+lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off, int n_loops)
+{
+    if (!s || n_loops < 0 || (n_loops > 0 && (!xy || !loop_off))) return fail(s, LBM_ERR_INVALID_ARG, "bad geometry arguments");
+    free_all(s);
+    const lbm_config &c = s->cfg;
+    lbmgrid::Spec sp{c.levels, c.nx0, c.ny0, c.layers, c.x0, c.y0, c.h0, c.d_wr, c.d_wv, c.periodic, c.solid_walls, c.wall_model};
+    std::string msg;
+    int rc = lbmgrid::build(sp, xy, loop_off, n_loops, s->g, msg);
+    if (rc != 0) return fail(s, (lbm_status)rc, msg);
+    const int L = s->L;
+    bool ok = true;
+    // per-level flag words and device arrays
+    for (int l = 0; l < L; l++) {
+        lbmgrid::Level &G = s->g.lv[l];
+        HostLevelDev &H = s->lv[l];
+        const long long ns = (long long)G.ntiles * LBM_TILE;
+        H.flags.assign(ns, 0);
+        std::vector<float> dist(ns, 0.f);
+        std::vector<int> rec(l == L - 1 ? ns : 1, -1);
+        for (int t = 0; t < G.ntiles; t++)
+            for (int c2 = 0; c2 < LBM_TILE; c2++) {
+                long long i = (long long)G.tile_x[t] * LBM_TX + (c2 & 31), j = (long long)G.tile_y[t] * LBM_TY + (c2 >> 5);
+                long b = G.idx(i, j);
+                if (b < 0 || G.kind[b] == KIND_ABSENT) continue;
+                uint32_t f = G.kind[b];
+                if (G.solid[b]) f |= FL_SOLID;
+                if (G.band[b]) f |= FL_BAND;
+                if (G.bnode[b]) f |= FL_BNODE;
+                for (int d = 1; d < 9; d++) {
+                    if (G.coal[b] >> d & 1) f |= 1u << (FL_COAL_SHIFT + d - 1);
+                    if (G.cut[b] >> d & 1) f |= 1u << (FL_CUT_SHIFT + d - 1);
+                }
+                if (l == 0 && !c.periodic) {
+                    if (i == 0) f |= FL_INLET;
+                    if (i == c.nx0 - 1) f |= FL_OUTLET;
+                    if (j == 0) f |= FL_BOTTOM;
+                    if (j == c.ny0 - 1) f |= FL_TOP;
+                }
+                long long sl = (long long)t * LBM_TILE + c2;
+                H.flags[sl] = f;
+                dist[sl] = G.dist[b];
+                if (l == L - 1) rec[sl] = G.rec[b];
+            }
+        LevelView &v = H.v;
+        v.ntiles = G.ntiles;
+        v.ns = ns;
+        v.tile_x = upload(s, G.tile_x, ok);
+        v.tile_y = upload(s, G.tile_y, ok);
+        v.nbr = upload(s, G.nbr, ok);
+        v.child = upload(s, G.child, ok);
+        v.flags = upload(s, H.flags, ok);
+        v.dist = upload(s, dist, ok);
+        v.rec = (l == L - 1) ? upload(s, rec, ok) : nullptr;
+        for (int b = 0; b < 2; b++) {
+            v.f[b] = (float *)dalloc(s, 9 * ns * sizeof(float));
+            v.chi[b] = (float *)dalloc(s, ns * sizeof(float));
+            ok = ok && v.f[b] && v.chi[b];
+        }
+        v.drho = (float *)dalloc(s, ns * sizeof(float));
+        v.ux = (float *)dalloc(s, ns * sizeof(float));
+        v.uy = (float *)dalloc(s, ns * sizeof(float));
+        ok = ok && v.drho && v.ux && v.uy;
+        v.nu = (float)(s->U * (c.chord / c.h0) * (double)(1LL << l) / c.Re);
+        if (!ok) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
+    }
+    // wall records
+    const int nr = (int)s->g.recs.size();
+    {
+        const lbmgrid::Level &G = s->g.lv[L - 1];
+        std::vector<int> bslot(nr), nsv(nr), st_slot((size_t)nr * 16, -1), loop(nr);
+        std::vector<float> st_dx((size_t)nr * 16, 0.f), st_dy((size_t)nr * 16, 0.f), nx(nr), ny(nr), dwb(nr), q((size_t)nr * 9, 0.f);
+        for (int r = 0; r < nr; r++) {
+            const lbmgrid::Record &R = s->g.recs[r];
+            bslot[r] = (int)G.slot(R.i, R.j);
+            nsv[r] = R.ns;
+            for (int m = 0; m < R.ns; m++) {
+                st_slot[(size_t)r * 16 + m] = (int)G.slot(R.si[m], R.sj[m]);
+                st_dx[(size_t)r * 16 + m] = (float)(R.si[m] + 0.5 - R.r[0]);
+                st_dy[(size_t)r * 16 + m] = (float)(R.sj[m] + 0.5 - R.r[1]);
+            }
+            nx[r] = (float)R.n[0]; ny[r] = (float)R.n[1]; dwb[r] = (float)R.dwb;
+            for (int d = 0; d < 9; d++) q[(size_t)r * 9 + d] = (float)R.q[d];
+            loop[r] = R.loop;
+        }
+        RecView &v = s->rec;
+        v.n = nr;
+        v.bslot = upload(s, bslot, ok);
+        v.ns = upload(s, nsv, ok);
+        v.st_slot = upload(s, st_slot, ok);
+        v.st_dx = upload(s, st_dx, ok);
+        v.st_dy = upload(s, st_dy, ok);
+        v.nx = upload(s, nx, ok);
+        v.ny = upload(s, ny, ok);
+        v.dwb = upload(s, dwb, ok);
+        v.q = upload(s, q, ok);
+        v.loop = upload(s, loop, ok);
+        s->d_slip = (float *)dalloc(s, 2 * (size_t)std::max(n_loops, 1) * sizeof(float));
+        v.slip = s->d_slip;
+        float **outs[8] = {&v.drhoW, &v.uWx, &v.uWy, &v.utau, &v.chiB, &v.tx, &v.ty, &v.ut};
+        for (auto o : outs) { *o = (float *)dalloc(s, (size_t)std::max(nr, 1) * sizeof(float)); ok = ok && *o; }
+        if (!ok || !s->d_slip) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
+        CK(cudaMemsetAsync(s->d_slip, 0, 2 * (size_t)std::max(n_loops, 1) * sizeof(float), s->stream));
+        for (auto o : outs) CK(cudaMemsetAsync(*o, 0, (size_t)std::max(nr, 1) * sizeof(float), s->stream));
+    }
+    // surface segments for the loads
+    {
+        const size_t n = s->g.sa.size();
+        std::vector<double> tx(n), ty(n), nxv(n), nyv(n), ds(n);
+        for (size_t k2 = 0; k2 < n; k2++) {
+            double ax = (double)s->g.v[s->g.sa[k2]].x / 4096.0, ay = (double)s->g.v[s->g.sa[k2]].y / 4096.0;
+            double bx = (double)s->g.v[s->g.sb[k2]].x / 4096.0, by = (double)s->g.v[s->g.sb[k2]].y / 4096.0;
+            double len = std::sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+            tx[k2] = (bx - ax) / len; ty[k2] = (by - ay) / len; ds[k2] = len;
+            bool ccw = s->g.loop_ccw[s->g.sloop[k2]];
+            nxv[k2] = ccw ? ty[k2] : -ty[k2];
+            nyv[k2] = ccw ? -tx[k2] : tx[k2];
+        }
+        LoadsView &v = s->segs;
+        v.nseg = c.solid_walls ? (int)n : 0;
+        v.b1 = upload(s, s->g.seg_b1, ok);
+        v.b2 = upload(s, s->g.seg_b2, ok);
+        v.w1 = upload(s, s->g.seg_w1, ok);
+        v.w2 = upload(s, s->g.seg_w2, ok);
+        v.tx = upload(s, tx, ok);
+        v.ty = upload(s, ty, ok);
+        v.nx = upload(s, nxv, ok);
+        v.ny = upload(s, nyv, ok);
+        v.ds = upload(s, ds, ok);
+        v.cp = (double *)dalloc(s, std::max<size_t>(n, 1) * sizeof(double));
+        v.cf = (double *)dalloc(s, std::max<size_t>(n, 1) * sizeof(double));
+        if (!ok || !v.cp || !v.cf) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
+    }
+    s->d_status = (int *)dalloc(s, 16);
+    s->d_acc = (double *)dalloc(s, 8 * sizeof(double));
+    if (!s->d_status || !s->d_acc) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
+    CK(cudaMemsetAsync(s->d_status, 0, 16, s->stream));
+    // constants and initial state: equilibrium of rho = 1, u = (U, 0), chi = chi_inf
+    s->k.level0_edges = !c.periodic;
+    s->k.nx0 = c.nx0; s->k.ny0 = c.ny0; s->k.ntx0 = s->g.lv[0].ntx;
+    s->k.turbulence = c.turbulence; s->k.wall_model = c.wall_model;
+    s->k.U = (float)s->U; s->k.chi_inf = (float)c.chi_inf;
+    s->k.d_wr = (float)c.d_wr; s->k.d_wv = (float)c.d_wv;
+    float g9[9];
+    feq_shifted(1.0, s->U, 0.0, g9);
+    for (int l = 0; l < L; l++) lbmdev::launch_init_feq(s->stream, s->lv[l].v, g9, (float)s->U, (float)c.chi_inf);
+    for (int l = 0; l < LBM_MAXL; l++) s->parity[l] = 0;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    lbm_status st = capture_graphs(s);
+    if (st != LBM_OK) { free_all(s); return st; }
+    s->step = 0;
+    s->have_cl = false;
+    s->n_loops = n_loops;
+    s->geometry = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wall_slip(lbm_solver *s, const double *uw, int n_loops)
+{
+    if (!s || !uw) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (n_loops != s->n_loops) return fail(s, LBM_ERR_INVALID_ARG, "slip count differs from the loop count");
+    std::vector<float> h(2 * (size_t)n_loops);
+    for (int i = 0; i < 2 * n_loops; i++) h[i] = (float)uw[i];
+    CK(cudaMemcpyAsync(s->d_slip, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_step_async(lbm_solver *s, int n)
+{
+    if (!s) return LBM_ERR_INVALID_ARG;
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (n < 0) return fail(s, LBM_ERR_INVALID_ARG, "negative step count");
+    return enqueue_steps(s, n);
+}
+
+lbm_status lbm_synchronize(lbm_solver *s)
+{
+    if (!s) return LBM_ERR_INVALID_ARG;
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    lbm_status st = enqueue_mass(s);
+    if (st != LBM_OK) return st;
+    CK(cudaGetLastError());
+    return check_status(s);
+}
+
+lbm_status lbm_step(lbm_solver *s, int n)
+{
+    lbm_status st = lbm_step_async(s, n);
+    if (st != LBM_OK) return st;
+    return lbm_synchronize(s);
+}
+
+lbm_status lbm_get_level_box(lbm_solver *s, int level, int *i0, int *j0, int *nx, int *ny)
+{
+    if (!s || !i0 || !j0 || !nx || !ny) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (level < 0 || level >= s->L) return fail(s, LBM_ERR_INVALID_ARG, "level out of range");
+    const lbmgrid::Level &G = s->g.lv[level];
+    *i0 = G.pi0; *j0 = G.pj0; *nx = G.pnx; *ny = G.pny;
+    return LBM_OK;
+}
+
+static lbm_status download_level(lbm_solver *s, int l, std::vector<float> &dr, std::vector<float> &ux,
+                                 std::vector<float> &uy, std::vector<float> &chi)
+{
+    const LevelView &v = s->lv[l].v;
+    dr.resize(v.ns); ux.resize(v.ns); uy.resize(v.ns); chi.resize(v.ns);
+    CK(cudaMemcpyAsync(dr.data(), v.drho, v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(ux.data(), v.ux, v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(uy.data(), v.uy, v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(chi.data(), v.chi[s->parity[l]], v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+static unsigned char mask_of(uint32_t f)
+{
+    uint32_t kd = f & FL_KIND_MASK;
+    if (kd == KIND_ABSENT) return 0;
+    if (f & FL_SOLID) return 5;
+    if (kd == KIND_COVERED) return 3;
+    if (kd == KIND_GHOST) return 4;
+    return (f & FL_BNODE) ? 2 : 1;
+}
+
+lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, double *uy, double *chi,
+                          unsigned char *mask, int cap)
+{
+    int i0, j0, nx, ny;
+    lbm_status st = lbm_get_level_box(s, level, &i0, &j0, &nx, &ny);
+    if (st != LBM_OK) return st;
+    if ((long long)nx * ny > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    std::vector<float> dr, u, v, c2;
+    st = download_level(s, level, dr, u, v, c2);
+    if (st != LBM_OK) return st;
+    const lbmgrid::Level &G = s->g.lv[level];
+    const std::vector<uint32_t> &fl = s->lv[level].flags;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long sl = G.slot(i0 + i, j0 + j);
+            long long o = (long long)j * nx + i;
+            unsigned char m = sl >= 0 ? mask_of(fl[sl]) : 0;
+            if (mask) mask[o] = m;
+            bool has = m >= 1 && m <= 4;
+            if (rho) rho[o] = has ? 1.0 + (double)dr[sl] : NAN;
+            if (ux) ux[o] = has ? (double)u[sl] : NAN;
+            if (uy) uy[o] = has ? (double)v[sl] : NAN;
+            if (chi) chi[o] = has ? (double)c2[sl] : NAN;
+        }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_wall_distance(lbm_solver *s, int level, double *d, int cap)
+{
+    int i0, j0, nx, ny;
+    lbm_status st = lbm_get_level_box(s, level, &i0, &j0, &nx, &ny);
+    if (st != LBM_OK) return st;
+    if (!d || (long long)nx * ny > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    const lbmgrid::Level &G = s->g.lv[level];
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long b = G.idx(i0 + i, j0 + j);
+            bool act = b >= 0 && G.kind[b] == KIND_ACTIVE && !G.solid[b];
+            d[(long long)j * nx + i] = act ? (double)G.dist[b] : NAN;
+        }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const double *ux, const double *uy,
+                          const double *chi)
+{
+    int i0, j0, nx, ny;
+    lbm_status st = lbm_get_level_box(s, level, &i0, &j0, &nx, &ny);
+    if (st != LBM_OK) return st;
+    const LevelView &v = s->lv[level].v;
+    const int p = s->parity[level];
+    std::vector<float> dr, u, w, c2, c3(v.ns), f(9 * (size_t)v.ns);
+    st = download_level(s, level, dr, u, w, c2);
+    if (st != LBM_OK) return st;
+    CK(cudaMemcpyAsync(c3.data(), v.chi[p ^ 1], v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(f.data(), v.f[p], 9 * v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const lbmgrid::Level &G = s->g.lv[level];
+    const std::vector<uint32_t> &fl = s->lv[level].flags;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            long sl = G.slot(i0 + i, j0 + j);
+            if (sl < 0) continue;
+            uint32_t fw = fl[sl];
+            if ((fw & FL_KIND_MASK) != KIND_ACTIVE || (fw & FL_SOLID)) continue;
+            long long o = (long long)j * nx + i;
+            double r = rho ? rho[o] : 1.0 + (double)dr[sl];
+            double a = ux ? ux[o] : (double)u[sl];
+            double b = uy ? uy[o] : (double)w[sl];
+            dr[sl] = (float)(r - 1.0); u[sl] = (float)a; w[sl] = (float)b;
+            if (chi) { c2[sl] = (float)chi[o]; c3[sl] = (float)chi[o]; }
+            float g9[9];
+            feq_shifted(r, a, b, g9);
+            for (int q = 0; q < 9; q++) f[(size_t)q * v.ns + sl] = g9[q];
+        }
+    CK(cudaMemcpyAsync(v.drho, dr.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(v.ux, u.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(v.uy, w.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(v.chi[p], c2.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(v.chi[p ^ 1], c3.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(v.f[p], f.data(), 9 * v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    // re-synchronise the interfaces: restriction bottom-up, then explosion and ghost reconstruction
+    for (int l = s->L - 2; l >= 0; l--)
+        lbmdev::launch_restrict(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], s->parity[l + 1]);
+    for (int l = 0; l < s->L - 1; l++)
+        lbmdev::launch_explode_prolong(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], s->parity[l + 1], s->k);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_loads(lbm_solver *s, lbm_loads *out, double *cp_seg, double *cf_seg, int cap, int *n_seg)
+{
+    if (!s || !out) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    const int nseg = s->segs.nseg;
+    if (n_seg) *n_seg = nseg;
+    lbmdev::launch_wallfn(s->stream, s->lv[s->L - 1].v, s->rec, s->k);
+    CK(cudaMemsetAsync(s->d_acc, 0, 4 * sizeof(double), s->stream));
+    lbmdev::launch_loads(s->stream, s->segs, s->rec, (float)s->U, s->d_acc);
+    lbm_status st = enqueue_mass(s);
+    if (st != LBM_OK) return st;
+    double acc[5];
+    CK(cudaMemcpyAsync(acc, s->d_acc, 5 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (cp_seg && cap > 0) CK(cudaMemcpyAsync(cp_seg, s->segs.cp, std::min(cap, nseg) * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (cf_seg && cap > 0) CK(cudaMemcpyAsync(cf_seg, s->segs.cf, std::min(cap, nseg) * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaGetLastError());
+    st = check_status(s);
+    if (st != LBM_OK) return st;
+    const double chord = s->cfg.chord / (s->cfg.h0 / (double)(1LL << (s->L - 1)));
+    out->CDf = acc[0] / chord;
+    out->CDp = acc[2] / chord;
+    out->CD = out->CDf + out->CDp;
+    out->CL = acc[3] / chord;
+    out->mass = acc[4];
+    out->dCL = s->have_cl ? out->CL - s->last_cl : 0.0;
+    s->last_cl = out->CL;
+    s->have_cl = true;
+    out->step = s->step;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_cut_links(lbm_solver *s, int *ijd, double *q, int cap, int *n)
+{
+    if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    const lbmgrid::Level &G = s->g.lv[s->L - 1];
+    int cnt = 0;
+    for (const auto &R : s->g.recs) {
+        uint16_t m = G.cut[G.idx(R.i, R.j)];
+        for (int d = 1; d < 9; d++) {
+            if (!(m >> d & 1)) continue;
+            if (ijd && q && cnt < cap) { ijd[3 * cnt] = R.i; ijd[3 * cnt + 1] = R.j; ijd[3 * cnt + 2] = d; q[cnt] = R.q[d]; }
+            cnt++;
+        }
+    }
+    *n = cnt;
+    return (ijd && cnt > cap) ? fail(s, LBM_ERR_INVALID_ARG, "capacity too small") : LBM_OK;
+}
+
+lbm_status lbm_get_wall_records(lbm_solver *s, int *ij, double *geo, int *nst, int cap, int *n)
+{
+    if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    const int nr = (int)s->g.recs.size();
+    *n = nr;
+    if (!ij) return LBM_OK;
+    if (nr > cap || !geo || !nst) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    for (int r = 0; r < nr; r++) {
+        const lbmgrid::Record &R = s->g.recs[r];
+        ij[2 * r] = R.i; ij[2 * r + 1] = R.j;
+        double *gg = geo + 9 * r;
+        gg[0] = R.iw[0]; gg[1] = R.iw[1]; gg[2] = R.n[0]; gg[3] = R.n[1]; gg[4] = R.dwb;
+        gg[5] = R.r[0]; gg[6] = R.r[1]; gg[7] = R.loop; gg[8] = R.seg;
+        nst[r] = R.ns;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_wall_state(lbm_solver *s, double *st8, int cap, int *n)
+{
+    if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    const int nr = s->rec.n;
+    *n = nr;
+    if (!st8) return LBM_OK;
+    if (nr > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    if (nr == 0) return LBM_OK;
+    lbmdev::launch_wallfn(s->stream, s->lv[s->L - 1].v, s->rec, s->k);
+    std::vector<float> a[8];
+    float *src[8] = {s->rec.drhoW, s->rec.uWx, s->rec.uWy, s->rec.utau, s->rec.chiB, s->rec.tx, s->rec.ty, s->rec.ut};
+    for (int m = 0; m < 8; m++) {
+        a[m].resize(nr);
+        CK(cudaMemcpyAsync(a[m].data(), src[m], nr * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    for (int r = 0; r < nr; r++) {
+        st8[8 * r] = 1.0 + (double)a[0][r];
+        for (int m = 1; m < 8; m++) st8[8 * r + m] = a[m][r];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_info(lbm_solver *s, lbm_info *out)
+{
+    if (!s || !out) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    std::memset(out, 0, sizeof *out);
+    out->levels = s->L;
+    long long nu = 0;
+    for (int l = 0; l < s->L; l++) {
+        const lbmgrid::Level &G = s->g.lv[l];
+        long long act = 0, pres = 0;
+        for (size_t b = 0; b < G.kind.size(); b++) {
+            if (G.kind[b] != KIND_ABSENT) pres++;
+            if (G.kind[b] == KIND_ACTIVE && !G.solid[b]) act++;
+        }
+        out->cells_active[l] = act;
+        out->cells_present[l] = pres;
+        out->slots[l] = (long long)G.ntiles * LBM_TILE;
+        nu += act << l;
+    }
+    out->node_updates_per_step = nu;
+    out->wall_records = (long long)s->g.recs.size();
+    out->cut_links = s->g.n_cut;
+    out->surface_segments = s->segs.nseg;
+    out->kernels_per_step = s->kernels_per_step;
+    // 9 populations read + 9 written (FP32), nu_tilde read, rho and u written
+    out->bytes_per_node_update = 72.0 + (s->cfg.turbulence ? 4.0 : 0.0) + 12.0;
+    out->device_bytes = s->device_bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_time_kernels(lbm_solver *s, int n, lbm_kernel_times *out)
+{
+    if (!s || !out || n < 0) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    std::memset(out, 0, sizeof *out);
+    out->n_classes = KC_N;
+    for (int c2 = 0; c2 < KC_N; c2++) std::snprintf(out->name[c2], 32, "%s", KC_NAME[c2]);
+    for (int it = 0; it < n; it++) {
+        s->timing = true;
+        s->ev_used = 0;
+        s->ev_marks.clear();
+        s->ev_cells.clear();
+        long long nk = 0;
+        advance(s, s->stream, 0, nk);
+        s->timing = false;
+        s->step++;
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s->stream));
+        for (size_t m = 0; m < s->ev_marks.size(); m++) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, s->ev_pool[s->ev_marks[m].second], s->ev_pool[s->ev_marks[m].second + 1]));
+            int cls = s->ev_marks[m].first;
+            out->total_ms[cls] += ms;
+            out->launches[cls]++;
+            out->cells[cls] += s->ev_cells[m];
+        }
+    }
+    return check_status(s);
+}
+
+}  // extern "C"
