@@ -165,7 +165,10 @@ def gpu_arm(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     pkg.library()
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream (the legacy default stream has handle 0, which the library
+    # would replace by a stream of its own): events and steps share this stream
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     cfg, loops = W.naca0012_large()
     s = pkg.Solver(cfg, stream=stream)
     s.set_geometry(loops)
@@ -305,7 +308,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--cpu-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hbm-grid", action="store_true")
     args = ap.parse_args()

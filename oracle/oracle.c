@@ -615,15 +615,19 @@ int oracle_set_geometry(oracle_solver *s, const double *xy, const int *loop_off,
         int a = loop_off[lp], b = loop_off[lp + 1];
         if (b - a < 3) return fail(s, -5, "loop with fewer than 3 vertices");
         i128 area2 = 0;
+        int nl = 0;
         for (int k = a; k < b; k++) {
             int k2 = (k + 1 < b) ? k + 1 : a;
-            s->sa[s->nseg] = k; s->sb[s->nseg] = k2; s->sloop[s->nseg] = lp; s->nseg++;
+            /* reading: vertices that coincide on the fixed-point grid are merged; a
+               zero-length segment has no normal and adds nothing to eq 30 */
+            if (s->v[k].x == s->v[k2].x && s->v[k].y == s->v[k2].y) continue;
+            s->sa[s->nseg] = k; s->sb[s->nseg] = k2; s->sloop[s->nseg] = lp; s->nseg++; nl++;
             area2 += (i128)s->v[k].x * s->v[k2].y - (i128)s->v[k2].x * s->v[k].y;
             long long ex = s->v[k2].x - s->v[k].x, ey = s->v[k2].y - s->v[k].y;
             if (llabs(ex) > (1LL << 30) || llabs(ey) > (1LL << 30))
                 return fail(s, -5, "wall segment longer than 2^18 finest cells");
         }
-        if (area2 == 0) return fail(s, -5, "degenerate loop");
+        if (area2 == 0 || nl < 3) return fail(s, -5, "degenerate loop");
         s->loop_ccw[lp] = area2 > 0;
     }
     /* level 0: every cell of the box is present and active */

@@ -292,14 +292,17 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
         int a = loop_off[lp], b = loop_off[lp + 1];
         if (b - a < 3) return failmsg(msg, "loop with fewer than 3 vertices");
         i128 area2 = 0;
+        int nl = 0;
         for (int k = a; k < b; k++) {
             int k2 = (k + 1 < b) ? k + 1 : a;
-            g.sa.push_back(k); g.sb.push_back(k2); g.sloop.push_back(lp);
+            // vertices that coincide after snapping are merged: no zero-length segments
+            if (g.v[k].x == g.v[k2].x && g.v[k].y == g.v[k2].y) continue;
+            g.sa.push_back(k); g.sb.push_back(k2); g.sloop.push_back(lp); nl++;
             area2 += (i128)g.v[k].x * g.v[k2].y - (i128)g.v[k2].x * g.v[k].y;
             if (std::llabs(g.v[k2].x - g.v[k].x) > (1LL << 30) || std::llabs(g.v[k2].y - g.v[k].y) > (1LL << 30))
                 return failmsg(msg, "wall segment longer than 2^18 finest cells");
         }
-        if (area2 == 0) return failmsg(msg, "degenerate loop");
+        if (area2 == 0 || nl < 3) return failmsg(msg, "degenerate loop");
         g.loop_ccw[lp] = area2 > 0;
     }
     if (!sp.solid_walls) g.loop_ccw.assign(std::max(n_loops, 1), 1);

@@ -39,3 +39,18 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
         assert "not built" in str(e)
     else:  # pragma: no cover
         raise AssertionError("library() must raise when liblbm.so is missing")
+
+
+def test_create_rejects_invalid_configurations():
+    # validation happens on the host before any CUDA call
+    from paper_2601_18443_gb300 import workloads as W
+    bad = [dict(levels=0), dict(levels=17), dict(nx0=2), dict(h0=0.0), dict(layers=2), dict(Re=0.0),
+           dict(Ma=-1.0), dict(chord=0.0), dict(store=7), dict(periodic=1, nx0=48), dict(wall_model=5)]
+    for kw in bad:
+        cfg = W.base_config(**kw)
+        try:
+            pkg.Solver(cfg)
+        except pkg.LBMError as e:
+            assert e.code == -1, (kw, e.code)
+        else:  # pragma: no cover
+            raise AssertionError(f"accepted invalid configuration {kw}")

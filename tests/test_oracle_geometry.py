@@ -170,3 +170,23 @@ def test_naca_generator():
     seg = np.linalg.norm(np.diff(np.vstack([loop, loop[:1]]), axis=0), axis=1)
     assert seg.max() <= 0.5 / 256 + 1e-15
     assert y.max() == pytest.approx(0.06, abs=2e-4)
+
+
+def test_coincident_vertices_are_merged():
+    # a wall polyline with repeated vertices describes the same wall: same grid, cut links and loads
+    cfg = W.base_config(levels=2, nx0=48, ny0=32, h0=1.0, layers=4, Re=200.0, wall_model=3)
+    base = np.array([[18.3, 12.2], [29.7, 13.1], [27.4, 19.6], [19.1, 18.4]])
+    dup = np.array([base[0], base[1], base[1], base[2], base[3], base[3], base[3]])
+    out = []
+    for loop in (base, dup):
+        s = oracle.Solver(cfg)
+        s.set_geometry([loop])
+        s.step(3)
+        ld = s.get_loads()
+        out.append(([s.get_fields(l)["mask"] for l in range(2)], s.cut_links(), ld))
+    (ma, ca, la), (mb, cb, lb) = out
+    assert all(np.array_equal(x, y) for x, y in zip(ma, mb))
+    assert np.array_equal(ca[0], cb[0]) and np.array_equal(ca[1], cb[1])
+    assert len(la["cp"]) == len(lb["cp"]) == 4
+    for key in ("CL", "CD", "CDp", "CDf"):
+        assert np.isfinite(lb[key]) and lb[key] == la[key]
