@@ -210,7 +210,7 @@ def gpu_arm(args, rank, world, dist):
 
     # dominant kernel: per-launch CUDA events on the solver stream over the same workload
     kt = s.time_kernels(max(2, min(10, K)))
-    fin = kt["stream_collide_finest"]
+    fin = kt["level_step_finest"]
     avg_ms = fin["ms"] / max(fin["launches"], 1)
     act_fin = info["cells_active"][-1]
     bpn = info["bytes_per_node_update"]
@@ -259,10 +259,10 @@ def gpu_arm(args, rank, world, dist):
                        "cells_active_per_level": [int(x) for x in info["cells_active"]],
                        "l2": "512 MB buffer written between timed steps (outside the events)",
                        "replicas": world, "parallelism": f"replicas{world}"},
-            "gbs_full_step_algorithmic": round(value * 1e6 * (bpn + (20.0 if cfg["turbulence"] else 0.0)) / 1e9, 1),
+            "gbs_full_step_algorithmic": round(value * 1e6 * bpn / 1e9, 1),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None,
-                         "kernel": "k_stream_collide (finest level)", "peak_kind": peak_kind,
+                         "kernel": "k_level (finest level: wall function + SA-neg + stream-collide)", "peak_kind": peak_kind,
                          "bytes_per_launch": int(act_fin * bpn), "avg_launch_ms": round(avg_ms, 5),
                          "share_of_step": round(fin["ms"] / total_kt, 3) if total_kt > 0 else None},
             "kernel_times": {k: {"ms_per_step": round(v["ms"] / max(2, min(10, K)), 4), "launches": v["launches"]}
@@ -291,15 +291,37 @@ def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096):
     s.step(3)
     kt = s.time_kernels(5)
     info = s.info()
-    sc = kt["stream_collide_finest"]
+    sc = kt["level_step_finest"]
     avg = sc["ms"] / sc["launches"]
     bpl = info["cells_active"][0] * info["bytes_per_node_update"]
     s.close()
     ach = bpl / (avg * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-            "kernel": "k_stream_collide", "grid": f"{n}x{n} periodic, 1 level, SA on", "bytes_per_launch": int(bpl),
+            "kernel": "k_level", "grid": f"{n}x{n} periodic, 1 level, SA on", "bytes_per_launch": int(bpl),
             "avg_launch_ms": round(avg, 4), "mlups": round(info["cells_active"][0] / avg / 1e3, 1),
             "peak_kind": peak_kind}
+
+
+def profile_case(args):
+    """Small cases for ncu captures: 'hbm_grid' (one periodic 4096 x 4096 level) or
+    'workload' (the benchmark workload); a few steps each, no timing."""
+    import torch
+
+    import paper_2601_18443_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    if args.profile_case == "hbm_grid":
+        cfg = W.base_config(levels=1, nx0=4096, ny0=4096, h0=1.0, Re=1000.0, Ma=0.1, periodic=1, solid_walls=0,
+                            turbulence=1, wall_model=3)
+        loops = []
+    else:
+        cfg, loops = W.naca0012_large()
+    s = pkg.Solver(cfg)
+    s.set_geometry(loops)
+    s.step(args.steps)
+    print("profile case", args.profile_case, "ok", flush=True)
+    s.close()
+    return 0
 
 
 def main():
@@ -311,7 +333,10 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hbm-grid", action="store_true")
+    ap.add_argument("--profile-case", choices=["hbm_grid", "workload"], default=None)
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

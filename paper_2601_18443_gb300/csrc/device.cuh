@@ -8,19 +8,24 @@
 
 namespace lbmdev {
 
-// One level of the sparse tiled grid (device pointers).
+// One level of the sparse tiled grid (device pointers).  Slot indices are 32-bit:
+// the host rejects levels with 9 * n_slots >= 2^31.
 struct LevelView {
     int ntiles;
-    long long ns;                 // cell slots = ntiles * 256
+    int ns;                       // cell slots = ntiles * 256
+    int n_wall_tiles;             // tiles [0, n_wall_tiles) hold boundary nodes
     const int *tile_x, *tile_y;   // tile coordinates (global, in tiles)
     const int *nbr;               // 9 per tile, D2Q9 order, -1 absent
     const int *child;             // 4 per tile: tiles of level l+1, index b * 2 + a
+    const int *parent;            // tile of level l-1 holding the parents, or -1
+    const int *band_tiles;        // tiles with band cells
+    int n_band_tiles;
     const uint32_t *flags;        // per slot
     const float *dist;            // wall distance (level lattice units)
     const int *rec;               // wall record of a B node (finest level) or nullptr
-    float *f[2];                  // populations f - w, [q * ns + slot]
-    float *drho, *ux, *uy;        // macroscopic fields at the level's current time (rho - 1)
-    float *chi[2];                // nu_tilde / nu
+    float *f[2];                  // populations f - w, [q * ns + slot], two lattices
+    float *drho[2], *ux[2], *uy[2];  // macroscopic fields (rho - 1, u) at the two time levels
+    float *chi[2];                // nu_tilde / nu at the two time levels
     float nu;                     // lattice viscosity of the level
 };
 
@@ -48,15 +53,24 @@ struct StepConsts {
     float d_wr, d_wv;
 };
 
+// What one launch of the fused level kernel does besides the level's own update.
+struct LevelStep {
+    int p;              // time level of this level (reads [p], writes [p ^ 1])
+    int pf;             // time level of level l+1 (coalescence source, explosion target)
+    int has_child;      // level l+1 exists
+    int is_level0;      // level 0 (box-edge conditions may apply)
+    int wall;           // this level holds the wall records (finest level)
+    int restrict_up;    // write the restriction of this level's new fields into level l-1
+    int pp;             // time level of level l-1 (restriction writes [pp ^ 1])
+};
+
 // launchers (kernels.cu); all enqueue on the given stream
-void launch_stream_collide(cudaStream_t st, const LevelView &P, const LevelView *F, int cur, int fcur, int fchicur,
-                           const RecView &R, const StepConsts &k, int is_level0);
-void launch_sa(cudaStream_t st, const LevelView &P, const LevelView *F, int cur, const RecView &R,
-               const StepConsts &k, int is_level0);
-void launch_wallfn(cudaStream_t st, const LevelView &P, const RecView &R, const StepConsts &k);
-void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pchi, int fchi);
-void launch_explode_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int cur, int fcur,
-                            const StepConsts &k);
+void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,
+                  const StepConsts &k, const LevelStep &ls);
+void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p);
+void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k);
+void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pp, int pf);
+void launch_explode_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pf);
 void launch_init_feq(cudaStream_t st, const LevelView &P, const float *feq9, float U, float chi_inf);
 
 struct LoadsView {
@@ -66,6 +80,6 @@ struct LoadsView {
     double *cp, *cf;
 };
 void launch_loads(cudaStream_t st, const LoadsView &S, const RecView &R, float U, double *acc4);
-void launch_mass(cudaStream_t st, const LevelView &P, double area, double *acc, int *status);
+void launch_mass(cudaStream_t st, const LevelView &P, int p, double area, double *acc, int *status);
 
 }  // namespace lbmdev

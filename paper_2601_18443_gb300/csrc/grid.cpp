@@ -521,20 +521,45 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
         P.ntx = (int)fdiv(a1, LBM_TX) - P.tx0 + 1; P.nty = (int)fdiv(b1, LBM_TY) - P.ty0 + 1;
         P.tile_of.assign((size_t)P.ntx * P.nty, -1);
         P.tile_x.clear(); P.tile_y.clear();
+        // Level 0 keeps every tile of its box in row-major order (the box-edge conditions
+        // address it arithmetically).  Finer levels keep tiles with at least one non-solid
+        // present cell -- solid cells carry no state: no population is ever pulled from
+        // them and no stencil reads them -- and list tiles with boundary nodes first, so
+        // that their wall-function work starts in the first wave of every launch.
+        std::vector<int> cand_x[2], cand_y[2];
         for (int ty = 0; ty < P.nty; ty++)
             for (int tx = 0; tx < P.ntx; tx++) {
-                bool any = false;
+                bool any = false, wall = false;
                 int gx = (P.tx0 + tx) * LBM_TX, gy = (P.ty0 + ty) * LBM_TY;
-                for (int y = 0; y < LBM_TY && !any; y++)
-                    for (int x = 0; x < LBM_TX && !any; x++) {
+                for (int y = 0; y < LBM_TY; y++)
+                    for (int x = 0; x < LBM_TX; x++) {
                         long c = P.idx(gx + x, gy + y);
-                        any = c >= 0 && P.kind[c] != KIND_ABSENT;
+                        if (c < 0 || P.kind[c] == KIND_ABSENT) continue;
+                        if (l == 0 || !P.solid[c]) any = true;
+                        if (P.bnode[c]) wall = true;
                     }
                 if (!any) continue;
+                int cls = (l > 0 && wall) ? 0 : 1;
+                cand_x[cls].push_back(P.tx0 + tx); cand_y[cls].push_back(P.ty0 + ty);
+            }
+        P.n_wall_tiles = (int)cand_x[0].size();
+        for (int cls = 0; cls < 2; cls++)
+            for (size_t m = 0; m < cand_x[cls].size(); m++) {
+                int tx = cand_x[cls][m] - P.tx0, ty = cand_y[cls][m] - P.ty0;
                 P.tile_of[(size_t)ty * P.ntx + tx] = (int)P.tile_x.size();
-                P.tile_x.push_back(P.tx0 + tx); P.tile_y.push_back(P.ty0 + ty);
+                P.tile_x.push_back(cand_x[cls][m]); P.tile_y.push_back(cand_y[cls][m]);
             }
         P.ntiles = (int)P.tile_x.size();
+        P.band_tiles.clear();
+        for (int t = 0; t < P.ntiles; t++) {
+            bool band = false;
+            for (int y = 0; y < LBM_TY && !band; y++)
+                for (int x = 0; x < LBM_TX && !band; x++) {
+                    long c = P.idx(P.tile_x[t] * LBM_TX + x, P.tile_y[t] * LBM_TY + y);
+                    band = c >= 0 && P.band[c] && !P.solid[c];
+                }
+            if (band) P.band_tiles.push_back(t);
+        }
         P.nbr.assign((size_t)P.ntiles * 9, -1);
         const bool wrap = (l == 0 && sp.periodic);
         const int wtx = sp.nx0 / LBM_TX, wty = sp.ny0 / LBM_TY;
@@ -545,6 +570,17 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                 if (tx < P.tx0 || ty < P.ty0 || tx >= P.tx0 + P.ntx || ty >= P.ty0 + P.nty) continue;
                 P.nbr[(size_t)t * 9 + d] = P.tile_of[(size_t)(ty - P.ty0) * P.ntx + (tx - P.tx0)];
             }
+    }
+    for (int l = 0; l < L; l++) {
+        Level &P = g.lv[l];
+        P.parent.assign((size_t)P.ntiles, -1);
+        if (l == 0) continue;
+        const Level &C = g.lv[l - 1];
+        for (int t = 0; t < P.ntiles; t++) {
+            int tx = P.tile_x[t] >> 1, ty = P.tile_y[t] >> 1;
+            if (tx < C.tx0 || ty < C.ty0 || tx >= C.tx0 + C.ntx || ty >= C.ty0 + C.nty) continue;
+            P.parent[t] = C.tile_of[(size_t)(ty - C.ty0) * C.ntx + (tx - C.tx0)];
+        }
     }
     for (int l = 0; l < L; l++) {
         Level &P = g.lv[l];

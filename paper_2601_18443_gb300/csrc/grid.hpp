@@ -38,7 +38,10 @@ struct Level {
     std::vector<int> tile_x, tile_y;
     std::vector<int> nbr;           // 9 per tile (D2Q9 order), -1 absent
     std::vector<int> child;         // 4 per tile: level l+1 tiles (b * 2 + a)
+    std::vector<int> parent;        // level l-1 tile holding the parents of this tile's cells, or -1
+    std::vector<int> band_tiles;    // tiles holding at least one band cell (explosion / prolongation)
     int ntiles = 0;
+    int n_wall_tiles = 0;           // tiles holding boundary nodes come first in the tile order
 
     long idx(long long i, long long j) const {
         if (i < bi0 || j < bj0 || i >= bi0 + bnx || j >= bj0 + bny) return -1;

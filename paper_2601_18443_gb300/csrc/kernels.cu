@@ -5,14 +5,24 @@
 // thread.  The collision is the central-moment operator of eqs 5-7 evaluated in
 // closed form on the shifted raw moments (rest-state moments subtracted
 // analytically), so that FP32 keeps the small departures from rest exact to
-// ~1e-7 relative.  No step is a dense contraction; the kernels are HBM/L2 bound.
+// ~1e-7 relative.  No step is a dense contraction; the kernels are bound by
+// memory bandwidth (HBM, or L2 where a level stays resident across sub-steps).
+//
+// One launch of k_level advances every active cell of a level by one level step:
+// wall function of its boundary node (finest level, Sec 2.3 steps 1-5), SA-neg
+// update of chi (Sec 2.2), pull streaming with coalescence from the finer level and
+// Yu's slip bounce-back on cut links (eq 27), central-moment collision relaxing with
+// nu + nu_t, explosion into the finer level's ghosts, and -- on the second sub-step
+// of a level -- the restriction of the new fields into the covered parents.  Fields
+// of time t are read from buffer [p] and those of t + 1 written to [p ^ 1], so that
+// no cell reads a value another block of the same launch writes.
 #include <math.h>
 
 #include "device.cuh"
 
 namespace lbmdev {
 
-// ------------------------------------------------------------------ lattice
+// ------------------------------------------------------------------ lattice (eq 2)
 __host__ __device__ constexpr int cxq(int q) { return q == 1 || q == 5 || q == 7 ? 1 : (q == 2 || q == 6 || q == 8 ? -1 : 0); }
 __host__ __device__ constexpr int cyq(int q) { return q == 3 || q == 5 || q == 8 ? 1 : (q == 4 || q == 6 || q == 7 ? -1 : 0); }
 __host__ __device__ constexpr int oppq(int q) { return q == 0 ? 0 : (q & 1 ? q + 1 : q - 1); }
@@ -22,39 +32,39 @@ __host__ __device__ constexpr int mirror_y(int q)
 {
     return q == 3 ? 4 : q == 4 ? 3 : q == 5 ? 7 : q == 7 ? 5 : q == 6 ? 8 : q == 8 ? 6 : q;
 }
-
-__device__ __forceinline__ int dir_of(int sx, int sy)
+// D2Q9 index of the offset (sx, sy) stored at position (sy + 1) * 3 + (sx + 1)
+__host__ __device__ constexpr int dir_of3(int m)
 {
-    // D2Q9 index of the unit offset (sx, sy)
-    return sy == 0 ? (sx == 0 ? 0 : (sx > 0 ? 1 : 2)) : (sy > 0 ? (sx == 0 ? 3 : (sx > 0 ? 5 : 8)) : (sx == 0 ? 4 : (sx > 0 ? 7 : 6)));
+    return m == 4 ? 0 : m == 5 ? 1 : m == 3 ? 2 : m == 7 ? 3 : m == 1 ? 4 : m == 8 ? 5 : m == 0 ? 6 : m == 2 ? 7 : 8;
 }
 
-// slot of the cell at offset (dx, dy) from (lx, ly) in tile t, or -1
-__device__ __forceinline__ long long nb_slot(const LevelView &P, int t, int lx, int ly, int dx, int dy)
+// The 3 x 3 block of tiles around the block's tile, staged in shared memory.
+__device__ __forceinline__ void load_nb3(const LevelView &P, int t, int *nb3)
 {
-    int nx = lx + dx, ny = ly + dy;
-    int sx = nx < 0 ? -1 : (nx >= LBM_TX ? 1 : 0);
-    int sy = ny < 0 ? -1 : (ny >= LBM_TY ? 1 : 0);
-    int tt = t;
-    if (sx | sy) {
-        tt = P.nbr[t * 9 + dir_of(sx, sy)];
-        if (tt < 0) return -1;
-    }
-    return (long long)tt * LBM_TILE + ((ny + LBM_TY) & (LBM_TY - 1)) * LBM_TX + ((nx + LBM_TX) & (LBM_TX - 1));
+    if (threadIdx.x < 9) nb3[threadIdx.x] = P.nbr[t * 9 + dir_of3(threadIdx.x)];
+}
+
+// slot of the cell at offset (dx, dy) from (lx, ly), or -1 if its tile is absent
+__device__ __forceinline__ int nb_slot(const int *nb3, int lx, int ly, int dx, int dy)
+{
+    const int nx = lx + dx, ny = ly + dy;
+    const int sx = nx < 0 ? 0 : (nx >= LBM_TX ? 2 : 1);
+    const int sy = ny < 0 ? 0 : (ny >= LBM_TY ? 2 : 1);
+    const int tt = nb3[sy * 3 + sx];
+    return tt < 0 ? -1 : tt * LBM_TILE + (ny & (LBM_TY - 1)) * LBM_TX + (nx & (LBM_TX - 1));
 }
 
 // level 0 covers its whole box with tiles in row-major order
-__device__ __forceinline__ long long slot0(const StepConsts &k, int i, int j)
+__device__ __forceinline__ int slot0(const StepConsts &k, int i, int j)
 {
-    return ((long long)(j >> 3) * k.ntx0 + (i >> 5)) * LBM_TILE + (j & 7) * LBM_TX + (i & 31);
+    return ((j >> 3) * k.ntx0 + (i >> 5)) * LBM_TILE + (j & 7) * LBM_TX + (i & 31);
 }
 
 // the tile of level l+1 holding the four children of (lx, ly) and their first slot
-__device__ __forceinline__ long long child_base(const LevelView &P, int t, int lx, int ly)
+__device__ __forceinline__ int child_base(const LevelView &P, int t, int lx, int ly)
 {
-    int ct = P.child[t * 4 + ((2 * ly) >> 3) * 2 + ((2 * lx) >> 5)];
-    if (ct < 0) return -1;
-    return (long long)ct * LBM_TILE + ((2 * ly) & 7) * LBM_TX + ((2 * lx) & 31);
+    const int ct = P.child[t * 4 + ((2 * ly) >> 3) * 2 + ((2 * lx) >> 5)];
+    return ct < 0 ? -1 : ct * LBM_TILE + ((2 * ly) & 7) * LBM_TX + ((2 * lx) & 31);
 }
 
 // ------------------------------------------------------------------ SA-neg constants (Sec 2.2)
@@ -124,168 +134,25 @@ __device__ __forceinline__ float delta_of(float nu, float chi, int turbulence)
     return 12.0f * nue / (1.0f + 6.0f * nue);
 }
 
-// ------------------------------------------------------------------ stream + collide
-__device__ __forceinline__ float pull0(const StepConsts &k, const float *fc, long long ns, int i, int j, int q)
-{
-    // post-stream value at level-0 cell (i, j), direction q, source inside the box in x
-    int si = i - cxq(q), sj = j - cyq(q);
-    if (sj >= 0 && sj < k.ny0) return fc[q * ns + slot0(k, si, sj)];
-    return fc[mirror_y(q) * ns + slot0(k, si, j)];
-}
-
-__global__ void __launch_bounds__(256) k_stream_collide(LevelView P, LevelView F, int has_child, int cur, int fcur,
-                                                         int fchicur, RecView R, StepConsts k, int is_level0)
-{
-    const int t = blockIdx.x, c = threadIdx.x;
-    const int lx = c & (LBM_TX - 1), ly = c >> 5;
-    const long long slot = (long long)t * LBM_TILE + c;
-    const uint32_t fl = P.flags[slot];
-    const uint32_t kind = fl & FL_KIND_MASK;
-    if (kind == KIND_ABSENT || (fl & FL_SOLID)) return;
-    const long long ns = P.ns;
-    const float *fc = P.f[cur];
-    float *fn = P.f[cur ^ 1];
-
-    if (kind == KIND_COVERED) {
-        // restriction of the macroscopic fields from the four children (time t+1)
-        long long cb = child_base(P, t, lx, ly);
-        if (cb < 0) return;
-        float sdr = 0.f, sr = 0.f, sx = 0.f, sy = 0.f, sc = 0.f;
-        int n = 0;
-        const long long off[4] = {0, 1, LBM_TX, LBM_TX + 1};
-#pragma unroll
-        for (int m = 0; m < 4; m++) {
-            long long cs = cb + off[m];
-            if (F.flags[cs] & FL_SOLID) continue;
-            float dr = F.drho[cs], r = 1.0f + dr;
-            sdr += dr; sr += r; sx += r * F.ux[cs]; sy += r * F.uy[cs]; sc += F.chi[fchicur][cs];
-            n++;
-        }
-        if (n == 0) return;
-        P.drho[slot] = sdr / n; P.ux[slot] = sx / sr; P.uy[slot] = sy / sr;
-        P.chi[cur ^ 1][slot] = sc / n;
-        return;
-    }
-    if (kind == KIND_GHOST) {
-        // ghosts are streamed (relayed), never collided
-#pragma unroll
-        for (int q = 0; q < 9; q++) {
-            long long s = nb_slot(P, t, lx, ly, -cxq(q), -cyq(q));
-            bool ok = false;
-            if (s >= 0) {
-                uint32_t fs = P.flags[s];
-                uint32_t ks = fs & FL_KIND_MASK;
-                ok = (ks == KIND_ACTIVE || ks == KIND_GHOST) && !(fs & FL_SOLID);
-            }
-            fn[q * ns + slot] = ok ? fc[q * ns + s] : fc[q * ns + slot];
-        }
-        return;
-    }
-
-    float g[9];
-    g[0] = fc[slot];
-    const bool edge = is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
-    if (!edge) {
-#pragma unroll
-        for (int q = 1; q < 9; q++) {
-            if (fl & (1u << (FL_COAL_SHIFT + q - 1))) {
-                // coalescence: mean of the four ghost children after the two fine sub-steps
-                long long cb = child_base(P, t, lx, ly);
-                const float *ff = F.f[fcur] + q * F.ns;
-                g[q] = cb >= 0 ? 0.25f * (ff[cb] + ff[cb + 1] + ff[cb + LBM_TX] + ff[cb + LBM_TX + 1]) : fc[q * ns + slot];
-            } else if (fl & (1u << (FL_CUT_SHIFT + q - 1))) {
-                // Yu interpolated bounce-back with the slip velocity of the wall record (eq 27)
-                const int r = P.rec[slot];
-                const int qo = oppq(q);
-                const float qf = R.q[r * 9 + q];
-                const float mom = 6.0f * wq(q) * (1.0f + R.drhoW[r]) * (cxq(q) * R.uWx[r] + cyq(q) * R.uWy[r]);
-                long long sf = nb_slot(P, t, lx, ly, cxq(q), cyq(q));
-                bool ok = false;
-                if (sf >= 0) {
-                    uint32_t ff = P.flags[sf];
-                    ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
-                }
-                if (ok)
-                    g[q] = ((1.0f - qf) * fc[qo * ns + sf] + qf * fc[qo * ns + slot] + mom) / (1.0f + qf) +
-                           qf / (1.0f + qf) * fc[q * ns + slot];
-                else
-                    g[q] = fc[qo * ns + slot] + mom;                // half-way form, eq 24
-            } else {
-                long long s = nb_slot(P, t, lx, ly, -cxq(q), -cyq(q));
-                g[q] = fc[q * ns + (s >= 0 ? s : slot)];
-            }
-        }
-    } else {
-        // level-0 box edge: in-box pulls, symmetry planes, Zou-He inlet, extrapolated outlet
-        const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
-#pragma unroll
-        for (int q = 1; q < 9; q++) {
-            int si = i - cxq(q), sj = j - cyq(q);
-            bool xin = si >= 0 && si < k.nx0, yin = sj >= 0 && sj < k.ny0;
-            if (xin && yin) g[q] = fc[q * ns + slot0(k, si, sj)];
-            else if (xin) g[q] = fc[mirror_y(q) * ns + slot0(k, si, j)];
-            else g[q] = 0.0f;
-        }
-        if (i == 0) {
-            const float U = k.U;
-            float S = g[0] + g[3] + g[4] + 2.0f * (g[2] + g[6] + g[8]);       // sum of w over these is 1
-            float rho = (1.0f + S) / (1.0f - U);
-            g[1] = g[2] + (2.0f / 3.0f) * rho * U;
-            g[5] = g[6] - 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
-            g[7] = g[8] + 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
-        }
-        if (i == k.nx0 - 1) {
-            const int qs[3] = {2, 6, 8};
-#pragma unroll
-            for (int m = 0; m < 3; m++) {
-                int q = qs[m];
-                g[q] = 2.0f * pull0(k, fc, ns, k.nx0 - 2, j, q) - pull0(k, fc, ns, k.nx0 - 3, j, q);
-            }
-        }
-    }
-    // macroscopic fields (eq 3)
-    const float drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
-    const float rho = 1.0f + drho;
-    const float ux = (g[1] - g[2] + g[5] - g[6] + g[7] - g[8]) / rho;
-    const float uy = (g[3] - g[4] + g[5] - g[6] - g[7] + g[8]) / rho;
-    P.drho[slot] = drho; P.ux[slot] = ux; P.uy[slot] = uy;
-    const float chi = k.turbulence ? P.chi[cur ^ 1][slot] : 0.0f;
-    float o[9];
-    collide_cm(g, drho, ux, uy, delta_of(P.nu, chi, k.turbulence), o);
-#pragma unroll
-    for (int q = 0; q < 9; q++) fn[q * ns + slot] = o[q];
-    if (has_child && (fl & FL_BAND)) {
-        // explosion: post-collision populations copied to the four ghost children
-        long long cb = child_base(P, t, lx, ly);
-        if (cb >= 0) {
-#pragma unroll
-            for (int q = 0; q < 9; q++) {
-                float *ff = F.f[fcur] + q * F.ns;
-                ff[cb] = o[q]; ff[cb + 1] = o[q]; ff[cb + LBM_TX] = o[q]; ff[cb + LBM_TX + 1] = o[q];
-            }
-        }
-    }
-}
-
 // ------------------------------------------------------------------ SA-neg (Sec 2.2)
 struct Stencil {
     float chi[9], ux[9], uy[9];
 };
 
-__device__ __forceinline__ void gather(const LevelView &P, const float *chi, int t, int lx, int ly, long long slot,
-                                       Stencil &S)
+__device__ __forceinline__ void gather(const int *nb3, const float *chi, const float *ux, const float *uy, int lx,
+                                       int ly, int slot, Stencil &S)
 {
 #pragma unroll
     for (int q = 0; q < 9; q++) {
-        long long s = q == 0 ? slot : nb_slot(P, t, lx, ly, cxq(q), cyq(q));
+        int s = q == 0 ? slot : nb_slot(nb3, lx, ly, cxq(q), cyq(q));
         if (s < 0) s = slot;
-        S.chi[q] = chi[s]; S.ux[q] = P.ux[s]; S.uy[q] = P.uy[s];
+        S.chi[q] = __ldg(chi + s); S.ux[q] = __ldg(ux + s); S.uy[q] = __ldg(uy + s);
     }
 }
 
 // level-0 box edge: neighbours across the top/bottom symmetry planes are mirror images
-__device__ __forceinline__ void gather0(const LevelView &P, const float *chi, const StepConsts &k, int i, int j,
-                                        Stencil &S)
+__device__ __forceinline__ void gather0(const float *chi, const float *ux, const float *uy, const StepConsts &k, int i,
+                                        int j, Stencil &S)
 {
 #pragma unroll
     for (int q = 0; q < 9; q++) {
@@ -295,8 +162,8 @@ __device__ __forceinline__ void gather0(const LevelView &P, const float *chi, co
         if (jj >= k.ny0) { jj = k.ny0 - 1; sg = -1.0f; }
         if (ii < 0) ii = 0;
         if (ii >= k.nx0) ii = k.nx0 - 1;
-        long long s = slot0(k, ii, jj);
-        S.chi[q] = chi[s]; S.ux[q] = P.ux[s]; S.uy[q] = sg * P.uy[s];
+        const int s = slot0(k, ii, jj);
+        S.chi[q] = chi[s]; S.ux[q] = ux[s]; S.uy[q] = sg * uy[s];
     }
 }
 
@@ -357,52 +224,6 @@ __device__ float sa_update(const Stencil &S, float d, float nu)
     return chi + conv + src + diff;
 }
 
-__global__ void __launch_bounds__(256) k_sa(LevelView P, LevelView F, int has_child, int cur, RecView R,
-                                             StepConsts k, int is_level0)
-{
-    const int t = blockIdx.x, c = threadIdx.x;
-    const int lx = c & (LBM_TX - 1), ly = c >> 5;
-    const long long slot = (long long)t * LBM_TILE + c;
-    const uint32_t fl = P.flags[slot];
-    if ((fl & FL_KIND_MASK) != KIND_ACTIVE || (fl & FL_SOLID)) return;
-    const float *chi = P.chi[cur];
-    float *chin = P.chi[cur ^ 1];
-    const bool edge = is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
-    Stencil S;
-    if (has_child && (fl & FL_BAND)) {
-        // ghost children of the next level: LSQ linear reconstruction about this cell (time t)
-        gather(P, chi, t, lx, ly, slot, S);
-        float gcx, gcy, gux, guy, gvx, gvy;
-        lsq_grad(S.chi, gcx, gcy); lsq_grad(S.ux, gux, guy); lsq_grad(S.uy, gvx, gvy);
-        long long cb = child_base(P, t, lx, ly);
-        if (cb >= 0) {
-            const float dr = P.drho[slot];
-#pragma unroll
-            for (int m = 0; m < 4; m++) {
-                const int a = m & 1, b = m >> 1;
-                const float ox = 0.5f * (a - 0.5f), oy = 0.5f * (b - 0.5f);
-                const long long cs = cb + b * LBM_TX + a;
-                const float vc = S.chi[0] + gcx * ox + gcy * oy;
-                F.chi[0][cs] = vc; F.chi[1][cs] = vc;
-                F.ux[cs] = S.ux[0] + gux * ox + guy * oy;
-                F.uy[cs] = S.uy[0] + gvx * ox + gvy * oy;
-                F.drho[cs] = dr;
-            }
-        }
-    }
-    if (fl & FL_BNODE) { chin[slot] = R.chiB[P.rec[slot]]; return; }   // Dirichlet nu_t~_B (Sec 2.2)
-    if (edge) {
-        const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
-        if (fl & FL_INLET) { chin[slot] = k.chi_inf; return; }
-        const int ic = (fl & FL_OUTLET) ? k.nx0 - 2 : i;                   // outlet: copy of its neighbour
-        gather0(P, chi, k, ic, j, S);
-        chin[slot] = sa_update(S, P.dist[slot0(k, ic, j)], P.nu);
-        return;
-    }
-    if (!(has_child && (fl & FL_BAND))) gather(P, chi, t, lx, ly, slot, S);
-    chin[slot] = sa_update(S, P.dist[slot], P.nu);
-}
-
 // ------------------------------------------------------------------ wall function (Sec 2.3 steps 1-5)
 #define WF_B 5.033908790505579f
 #define WF_A1 8.148221580024245f
@@ -428,76 +249,61 @@ __device__ __forceinline__ float wf_dudy(float y)
     return (SA_CV1_3 + k3) / (SA_CV1_3 + k3 * (1.0f + SA_KAPPA * y));
 }
 
-// friction velocity from u_t at distance y (Newton inside a sign bracket, bounded iterations)
-__device__ float wf_utau(float ut, float y, float nu)
+// Friction velocity from u_t at distance y (step 3): Newton on g(u) = u u+(u y / nu) - u_t,
+// g' = u+ + y+ du+/dy+ > 0, started from the previous sub-step's value when there is one,
+// else from the viscous-sublayer value (which lies left of the root, since u+ <= y+).
+// Every evaluation narrows a sign bracket; steps leaving it are replaced by bisection
+// (or doubling while no right end is known).  At most 24 evaluations.
+__device__ float wf_utau(float ut, float y, float nu, float guess)
 {
     if (!(ut > 0.0f)) return 0.0f;
-    float lo = 0.0f, hi = sqrtf(ut * nu / y);
-    for (int it = 0; it < 128; it++) {
-        if (hi * wf_uplus(hi * y / nu) - ut > 0.0f) break;
-        lo = hi;
-        hi *= 2.0f;
-    }
-    float u = 0.5f * (lo + hi);
-    for (int it = 0; it < 40; it++) {
+    float lo = 0.0f, hi = INFINITY;
+    float u = guess > 0.0f ? guess : sqrtf(ut * nu / y);
+    for (int it = 0; it < 24; it++) {
         const float yp = u * y / nu;
         const float up = wf_uplus(yp);
         const float gv = u * up - ut;
         if (gv > 0.0f) hi = u; else lo = u;
         const float gp = up + yp * wf_dudy(yp);
-        float un = gp > 0.0f ? u - gv / gp : 0.5f * (lo + hi);
-        if (!(un > lo && un < hi)) un = 0.5f * (lo + hi);
-        const bool done = fabsf(un - u) <= 2e-7f * un;
+        float un = gp > 0.0f ? u - gv / gp : -1.0f;
+        if (!(un > lo && un < hi)) un = isinf(hi) ? 2.0f * fmaxf(u, lo) : 0.5f * (lo + hi);
+        const bool done = fabsf(un - u) <= 1e-6f * un;
         u = un;
-        if (done || hi - lo <= 2e-7f * hi) break;
+        if (done) break;
     }
     return u;
 }
 
-// one half-warp per wall record: the 16 lanes hold the 4 x 4 reference stencil
-__global__ void __launch_bounds__(256) k_wallfn(LevelView P, RecView R, StepConsts k)
+// Wall state of one boundary node from the macroscopic fields at time level p:
+// steps 1-5 of Sec 2.3 (IDW density and LSQ velocity at R, tangential part, u_tau from
+// eq 22, u_V, slip velocity of eq 28 along t) and the SA Dirichlet value (Sec 2.2).
+// Writes the record's state arrays; returns rho_W - 1, u_W and chi_B.
+__device__ void wall_record(const LevelView &P, int p, const RecView &R, const StepConsts &k, int r, float &drW,
+                            float &uWx, float &uWy, float &chiB)
 {
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = gt >> 4, m = gt & 15;
-    const bool valid = r < R.n;
-    float v[13];
-#pragma unroll
-    for (int a = 0; a < 13; a++) v[a] = 0.0f;
-    if (valid && m < R.ns[r]) {
-        const long long s = R.st_slot[r * 16 + m];
-        const float dx = R.st_dx[r * 16 + m], dy = R.st_dy[r * 16 + m];
-        const float dr = P.drho[s], u = P.ux[s], w = P.uy[s];
-        const float wt = 1.0f / fmaxf(dx * dx + dy * dy, 1e-20f);
-        v[0] = wt; v[1] = wt * dr; v[2] = wt * u; v[3] = wt * w;                  // IDW sums
-        v[4] = 1.0f; v[5] = dx; v[6] = dy; v[7] = dx * dx; v[8] = dx * dy; v[9] = dy * dy;   // LSQ normal matrix
-        v[10] = u; v[11] = u * dx; v[12] = u * dy;
-    }
-    // the v-component LSQ right-hand side uses a second pass of the same lanes
-    float wv0 = 0.f, wv1 = 0.f, wv2 = 0.f;
-    if (valid && m < R.ns[r]) {
-        const long long s = R.st_slot[r * 16 + m];
-        const float dx = R.st_dx[r * 16 + m], dy = R.st_dy[r * 16 + m], w = P.uy[s];
-        wv0 = w; wv1 = w * dx; wv2 = w * dy;
-    }
-#pragma unroll
-    for (int off = 8; off >= 1; off >>= 1) {
-#pragma unroll
-        for (int a = 0; a < 13; a++) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
-        wv0 += __shfl_xor_sync(0xffffffffu, wv0, off);
-        wv1 += __shfl_xor_sync(0xffffffffu, wv1, off);
-        wv2 += __shfl_xor_sync(0xffffffffu, wv2, off);
-    }
-    if (!valid || m != 0) return;
+    const float *dr = P.drho[p], *ux = P.ux[p], *uy = P.uy[p];
     const int ns = R.ns[r];
+    float sw = 0.f, swr = 0.f, swu = 0.f, swv = 0.f;
+    float A0 = 0.f, A1 = 0.f, A2 = 0.f, A4 = 0.f, A5 = 0.f, A8 = 0.f;
+    float bu0 = 0.f, bu1 = 0.f, bu2 = 0.f, bv0 = 0.f, bv1 = 0.f, bv2 = 0.f;
+    for (int m = 0; m < ns; m++) {
+        const int s = R.st_slot[r * 16 + m];
+        const float dx = R.st_dx[r * 16 + m], dy = R.st_dy[r * 16 + m];
+        const float d = dr[s], u = ux[s], v = uy[s];
+        const float w = 1.0f / fmaxf(dx * dx + dy * dy, 1e-20f);
+        sw += w; swr += w * d; swu += w * u; swv += w * v;
+        A0 += 1.0f; A1 += dx; A2 += dy; A4 += dx * dx; A5 += dx * dy; A8 += dy * dy;
+        bu0 += u; bu1 += u * dx; bu2 += u * dy;
+        bv0 += v; bv1 += v * dx; bv2 += v * dy;
+    }
     float drR = 0.f, uR = 0.f, vR = 0.f;
-    if (ns > 0) { drR = v[1] / v[0]; uR = v[2] / v[0]; vR = v[3] / v[0]; }
+    if (ns > 0) { drR = swr / sw; uR = swu / sw; vR = swv / sw; }
     // unweighted linear LSQ u = a + b dx + c dy: intercept a by Cramer's rule
-    const float A0 = v[4], A1 = v[5], A2 = v[6], A4 = v[7], A5 = v[8], A8 = v[9];
     const float det = A0 * (A4 * A8 - A5 * A5) - A1 * (A1 * A8 - A5 * A2) + A2 * (A1 * A5 - A4 * A2);
     if (ns >= 3 && det > 1e-9f * A0 * A4 * A8) {
         const float c0 = A4 * A8 - A5 * A5, c1 = A2 * A5 - A1 * A8, c2 = A1 * A5 - A2 * A4;
-        uR = (c0 * v[10] + c1 * v[11] + c2 * v[12]) / det;
-        vR = (c0 * wv0 + c1 * wv1 + c2 * wv2) / det;
+        uR = (c0 * bu0 + c1 * bu1 + c2 * bu2) / det;
+        vR = (c0 * bv0 + c1 * bv1 + c2 * bv2) / det;
     }
     const float nx = R.nx[r], ny = R.ny[r];
     const float un = uR * nx + vR * ny;
@@ -505,10 +311,11 @@ __global__ void __launch_bounds__(256) k_wallfn(LevelView P, RecView R, StepCons
     const float ut = sqrtf(utx * utx + uty * uty);
     float tx = -ny, ty = nx;
     if (ut > 0.0f) { tx = utx / ut; ty = uty / ut; }
-    float utau = 0.f, uWx = 0.f, uWy = 0.f, chiB = 0.f;
+    float utau = 0.f;
+    uWx = 0.f; uWy = 0.f; chiB = 0.f;
     if (k.wall_model == 0) {
         const float nu = P.nu;
-        utau = wf_utau(ut, k.d_wr, nu);                                     // step 3
+        utau = wf_utau(ut, k.d_wr, nu, R.utau[r]);                          // step 3
         const float ypv = utau * k.d_wv / nu;
         const float uV = utau * wf_uplus(ypv);                              // step 4
         const float uW = uV - utau * utau * k.d_wv / (nu * (1.0f + SA_KAPPA * ypv));   // eq 28
@@ -517,57 +324,299 @@ __global__ void __launch_bounds__(256) k_wallfn(LevelView P, RecView R, StepCons
     } else if (k.wall_model == 2) {
         uWx = R.slip[2 * R.loop[r]]; uWy = R.slip[2 * R.loop[r] + 1];
     }
+    drW = drR;
     R.drhoW[r] = drR; R.uWx[r] = uWx; R.uWy[r] = uWy; R.utau[r] = utau; R.chiB[r] = chiB;
     R.tx[r] = tx; R.ty[r] = ty; R.ut[r] = ut;
 }
 
+// ------------------------------------------------------------------ the fused level step
+template <bool WALL, bool CHILD>
+__global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, LevelView C, RecView R, StepConsts k,
+                                                   LevelStep ls)
+{
+    __shared__ int nb3[9];
+    __shared__ float sh[4][LBM_TILE];            // new rho - 1, u_x, u_y, chi (restriction)
+    __shared__ unsigned char sv[LBM_TILE];
+    const int t = blockIdx.x, c = threadIdx.x;
+    const int lx = c & (LBM_TX - 1), ly = c >> 5;
+    load_nb3(P, t, nb3);
+    __syncthreads();
+    const int slot = t * LBM_TILE + c;
+    const uint32_t fl = __ldg(P.flags + slot);
+    const uint32_t kind = fl & FL_KIND_MASK;
+    const bool fluid = !(fl & FL_SOLID);
+    const int ns = P.ns, p = ls.p;
+    const float *fc = P.f[p];
+    float *fn = P.f[p ^ 1];
+    bool valid = false;
+    float n_dr = 0.f, n_ux = 0.f, n_uy = 0.f, n_chi = 0.f;
+
+    if (kind == KIND_GHOST && fluid) {
+        // ghosts are streamed (relayed), never collided
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            const int s = q == 0 ? slot : nb_slot(nb3, lx, ly, -cxq(q), -cyq(q));
+            bool ok = false;
+            if (s >= 0) {
+                const uint32_t fs = __ldg(P.flags + s);
+                const uint32_t ks = fs & FL_KIND_MASK;
+                ok = (ks == KIND_ACTIVE || ks == KIND_GHOST) && !(fs & FL_SOLID);
+            }
+            fn[q * ns + slot] = __ldg(fc + q * ns + (ok ? s : slot));
+        }
+    } else if (kind == KIND_ACTIVE && fluid) {
+        const bool edge = ls.is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
+        const bool bnode = WALL && (fl & FL_BNODE);
+        // ---- wall function of the boundary node (Sec 2.3), fields at time t
+        float drW = 0.f, uWx = 0.f, uWy = 0.f, chiB = 0.f;
+        int r = -1;
+        if (bnode) {
+            r = P.rec[slot];
+            wall_record(P, p, R, k, r, drW, uWx, uWy, chiB);
+        }
+        // ---- SA-neg update of chi (Sec 2.2), fields at time t
+        float chin;
+        if (k.turbulence) {
+            if (bnode) {
+                chin = chiB;                                        // Dirichlet nu_t~_B (Sec 2.2)
+            } else if (edge) {
+                const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
+                if (fl & FL_INLET) {
+                    chin = k.chi_inf;
+                } else {
+                    const int ic = (fl & FL_OUTLET) ? k.nx0 - 2 : i;     // outlet: copy of its neighbour
+                    Stencil S;
+                    gather0(P.chi[p], P.ux[p], P.uy[p], k, ic, j, S);
+                    chin = sa_update(S, P.dist[slot0(k, ic, j)], P.nu);
+                }
+            } else {
+                Stencil S;
+                gather(nb3, P.chi[p], P.ux[p], P.uy[p], lx, ly, slot, S);
+                chin = sa_update(S, __ldg(P.dist + slot), P.nu);
+            }
+            P.chi[p ^ 1][slot] = chin;
+        } else {
+            chin = __ldg(P.chi[p] + slot);
+        }
+        // ---- pull streaming (eq 1) with coalescence, cut links and box edges
+        float g[9];
+        g[0] = __ldg(fc + slot);
+        if (!edge) {
+            int cb = -1;
+            if (CHILD && (fl & FL_BAND)) cb = child_base(P, t, lx, ly);
+#pragma unroll
+            for (int q = 1; q < 9; q++) {
+                if (CHILD && (fl & (1u << (FL_COAL_SHIFT + q - 1)))) {
+                    // coalescence: mean of the four ghost children after the two fine sub-steps
+                    const float *ff = F.f[ls.pf] + q * F.ns;
+                    g[q] = cb >= 0 ? 0.25f * (ff[cb] + ff[cb + 1] + ff[cb + LBM_TX] + ff[cb + LBM_TX + 1])
+                                   : __ldg(fc + q * ns + slot);
+                } else if (WALL && (fl & (1u << (FL_CUT_SHIFT + q - 1)))) {
+                    // Yu interpolated bounce-back with the slip velocity of the wall record (eq 27)
+                    const int qo = oppq(q);
+                    const float qf = R.q[r * 9 + q];
+                    const float mom = 6.0f * wq(q) * (1.0f + drW) * (cxq(q) * uWx + cyq(q) * uWy);
+                    const int sf = nb_slot(nb3, lx, ly, cxq(q), cyq(q));
+                    bool ok = false;
+                    if (sf >= 0) {
+                        const uint32_t ff = __ldg(P.flags + sf);
+                        ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
+                    }
+                    if (ok)
+                        g[q] = ((1.0f - qf) * __ldg(fc + qo * ns + sf) + qf * __ldg(fc + qo * ns + slot) + mom) /
+                                   (1.0f + qf) +
+                               qf / (1.0f + qf) * __ldg(fc + q * ns + slot);
+                    else
+                        g[q] = __ldg(fc + qo * ns + slot) + mom;            // half-way form, eq 24
+                } else {
+                    const int s = nb_slot(nb3, lx, ly, -cxq(q), -cyq(q));
+                    g[q] = __ldg(fc + q * ns + (s >= 0 ? s : slot));
+                }
+            }
+        } else {
+            // level-0 box edge: in-box pulls, symmetry planes, Zou-He inlet, extrapolated outlet (Sec 3.1.1)
+            const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
+#pragma unroll
+            for (int q = 1; q < 9; q++) {
+                const int si = i - cxq(q), sj = j - cyq(q);
+                const bool xin = si >= 0 && si < k.nx0, yin = sj >= 0 && sj < k.ny0;
+                if (xin && yin) g[q] = fc[q * ns + slot0(k, si, sj)];
+                else if (xin) g[q] = fc[mirror_y(q) * ns + slot0(k, si, j)];
+                else g[q] = 0.0f;
+            }
+            if (i == 0) {
+                const float U = k.U;
+                const float S = g[0] + g[3] + g[4] + 2.0f * (g[2] + g[6] + g[8]);   // sum of w over these is 1
+                const float rho = (1.0f + S) / (1.0f - U);
+                g[1] = g[2] + (2.0f / 3.0f) * rho * U;
+                g[5] = g[6] - 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
+                g[7] = g[8] + 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
+            }
+            if (i == k.nx0 - 1) {
+#pragma unroll
+                for (int m = 0; m < 3; m++) {
+                    const int q = m == 0 ? 2 : (m == 1 ? 6 : 8);
+                    float v[2];
+#pragma unroll
+                    for (int b = 0; b < 2; b++) {
+                        const int ii = k.nx0 - 2 - b, si = ii - cxq(q), sj = j - cyq(q);
+                        v[b] = (sj >= 0 && sj < k.ny0) ? fc[q * ns + slot0(k, si, sj)]
+                                                       : fc[mirror_y(q) * ns + slot0(k, si, j)];
+                    }
+                    g[q] = 2.0f * v[0] - v[1];
+                }
+            }
+        }
+        // ---- macroscopic fields (eq 3) and central-moment collision (eqs 5-11)
+        const float drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+        const float rho = 1.0f + drho;
+        const float ux = (g[1] - g[2] + g[5] - g[6] + g[7] - g[8]) / rho;
+        const float uy = (g[3] - g[4] + g[5] - g[6] - g[7] + g[8]) / rho;
+        P.drho[p ^ 1][slot] = drho; P.ux[p ^ 1][slot] = ux; P.uy[p ^ 1][slot] = uy;
+        float o[9];
+        collide_cm(g, drho, ux, uy, delta_of(P.nu, chin, k.turbulence), o);
+#pragma unroll
+        for (int q = 0; q < 9; q++) fn[q * ns + slot] = o[q];
+        if (CHILD && (fl & FL_BAND)) {
+            // explosion: post-collision populations copied to the four ghost children
+            const int cb = child_base(P, t, lx, ly);
+            if (cb >= 0) {
+#pragma unroll
+                for (int q = 0; q < 9; q++) {
+                    float *ff = F.f[ls.pf] + q * F.ns;
+                    ff[cb] = o[q]; ff[cb + 1] = o[q]; ff[cb + LBM_TX] = o[q]; ff[cb + LBM_TX + 1] = o[q];
+                }
+            }
+        }
+        valid = true;
+        n_dr = drho; n_ux = ux; n_uy = uy; n_chi = chin;
+    }
+
+    if (ls.restrict_up) {
+        // restriction into the covered parents (their children are this level's active
+        // cells; a 2 x 2 group of children never straddles a tile): rho and chi are the
+        // means over the fluid children, u is mass-weighted (Rohde transfers, Sec 2.1)
+        sh[0][c] = n_dr; sh[1][c] = n_ux; sh[2][c] = n_uy; sh[3][c] = n_chi;
+        sv[c] = valid;
+        __syncthreads();
+        if (!(lx & 1) && !(ly & 1) && kind == KIND_ACTIVE) {
+            const int pt = P.parent[t];
+            float sdr = 0.f, sr = 0.f, sx = 0.f, sy = 0.f, sc = 0.f;
+            int n = 0;
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const int cc = c + (m & 1) + (m >> 1) * LBM_TX;
+                if (!sv[cc]) continue;
+                const float dr = sh[0][cc], rr = 1.0f + dr;
+                sdr += dr; sr += rr; sx += rr * sh[1][cc]; sy += rr * sh[2][cc]; sc += sh[3][cc];
+                n++;
+            }
+            if (pt >= 0 && n > 0) {
+                const int px = (P.tile_x[t] & 1) * (LBM_TX / 2) + (lx >> 1);
+                const int py = (P.tile_y[t] & 1) * (LBM_TY / 2) + (ly >> 1);
+                const int ps = pt * LBM_TILE + py * LBM_TX + px;
+                const int q1 = ls.pp ^ 1;
+                C.drho[q1][ps] = sdr / n; C.ux[q1][ps] = sx / sr; C.uy[q1][ps] = sy / sr;
+                C.chi[q1][ps] = sc / n;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ prolongation (Sec 2.2)
+// ghost children of the band cells of level l: linear LSQ reconstruction of chi and u
+// about the parent (fields at time t), rho copied; written to both time levels of l+1
+__global__ void __launch_bounds__(256) k_prolong(LevelView P, LevelView F, int p)
+{
+    __shared__ int nb3[9];
+    const int t = P.band_tiles[blockIdx.x], c = threadIdx.x;
+    const int lx = c & 31, ly = c >> 5;
+    load_nb3(P, t, nb3);
+    __syncthreads();
+    const int slot = t * LBM_TILE + c;
+    const uint32_t fl = P.flags[slot];
+    if ((fl & FL_KIND_MASK) != KIND_ACTIVE || (fl & FL_SOLID) || !(fl & FL_BAND)) return;
+    const int cb = child_base(P, t, lx, ly);
+    if (cb < 0) return;
+    Stencil S;
+    gather(nb3, P.chi[p], P.ux[p], P.uy[p], lx, ly, slot, S);
+    float gcx, gcy, gux, guy, gvx, gvy;
+    lsq_grad(S.chi, gcx, gcy); lsq_grad(S.ux, gux, guy); lsq_grad(S.uy, gvx, gvy);
+    const float dr = P.drho[p][slot];
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const int a = m & 1, b = m >> 1;
+        const float ox = 0.5f * (a - 0.5f), oy = 0.5f * (b - 0.5f);
+        const int cs = cb + b * LBM_TX + a;
+        const float vc = S.chi[0] + gcx * ox + gcy * oy;
+        const float vu = S.ux[0] + gux * ox + guy * oy;
+        const float vv = S.uy[0] + gvx * ox + gvy * oy;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            F.chi[h][cs] = vc; F.ux[h][cs] = vu; F.uy[h][cs] = vv; F.drho[h][cs] = dr;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ wall-state query
+__global__ void __launch_bounds__(128) k_wallfn(LevelView P, int p, RecView R, StepConsts k)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R.n) return;
+    float drW, uWx, uWy, chiB;
+    wall_record(P, p, R, k, r, drW, uWx, uWy, chiB);
+}
+
 // ------------------------------------------------------------------ interface sync (set_fields)
-__global__ void k_restrict(LevelView P, LevelView F, int pchi, int fchi)
+__global__ void k_restrict(LevelView P, LevelView F, int pp, int pf)
 {
     const int t = blockIdx.x, c = threadIdx.x;
-    const long long slot = (long long)t * LBM_TILE + c;
+    const int slot = t * LBM_TILE + c;
     const uint32_t fl = P.flags[slot];
     if ((fl & FL_KIND_MASK) != KIND_COVERED) return;
-    long long cb = child_base(P, t, c & 31, c >> 5);
+    const int cb = child_base(P, t, c & 31, c >> 5);
     if (cb < 0) return;
     float sdr = 0.f, sr = 0.f, sx = 0.f, sy = 0.f, sc = 0.f;
     int n = 0;
-    const long long off[4] = {0, 1, LBM_TX, LBM_TX + 1};
     for (int m = 0; m < 4; m++) {
-        long long cs = cb + off[m];
+        const int cs = cb + (m & 1) + (m >> 1) * LBM_TX;
         if (F.flags[cs] & FL_SOLID) continue;
-        float dr = F.drho[cs], r = 1.0f + dr;
-        sdr += dr; sr += r; sx += r * F.ux[cs]; sy += r * F.uy[cs]; sc += F.chi[fchi][cs];
+        const float dr = F.drho[pf][cs], r = 1.0f + dr;
+        sdr += dr; sr += r; sx += r * F.ux[pf][cs]; sy += r * F.uy[pf][cs]; sc += F.chi[pf][cs];
         n++;
     }
     if (n == 0) return;
-    P.drho[slot] = sdr / n; P.ux[slot] = sx / sr; P.uy[slot] = sy / sr;
-    P.chi[pchi][slot] = sc / n;
+    P.drho[pp][slot] = sdr / n; P.ux[pp][slot] = sx / sr; P.uy[pp][slot] = sy / sr;
+    P.chi[pp][slot] = sc / n;
 }
 
-__global__ void k_explode_prolong(LevelView P, LevelView F, int cur, int fcur, StepConsts k)
+__global__ void k_explode_prolong(LevelView P, LevelView F, int p, int pf)
 {
+    __shared__ int nb3[9];
     const int t = blockIdx.x, c = threadIdx.x;
     const int lx = c & 31, ly = c >> 5;
-    const long long slot = (long long)t * LBM_TILE + c;
+    load_nb3(P, t, nb3);
+    __syncthreads();
+    const int slot = t * LBM_TILE + c;
     const uint32_t fl = P.flags[slot];
     if ((fl & FL_KIND_MASK) != KIND_ACTIVE || (fl & FL_SOLID) || !(fl & FL_BAND)) return;
-    long long cb = child_base(P, t, lx, ly);
+    const int cb = child_base(P, t, lx, ly);
     if (cb < 0) return;
     Stencil S;
-    gather(P, P.chi[cur], t, lx, ly, slot, S);
+    gather(nb3, P.chi[p], P.ux[p], P.uy[p], lx, ly, slot, S);
     float gcx, gcy, gux, guy, gvx, gvy;
     lsq_grad(S.chi, gcx, gcy); lsq_grad(S.ux, gux, guy); lsq_grad(S.uy, gvx, gvy);
     for (int m = 0; m < 4; m++) {
         const int a = m & 1, b = m >> 1;
         const float ox = 0.5f * (a - 0.5f), oy = 0.5f * (b - 0.5f);
-        const long long cs = cb + b * LBM_TX + a;
+        const int cs = cb + b * LBM_TX + a;
         const float vc = S.chi[0] + gcx * ox + gcy * oy;
-        F.chi[0][cs] = vc; F.chi[1][cs] = vc;
-        F.ux[cs] = S.ux[0] + gux * ox + guy * oy;
-        F.uy[cs] = S.uy[0] + gvx * ox + gvy * oy;
-        F.drho[cs] = P.drho[slot];
-        for (int q = 0; q < 9; q++) F.f[fcur][q * F.ns + cs] = P.f[cur][q * P.ns + slot];
+        const float vu = S.ux[0] + gux * ox + guy * oy;
+        const float vv = S.uy[0] + gvx * ox + gvy * oy;
+        for (int h = 0; h < 2; h++) {
+            F.chi[h][cs] = vc; F.ux[h][cs] = vu; F.uy[h][cs] = vv; F.drho[h][cs] = P.drho[p][slot];
+        }
+        for (int q = 0; q < 9; q++) F.f[pf][q * F.ns + cs] = P.f[p][q * P.ns + slot];
     }
 }
 
@@ -575,19 +624,20 @@ struct Feq9 { float g[9]; };
 
 __global__ void k_init(LevelView P, Feq9 e, float U, float chi_inf)
 {
-    const long long slot = (long long)blockIdx.x * LBM_TILE + threadIdx.x;
+    const int slot = blockIdx.x * LBM_TILE + threadIdx.x;
     const uint32_t fl = P.flags[slot];
     const bool present = (fl & FL_KIND_MASK) != KIND_ABSENT;
     for (int q = 0; q < 9; q++) {
-        float v = present ? e.g[q] : 0.0f;
+        const float v = present ? e.g[q] : 0.0f;
         P.f[0][q * P.ns + slot] = v;
         P.f[1][q * P.ns + slot] = v;
     }
-    P.drho[slot] = 0.0f;
-    P.ux[slot] = present ? U : 0.0f;
-    P.uy[slot] = 0.0f;
-    P.chi[0][slot] = chi_inf;
-    P.chi[1][slot] = chi_inf;
+    for (int h = 0; h < 2; h++) {
+        P.drho[h][slot] = 0.0f;
+        P.ux[h][slot] = present ? U : 0.0f;
+        P.uy[h][slot] = 0.0f;
+        P.chi[h][slot] = chi_inf;
+    }
 }
 
 // ------------------------------------------------------------------ FP64 reductions
@@ -639,15 +689,15 @@ __global__ void __launch_bounds__(256) k_loads(LoadsView S, RecView R, float U, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_mass(LevelView P, double area, double *acc, int *status)
+__global__ void __launch_bounds__(256) k_mass(LevelView P, int p, double area, double *acc, int *status)
 {
     __shared__ double red[8];
-    const long long slot = (long long)blockIdx.x * LBM_TILE + threadIdx.x;
+    const int slot = blockIdx.x * LBM_TILE + threadIdx.x;
     const uint32_t fl = P.flags[slot];
     double v = 0;
     if ((fl & FL_KIND_MASK) == KIND_ACTIVE && !(fl & FL_SOLID)) {
-        const float dr = P.drho[slot], u = P.ux[slot], w = P.uy[slot];
-        if (!(isfinite(dr) && isfinite(u) && isfinite(w))) atomicOr(status, 1);
+        const float dr = P.drho[p][slot], u = P.ux[p][slot], w = P.uy[p][slot], x = P.chi[p][slot];
+        if (!(isfinite(dr) && isfinite(u) && isfinite(w) && isfinite(x))) atomicOr(status, 1);
         v = area * (1.0 + (double)dr);
     }
     v = warp_sum(v);
@@ -661,36 +711,38 @@ __global__ void __launch_bounds__(256) k_mass(LevelView P, double area, double *
 }
 
 // ------------------------------------------------------------------ launchers
-void launch_stream_collide(cudaStream_t st, const LevelView &P, const LevelView *F, int cur, int fcur, int fchicur,
-                           const RecView &R, const StepConsts &k, int is_level0)
+void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,
+                  const StepConsts &k, const LevelStep &ls)
 {
-    LevelView Fv = F ? *F : P;
-    k_stream_collide<<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, F != nullptr, cur, fcur, fchicur, R, k, is_level0);
+    const LevelView Fv = F ? *F : P, Cv = C ? *C : P;
+    if (ls.wall) {
+        if (F) k_level<true, true><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
+        else k_level<true, false><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
+    } else {
+        if (F) k_level<false, true><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
+        else k_level<false, false><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
+    }
 }
 
-void launch_sa(cudaStream_t st, const LevelView &P, const LevelView *F, int cur, const RecView &R,
-               const StepConsts &k, int is_level0)
+void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p)
 {
-    LevelView Fv = F ? *F : P;
-    k_sa<<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, F != nullptr, cur, R, k, is_level0);
+    if (P.n_band_tiles > 0) k_prolong<<<P.n_band_tiles, LBM_TILE, 0, st>>>(P, F, p);
 }
 
-void launch_wallfn(cudaStream_t st, const LevelView &P, const RecView &R, const StepConsts &k)
+void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k)
 {
     if (R.n <= 0) return;
-    const long long threads = (long long)R.n * 16;
-    k_wallfn<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, R, k);
+    k_wallfn<<<(R.n + 127) / 128, 128, 0, st>>>(P, p, R, k);
 }
 
-void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pchi, int fchi)
+void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pp, int pf)
 {
-    k_restrict<<<P.ntiles, LBM_TILE, 0, st>>>(P, F, pchi, fchi);
+    k_restrict<<<P.ntiles, LBM_TILE, 0, st>>>(P, F, pp, pf);
 }
 
-void launch_explode_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int cur, int fcur,
-                            const StepConsts &k)
+void launch_explode_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pf)
 {
-    k_explode_prolong<<<P.ntiles, LBM_TILE, 0, st>>>(P, F, cur, fcur, k);
+    k_explode_prolong<<<P.ntiles, LBM_TILE, 0, st>>>(P, F, p, pf);
 }
 
 void launch_init_feq(cudaStream_t st, const LevelView &P, const float *feq9, float U, float chi_inf)
@@ -706,9 +758,9 @@ void launch_loads(cudaStream_t st, const LoadsView &S, const RecView &R, float U
     k_loads<<<(S.nseg + 255) / 256, 256, 0, st>>>(S, R, U, acc4);
 }
 
-void launch_mass(cudaStream_t st, const LevelView &P, double area, double *acc, int *status)
+void launch_mass(cudaStream_t st, const LevelView &P, int p, double area, double *acc, int *status)
 {
-    k_mass<<<P.ntiles, LBM_TILE, 0, st>>>(P, area, acc, status);
+    k_mass<<<P.ntiles, LBM_TILE, 0, st>>>(P, p, area, acc, status);
 }
 
 }  // namespace lbmdev

@@ -132,8 +132,8 @@ static T *upload(lbm_solver *s, const std::vector<T> &h, bool &ok)
 
 // ---------------------------------------------------------------- scheduler
 // Kernel classes for lbm_time_kernels.
-enum { KC_SC_FINEST = 0, KC_SC_COARSE = 1, KC_SA = 2, KC_WALLFN = 3, KC_N = 4 };
-static const char *KC_NAME[KC_N] = {"stream_collide_finest", "stream_collide_coarse", "sa_neg", "wall_function"};
+enum { KC_LEVEL_FINEST = 0, KC_LEVEL_COARSE = 1, KC_PROLONG = 2, KC_N = 3 };
+static const char *KC_NAME[KC_N] = {"level_step_finest", "level_step_coarse", "prolong"};
 
 static void mark_begin(lbm_solver *s)
 {
@@ -157,31 +157,36 @@ static void mark_end(lbm_solver *s, int cls, long long cells)
     s->ev_used += 2;
 }
 
-static void advance(lbm_solver *s, cudaStream_t st, int l, long long &nk)
+// One level-l step (Sec 2.1 recursive sub-cycling): the ghost fields of level l+1 are
+// reconstructed from level l at time t, level l+1 takes two sub-steps (the second one
+// restricts its new fields into the covered cells of level l), then one fused launch
+// advances level l itself (wall function on the finest level, SA-neg, stream with
+// coalescence and cut links, collide, explode).
+static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long long &nk)
 {
     const int L = s->L;
     LevelView &P = s->lv[l].v;
     const LevelView *F = (l < L - 1) ? &s->lv[l + 1].v : nullptr;
-    if (l == L - 1 && s->rec.n > 0) {
+    const LevelView *C = (l > 0) ? &s->lv[l - 1].v : nullptr;
+    if (F) {
         mark_begin(s);
-        lbmdev::launch_wallfn(st, P, s->rec, s->k);
-        mark_end(s, KC_WALLFN, (long long)s->rec.n * 16);
-        nk++;
+        lbmdev::launch_prolong(st, P, *F, s->parity[l]);
+        mark_end(s, KC_PROLONG, (long long)P.n_band_tiles * LBM_TILE);
+        nk += P.n_band_tiles > 0;
+        advance(s, st, l + 1, 0, nk);
+        advance(s, st, l + 1, 1, nk);
     }
-    if (s->cfg.turbulence) {
-        mark_begin(s);
-        lbmdev::launch_sa(st, P, F, s->parity[l], s->rec, s->k, l == 0);
-        mark_end(s, KC_SA, P.ns);
-        nk++;
-    }
-    if (l < L - 1) {
-        advance(s, st, l + 1, nk);
-        advance(s, st, l + 1, nk);
-    }
+    lbmdev::LevelStep ls;
+    ls.p = s->parity[l];
+    ls.pf = F ? s->parity[l + 1] : 0;
+    ls.has_child = F != nullptr;
+    ls.is_level0 = l == 0;
+    ls.wall = (l == L - 1) && s->rec.n > 0;
+    ls.restrict_up = restrict_up && C != nullptr;
+    ls.pp = C ? s->parity[l - 1] : 0;
     mark_begin(s);
-    lbmdev::launch_stream_collide(st, P, F, s->parity[l], F ? s->parity[l + 1] : 0, F ? s->parity[l + 1] : 0, s->rec,
-                                  s->k, l == 0);
-    mark_end(s, l == L - 1 ? KC_SC_FINEST : KC_SC_COARSE, P.ns);
+    lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls);
+    mark_end(s, l == L - 1 ? KC_LEVEL_FINEST : KC_LEVEL_COARSE, P.ns);
     nk++;
     s->parity[l] ^= 1;
 }
@@ -193,7 +198,7 @@ static lbm_status capture_graphs(lbm_solver *s)
         cudaGraph_t gr;
         long long nk = 0;
         CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-        advance(s, s->cap_stream, 0, nk);
+        advance(s, s->cap_stream, 0, 0, nk);
         CK(cudaStreamEndCapture(s->cap_stream, &gr));
         CK(cudaGraphInstantiate(&s->graph[b], gr, 0));
         cudaGraphDestroy(gr);
@@ -218,7 +223,7 @@ static lbm_status enqueue_mass(lbm_solver *s)
     CK(cudaMemsetAsync(s->d_acc + 4, 0, sizeof(double), s->stream));
     for (int l = 0; l < s->L; l++) {
         double area = (double)(1LL << (s->L - 1 - l));
-        lbmdev::launch_mass(s->stream, s->lv[l].v, area * area, s->d_acc + 4, s->d_status);
+        lbmdev::launch_mass(s->stream, s->lv[l].v, s->parity[l], area * area, s->d_acc + 4, s->d_status);
     }
     return LBM_OK;
 }
@@ -294,6 +299,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         lbmgrid::Level &G = s->g.lv[l];
         HostLevelDev &H = s->lv[l];
         const long long ns = (long long)G.ntiles * LBM_TILE;
+        if (9 * ns >= (1LL << 31)) { free_all(s); return fail(s, LBM_ERR_INVALID_ARG, "level too large for 32-bit slot indices"); }
         H.flags.assign(ns, 0);
         std::vector<float> dist(ns, 0.f);
         std::vector<int> rec(l == L - 1 ? ns : 1, -1);
@@ -323,23 +329,26 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
             }
         LevelView &v = H.v;
         v.ntiles = G.ntiles;
-        v.ns = ns;
+        v.ns = (int)ns;
+        v.n_wall_tiles = G.n_wall_tiles;
         v.tile_x = upload(s, G.tile_x, ok);
         v.tile_y = upload(s, G.tile_y, ok);
         v.nbr = upload(s, G.nbr, ok);
         v.child = upload(s, G.child, ok);
+        v.parent = upload(s, G.parent, ok);
+        v.band_tiles = upload(s, G.band_tiles, ok);
+        v.n_band_tiles = (int)G.band_tiles.size();
         v.flags = upload(s, H.flags, ok);
         v.dist = upload(s, dist, ok);
         v.rec = (l == L - 1) ? upload(s, rec, ok) : nullptr;
         for (int b = 0; b < 2; b++) {
             v.f[b] = (float *)dalloc(s, 9 * ns * sizeof(float));
             v.chi[b] = (float *)dalloc(s, ns * sizeof(float));
-            ok = ok && v.f[b] && v.chi[b];
+            v.drho[b] = (float *)dalloc(s, ns * sizeof(float));
+            v.ux[b] = (float *)dalloc(s, ns * sizeof(float));
+            v.uy[b] = (float *)dalloc(s, ns * sizeof(float));
+            ok = ok && v.f[b] && v.chi[b] && v.drho[b] && v.ux[b] && v.uy[b];
         }
-        v.drho = (float *)dalloc(s, ns * sizeof(float));
-        v.ux = (float *)dalloc(s, ns * sizeof(float));
-        v.uy = (float *)dalloc(s, ns * sizeof(float));
-        ok = ok && v.drho && v.ux && v.uy;
         v.nu = (float)(s->U * (c.chord / c.h0) * (double)(1LL << l) / c.Re);
         if (!ok) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
     }
@@ -486,23 +495,25 @@ static lbm_status download_level(lbm_solver *s, int l, std::vector<float> &dr, s
                                  std::vector<float> &uy, std::vector<float> &chi)
 {
     const LevelView &v = s->lv[l].v;
+    const int p = s->parity[l];
+    const size_t nb = (size_t)v.ns * sizeof(float);
     dr.resize(v.ns); ux.resize(v.ns); uy.resize(v.ns); chi.resize(v.ns);
-    CK(cudaMemcpyAsync(dr.data(), v.drho, v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(ux.data(), v.ux, v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(uy.data(), v.uy, v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(chi.data(), v.chi[s->parity[l]], v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(dr.data(), v.drho[p], nb, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(ux.data(), v.ux[p], nb, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(uy.data(), v.uy[p], nb, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(chi.data(), v.chi[p], nb, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return LBM_OK;
 }
 
-static unsigned char mask_of(uint32_t f)
+// mask code of a cell from the host copy of the grid (solid-only tiles have no slots)
+static unsigned char mask_of(const lbmgrid::Level &G, long b)
 {
-    uint32_t kd = f & FL_KIND_MASK;
-    if (kd == KIND_ABSENT) return 0;
-    if (f & FL_SOLID) return 5;
-    if (kd == KIND_COVERED) return 3;
-    if (kd == KIND_GHOST) return 4;
-    return (f & FL_BNODE) ? 2 : 1;
+    if (b < 0 || G.kind[b] == KIND_ABSENT) return 0;
+    if (G.solid[b]) return 5;
+    if (G.kind[b] == KIND_COVERED) return 3;
+    if (G.kind[b] == KIND_GHOST) return 4;
+    return G.bnode[b] ? 2 : 1;
 }
 
 lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, double *uy, double *chi,
@@ -516,14 +527,13 @@ lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, dou
     st = download_level(s, level, dr, u, v, c2);
     if (st != LBM_OK) return st;
     const lbmgrid::Level &G = s->g.lv[level];
-    const std::vector<uint32_t> &fl = s->lv[level].flags;
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             long sl = G.slot(i0 + i, j0 + j);
             long long o = (long long)j * nx + i;
-            unsigned char m = sl >= 0 ? mask_of(fl[sl]) : 0;
+            unsigned char m = mask_of(G, G.idx(i0 + i, j0 + j));
             if (mask) mask[o] = m;
-            bool has = m >= 1 && m <= 4;
+            bool has = m >= 1 && m <= 4 && sl >= 0;
             if (rho) rho[o] = has ? 1.0 + (double)dr[sl] : NAN;
             if (ux) ux[o] = has ? (double)u[sl] : NAN;
             if (uy) uy[o] = has ? (double)v[sl] : NAN;
@@ -580,9 +590,9 @@ lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const dou
             feq_shifted(r, a, b, g9);
             for (int q = 0; q < 9; q++) f[(size_t)q * v.ns + sl] = g9[q];
         }
-    CK(cudaMemcpyAsync(v.drho, dr.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(v.ux, u.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(v.uy, w.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(v.drho[p], dr.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(v.ux[p], u.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(v.uy[p], w.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.chi[p], c2.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.chi[p ^ 1], c3.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.f[p], f.data(), 9 * v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
@@ -590,7 +600,7 @@ lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const dou
     for (int l = s->L - 2; l >= 0; l--)
         lbmdev::launch_restrict(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], s->parity[l + 1]);
     for (int l = 0; l < s->L - 1; l++)
-        lbmdev::launch_explode_prolong(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], s->parity[l + 1], s->k);
+        lbmdev::launch_explode_prolong(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], s->parity[l + 1]);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
     return LBM_OK;
@@ -602,7 +612,7 @@ lbm_status lbm_get_loads(lbm_solver *s, lbm_loads *out, double *cp_seg, double *
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     const int nseg = s->segs.nseg;
     if (n_seg) *n_seg = nseg;
-    lbmdev::launch_wallfn(s->stream, s->lv[s->L - 1].v, s->rec, s->k);
+    lbmdev::launch_wallfn(s->stream, s->lv[s->L - 1].v, s->parity[s->L - 1], s->rec, s->k);
     CK(cudaMemsetAsync(s->d_acc, 0, 4 * sizeof(double), s->stream));
     lbmdev::launch_loads(s->stream, s->segs, s->rec, (float)s->U, s->d_acc);
     lbm_status st = enqueue_mass(s);
@@ -673,7 +683,7 @@ lbm_status lbm_get_wall_state(lbm_solver *s, double *st8, int cap, int *n)
     if (!st8) return LBM_OK;
     if (nr > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
     if (nr == 0) return LBM_OK;
-    lbmdev::launch_wallfn(s->stream, s->lv[s->L - 1].v, s->rec, s->k);
+    lbmdev::launch_wallfn(s->stream, s->lv[s->L - 1].v, s->parity[s->L - 1], s->rec, s->k);
     std::vector<float> a[8];
     float *src[8] = {s->rec.drhoW, s->rec.uWx, s->rec.uWy, s->rec.utau, s->rec.chiB, s->rec.tx, s->rec.ty, s->rec.ut};
     for (int m = 0; m < 8; m++) {
@@ -712,8 +722,9 @@ lbm_status lbm_get_info(lbm_solver *s, lbm_info *out)
     out->cut_links = s->g.n_cut;
     out->surface_segments = s->segs.nseg;
     out->kernels_per_step = s->kernels_per_step;
-    // 9 populations read + 9 written (FP32), nu_tilde read, rho and u written
-    out->bytes_per_node_update = 72.0 + (s->cfg.turbulence ? 4.0 : 0.0) + 12.0;
+    // fused level step: 9 populations read + 9 written (FP32), rho and u written; with
+    // SA-neg also nu_tilde read and written, u read for the stencil, wall distance read
+    out->bytes_per_node_update = 72.0 + 12.0 + (s->cfg.turbulence ? 8.0 + 8.0 + 4.0 : 0.0);
     out->device_bytes = s->device_bytes;
     return LBM_OK;
 }
@@ -731,7 +742,7 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n, lbm_kernel_times *out)
         s->ev_marks.clear();
         s->ev_cells.clear();
         long long nk = 0;
-        advance(s, s->stream, 0, nk);
+        advance(s, s->stream, 0, 0, nk);
         s->timing = false;
         s->step++;
         CK(cudaGetLastError());
