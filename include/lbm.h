@@ -166,6 +166,32 @@ lbm_status lbm_get_info(lbm_solver *s, lbm_info *out);
  * the solver stream; accumulate device time per kernel class.  Same results as lbm_step. */
 lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times *out);
 
+/* Largest n_cells that lbm_level_mass_noalloc accepts (its fixed scratch holds 4096
+ * per-block partial sums of at most 16384 cells each). */
+#define LBM_NOALLOC_MAX_CELLS 67108864LL
+
+/* FP64 mass and finiteness check of one level's fields, allocating nothing.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (code running inside another framework's stream capture, real-time loops
+ * with a fixed memory plan, allocators owned by someone else).  It computes the same
+ * quantities as the mass of lbm_get_loads and the non-finite check of lbm_step:
+ *   *mass_out = sum over cells with (flags & 3) == 1 (active) and flags bit 2 clear
+ *               (fluid) of area * (1 + drho), in FP64;
+ *   *nonfinite_out = 1 if any such cell has a non-finite drho, ux, uy or nu_tilde_ratio.
+ * All array arguments and both outputs are DEVICE pointers of n_cells elements (outputs:
+ * one element), owned by the caller and on the current device; stream is a
+ * cudaStream_t (NULL = legacy default stream).  The call only enqueues work: read the
+ * outputs after synchronising the stream.
+ * Scratch: a fixed 48 KB array in device memory (file scope), held by every GPU that
+ * loads the library until the process exits.  The first call on a device looks up that
+ * array's device address (make it before any stream capture).  Every call on a device
+ * shares the array: calls that overlap on the GPU (other streams, other threads) race.
+ * Errors: LBM_ERR_INVALID_ARG for n_cells < 0, n_cells > LBM_NOALLOC_MAX_CELLS or a NULL
+ * pointer (nothing is launched); LBM_ERR_CUDA if the device or the launch fails. */
+lbm_status lbm_level_mass_noalloc(const unsigned int *flags, const float *drho, const float *ux, const float *uy,
+                                  const float *nu_tilde_ratio, long long n_cells, double area, double *mass_out,
+                                  int *nonfinite_out, void *stream);
+
 /* Per-handle message of the last error. */
 const char *lbm_last_error(const lbm_solver *s);
 

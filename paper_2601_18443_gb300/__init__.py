@@ -91,6 +91,7 @@ def library():
         "lbm_get_wall_distance": ([vp, C.c_int, dp, C.c_int], C.c_int),
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
+        "lbm_level_mass_noalloc": ([vp, vp, vp, vp, vp, C.c_longlong, C.c_double, vp, vp, vp], C.c_int),
         "lbm_last_error": ([vp], C.c_char_p),
         "lbm_destroy": ([vp], None),
     }
@@ -258,3 +259,10 @@ class Solver:
         self._check(self._lib.lbm_time_kernels(self._h, int(n), C.byref(out)))
         return {out.name[i].value.decode(): dict(ms=out.total_ms[i], launches=out.launches[i], cells=out.cells[i])
                 for i in range(out.n_classes)}
+
+
+def level_mass_noalloc(flags, drho, ux, uy, chi, n_cells, area, mass_out, nonfinite_out, stream=0):
+    """lbm_level_mass_noalloc on caller-owned device buffers given as raw device addresses
+    (for example ``tensor.data_ptr()``); returns the status code.  Only enqueues work."""
+    return library().lbm_level_mass_noalloc(flags, drho, ux, uy, chi, int(n_cells), float(area), mass_out,
+                                            nonfinite_out, stream)

@@ -38,7 +38,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     tag = f".{os.getpid()}"
     objs = {name: os.path.join(OUT_DIR, name.rsplit(".", 1)[0] + tag + ".o")
-            for name in ("grid.cpp", "kernels.cu", "lbm_capi.cu")}
+            for name in ("grid.cpp", "kernels.cu", "lbm_capi.cu", "noalloc.cu")}
     cuflags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp",
                "-Xptxas", "-v" if verbose else "-O3"] + ARCH
     cmds = [
@@ -46,6 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
          os.path.join(CSRC, "grid.cpp"), "-o", objs["grid.cpp"]],
         [nvcc] + cuflags + ["-c", os.path.join(CSRC, "kernels.cu"), "-o", objs["kernels.cu"]],
         [nvcc] + cuflags + ["-c", os.path.join(CSRC, "lbm_capi.cu"), "-o", objs["lbm_capi.cu"]],
+        [nvcc] + cuflags + ["-c", os.path.join(CSRC, "noalloc.cu"), "-o", objs["noalloc.cu"]],
     ]
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     logs = []
