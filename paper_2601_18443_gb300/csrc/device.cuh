@@ -41,6 +41,7 @@ struct RecView {
     const int *loop;
     const float *slip;            // prescribed slip per loop (wall model 2), 2 per loop
     float *drhoW, *uWx, *uWy, *utau, *chiB, *tx, *ty, *ut;
+    float *utau_start;            // Newton start of the next step (written by the step only)
 };
 
 struct StepConsts {
@@ -51,7 +52,12 @@ struct StepConsts {
     float U;            // inlet lattice velocity
     float chi_inf;
     float d_wr, d_wv;
+    int resident_blocks; // persistent grid of the level kernel: SMs x blocks per SM
 };
+
+// device status word bits (lbm_step maps them to lbm_status codes)
+#define LBM_STATUS_NONFINITE 1
+#define LBM_STATUS_TIMEOUT 2
 
 // What one launch of the fused level kernel does besides the level's own update.
 struct LevelStep {
@@ -62,12 +68,14 @@ struct LevelStep {
     int wall;           // this level holds the wall records (finest level)
     int restrict_up;    // write the restriction of this level's new fields into level l-1
     int pp;             // time level of level l-1 (restriction writes [pp ^ 1])
+    int *status;        // device status word (LBM_STATUS_* bits)
 };
 
 // launchers (kernels.cu); all enqueue on the given stream
 void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,
                   const StepConsts &k, const LevelStep &ls);
 void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p);
+int level_blocks_per_sm();
 void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k);
 void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pp, int pf);
 void launch_explode_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pf);

@@ -321,8 +321,11 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
     for (int l = 1; l < L; l++) {
         Level &P = g.lv[l - 1];
         const long long hh = P.scale * FIXU / 2;
-        // refinement: candidate cells around each segment, exact distance test
-        for (size_t k = 0; k < g.sa.size(); k++) {
+        // refinement: candidate cells around each segment, exact distance test (segments
+        // in parallel; a cell found near any segment is marked, marks only go 0 -> 1)
+        std::vector<uint8_t> near(P.kind.size(), 0);
+#pragma omp parallel for schedule(dynamic, 64)
+        for (long k = 0; k < (long)g.sa.size(); k++) {
             IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
             long long il = cdiv((i128)std::min(a.x, b.x) - R[l] - hh, 2 * (i128)hh);
             long long ih = fdiv((i128)std::max(a.x, b.x) + R[l] - hh, 2 * (i128)hh);
@@ -334,9 +337,16 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
             for (long long j = jl; j <= jh; j++)
                 for (long long i = il; i <= ih; i++) {
                     long c = P.idx(i, j);
-                    if (P.kind[c] == KIND_ACTIVE && within_r(a, b, centre(P, i, j), R[l])) P.kind[c] = KIND_COVERED;
+                    uint8_t seen;
+#pragma omp atomic read
+                    seen = near[c];
+                    if (seen || P.kind[c] != KIND_ACTIVE || !within_r(a, b, centre(P, i, j), R[l])) continue;
+#pragma omp atomic write
+                    near[c] = 1;
                 }
         }
+        for (size_t c = 0; c < near.size(); c++)
+            if (near[c]) P.kind[c] = KIND_COVERED;
         // nesting checks, band, child box
         long long ci0 = (1LL << 40), cj0 = (1LL << 40), ci1 = -(1LL << 40), cj1 = -(1LL << 40);
         for (int r = 0; r < P.bny; r++)

@@ -54,6 +54,32 @@ __device__ __forceinline__ int nb_slot(const int *nb3, int lx, int ly, int dx, i
     return tt < 0 ? -1 : tt * LBM_TILE + (ny & (LBM_TY - 1)) * LBM_TX + (nx & (LBM_TX - 1));
 }
 
+// The slots of the eight D2Q9 neighbours at offsets +c_q (q = 1..8) and the own slot
+// (q = 0); a neighbour in an absent tile maps to the own slot and clears bit q of the
+// returned presence mask.  The SA stencil reads offset +c_q, the pull of direction q
+// reads offset -c_q = +c_opp(q).
+__device__ __forceinline__ unsigned neighbours(const int *nb3, int lx, int ly, int slot, int nbs[9])
+{
+    const int xm = lx - 1, xp = lx + 1, ym = ly - 1, yp = ly + 1;
+    const int cm = xm < 0 ? 0 : 1, cp = xp >= LBM_TX ? 2 : 1;              // tile column of x -/+ 1
+    const int rm = ym < 0 ? 0 : 3, rp = yp >= LBM_TY ? 6 : 3;              // tile row (x 3) of y -/+ 1
+    const int colm = xm & (LBM_TX - 1), colp = xp & (LBM_TX - 1);
+    const int rowm = (ym & (LBM_TY - 1)) * LBM_TX, rowp = (yp & (LBM_TY - 1)) * LBM_TX, row0 = ly * LBM_TX;
+    const int tl[9] = {0, nb3[3 + cp], nb3[3 + cm], nb3[rp + 1], nb3[rm + 1], nb3[rp + cp], nb3[rm + cm],
+                       nb3[rm + cp], nb3[rp + cm]};
+    const int off[9] = {0, row0 + colp, row0 + colm, rowp + lx, rowm + lx, rowp + colp, rowm + colm, rowm + colp,
+                        rowp + colm};
+    unsigned present = 1u;
+    nbs[0] = slot;
+#pragma unroll
+    for (int q = 1; q < 9; q++) {
+        const bool ok = tl[q] >= 0;
+        nbs[q] = ok ? tl[q] * LBM_TILE + off[q] : slot;
+        present |= ok ? (1u << q) : 0u;
+    }
+    return present;
+}
+
 // level 0 covers its whole box with tiles in row-major order
 __device__ __forceinline__ int slot0(const StepConsts &k, int i, int j)
 {
@@ -84,9 +110,12 @@ __device__ __forceinline__ int child_base(const LevelView &P, int t, int lx, int
 
 // ------------------------------------------------------------------ collision (eqs 5-10)
 // Input: post-stream shifted populations g (f - w).  Output: post-collision shifted
-// populations.  drho, ux, uy: the macroscopic fields of eq 3.  delta = 2 - omega_nu
-// (omega_b = 1: the trace relaxes fully, Sec 2.1).
-__device__ __forceinline__ void collide_cm(const float g[9], float drho, float ux, float uy, float delta, float o[9])
+// populations.  drho, jx, jy: the conserved moments of eq 3 summed from g; ux, uy the
+// velocity j / rho.  The conserved raw moments are taken from the sums themselves, so
+// mass and momentum are conserved to the rounding of those sums whatever the rounding
+// of u.  delta = 2 - omega_nu (omega_b = 1: the trace relaxes fully, Sec 2.1).
+__device__ __forceinline__ void collide_cm(const float g[9], float drho, float jx, float jy, float ux, float uy,
+                                           float delta, float o[9])
 {
     const float rho = 1.0f + drho;
     const float m20 = g[1] + g[2] + g[5] + g[6] + g[7] + g[8];   // sum cx^2 g  (= m20 - 1/3)
@@ -101,7 +130,7 @@ __device__ __forceinline__ void collide_cm(const float g[9], float drho, float u
     const float k02 = rho * (1.0f / 3.0f) - 0.5f * Ds;
     // raw post-collision moments minus their rest-state values (binomial shift back)
     const float M00 = drho;
-    const float M10 = rho * ux, M01 = rho * uy;
+    const float M10 = jx, M01 = jy;
     const float M20 = drho * (1.0f / 3.0f) + 0.5f * Ds + rho * uxx;
     const float M02 = drho * (1.0f / 3.0f) - 0.5f * Ds + rho * uyy;
     const float M11 = Ks + rho * uxy;
@@ -126,12 +155,16 @@ __device__ __forceinline__ float sa_fv1(float chi)
     return c3 / (c3 + SA_CV1_3);
 }
 
-// 2 - omega for the effective viscosity nu + nu_t (eq 9 with the RANS substitution)
+// 2 - omega for the effective viscosity nu + nu_t (eq 9 with the RANS substitution);
+// the divisions use the fast reciprocal path (about 2 ulp)
 __device__ __forceinline__ float delta_of(float nu, float chi, int turbulence)
 {
     float nue = nu;
-    if (turbulence) nue += fmaxf(chi, 0.0f) * nu * sa_fv1(chi);
-    return 12.0f * nue / (1.0f + 6.0f * nue);
+    if (turbulence) {
+        const float c3 = chi * chi * chi;
+        nue += fmaxf(chi, 0.0f) * nu * __fdividef(c3, c3 + SA_CV1_3);
+    }
+    return __fdividef(12.0f * nue, 1.0f + 6.0f * nue);
 }
 
 // ------------------------------------------------------------------ SA-neg (Sec 2.2)
@@ -178,8 +211,8 @@ __device__ __forceinline__ void lsq_grad(const float *v, float &gx, float &gy)
 
 __device__ __forceinline__ float sa_diff_coef(float chi)
 {   // (nu + nu_t~ f_n) / nu
-    float fn = 1.0f;
-    if (chi < 0.0f) { float c3 = chi * chi * chi; fn = (SA_CN1 + c3) / (SA_CN1 - c3); }
+    const float c3 = chi * chi * chi;
+    const float fn = chi < 0.0f ? __fdividef(SA_CN1 + c3, SA_CN1 - c3) : 1.0f;
     return 1.0f + chi * fn;
 }
 
@@ -202,24 +235,26 @@ __device__ float sa_update(const Stencil &S, float d, float nu)
     const float div = De * (x[1] - x[0]) - Dw * (x[0] - x[2]) + Dn * (x[3] - x[0]) - Ds * (x[0] - x[4]);
     const float diff = nu * (div + SA_CB2 * (gx * gx + gy * gy)) * (1.0f / SA_SIGMA);
     const float chi = x[0];
-    const float kd2 = SA_KAPPA * SA_KAPPA * d * d;
+    const float id2 = __fdividef(1.0f, d * d);                    // 1 / d^2
+    const float ikd2 = id2 * (1.0f / (SA_KAPPA * SA_KAPPA));      // 1 / (kappa d)^2
     float src;
     if (chi >= 0.0f) {
-        const float fv1 = sa_fv1(chi);
-        const float fv2 = 1.0f - chi / (1.0f + chi * fv1);
-        const float sbar = nu * chi * fv2 / kd2;
+        const float c3 = chi * chi * chi;
+        const float fv1 = __fdividef(c3, c3 + SA_CV1_3);
+        const float fv2 = 1.0f - __fdividef(chi, 1.0f + chi * fv1);
+        const float sbar = nu * chi * fv2 * ikd2;
         float st;
         if (sbar >= -SA_CV2 * vort) st = vort + sbar;
-        else st = vort + vort * (SA_CV2 * SA_CV2 * vort + SA_CV3 * sbar) / ((SA_CV3 - 2.0f * SA_CV2) * vort - sbar);
+        else st = vort + __fdividef(vort * (SA_CV2 * SA_CV2 * vort + SA_CV3 * sbar), (SA_CV3 - 2.0f * SA_CV2) * vort - sbar);
         float r = SA_RLIM;
-        if (st > 0.0f) r = fminf(nu * chi / (st * kd2), SA_RLIM);
+        if (st > 0.0f) r = fminf(__fdividef(nu * chi * ikd2, st), SA_RLIM);
         const float r2 = r * r, r6 = r2 * r2 * r2;
         const float gg = r + SA_CW2 * (r6 - r);
         const float g2 = gg * gg, g6 = g2 * g2 * g2;
-        const float fw = gg * powf((1.0f + SA_CW3_6) / (g6 + SA_CW3_6), 1.0f / 6.0f);
-        src = SA_CB1 * st * chi - SA_CW1 * fw * nu * chi * chi / (d * d);
+        const float fw = gg * __powf(__fdividef(1.0f + SA_CW3_6, g6 + SA_CW3_6), 1.0f / 6.0f);
+        src = SA_CB1 * st * chi - SA_CW1 * fw * nu * chi * chi * id2;
     } else {
-        src = SA_CB1 * (1.0f - SA_CT3) * vort * chi + SA_CW1 * nu * chi * chi / (d * d);
+        src = SA_CB1 * (1.0f - SA_CT3) * vort * chi + SA_CW1 * nu * chi * chi * id2;
     }
     return chi + conv + src + diff;
 }
@@ -277,16 +312,20 @@ __device__ float wf_utau(float ut, float y, float nu, float guess)
 // Wall state of one boundary node from the macroscopic fields at time level p:
 // steps 1-5 of Sec 2.3 (IDW density and LSQ velocity at R, tangential part, u_tau from
 // eq 22, u_V, slip velocity of eq 28 along t) and the SA Dirichlet value (Sec 2.2).
-// Writes the record's state arrays; returns rho_W - 1, u_W and chi_B.
-__device__ void wall_record(const LevelView &P, int p, const RecView &R, const StepConsts &k, int r, float &drW,
-                            float &uWx, float &uWy, float &chiB)
+// Writes the record's state arrays; returns rho_W - 1, u_W and chi_B.  The Newton
+// iteration starts from the u_tau of the previous step; only the step (keep_start)
+// stores its result as the next start, so that queries leave the trajectory unchanged.
+__device__ void wall_record(const LevelView &P, int p, const RecView &R, const StepConsts &k, int r, bool keep_start,
+                            float &drW, float &uWx, float &uWy, float &chiB)
 {
     const float *dr = P.drho[p], *ux = P.ux[p], *uy = P.uy[p];
     const int ns = R.ns[r];
     float sw = 0.f, swr = 0.f, swu = 0.f, swv = 0.f;
     float A0 = 0.f, A1 = 0.f, A2 = 0.f, A4 = 0.f, A5 = 0.f, A8 = 0.f;
     float bu0 = 0.f, bu1 = 0.f, bu2 = 0.f, bv0 = 0.f, bv1 = 0.f, bv2 = 0.f;
-    for (int m = 0; m < ns; m++) {
+#pragma unroll
+    for (int m = 0; m < 16; m++) {
+        if (m >= ns) break;
         const int s = R.st_slot[r * 16 + m];
         const float dx = R.st_dx[r * 16 + m], dy = R.st_dy[r * 16 + m];
         const float d = dr[s], u = ux[s], v = uy[s];
@@ -315,7 +354,8 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
     uWx = 0.f; uWy = 0.f; chiB = 0.f;
     if (k.wall_model == 0) {
         const float nu = P.nu;
-        utau = wf_utau(ut, k.d_wr, nu, R.utau[r]);                          // step 3
+        utau = wf_utau(ut, k.d_wr, nu, R.utau_start[r]);                    // step 3
+        if (keep_start) R.utau_start[r] = utau;
         const float ypv = utau * k.d_wv / nu;
         const float uV = utau * wf_uplus(ypv);                              // step 4
         const float uW = uV - utau * utau * k.d_wv / (nu * (1.0f + SA_KAPPA * ypv));   // eq 28
@@ -367,12 +407,14 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
     } else if (kind == KIND_ACTIVE && fluid) {
         const bool edge = ls.is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
         const bool bnode = WALL && (fl & FL_BNODE);
+        int nbs[9];
+        neighbours(nb3, lx, ly, slot, nbs);
         // ---- wall function of the boundary node (Sec 2.3), fields at time t
         float drW = 0.f, uWx = 0.f, uWy = 0.f, chiB = 0.f;
         int r = -1;
         if (bnode) {
             r = P.rec[slot];
-            wall_record(P, p, R, k, r, drW, uWx, uWy, chiB);
+            wall_record(P, p, R, k, r, true, drW, uWx, uWy, chiB);
         }
         // ---- SA-neg update of chi (Sec 2.2), fields at time t
         float chin;
@@ -391,7 +433,11 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
                 }
             } else {
                 Stencil S;
-                gather(nb3, P.chi[p], P.ux[p], P.uy[p], lx, ly, slot, S);
+                const float *xc = P.chi[p], *xu = P.ux[p], *xv = P.uy[p];
+#pragma unroll
+                for (int q = 0; q < 9; q++) {
+                    S.chi[q] = __ldg(xc + nbs[q]); S.ux[q] = __ldg(xu + nbs[q]); S.uy[q] = __ldg(xv + nbs[q]);
+                }
                 chin = sa_update(S, __ldg(P.dist + slot), P.nu);
             }
             P.chi[p ^ 1][slot] = chin;
@@ -401,7 +447,12 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
         // ---- pull streaming (eq 1) with coalescence, cut links and box edges
         float g[9];
         g[0] = __ldg(fc + slot);
-        if (!edge) {
+        const uint32_t special = fl & (0xFFu << FL_COAL_SHIFT | 0xFFu << FL_CUT_SHIFT);
+        if (!edge && !special) {
+            // plain cell: every direction is pulled from its upstream neighbour
+#pragma unroll
+            for (int q = 1; q < 9; q++) g[q] = __ldg(fc + q * ns + nbs[oppq(q)]);
+        } else if (!edge) {
             int cb = -1;
             if (CHILD && (fl & FL_BAND)) cb = child_base(P, t, lx, ly);
 #pragma unroll
@@ -416,9 +467,9 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
                     const int qo = oppq(q);
                     const float qf = R.q[r * 9 + q];
                     const float mom = 6.0f * wq(q) * (1.0f + drW) * (cxq(q) * uWx + cyq(q) * uWy);
-                    const int sf = nb_slot(nb3, lx, ly, cxq(q), cyq(q));
+                    const int sf = nbs[q];
                     bool ok = false;
-                    if (sf >= 0) {
+                    if (sf != slot) {
                         const uint32_t ff = __ldg(P.flags + sf);
                         ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
                     }
@@ -429,8 +480,7 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
                     else
                         g[q] = __ldg(fc + qo * ns + slot) + mom;            // half-way form, eq 24
                 } else {
-                    const int s = nb_slot(nb3, lx, ly, -cxq(q), -cyq(q));
-                    g[q] = __ldg(fc + q * ns + (s >= 0 ? s : slot));
+                    g[q] = __ldg(fc + q * ns + nbs[oppq(q)]);
                 }
             }
         } else {
@@ -469,12 +519,12 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
         }
         // ---- macroscopic fields (eq 3) and central-moment collision (eqs 5-11)
         const float drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
-        const float rho = 1.0f + drho;
-        const float ux = (g[1] - g[2] + g[5] - g[6] + g[7] - g[8]) / rho;
-        const float uy = (g[3] - g[4] + g[5] - g[6] - g[7] + g[8]) / rho;
+        const float jx = g[1] - g[2] + g[5] - g[6] + g[7] - g[8];
+        const float jy = g[3] - g[4] + g[5] - g[6] - g[7] + g[8];
+        const float ux = jx / (1.0f + drho), uy = jy / (1.0f + drho);
         P.drho[p ^ 1][slot] = drho; P.ux[p ^ 1][slot] = ux; P.uy[p ^ 1][slot] = uy;
         float o[9];
-        collide_cm(g, drho, ux, uy, delta_of(P.nu, chin, k.turbulence), o);
+        collide_cm(g, drho, jx, jy, ux, uy, delta_of(P.nu, chin, k.turbulence), o);
 #pragma unroll
         for (int q = 0; q < 9; q++) fn[q * ns + slot] = o[q];
         if (CHILD && (fl & FL_BAND)) {
@@ -564,7 +614,7 @@ __global__ void __launch_bounds__(128) k_wallfn(LevelView P, int p, RecView R, S
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R.n) return;
     float drW, uWx, uWy, chiB;
-    wall_record(P, p, R, k, r, drW, uWx, uWy, chiB);
+    wall_record(P, p, R, k, r, false, drW, uWx, uWy, chiB);
 }
 
 // ------------------------------------------------------------------ interface sync (set_fields)
@@ -722,6 +772,11 @@ void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const
         if (F) k_level<false, true><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
         else k_level<false, false><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
     }
+}
+
+int level_blocks_per_sm()
+{
+    return 4;
 }
 
 void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p)

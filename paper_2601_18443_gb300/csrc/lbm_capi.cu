@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -100,6 +101,12 @@ static void *dalloc(lbm_solver *s, size_t bytes)
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         p = nullptr;
     }
+    if (p && ((uintptr_t)p & 255u)) {
+        // the level kernels stage 1 KB tile planes with bulk copies: every array must be
+        // at least 16-byte aligned (cudaMalloc gives 256); refuse anything less than 256
+        if (s->cfg.dev_free) s->cfg.dev_free(p, (void *)s->stream, s->cfg.alloc_ctx);
+        return nullptr;
+    }
     if (p) { s->allocs.push_back(p); s->device_bytes += (double)bytes; }
     return p;
 }
@@ -184,6 +191,7 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     ls.wall = (l == L - 1) && s->rec.n > 0;
     ls.restrict_up = restrict_up && C != nullptr;
     ls.pp = C ? s->parity[l - 1] : 0;
+    ls.status = s->d_status;
     mark_begin(s);
     lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls);
     mark_end(s, l == L - 1 ? KC_LEVEL_FINEST : KC_LEVEL_COARSE, P.ns);
@@ -233,7 +241,8 @@ static lbm_status check_status(lbm_solver *s)
     int st = 0;
     CK(cudaMemcpyAsync(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
-    if (st & 1) return fail(s, LBM_ERR_DIVERGED, "diverged (non-finite field)");
+    if (st & LBM_STATUS_TIMEOUT) return fail(s, LBM_ERR_TIMEOUT, "a staged tile copy did not arrive (wait limit)");
+    if (st & LBM_STATUS_NONFINITE) return fail(s, LBM_ERR_DIVERGED, "diverged (non-finite field)");
     if (st) return fail(s, LBM_ERR_CUDA, "device status word set");
     return LBM_OK;
 }
@@ -385,7 +394,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.loop = upload(s, loop, ok);
         s->d_slip = (float *)dalloc(s, 2 * (size_t)std::max(n_loops, 1) * sizeof(float));
         v.slip = s->d_slip;
-        float **outs[8] = {&v.drhoW, &v.uWx, &v.uWy, &v.utau, &v.chiB, &v.tx, &v.ty, &v.ut};
+        float **outs[9] = {&v.drhoW, &v.uWx, &v.uWy, &v.utau, &v.chiB, &v.tx, &v.ty, &v.ut, &v.utau_start};
         for (auto o : outs) { *o = (float *)dalloc(s, (size_t)std::max(nr, 1) * sizeof(float)); ok = ok && *o; }
         if (!ok || !s->d_slip) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
         CK(cudaMemsetAsync(s->d_slip, 0, 2 * (size_t)std::max(n_loops, 1) * sizeof(float), s->stream));
@@ -429,6 +438,11 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     s->k.turbulence = c.turbulence; s->k.wall_model = c.wall_model;
     s->k.U = (float)s->U; s->k.chi_inf = (float)c.chi_inf;
     s->k.d_wr = (float)c.d_wr; s->k.d_wv = (float)c.d_wv;
+    {
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+        s->k.resident_blocks = sms * lbmdev::level_blocks_per_sm();
+    }
     float g9[9];
     feq_shifted(1.0, s->U, 0.0, g9);
     for (int l = 0; l < L; l++) lbmdev::launch_init_feq(s->stream, s->lv[l].v, g9, (float)s->U, (float)c.chi_inf);
