@@ -75,7 +75,7 @@ def assert_fields(g, r, levels, turbulent=True, tol=TOL_FIELD):
         assert e["chi"] <= tol, e
     if e["drho_rms"] > 1e-5:
         # rho - 1 well above the FP32 resolution of rho: its own relative error is meaningful
-        assert e["drho"] <= TOL_DRHO, e
+        assert e["drho"] <= TOL_DRHO * (tol / TOL_FIELD), e
     return e
 
 
