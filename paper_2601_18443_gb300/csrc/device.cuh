@@ -23,7 +23,8 @@ struct LevelView {
     const uint32_t *flags;        // per slot
     const float *dist;            // wall distance (level lattice units)
     const int *rec;               // wall record of a B node (finest level) or nullptr
-    float *f[2];                  // populations f - w, [q * ns + slot], two lattices
+    void *f[2];                   // populations f - w, [q * ns + slot], two lattices (storage type: store)
+    int store;                    // 0 FP32, 1 FP16, 2 BF16 population storage (arithmetic is FP32)
     float *drho[2], *ux[2], *uy[2];  // macroscopic fields (rho - 1, u) at the two time levels
     float *chi[2];                // nu_tilde / nu at the two time levels
     float nu;                     // lattice viscosity of the level
@@ -35,7 +36,8 @@ struct RecView {
     const int *bslot;             // slot of the boundary node
     const int *ns;                // reference stencil size
     const int *st_slot;           // 16 per record
-    const float *st_dx, *st_dy;   // stencil cell centre minus R (finest cells)
+    const float *st_wr;           // 16 per record: inverse-distance weights of rho at R (normalised)
+    const float *st_wu;           // 16 per record: weights of u at R (intercept row of the linear LSQ, or the IDW weights)
     const float *nx, *ny, *dwb;   // unit normal (wall -> fluid), wall distance of B
     const float *q;               // 9 per record: wall fraction of cut pulled directions
     const int *loop;

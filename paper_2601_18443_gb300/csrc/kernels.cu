@@ -16,6 +16,8 @@
 // of a level -- the restriction of the new fields into the covered parents.  Fields
 // of time t are read from buffer [p] and those of t + 1 written to [p ^ 1], so that
 // no cell reads a value another block of the same launch writes.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "device.cuh"
@@ -42,6 +44,17 @@ __host__ __device__ constexpr int dir_of3(int m)
 __device__ __forceinline__ void load_nb3(const LevelView &P, int t, int *nb3)
 {
     if (threadIdx.x < 9) nb3[threadIdx.x] = P.nbr[t * 9 + dir_of3(threadIdx.x)];
+}
+
+// Thread -> cell map of the level kernel: warp w covers the 16 x 2 cells
+// x in [16 (w & 1), +16), y in {2 (w >> 1), +1}, so that every 2 x 2 group of children
+// (restriction) lies inside one warp.  A warp still reads two 64-byte row segments per
+// plane, i.e. whole 32-byte sectors.
+__device__ __forceinline__ void cell_of_thread(int c, int &lx, int &ly)
+{
+    const int w = c >> 5, lane = c & 31;
+    lx = (w & 1) * 16 + (lane & 15);
+    ly = (w >> 1) * 2 + (lane >> 4);
 }
 
 // slot of the cell at offset (dx, dy) from (lx, ly), or -1 if its tile is absent
@@ -91,6 +104,42 @@ __device__ __forceinline__ int child_base(const LevelView &P, int t, int lx, int
 {
     const int ct = P.child[t * 4 + ((2 * ly) >> 3) * 2 + ((2 * lx) >> 5)];
     return ct < 0 ? -1 : ct * LBM_TILE + ((2 * ly) & 7) * LBM_TX + ((2 * lx) & 31);
+}
+
+// ------------------------------------------------------------------ population storage
+// Populations are stored shifted (f - w) in FP32, FP16 or BF16; every load converts to
+// FP32 and every store rounds to nearest, so the arithmetic is FP32 in all three forms.
+template <typename T> struct PopIO;
+template <> struct PopIO<float> {
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float ldp(const float *p) { return *p; }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct PopIO<__half> {
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ldp(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct PopIO<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ldp(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ------------------------------------------------------------------ programmatic dependent launch
+// The level-step kernels are launched with programmatic stream serialization: the next
+// kernel's blocks may be scheduled while this one drains.  Each kernel reads only the
+// static tile tables before griddep_wait(), which returns once the preceding kernel has
+// completed and its writes are visible; griddep_launch() lets the next kernel start
+// being scheduled as soon as every block of this one has begun.
+__device__ __forceinline__ void griddep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void griddep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ SA-neg constants (Sec 2.2)
@@ -200,13 +249,12 @@ __device__ __forceinline__ void gather0(const float *chi, const float *ux, const
     }
 }
 
-// LSQ gradient over the full D2Q9 neighbourhood: sum_k c_k (phi_k - phi_0) / 6
+// LSQ gradient over the full D2Q9 neighbourhood: the normal matrix is 6 I, so the
+// gradient is sum_k c_k (phi_k - phi_0) / 6 = sum_k c_k phi_k / 6 (sum_k c_k = 0)
 __device__ __forceinline__ void lsq_grad(const float *v, float &gx, float &gy)
 {
-    float sx = 0.f, sy = 0.f;
-#pragma unroll
-    for (int q = 1; q < 9; q++) { sx += cxq(q) * (v[q] - v[0]); sy += cyq(q) * (v[q] - v[0]); }
-    gx = sx * (1.0f / 6.0f); gy = sy * (1.0f / 6.0f);
+    gx = ((v[1] - v[2]) + (v[5] - v[6]) + (v[7] - v[8])) * (1.0f / 6.0f);
+    gy = ((v[3] - v[4]) + (v[5] - v[6]) + (v[8] - v[7])) * (1.0f / 6.0f);
 }
 
 __device__ __forceinline__ float sa_diff_coef(float chi)
@@ -229,9 +277,17 @@ __device__ float sa_update(const Stencil &S, float d, float nu)
     const float gxy = 0.25f * (x[5] - x[8] - x[7] + x[6]);
     const float u = S.ux[0], v = S.uy[0];
     const float conv = -(u * gx + v * gy) + 0.5f * (u * u * gxx + 2.0f * u * v * gxy + v * v * gyy);
-    const float Dc = sa_diff_coef(x[0]);
-    const float De = 0.5f * (Dc + sa_diff_coef(x[1])), Dw = 0.5f * (Dc + sa_diff_coef(x[2]));
-    const float Dn = 0.5f * (Dc + sa_diff_coef(x[3])), Ds = 0.5f * (Dc + sa_diff_coef(x[4]));
+    float Dc, De, Dw, Dn, Ds;
+    if (fminf(fminf(x[0], x[1]), fminf(fminf(x[2], x[3]), x[4])) >= 0.0f) {
+        // nu_t~ >= 0 on the whole stencil: f_n = 1
+        Dc = 1.0f + x[0];
+        De = 0.5f * (Dc + 1.0f + x[1]); Dw = 0.5f * (Dc + 1.0f + x[2]);
+        Dn = 0.5f * (Dc + 1.0f + x[3]); Ds = 0.5f * (Dc + 1.0f + x[4]);
+    } else {
+        Dc = sa_diff_coef(x[0]);
+        De = 0.5f * (Dc + sa_diff_coef(x[1])); Dw = 0.5f * (Dc + sa_diff_coef(x[2]));
+        Dn = 0.5f * (Dc + sa_diff_coef(x[3])); Ds = 0.5f * (Dc + sa_diff_coef(x[4]));
+    }
     const float div = De * (x[1] - x[0]) - Dw * (x[0] - x[2]) + Dn * (x[3] - x[0]) - Ds * (x[0] - x[4]);
     const float diff = nu * (div + SA_CB2 * (gx * gx + gy * gy)) * (1.0f / SA_SIGMA);
     const float chi = x[0];
@@ -319,30 +375,14 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
                             float &drW, float &uWx, float &uWy, float &chiB)
 {
     const float *dr = P.drho[p], *ux = P.ux[p], *uy = P.uy[p];
-    const int ns = R.ns[r];
-    float sw = 0.f, swr = 0.f, swu = 0.f, swv = 0.f;
-    float A0 = 0.f, A1 = 0.f, A2 = 0.f, A4 = 0.f, A5 = 0.f, A8 = 0.f;
-    float bu0 = 0.f, bu1 = 0.f, bu2 = 0.f, bv0 = 0.f, bv1 = 0.f, bv2 = 0.f;
+    // step 1: rho_R and u_R as fixed weighted sums over the 16-entry stencil (unused
+    // entries carry zero weight); all 48 loads are independent
+    float drR = 0.f, uR = 0.f, vR = 0.f;
 #pragma unroll
     for (int m = 0; m < 16; m++) {
-        if (m >= ns) break;
         const int s = R.st_slot[r * 16 + m];
-        const float dx = R.st_dx[r * 16 + m], dy = R.st_dy[r * 16 + m];
-        const float d = dr[s], u = ux[s], v = uy[s];
-        const float w = 1.0f / fmaxf(dx * dx + dy * dy, 1e-20f);
-        sw += w; swr += w * d; swu += w * u; swv += w * v;
-        A0 += 1.0f; A1 += dx; A2 += dy; A4 += dx * dx; A5 += dx * dy; A8 += dy * dy;
-        bu0 += u; bu1 += u * dx; bu2 += u * dy;
-        bv0 += v; bv1 += v * dx; bv2 += v * dy;
-    }
-    float drR = 0.f, uR = 0.f, vR = 0.f;
-    if (ns > 0) { drR = swr / sw; uR = swu / sw; vR = swv / sw; }
-    // unweighted linear LSQ u = a + b dx + c dy: intercept a by Cramer's rule
-    const float det = A0 * (A4 * A8 - A5 * A5) - A1 * (A1 * A8 - A5 * A2) + A2 * (A1 * A5 - A4 * A2);
-    if (ns >= 3 && det > 1e-9f * A0 * A4 * A8) {
-        const float c0 = A4 * A8 - A5 * A5, c1 = A2 * A5 - A1 * A8, c2 = A1 * A5 - A2 * A4;
-        uR = (c0 * bu0 + c1 * bu1 + c2 * bu2) / det;
-        vR = (c0 * bv0 + c1 * bv1 + c2 * bv2) / det;
+        const float wr = R.st_wr[r * 16 + m], wu = R.st_wu[r * 16 + m];
+        drR += wr * dr[s]; uR += wu * ux[s]; vR += wu * uy[s];
     }
     const float nx = R.nx[r], ny = R.ny[r];
     const float un = uR * nx + vR * ny;
@@ -370,24 +410,28 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
 }
 
 // ------------------------------------------------------------------ the fused level step
-template <bool WALL, bool CHILD>
-__global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, LevelView C, RecView R, StepConsts k,
+template <bool WALL, bool CHILD, typename T>
+__global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, LevelView C, RecView R, StepConsts k,
                                                    LevelStep ls)
 {
-    __shared__ int nb3[9];
-    __shared__ float sh[4][LBM_TILE];            // new rho - 1, u_x, u_y, chi (restriction)
-    __shared__ unsigned char sv[LBM_TILE];
+    using IO = PopIO<T>;
+    __shared__ int nb3w[LBM_TILE / 32][9];       // one copy per warp: no block-wide barrier
     const int t = blockIdx.x, c = threadIdx.x;
-    const int lx = c & (LBM_TX - 1), ly = c >> 5;
-    load_nb3(P, t, nb3);
-    __syncthreads();
-    const int slot = t * LBM_TILE + c;
+    const int lane = c & 31;
+    int lx, ly;
+    cell_of_thread(c, lx, ly);
+    int *nb3 = nb3w[c >> 5];
+    if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
+    __syncwarp();
+    griddep_launch();
+    griddep_wait();
+    const int slot = t * LBM_TILE + ly * LBM_TX + lx;
     const uint32_t fl = __ldg(P.flags + slot);
     const uint32_t kind = fl & FL_KIND_MASK;
     const bool fluid = !(fl & FL_SOLID);
     const int ns = P.ns, p = ls.p;
-    const float *fc = P.f[p];
-    float *fn = P.f[p ^ 1];
+    const T *fc = static_cast<const T *>(P.f[p]);
+    T *fn = static_cast<T *>(P.f[p ^ 1]);
     bool valid = false;
     float n_dr = 0.f, n_ux = 0.f, n_uy = 0.f, n_chi = 0.f;
 
@@ -402,7 +446,7 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
                 const uint32_t ks = fs & FL_KIND_MASK;
                 ok = (ks == KIND_ACTIVE || ks == KIND_GHOST) && !(fs & FL_SOLID);
             }
-            fn[q * ns + slot] = __ldg(fc + q * ns + (ok ? s : slot));
+            IO::st(fn + q * ns + slot, IO::ld(fc + q * ns + (ok ? s : slot)));
         }
     } else if (kind == KIND_ACTIVE && fluid) {
         const bool edge = ls.is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
@@ -446,12 +490,12 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
         }
         // ---- pull streaming (eq 1) with coalescence, cut links and box edges
         float g[9];
-        g[0] = __ldg(fc + slot);
+        g[0] = IO::ld(fc + slot);
         const uint32_t special = fl & (0xFFu << FL_COAL_SHIFT | 0xFFu << FL_CUT_SHIFT);
         if (!edge && !special) {
             // plain cell: every direction is pulled from its upstream neighbour
 #pragma unroll
-            for (int q = 1; q < 9; q++) g[q] = __ldg(fc + q * ns + nbs[oppq(q)]);
+            for (int q = 1; q < 9; q++) g[q] = IO::ld(fc + q * ns + nbs[oppq(q)]);
         } else if (!edge) {
             int cb = -1;
             if (CHILD && (fl & FL_BAND)) cb = child_base(P, t, lx, ly);
@@ -459,9 +503,10 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
             for (int q = 1; q < 9; q++) {
                 if (CHILD && (fl & (1u << (FL_COAL_SHIFT + q - 1)))) {
                     // coalescence: mean of the four ghost children after the two fine sub-steps
-                    const float *ff = F.f[ls.pf] + q * F.ns;
-                    g[q] = cb >= 0 ? 0.25f * (ff[cb] + ff[cb + 1] + ff[cb + LBM_TX] + ff[cb + LBM_TX + 1])
-                                   : __ldg(fc + q * ns + slot);
+                    const T *ff = static_cast<const T *>(F.f[ls.pf]) + q * F.ns;
+                    g[q] = cb >= 0 ? 0.25f * (IO::ldp(ff + cb) + IO::ldp(ff + cb + 1) + IO::ldp(ff + cb + LBM_TX) +
+                                              IO::ldp(ff + cb + LBM_TX + 1))
+                                   : IO::ld(fc + q * ns + slot);
                 } else if (WALL && (fl & (1u << (FL_CUT_SHIFT + q - 1)))) {
                     // Yu interpolated bounce-back with the slip velocity of the wall record (eq 27)
                     const int qo = oppq(q);
@@ -474,13 +519,13 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
                         ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
                     }
                     if (ok)
-                        g[q] = ((1.0f - qf) * __ldg(fc + qo * ns + sf) + qf * __ldg(fc + qo * ns + slot) + mom) /
+                        g[q] = ((1.0f - qf) * IO::ld(fc + qo * ns + sf) + qf * IO::ld(fc + qo * ns + slot) + mom) /
                                    (1.0f + qf) +
-                               qf / (1.0f + qf) * __ldg(fc + q * ns + slot);
+                               qf / (1.0f + qf) * IO::ld(fc + q * ns + slot);
                     else
-                        g[q] = __ldg(fc + qo * ns + slot) + mom;            // half-way form, eq 24
+                        g[q] = IO::ld(fc + qo * ns + slot) + mom;           // half-way form, eq 24
                 } else {
-                    g[q] = __ldg(fc + q * ns + nbs[oppq(q)]);
+                    g[q] = IO::ld(fc + q * ns + nbs[oppq(q)]);
                 }
             }
         } else {
@@ -490,8 +535,8 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
             for (int q = 1; q < 9; q++) {
                 const int si = i - cxq(q), sj = j - cyq(q);
                 const bool xin = si >= 0 && si < k.nx0, yin = sj >= 0 && sj < k.ny0;
-                if (xin && yin) g[q] = fc[q * ns + slot0(k, si, sj)];
-                else if (xin) g[q] = fc[mirror_y(q) * ns + slot0(k, si, j)];
+                if (xin && yin) g[q] = IO::ld(fc + q * ns + slot0(k, si, sj));
+                else if (xin) g[q] = IO::ld(fc + mirror_y(q) * ns + slot0(k, si, j));
                 else g[q] = 0.0f;
             }
             if (i == 0) {
@@ -510,8 +555,8 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
 #pragma unroll
                     for (int b = 0; b < 2; b++) {
                         const int ii = k.nx0 - 2 - b, si = ii - cxq(q), sj = j - cyq(q);
-                        v[b] = (sj >= 0 && sj < k.ny0) ? fc[q * ns + slot0(k, si, sj)]
-                                                       : fc[mirror_y(q) * ns + slot0(k, si, j)];
+                        v[b] = (sj >= 0 && sj < k.ny0) ? IO::ld(fc + q * ns + slot0(k, si, sj))
+                                                       : IO::ld(fc + mirror_y(q) * ns + slot0(k, si, j));
                     }
                     g[q] = 2.0f * v[0] - v[1];
                 }
@@ -521,20 +566,22 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
         const float drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
         const float jx = g[1] - g[2] + g[5] - g[6] + g[7] - g[8];
         const float jy = g[3] - g[4] + g[5] - g[6] - g[7] + g[8];
-        const float ux = jx / (1.0f + drho), uy = jy / (1.0f + drho);
+        const float irho = 1.0f / (1.0f + drho);
+        const float ux = jx * irho, uy = jy * irho;
         P.drho[p ^ 1][slot] = drho; P.ux[p ^ 1][slot] = ux; P.uy[p ^ 1][slot] = uy;
         float o[9];
         collide_cm(g, drho, jx, jy, ux, uy, delta_of(P.nu, chin, k.turbulence), o);
 #pragma unroll
-        for (int q = 0; q < 9; q++) fn[q * ns + slot] = o[q];
+        for (int q = 0; q < 9; q++) IO::st(fn + q * ns + slot, o[q]);
         if (CHILD && (fl & FL_BAND)) {
             // explosion: post-collision populations copied to the four ghost children
             const int cb = child_base(P, t, lx, ly);
             if (cb >= 0) {
 #pragma unroll
                 for (int q = 0; q < 9; q++) {
-                    float *ff = F.f[ls.pf] + q * F.ns;
-                    ff[cb] = o[q]; ff[cb + 1] = o[q]; ff[cb + LBM_TX] = o[q]; ff[cb + LBM_TX + 1] = o[q];
+                    T *ff = static_cast<T *>(F.f[ls.pf]) + q * F.ns;
+                    IO::st(ff + cb, o[q]); IO::st(ff + cb + 1, o[q]);
+                    IO::st(ff + cb + LBM_TX, o[q]); IO::st(ff + cb + LBM_TX + 1, o[q]);
                 }
             }
         }
@@ -544,30 +591,29 @@ __global__ void __launch_bounds__(256, 4) k_level(LevelView P, LevelView F, Leve
 
     if (ls.restrict_up) {
         // restriction into the covered parents (their children are this level's active
-        // cells; a 2 x 2 group of children never straddles a tile): rho and chi are the
-        // means over the fluid children, u is mass-weighted (Rohde transfers, Sec 2.1)
-        sh[0][c] = n_dr; sh[1][c] = n_ux; sh[2][c] = n_uy; sh[3][c] = n_chi;
-        sv[c] = valid;
-        __syncthreads();
-        if (!(lx & 1) && !(ly & 1) && kind == KIND_ACTIVE) {
-            const int pt = P.parent[t];
-            float sdr = 0.f, sr = 0.f, sx = 0.f, sy = 0.f, sc = 0.f;
-            int n = 0;
+        // cells; a 2 x 2 group of children lies inside one warp, lanes l, l+1, l+16, l+17):
+        // rho and chi are the means over the fluid children, u is mass-weighted (Rohde
+        // transfers, Sec 2.1)
+        const float rr = valid ? 1.0f + n_dr : 0.0f;
+        float a0 = valid ? n_dr : 0.0f, a1 = rr, a2 = rr * n_ux, a3 = rr * n_uy, a4 = valid ? n_chi : 0.0f;
+        float a5 = valid ? 1.0f : 0.0f;
+        // sum over (l, l+1) then over (l, l+16)
 #pragma unroll
-            for (int m = 0; m < 4; m++) {
-                const int cc = c + (m & 1) + (m >> 1) * LBM_TX;
-                if (!sv[cc]) continue;
-                const float dr = sh[0][cc], rr = 1.0f + dr;
-                sdr += dr; sr += rr; sx += rr * sh[1][cc]; sy += rr * sh[2][cc]; sc += sh[3][cc];
-                n++;
-            }
+        for (int d = 1; d <= 16; d <<= 4) {
+            a0 += __shfl_down_sync(0xffffffffu, a0, d); a1 += __shfl_down_sync(0xffffffffu, a1, d);
+            a2 += __shfl_down_sync(0xffffffffu, a2, d); a3 += __shfl_down_sync(0xffffffffu, a3, d);
+            a4 += __shfl_down_sync(0xffffffffu, a4, d); a5 += __shfl_down_sync(0xffffffffu, a5, d);
+        }
+        if (!(lane & 1) && lane < 16 && kind == KIND_ACTIVE) {
+            const int pt = P.parent[t];
+            const int n = (int)a5;
             if (pt >= 0 && n > 0) {
                 const int px = (P.tile_x[t] & 1) * (LBM_TX / 2) + (lx >> 1);
                 const int py = (P.tile_y[t] & 1) * (LBM_TY / 2) + (ly >> 1);
                 const int ps = pt * LBM_TILE + py * LBM_TX + px;
                 const int q1 = ls.pp ^ 1;
-                C.drho[q1][ps] = sdr / n; C.ux[q1][ps] = sx / sr; C.uy[q1][ps] = sy / sr;
-                C.chi[q1][ps] = sc / n;
+                C.drho[q1][ps] = a0 / n; C.ux[q1][ps] = a2 / a1; C.uy[q1][ps] = a3 / a1;
+                C.chi[q1][ps] = a4 / n;
             }
         }
     }
@@ -583,6 +629,8 @@ __global__ void __launch_bounds__(256) k_prolong(LevelView P, LevelView F, int p
     const int lx = c & 31, ly = c >> 5;
     load_nb3(P, t, nb3);
     __syncthreads();
+    griddep_launch();
+    griddep_wait();
     const int slot = t * LBM_TILE + c;
     const uint32_t fl = P.flags[slot];
     if ((fl & FL_KIND_MASK) != KIND_ACTIVE || (fl & FL_SOLID) || !(fl & FL_BAND)) return;
@@ -640,6 +688,7 @@ __global__ void k_restrict(LevelView P, LevelView F, int pp, int pf)
     P.chi[pp][slot] = sc / n;
 }
 
+template <typename T>
 __global__ void k_explode_prolong(LevelView P, LevelView F, int p, int pf)
 {
     __shared__ int nb3[9];
@@ -666,12 +715,14 @@ __global__ void k_explode_prolong(LevelView P, LevelView F, int p, int pf)
         for (int h = 0; h < 2; h++) {
             F.chi[h][cs] = vc; F.ux[h][cs] = vu; F.uy[h][cs] = vv; F.drho[h][cs] = P.drho[p][slot];
         }
-        for (int q = 0; q < 9; q++) F.f[pf][q * F.ns + cs] = P.f[p][q * P.ns + slot];
+        for (int q = 0; q < 9; q++)
+            static_cast<T *>(F.f[pf])[q * F.ns + cs] = static_cast<const T *>(P.f[p])[q * P.ns + slot];
     }
 }
 
 struct Feq9 { float g[9]; };
 
+template <typename T>
 __global__ void k_init(LevelView P, Feq9 e, float U, float chi_inf)
 {
     const int slot = blockIdx.x * LBM_TILE + threadIdx.x;
@@ -679,8 +730,8 @@ __global__ void k_init(LevelView P, Feq9 e, float U, float chi_inf)
     const bool present = (fl & FL_KIND_MASK) != KIND_ABSENT;
     for (int q = 0; q < 9; q++) {
         const float v = present ? e.g[q] : 0.0f;
-        P.f[0][q * P.ns + slot] = v;
-        P.f[1][q * P.ns + slot] = v;
+        PopIO<T>::st(static_cast<T *>(P.f[0]) + q * P.ns + slot, v);
+        PopIO<T>::st(static_cast<T *>(P.f[1]) + q * P.ns + slot, v);
     }
     for (int h = 0; h < 2; h++) {
         P.drho[h][slot] = 0.0f;
@@ -761,16 +812,45 @@ __global__ void __launch_bounds__(256) k_mass(LevelView P, int p, double area, d
 }
 
 // ------------------------------------------------------------------ launchers
+// launch with programmatic stream serialization (see griddep_wait)
+template <typename... Args>
+static void launch_pdl(void (*kern)(Args...), unsigned grid, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(LBM_TILE);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename T>
+static void launch_level_t(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
+                           const RecView &R, const StepConsts &k, const LevelStep &ls)
+{
+    if (ls.wall) {
+        if (child) launch_pdl(k_level<true, true, T>, P.ntiles, st, P, Fv, Cv, R, k, ls);
+        else launch_pdl(k_level<true, false, T>, P.ntiles, st, P, Fv, Cv, R, k, ls);
+    } else {
+        if (child) launch_pdl(k_level<false, true, T>, P.ntiles, st, P, Fv, Cv, R, k, ls);
+        else launch_pdl(k_level<false, false, T>, P.ntiles, st, P, Fv, Cv, R, k, ls);
+    }
+}
+
 void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,
                   const StepConsts &k, const LevelStep &ls)
 {
     const LevelView Fv = F ? *F : P, Cv = C ? *C : P;
-    if (ls.wall) {
-        if (F) k_level<true, true><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
-        else k_level<true, false><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
-    } else {
-        if (F) k_level<false, true><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
-        else k_level<false, false><<<P.ntiles, LBM_TILE, 0, st>>>(P, Fv, Cv, R, k, ls);
+    if (P.ntiles <= 0) return;
+    switch (P.store) {
+    case 1: launch_level_t<__half>(st, P, Fv, Cv, F != nullptr, R, k, ls); break;
+    case 2: launch_level_t<__nv_bfloat16>(st, P, Fv, Cv, F != nullptr, R, k, ls); break;
+    default: launch_level_t<float>(st, P, Fv, Cv, F != nullptr, R, k, ls); break;
     }
 }
 
@@ -781,7 +861,7 @@ int level_blocks_per_sm()
 
 void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p)
 {
-    if (P.n_band_tiles > 0) k_prolong<<<P.n_band_tiles, LBM_TILE, 0, st>>>(P, F, p);
+    if (P.n_band_tiles > 0) launch_pdl(k_prolong, (unsigned)P.n_band_tiles, st, P, F, p);
 }
 
 void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k)
@@ -797,14 +877,22 @@ void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, in
 
 void launch_explode_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pf)
 {
-    k_explode_prolong<<<P.ntiles, LBM_TILE, 0, st>>>(P, F, p, pf);
+    switch (P.store) {
+    case 1: k_explode_prolong<__half><<<P.ntiles, LBM_TILE, 0, st>>>(P, F, p, pf); break;
+    case 2: k_explode_prolong<__nv_bfloat16><<<P.ntiles, LBM_TILE, 0, st>>>(P, F, p, pf); break;
+    default: k_explode_prolong<float><<<P.ntiles, LBM_TILE, 0, st>>>(P, F, p, pf); break;
+    }
 }
 
 void launch_init_feq(cudaStream_t st, const LevelView &P, const float *feq9, float U, float chi_inf)
 {
     Feq9 e;
     for (int q = 0; q < 9; q++) e.g[q] = feq9[q];
-    k_init<<<P.ntiles, LBM_TILE, 0, st>>>(P, e, U, chi_inf);
+    switch (P.store) {
+    case 1: k_init<__half><<<P.ntiles, LBM_TILE, 0, st>>>(P, e, U, chi_inf); break;
+    case 2: k_init<__nv_bfloat16><<<P.ntiles, LBM_TILE, 0, st>>>(P, e, U, chi_inf); break;
+    default: k_init<float><<<P.ntiles, LBM_TILE, 0, st>>>(P, e, U, chi_inf); break;
+    }
 }
 
 void launch_loads(cudaStream_t st, const LoadsView &S, const RecView &R, float U, double *acc4)

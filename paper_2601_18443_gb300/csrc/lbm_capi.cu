@@ -1,6 +1,8 @@
 // lbm_capi.cu -- C ABI of the library (include/lbm.h): solver object, upload of
 // the tiled grid, the recursive level scheduler (Sec 2.1: each finer level takes
 // two sub-steps per parent step) captured into CUDA graphs, and host queries.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,6 +33,48 @@ void feq_shifted(double rho, double ux, double uy, float *g)
 {
     auto h = [](int c, double u) { return c == 0 ? 2.0 / 3.0 - u * u : 0.5 * (u * u + 1.0 / 3.0 + c * u); };
     for (int q = 0; q < 9; q++) g[q] = (float)(rho * h(CXh[q], ux) * h(CYh[q], uy) - WQh[q]);
+}
+
+// bytes of one stored population: FP32, FP16 or BF16
+size_t pop_bytes(int store) { return store == 0 ? 4 : 2; }
+
+// store one population value (rounded to nearest) into a host copy of a lattice
+void put_pop(int store, unsigned char *base, size_t idx, float v)
+{
+    if (store == 1) reinterpret_cast<__half *>(base)[idx] = __float2half_rn(v);
+    else if (store == 2) reinterpret_cast<__nv_bfloat16 *>(base)[idx] = __float2bfloat16_rn(v);
+    else reinterpret_cast<float *>(base)[idx] = v;
+}
+
+// Step 1 of Sec 2.3 as fixed linear combinations of the stencil values, from the static
+// geometry of a wall record: rho_R = sum wr_m rho_m with inverse-distance weights 1/d^2
+// (normalised), u_R = sum wu_m u_m with wu the intercept row of the unweighted linear
+// least-squares fit a + b dx + c dy, or the IDW weights when fewer than 3 points or a
+// near-singular normal matrix leave the fit undefined.  Computed in FP64.
+void stencil_weights(const lbmgrid::Record &R, double wr[16], double wu[16])
+{
+    double sw = 0.0, A[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double dx[16], dy[16];
+    for (int m = 0; m < R.ns; m++) {
+        dx[m] = R.si[m] + 0.5 - R.r[0];
+        dy[m] = R.sj[m] + 0.5 - R.r[1];
+        const double d2 = dx[m] * dx[m] + dy[m] * dy[m];
+        wr[m] = 1.0 / (d2 > 1e-20 ? d2 : 1e-20);
+        sw += wr[m];
+        const double phi[3] = {1.0, dx[m], dy[m]};
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) A[3 * a + b] += phi[a] * phi[b];
+    }
+    for (int m = 0; m < R.ns; m++) { wr[m] /= sw; wu[m] = wr[m]; }
+    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                       A[2] * (A[3] * A[7] - A[4] * A[6]);
+    if (R.ns >= 3 && det > 1e-9 * A[0] * A[4] * A[8]) {
+        // first column of A^-1 (A is symmetric) by cofactors
+        const double x0 = (A[4] * A[8] - A[5] * A[7]) / det;
+        const double x1 = -(A[3] * A[8] - A[5] * A[6]) / det;
+        const double x2 = (A[3] * A[7] - A[4] * A[6]) / det;
+        for (int m = 0; m < R.ns; m++) wu[m] = x0 + x1 * dx[m] + x2 * dy[m];
+    }
 }
 
 struct HostLevelDev {
@@ -255,7 +299,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
     if (!cfg || !out) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
     if (cfg->levels < 1 || cfg->levels > LBM_MAXL || cfg->nx0 < 4 || cfg->ny0 < 4 || !(cfg->h0 > 0) ||
-        cfg->layers < 3 || !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->chord > 0) || cfg->store != 0 ||
+        cfg->layers < 3 || !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->chord > 0) || cfg->store < 0 || cfg->store > 2 ||
         (cfg->periodic && (cfg->nx0 % LBM_TX || cfg->ny0 % LBM_TY)) || (!cfg->periodic && (cfg->nx0 < 8)) ||
         (cfg->wall_model != 0 && cfg->wall_model != 2 && cfg->wall_model != 3) || (!cfg->dev_alloc != !cfg->dev_free))
         return LBM_ERR_INVALID_ARG;
@@ -351,7 +395,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.dist = upload(s, dist, ok);
         v.rec = (l == L - 1) ? upload(s, rec, ok) : nullptr;
         for (int b = 0; b < 2; b++) {
-            v.f[b] = (float *)dalloc(s, 9 * ns * sizeof(float));
+            v.f[b] = dalloc(s, 9 * ns * pop_bytes(c.store));
             v.chi[b] = (float *)dalloc(s, ns * sizeof(float));
             v.drho[b] = (float *)dalloc(s, ns * sizeof(float));
             v.ux[b] = (float *)dalloc(s, ns * sizeof(float));
@@ -359,6 +403,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
             ok = ok && v.f[b] && v.chi[b] && v.drho[b] && v.ux[b] && v.uy[b];
         }
         v.nu = (float)(s->U * (c.chord / c.h0) * (double)(1LL << l) / c.Re);
+        v.store = c.store;
         if (!ok) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
     }
     // wall records
@@ -366,15 +411,18 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     {
         const lbmgrid::Level &G = s->g.lv[L - 1];
         std::vector<int> bslot(nr), nsv(nr), st_slot((size_t)nr * 16, -1), loop(nr);
-        std::vector<float> st_dx((size_t)nr * 16, 0.f), st_dy((size_t)nr * 16, 0.f), nx(nr), ny(nr), dwb(nr), q((size_t)nr * 9, 0.f);
+        std::vector<float> st_wr((size_t)nr * 16, 0.f), st_wu((size_t)nr * 16, 0.f), nx(nr), ny(nr), dwb(nr), q((size_t)nr * 9, 0.f);
         for (int r = 0; r < nr; r++) {
             const lbmgrid::Record &R = s->g.recs[r];
             bslot[r] = (int)G.slot(R.i, R.j);
             nsv[r] = R.ns;
-            for (int m = 0; m < R.ns; m++) {
-                st_slot[(size_t)r * 16 + m] = (int)G.slot(R.si[m], R.sj[m]);
-                st_dx[(size_t)r * 16 + m] = (float)(R.si[m] + 0.5 - R.r[0]);
-                st_dy[(size_t)r * 16 + m] = (float)(R.sj[m] + 0.5 - R.r[1]);
+            double wr[16], wu[16];
+            stencil_weights(R, wr, wu);
+            for (int m = 0; m < 16; m++) {
+                // unused entries point at the boundary node itself with zero weight
+                st_slot[(size_t)r * 16 + m] = m < R.ns ? (int)G.slot(R.si[m], R.sj[m]) : bslot[r];
+                st_wr[(size_t)r * 16 + m] = m < R.ns ? (float)wr[m] : 0.f;
+                st_wu[(size_t)r * 16 + m] = m < R.ns ? (float)wu[m] : 0.f;
             }
             nx[r] = (float)R.n[0]; ny[r] = (float)R.n[1]; dwb[r] = (float)R.dwb;
             for (int d = 0; d < 9; d++) q[(size_t)r * 9 + d] = (float)R.q[d];
@@ -385,8 +433,8 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.bslot = upload(s, bslot, ok);
         v.ns = upload(s, nsv, ok);
         v.st_slot = upload(s, st_slot, ok);
-        v.st_dx = upload(s, st_dx, ok);
-        v.st_dy = upload(s, st_dy, ok);
+        v.st_wr = upload(s, st_wr, ok);
+        v.st_wu = upload(s, st_wu, ok);
         v.nx = upload(s, nx, ok);
         v.ny = upload(s, ny, ok);
         v.dwb = upload(s, dwb, ok);
@@ -580,11 +628,13 @@ lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const dou
     if (st != LBM_OK) return st;
     const LevelView &v = s->lv[level].v;
     const int p = s->parity[level];
-    std::vector<float> dr, u, w, c2, c3(v.ns), f(9 * (size_t)v.ns);
+    const size_t pb = pop_bytes(s->cfg.store);
+    std::vector<float> dr, u, w, c2, c3(v.ns);
+    std::vector<unsigned char> f(9 * (size_t)v.ns * pb);
     st = download_level(s, level, dr, u, w, c2);
     if (st != LBM_OK) return st;
     CK(cudaMemcpyAsync(c3.data(), v.chi[p ^ 1], v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(f.data(), v.f[p], 9 * v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(f.data(), v.f[p], f.size(), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     const lbmgrid::Level &G = s->g.lv[level];
     const std::vector<uint32_t> &fl = s->lv[level].flags;
@@ -602,14 +652,14 @@ lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const dou
             if (chi) { c2[sl] = (float)chi[o]; c3[sl] = (float)chi[o]; }
             float g9[9];
             feq_shifted(r, a, b, g9);
-            for (int q = 0; q < 9; q++) f[(size_t)q * v.ns + sl] = g9[q];
+            for (int q = 0; q < 9; q++) put_pop(s->cfg.store, f.data(), (size_t)q * v.ns + sl, g9[q]);
         }
     CK(cudaMemcpyAsync(v.drho[p], dr.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.ux[p], u.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.uy[p], w.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.chi[p], c2.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.chi[p ^ 1], c3.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(v.f[p], f.data(), 9 * v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(v.f[p], f.data(), f.size(), cudaMemcpyHostToDevice, s->stream));
     // re-synchronise the interfaces: restriction bottom-up, then explosion and ghost reconstruction
     for (int l = s->L - 2; l >= 0; l--)
         lbmdev::launch_restrict(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], s->parity[l + 1]);
@@ -738,7 +788,7 @@ lbm_status lbm_get_info(lbm_solver *s, lbm_info *out)
     out->kernels_per_step = s->kernels_per_step;
     // fused level step: 9 populations read + 9 written (FP32), rho and u written; with
     // SA-neg also nu_tilde read and written, u read for the stencil, wall distance read
-    out->bytes_per_node_update = 72.0 + 12.0 + (s->cfg.turbulence ? 8.0 + 8.0 + 4.0 : 0.0);
+    out->bytes_per_node_update = 18.0 * (double)pop_bytes(s->cfg.store) + 12.0 + (s->cfg.turbulence ? 8.0 + 8.0 + 4.0 : 0.0);
     out->device_bytes = s->device_bytes;
     return LBM_OK;
 }
