@@ -249,6 +249,37 @@ def gpu_arm(args, rank, world, dist):
     if rank == 0 and not args.no_hbm_grid:
         hbm = hbm_grid_roofline(pkg, stream, peak, peak_kind)
 
+    # precision forms: the same workload with populations stored in FP16 / BF16
+    forms = None
+    if rank == 0 and not args.no_precision_forms:
+        forms = {}
+        for name, store in (("fp16", 1), ("bf16", 2)):
+            c2 = dict(cfg)
+            c2["store"] = store
+            s3 = pkg.Solver(c2, stream=stream)
+            s3.set_geometry(loops)
+            s3.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            kk = max(10, K // 2)
+            msum = 0.0
+            for _ in range(kk):
+                flush.fill_(1)
+                e0.record(stream)
+                s3.step_async(1)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                msum += e0.elapsed_time(e1)
+            s3.synchronize()
+            kt3 = s3.time_kernels(3)
+            f3 = kt3["level_step_finest"]
+            avg3 = f3["ms"] / max(f3["launches"], 1)
+            bpn3 = s3.info()["bytes_per_node_update"]
+            forms[name] = {"value": round(nu_step * kk / (msum * 1e-3) / 1e6, 2), "unit": "MLUPS",
+                           "ms_per_step": round(msum / kk, 4), "bytes_per_node_update": bpn3,
+                           "finest_kernel_gbs": round(act_fin * bpn3 / (avg3 * 1e-3) / 1e9, 1)}
+            s3.close()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": K,
@@ -276,6 +307,8 @@ def gpu_arm(args, rank, world, dist):
             line["cpu_baseline"] = cpu
         if hbm is not None:
             line["roofline_hbm_grid"] = hbm
+        if forms is not None:
+            line["precision_forms"] = forms
         print(json.dumps(line), flush=True)
     s.close()
     return 0
@@ -333,6 +366,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hbm-grid", action="store_true")
+    ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--profile-case", choices=["hbm_grid", "workload"], default=None)
     args = ap.parse_args()
     if args.profile_case:

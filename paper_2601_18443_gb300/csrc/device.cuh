@@ -55,6 +55,7 @@ struct StepConsts {
     float chi_inf;
     float d_wr, d_wv;
     int resident_blocks; // persistent grid of the level kernel: SMs x blocks per SM
+    float pshift[9];    // 16-bit storage holds g_q - pshift_q (pshift = f_eq(1, U, 0) - w); 0 for FP32
 };
 
 // device status word bits (lbm_step maps them to lbm_status codes)

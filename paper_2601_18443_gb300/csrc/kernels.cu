@@ -20,6 +20,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "device.cuh"
 
 namespace lbmdev {
@@ -410,11 +412,33 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
 }
 
 // ------------------------------------------------------------------ the fused level step
+// 16-bit storage keeps the populations relative to the free-stream equilibrium, so that
+// in most of the domain the stored values are small and their relative rounding is
+// small in absolute terms; FP32 storage keeps g = f - w itself.
+template <typename T> struct ShiftedIO {
+    const float *sh;
+    __device__ __forceinline__ float ld(const T *p, int q) const
+    {
+        if constexpr (std::is_same<T, float>::value) return PopIO<T>::ld(p);
+        else return PopIO<T>::ld(p) + sh[q];
+    }
+    __device__ __forceinline__ float ldp(const T *p, int q) const
+    {
+        if constexpr (std::is_same<T, float>::value) return PopIO<T>::ldp(p);
+        else return PopIO<T>::ldp(p) + sh[q];
+    }
+    __device__ __forceinline__ void st(T *p, int q, float v) const
+    {
+        if constexpr (std::is_same<T, float>::value) PopIO<T>::st(p, v);
+        else PopIO<T>::st(p, v - sh[q]);
+    }
+};
+
 template <bool WALL, bool CHILD, typename T>
 __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, LevelView C, RecView R, StepConsts k,
                                                    LevelStep ls)
 {
-    using IO = PopIO<T>;
+    const ShiftedIO<T> IO{k.pshift};
     __shared__ int nb3w[LBM_TILE / 32][9];       // one copy per warp: no block-wide barrier
     const int t = blockIdx.x, c = threadIdx.x;
     const int lane = c & 31;
@@ -446,7 +470,7 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
                 const uint32_t ks = fs & FL_KIND_MASK;
                 ok = (ks == KIND_ACTIVE || ks == KIND_GHOST) && !(fs & FL_SOLID);
             }
-            IO::st(fn + q * ns + slot, IO::ld(fc + q * ns + (ok ? s : slot)));
+            IO.st(fn + q * ns + slot, q, IO.ld(fc + q * ns + (ok ? s : slot), q));
         }
     } else if (kind == KIND_ACTIVE && fluid) {
         const bool edge = ls.is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
@@ -490,12 +514,12 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
         }
         // ---- pull streaming (eq 1) with coalescence, cut links and box edges
         float g[9];
-        g[0] = IO::ld(fc + slot);
+        g[0] = IO.ld(fc + slot, 0);
         const uint32_t special = fl & (0xFFu << FL_COAL_SHIFT | 0xFFu << FL_CUT_SHIFT);
         if (!edge && !special) {
             // plain cell: every direction is pulled from its upstream neighbour
 #pragma unroll
-            for (int q = 1; q < 9; q++) g[q] = IO::ld(fc + q * ns + nbs[oppq(q)]);
+            for (int q = 1; q < 9; q++) g[q] = IO.ld(fc + q * ns + nbs[oppq(q)], q);
         } else if (!edge) {
             int cb = -1;
             if (CHILD && (fl & FL_BAND)) cb = child_base(P, t, lx, ly);
@@ -504,9 +528,9 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
                 if (CHILD && (fl & (1u << (FL_COAL_SHIFT + q - 1)))) {
                     // coalescence: mean of the four ghost children after the two fine sub-steps
                     const T *ff = static_cast<const T *>(F.f[ls.pf]) + q * F.ns;
-                    g[q] = cb >= 0 ? 0.25f * (IO::ldp(ff + cb) + IO::ldp(ff + cb + 1) + IO::ldp(ff + cb + LBM_TX) +
-                                              IO::ldp(ff + cb + LBM_TX + 1))
-                                   : IO::ld(fc + q * ns + slot);
+                    g[q] = cb >= 0 ? 0.25f * (IO.ldp(ff + cb, q) + IO.ldp(ff + cb + 1, q) + IO.ldp(ff + cb + LBM_TX, q) +
+                                              IO.ldp(ff + cb + LBM_TX + 1, q))
+                                   : IO.ld(fc + q * ns + slot, q);
                 } else if (WALL && (fl & (1u << (FL_CUT_SHIFT + q - 1)))) {
                     // Yu interpolated bounce-back with the slip velocity of the wall record (eq 27)
                     const int qo = oppq(q);
@@ -519,13 +543,13 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
                         ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
                     }
                     if (ok)
-                        g[q] = ((1.0f - qf) * IO::ld(fc + qo * ns + sf) + qf * IO::ld(fc + qo * ns + slot) + mom) /
+                        g[q] = ((1.0f - qf) * IO.ld(fc + qo * ns + sf, qo) + qf * IO.ld(fc + qo * ns + slot, qo) + mom) /
                                    (1.0f + qf) +
-                               qf / (1.0f + qf) * IO::ld(fc + q * ns + slot);
+                               qf / (1.0f + qf) * IO.ld(fc + q * ns + slot, q);
                     else
-                        g[q] = IO::ld(fc + qo * ns + slot) + mom;           // half-way form, eq 24
+                        g[q] = IO.ld(fc + qo * ns + slot, qo) + mom;        // half-way form, eq 24
                 } else {
-                    g[q] = IO::ld(fc + q * ns + nbs[oppq(q)]);
+                    g[q] = IO.ld(fc + q * ns + nbs[oppq(q)], q);
                 }
             }
         } else {
@@ -535,8 +559,8 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
             for (int q = 1; q < 9; q++) {
                 const int si = i - cxq(q), sj = j - cyq(q);
                 const bool xin = si >= 0 && si < k.nx0, yin = sj >= 0 && sj < k.ny0;
-                if (xin && yin) g[q] = IO::ld(fc + q * ns + slot0(k, si, sj));
-                else if (xin) g[q] = IO::ld(fc + mirror_y(q) * ns + slot0(k, si, j));
+                if (xin && yin) g[q] = IO.ld(fc + q * ns + slot0(k, si, sj), q);
+                else if (xin) g[q] = IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
                 else g[q] = 0.0f;
             }
             if (i == 0) {
@@ -555,8 +579,8 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
 #pragma unroll
                     for (int b = 0; b < 2; b++) {
                         const int ii = k.nx0 - 2 - b, si = ii - cxq(q), sj = j - cyq(q);
-                        v[b] = (sj >= 0 && sj < k.ny0) ? IO::ld(fc + q * ns + slot0(k, si, sj))
-                                                       : IO::ld(fc + mirror_y(q) * ns + slot0(k, si, j));
+                        v[b] = (sj >= 0 && sj < k.ny0) ? IO.ld(fc + q * ns + slot0(k, si, sj), q)
+                                                       : IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
                     }
                     g[q] = 2.0f * v[0] - v[1];
                 }
@@ -572,7 +596,7 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
         float o[9];
         collide_cm(g, drho, jx, jy, ux, uy, delta_of(P.nu, chin, k.turbulence), o);
 #pragma unroll
-        for (int q = 0; q < 9; q++) IO::st(fn + q * ns + slot, o[q]);
+        for (int q = 0; q < 9; q++) IO.st(fn + q * ns + slot, q, o[q]);
         if (CHILD && (fl & FL_BAND)) {
             // explosion: post-collision populations copied to the four ghost children
             const int cb = child_base(P, t, lx, ly);
@@ -580,8 +604,8 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
 #pragma unroll
                 for (int q = 0; q < 9; q++) {
                     T *ff = static_cast<T *>(F.f[ls.pf]) + q * F.ns;
-                    IO::st(ff + cb, o[q]); IO::st(ff + cb + 1, o[q]);
-                    IO::st(ff + cb + LBM_TX, o[q]); IO::st(ff + cb + LBM_TX + 1, o[q]);
+                    IO.st(ff + cb, q, o[q]); IO.st(ff + cb + 1, q, o[q]);
+                    IO.st(ff + cb + LBM_TX, q, o[q]); IO.st(ff + cb + LBM_TX + 1, q, o[q]);
                 }
             }
         }
@@ -720,7 +744,7 @@ __global__ void k_explode_prolong(LevelView P, LevelView F, int p, int pf)
     }
 }
 
-struct Feq9 { float g[9]; };
+struct Feq9 { float g[9]; };   // values to store (already relative to the storage shift)
 
 template <typename T>
 __global__ void k_init(LevelView P, Feq9 e, float U, float chi_inf)

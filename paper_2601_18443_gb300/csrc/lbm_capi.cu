@@ -493,7 +493,10 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     }
     float g9[9];
     feq_shifted(1.0, s->U, 0.0, g9);
-    for (int l = 0; l < L; l++) lbmdev::launch_init_feq(s->stream, s->lv[l].v, g9, (float)s->U, (float)c.chi_inf);
+    for (int q = 0; q < 9; q++) s->k.pshift[q] = c.store != 0 ? g9[q] : 0.0f;
+    float st9[9];
+    for (int q = 0; q < 9; q++) st9[q] = g9[q] - s->k.pshift[q];
+    for (int l = 0; l < L; l++) lbmdev::launch_init_feq(s->stream, s->lv[l].v, st9, (float)s->U, (float)c.chi_inf);
     for (int l = 0; l < LBM_MAXL; l++) s->parity[l] = 0;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
@@ -652,7 +655,7 @@ lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const dou
             if (chi) { c2[sl] = (float)chi[o]; c3[sl] = (float)chi[o]; }
             float g9[9];
             feq_shifted(r, a, b, g9);
-            for (int q = 0; q < 9; q++) put_pop(s->cfg.store, f.data(), (size_t)q * v.ns + sl, g9[q]);
+            for (int q = 0; q < 9; q++) put_pop(s->cfg.store, f.data(), (size_t)q * v.ns + sl, g9[q] - s->k.pshift[q]);
         }
     CK(cudaMemcpyAsync(v.drho[p], dr.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.ux[p], u.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
