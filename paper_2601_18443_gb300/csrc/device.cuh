@@ -20,6 +20,8 @@ struct LevelView {
     const int *parent;            // tile of level l-1 holding the parents, or -1
     const int *band_tiles;        // tiles with band cells
     int n_band_tiles;
+    const int *work_tiles;        // tiles with active or ghost fluid cells (the level kernel's grid)
+    int n_work_tiles;
     const uint32_t *flags;        // per slot
     const float *dist;            // wall distance (level lattice units)
     const int *rec;               // wall record of a B node (finest level) or nullptr

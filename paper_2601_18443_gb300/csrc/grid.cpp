@@ -570,6 +570,16 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                 }
             if (band) P.band_tiles.push_back(t);
         }
+        P.work_tiles.clear();
+        for (int t = 0; t < P.ntiles; t++) {
+            bool work = false;
+            for (int y = 0; y < LBM_TY && !work; y++)
+                for (int x = 0; x < LBM_TX && !work; x++) {
+                    long c = P.idx(P.tile_x[t] * LBM_TX + x, P.tile_y[t] * LBM_TY + y);
+                    work = c >= 0 && !P.solid[c] && (P.kind[c] == KIND_ACTIVE || P.kind[c] == KIND_GHOST);
+                }
+            if (work) P.work_tiles.push_back(t);
+        }
         P.nbr.assign((size_t)P.ntiles * 9, -1);
         const bool wrap = (l == 0 && sp.periodic);
         const int wtx = sp.nx0 / LBM_TX, wty = sp.ny0 / LBM_TY;

@@ -40,6 +40,7 @@ struct Level {
     std::vector<int> child;         // 4 per tile: level l+1 tiles (b * 2 + a)
     std::vector<int> parent;        // level l-1 tile holding the parents of this tile's cells, or -1
     std::vector<int> band_tiles;    // tiles holding at least one band cell (explosion / prolongation)
+    std::vector<int> work_tiles;    // tiles holding at least one active or ghost fluid cell
     int ntiles = 0;
     int n_wall_tiles = 0;           // tiles holding boundary nodes come first in the tile order
 

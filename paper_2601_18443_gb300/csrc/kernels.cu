@@ -329,10 +329,12 @@ __device__ float sa_update(const Stencil &S, float d, float nu)
 #define WF_C4 3.639753186868684494f
 
 __device__ __forceinline__ float wf_uplus(float y)
-{   // eq 22, continuous arctangent branch
-    float t1 = (y + WF_A1) * (y + WF_A1) + WF_B1 * WF_B1;
-    float t2 = (y + WF_A2) * (y + WF_A2) + WF_B2 * WF_B2;
-    return WF_B + WF_C1 * logf(t1) - WF_C2 * logf(t2) - WF_C3 * atan2f(WF_B1, y + WF_A1) - WF_C4 * atan2f(WF_B2, y + WF_A2);
+{   // eq 22 on the continuous arctangent branch: with b > 0, atan2(b, x) = pi/2 - atan(x / b)
+    const float z1 = (y + WF_A1) * (1.0f / WF_B1), z2 = (y + WF_A2) * (1.0f / WF_B2);
+    const float t1 = (y + WF_A1) * (y + WF_A1) + WF_B1 * WF_B1;
+    const float t2 = (y + WF_A2) * (y + WF_A2) + WF_B2 * WF_B2;
+    return (WF_B - (WF_C3 + WF_C4) * 1.5707963267948966f) + WF_C1 * __logf(t1) - WF_C2 * __logf(t2) +
+           WF_C3 * atanf(z1) + WF_C4 * atanf(z2);
 }
 
 __device__ __forceinline__ float wf_dudy(float y)
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
 {
     const ShiftedIO<T> IO{k.pshift};
     __shared__ int nb3w[LBM_TILE / 32][9];       // one copy per warp: no block-wide barrier
-    const int t = blockIdx.x, c = threadIdx.x;
+    const int t = P.work_tiles[blockIdx.x], c = threadIdx.x;
     const int lane = c & 31;
     int lx, ly;
     cell_of_thread(c, lx, ly);
@@ -858,11 +860,11 @@ static void launch_level_t(cudaStream_t st, const LevelView &P, const LevelView 
                            const RecView &R, const StepConsts &k, const LevelStep &ls)
 {
     if (ls.wall) {
-        if (child) launch_pdl(k_level<true, true, T>, P.ntiles, st, P, Fv, Cv, R, k, ls);
-        else launch_pdl(k_level<true, false, T>, P.ntiles, st, P, Fv, Cv, R, k, ls);
+        if (child) launch_pdl(k_level<true, true, T>, P.n_work_tiles, st, P, Fv, Cv, R, k, ls);
+        else launch_pdl(k_level<true, false, T>, P.n_work_tiles, st, P, Fv, Cv, R, k, ls);
     } else {
-        if (child) launch_pdl(k_level<false, true, T>, P.ntiles, st, P, Fv, Cv, R, k, ls);
-        else launch_pdl(k_level<false, false, T>, P.ntiles, st, P, Fv, Cv, R, k, ls);
+        if (child) launch_pdl(k_level<false, true, T>, P.n_work_tiles, st, P, Fv, Cv, R, k, ls);
+        else launch_pdl(k_level<false, false, T>, P.n_work_tiles, st, P, Fv, Cv, R, k, ls);
     }
 }
 
@@ -870,7 +872,7 @@ void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const
                   const StepConsts &k, const LevelStep &ls)
 {
     const LevelView Fv = F ? *F : P, Cv = C ? *C : P;
-    if (P.ntiles <= 0) return;
+    if (P.n_work_tiles <= 0) return;
     switch (P.store) {
     case 1: launch_level_t<__half>(st, P, Fv, Cv, F != nullptr, R, k, ls); break;
     case 2: launch_level_t<__nv_bfloat16>(st, P, Fv, Cv, F != nullptr, R, k, ls); break;

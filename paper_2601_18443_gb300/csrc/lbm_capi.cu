@@ -391,6 +391,8 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.parent = upload(s, G.parent, ok);
         v.band_tiles = upload(s, G.band_tiles, ok);
         v.n_band_tiles = (int)G.band_tiles.size();
+        v.work_tiles = upload(s, G.work_tiles, ok);
+        v.n_work_tiles = (int)G.work_tiles.size();
         v.flags = upload(s, H.flags, ok);
         v.dist = upload(s, dist, ok);
         v.rec = (l == L - 1) ? upload(s, rec, ok) : nullptr;
