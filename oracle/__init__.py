@@ -46,7 +46,7 @@ class Config(C.Structure):
         ("chord", C.c_double), ("Re", C.c_double), ("Ma", C.c_double),
         ("chi_inf", C.c_double), ("d_wr", C.c_double), ("d_wv", C.c_double),
         ("turbulence", C.c_int), ("wall_model", C.c_int), ("periodic", C.c_int),
-        ("solid_walls", C.c_int),
+        ("solid_walls", C.c_int), ("sa_convection", C.c_int),
     ]
 
 
@@ -89,7 +89,9 @@ def lib():
             L.oracle_feq.argtypes = [C.c_double, C.c_double, C.c_double, dp]
             L.oracle_collide.argtypes = [dp, C.c_double, C.c_double, dp]
             L.oracle_sa_source.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
-            L.oracle_sa_update_point.argtypes = [dp, dp, dp, C.c_double, C.c_double]
+            L.oracle_sa_update_point.argtypes = [dp, dp, dp, C.c_double, C.c_double, C.c_int]
+            L.oracle_sa_convection.argtypes = [dp, C.c_double, C.c_double, C.c_int]
+            L.oracle_sa_convection.restype = C.c_double
             L.oracle_sa_update_point.restype = C.c_double
             _lib = L
     return _lib
@@ -137,9 +139,14 @@ def sa_source(chi, nu, vort, d):
     return float(P[0]), float(D[0])
 
 
-def sa_update_point(chi9, ux9, uy9, d, nu):
+def sa_update_point(chi9, ux9, uy9, d, nu, convection=0):
     a = [np.ascontiguousarray(x, dtype=np.float64) for x in (chi9, ux9, uy9)]
-    return lib().oracle_sa_update_point(_dp(a[0]), _dp(a[1]), _dp(a[2]), d, nu)
+    return lib().oracle_sa_update_point(_dp(a[0]), _dp(a[1]), _dp(a[2]), d, nu, int(convection))
+
+
+def sa_convection(nt9, u, v, scheme=0):
+    a = np.ascontiguousarray(nt9, dtype=np.float64)
+    return lib().oracle_sa_convection(_dp(a), float(u), float(v), int(scheme))
 
 
 # --- solver ------------------------------------------------------------------
@@ -155,7 +162,7 @@ class Solver:
         self._lib = lib()
         c = Config()
         for name, _ in Config._fields_:
-            setattr(c, name, cfg[name])
+            setattr(c, name, cfg.get(name, 0))
         self.cfg = dict(cfg)
         h = C.c_void_p()
         rc = self._lib.oracle_create(C.byref(c), C.byref(h))

@@ -280,12 +280,34 @@ static int lsq_gradient(int n, const double *dx, const double *dy, const double 
     return 0;
 }
 
+/* Convective increment -dt u . grad(nu_t~) over one step (dt = 1) at the centre of the
+ * D2Q9 neighbourhood nt9 (index k at offset (CX[k], CY[k])).
+ * scheme 0: Lax-Wendroff (Sec 2.2): -(u d_x + v d_y) phi + (1/2)(u^2 d_xx + 2 u v d_xy + v^2 d_yy) phi
+ *           with centred differences.
+ * scheme 1: first-order upwind (Sec 3.3, the alternative of Sec 2.2's footnote): one-sided
+ *           differences taken from the upstream side of each velocity component. */
+double oracle_sa_convection(const double *nt, double u, double v, int scheme)
+{
+    double c = nt[0], e = nt[1], w = nt[2], n = nt[3], s = nt[4];
+    double ne = nt[5], sw = nt[6], se = nt[7], nw = nt[8];
+    if (scheme == 1) {
+        double dx = u > 0.0 ? c - w : e - c;
+        double dy = v > 0.0 ? c - s : n - c;
+        return -(u * dx + v * dy);
+    }
+    double gx = 0.5 * (e - w), gy = 0.5 * (n - s);
+    double gxx = e - 2.0 * c + w, gyy = n - 2.0 * c + s, gxy = 0.25 * (ne - nw - se + sw);
+    return -(u * gx + v * gy) + 0.5 * (u * u * gxx + 2.0 * u * v * gxy + v * v * gyy);
+}
+
 /* One explicit Euler step (dt = 1 lattice step of the level) of eq 12 / eq 16
  * at a node with its 8 D2Q9 neighbours (index k at offset (CX[k], CY[k])).
- * Convection: Lax-Wendroff (Sec 2.2).  Diffusion: centred, conservative face
- * averages of nu + nu_t~ f_n.  c_b2 |grad nu_t~|^2 with centred gradients.
- * Vorticity from the LSQ velocity gradient.  Returns chi at the new time. */
-double oracle_sa_update_point(const double *chi9, const double *ux9, const double *uy9, double d, double nu)
+ * Convection: Lax-Wendroff (Sec 2.2) or first-order upwind (Sec 3.3).  Diffusion:
+ * centred, conservative face averages of nu + nu_t~ f_n.  c_b2 |grad nu_t~|^2 with
+ * centred gradients.  Vorticity from the LSQ velocity gradient.  Returns chi at the
+ * new time. */
+double oracle_sa_update_point(const double *chi9, const double *ux9, const double *uy9, double d, double nu,
+                              int convection)
 {
     double nt[9], dxk[8], dyk[8], du[8], dv[8];
     for (int k = 0; k < 9; k++) nt[k] = chi9[k] * nu;
@@ -299,10 +321,9 @@ double oracle_sa_update_point(const double *chi9, const double *ux9, const doubl
     double vort = fabs(dvdx - dudy);                         /* Omega = sqrt(2 W:W) in 2D */
     double c = nt[0], e = nt[1], w = nt[2], n = nt[3], s = nt[4];
     double ne = nt[5], sw = nt[6], se = nt[7], nw = nt[8];
+    (void)ne; (void)sw; (void)se; (void)nw;
     double gx = 0.5 * (e - w), gy = 0.5 * (n - s);
-    double gxx = e - 2.0 * c + w, gyy = n - 2.0 * c + s, gxy = 0.25 * (ne - nw - se + sw);
-    double u = ux9[0], v = uy9[0];
-    double conv = -(u * gx + v * gy) + 0.5 * (u * u * gxx + 2.0 * u * v * gxy + v * v * gyy);
+    double conv = oracle_sa_convection(nt, ux9[0], uy9[0], convection);
     double Dk[9];
     for (int k = 0; k < 9; k++) Dk[k] = sa_diffusivity(chi9[k], nu);
     double De = 0.5 * (Dk[0] + Dk[1]), Dw = 0.5 * (Dk[0] + Dk[2]);
@@ -795,12 +816,12 @@ int oracle_set_geometry(oracle_solver *s, const double *xy, const int *loop_off,
             for (int b = -1; b <= 2; b++)
                 for (int a = -1; a <= 2; a++) {
                     long kk = cidx(Fn, ic + a, jc + b);
-                    if (c->wall_model == 0 && (kk < 0 || Fn->kind[kk] != K_ACTIVE))
+                    if (c->wall_model <= 1 && (kk < 0 || Fn->kind[kk] != K_ACTIVE))
                         return fail(s, -5, "reference point stencil leaves the finest active level");
                     if (kk < 0 || Fn->kind[kk] != K_ACTIVE || Fn->solid[kk] || Fn->bnode[kk]) continue;
                     R0->si[R0->ns] = ic + a; R0->sj[R0->ns] = jc + b; R0->ns++;
                 }
-            if (c->wall_model == 0 && R0->ns == 0) return fail(s, -5, "empty reference stencil");
+            if (c->wall_model <= 1 && R0->ns == 0) return fail(s, -5, "empty reference stencil");
             r++;
         }
     /* surface elements -> two nearest boundary nodes (Sec 3.1.3) */
@@ -999,6 +1020,28 @@ static void wall_function(oracle_solver *s)
             R0->uW[1] = uW * R0->t[1];
             /* SA Dirichlet at B: nu_t~_B = nu kappa d+_WB (Sec 2.2) */
             R0->chiB = SA_KAPPA * utau * R0->dwb / nu;
+        } else if (c->wall_model == 1) {
+            /* Nishimura's slip adapted to RANS (Sec 3.1.5, eq 31).  Readings: u_tau from eq 22 at
+               R (step 3 kept: eq 31 needs it; the VN steps 4-5 are the ones replaced, as Sec 2.3
+               states); (nu_t)_R = IDW of the SA-neg eddy viscosity nu chi f_v1 over the R
+               stencil; slip along t = u_Rt/|u_Rt|; the SA Dirichlet value as in the VN method. */
+            double utau = oracle_wf_utau(ut, c->d_wr, nu);
+            double swn = 0, swt = 0;
+            for (int m = 0; m < R0->ns; m++) {
+                long kk = cidx(F, R0->si[m], R0->sj[m]);
+                double dx = R0->si[m] + 0.5 - R0->r[0], dy = R0->sj[m] + 0.5 - R0->r[1];
+                double d2 = dx * dx + dy * dy;
+                double w = 1.0 / (d2 > 1e-20 ? d2 : 1e-20);
+                double ch = F->chi[kk];
+                swn += w * (ch > 0 ? ch : 0.0) * nu * sa_fv1(ch);
+                swt += w;
+            }
+            double nutR = swt > 0 ? swn / swt : 0.0;
+            double uW = ut - utau * utau * c->d_wr / (nu + nutR);
+            R0->utau = utau;
+            R0->uW[0] = uW * R0->t[0];
+            R0->uW[1] = uW * R0->t[1];
+            R0->chiB = SA_KAPPA * utau * R0->dwb / nu;
         } else if (c->wall_model == 2) {
             R0->utau = 0;
             R0->uW[0] = s->loop_slip[2 * R0->loop];
@@ -1038,7 +1081,7 @@ static void sa_level(oracle_solver *s, int l)
                 if (kn < 0 || P->kind[kn] == K_ABSENT) { kn = k; sgn = 1.0; }   /* never taken on a valid grid */
                 ch[q] = P->chi[kn]; u[q] = P->ux[kn]; v[q] = sgn * P->uy[kn];
             }
-            P->chin[k] = oracle_sa_update_point(ch, u, v, P->d[k], P->nu);
+            P->chin[k] = oracle_sa_update_point(ch, u, v, P->d[k], P->nu, c->sa_convection);
         }
     if (edge) {
         for (int j = 0; j < c->ny0; j++) {

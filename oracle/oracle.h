@@ -26,9 +26,10 @@ typedef struct {
     double chi_inf;        /* inlet / initial nu_tilde / nu (Sec 3.1.1: 3)       */
     double d_wr, d_wv;     /* reference / virtual node wall distance, finest cells (Sec 2.3) */
     int turbulence;        /* 0 laminar, 1 SA-neg                                */
-    int wall_model;        /* 0 VN slip, 2 prescribed slip per loop, 3 no-slip   */
+    int wall_model;        /* 0 VN slip, 1 Nishimura slip (eq 31), 2 prescribed slip per loop, 3 no-slip */
     int periodic;          /* 1: periodic level-0 box, no domain BCs             */
     int solid_walls;       /* 1: loops are walls; 0: loops only drive refinement */
+    int sa_convection;     /* 0 Lax-Wendroff (Sec 2.2), 1 first-order upwind (Sec 3.3) */
 } oracle_config;
 
 typedef struct oracle_solver oracle_solver;
@@ -68,7 +69,8 @@ void   oracle_feq(double rho, double ux, double uy, double *feq9);           /* 
 void   oracle_collide(const double *f9, double omega_nu, double omega_b, double *out9); /* eqs 5-7 */
 void   oracle_sa_source(double chi, double nu, double vort, double d, double *P, double *D); /* eqs 11-17 */
 double oracle_sa_update_point(const double *chi9, const double *ux9, const double *uy9,
-                              double d, double nu);        /* explicit FD update, eqs 12/16 */
+                              double d, double nu, int convection); /* explicit FD update, eqs 12/16 */
+double oracle_sa_convection(const double *nt9, double u, double v, int scheme); /* convective increment */
 
 #ifdef __cplusplus
 }

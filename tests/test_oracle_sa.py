@@ -112,3 +112,43 @@ def test_diffusion_second_order():
         errs.append(abs((new - chi[0]) / h**2 - rhs))
     assert math.log2(errs[0] / errs[1]) > 1.8
     assert math.log2(errs[1] / errs[2]) > 1.8
+
+
+def _stencil(fn):
+    return np.array([fn(cx, cy) for cx, cy in zip(CX, CY)], dtype=np.float64)
+
+
+@pytest.mark.parametrize("u", [0.1, -0.1])
+def test_upwind_convection_takes_the_upstream_difference(u):
+    # first-order upwind (Sec 3.3) on phi = x^2: -u (phi_0 - phi_W) = u for u > 0 and
+    # -u (phi_E - phi_0) = -u for u < 0, i.e. +0.1 both times; Lax-Wendroff gives u^2 = 0.01
+    phi = _stencil(lambda x, y: float(x * x))
+    assert oracle.sa_convection(phi, u, 0.0, 1) == pytest.approx(0.1, abs=1e-15)
+    assert oracle.sa_convection(phi, u, 0.0, 0) == pytest.approx(0.01, abs=1e-15)
+    phi_y = _stencil(lambda x, y: float(y * y))
+    assert oracle.sa_convection(phi_y, 0.0, u, 1) == pytest.approx(0.1, abs=1e-15)
+
+
+def test_upwind_is_exact_for_linear_fields_and_monotone():
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        a, b, c = rng.normal(size=3)
+        u, v = rng.uniform(-0.5, 0.5, size=2)
+        lin = _stencil(lambda x, y: a + b * x + c * y)
+        assert oracle.sa_convection(lin, u, v, 1) == pytest.approx(-(u * b + v * c), abs=1e-13)
+        # |u| + |v| <= 1: the updated value is a convex combination of the centre and its
+        # upstream neighbours, so it stays inside their range
+        phi = rng.normal(size=9)
+        new = phi[0] + oracle.sa_convection(phi, u, v, 1)
+        ups = [phi[0], phi[2] if u > 0 else phi[1], phi[4] if v > 0 else phi[3]]
+        assert min(ups) - 1e-13 <= new <= max(ups) + 1e-13
+
+
+def test_sa_update_uses_the_requested_convection():
+    chi = _stencil(lambda x, y: 3.0 + 0.2 * x * x)
+    u9, v9 = np.full(9, 0.1), np.zeros(9)
+    nu = 1e-14                                   # diffusion and sources vanish with nu
+    lw = oracle.sa_update_point(chi, u9, v9, FAR, nu, 0)
+    up = oracle.sa_update_point(chi, u9, v9, FAR, nu, 1)
+    assert lw - 3.0 == pytest.approx(0.5 * 0.01 * 0.4, rel=1e-9)
+    assert up - 3.0 == pytest.approx(-0.1 * (0.0 - 0.2), rel=1e-9)

@@ -9,6 +9,7 @@ import oracle
 
 KAPPA = 0.41          # Sec 2.2 constants
 CV1 = 7.1
+CV1_3 = CV1**3
 
 
 def eq21(yp):
@@ -61,3 +62,34 @@ def test_inversion_recovers_utau(yp):
 
 def test_inversion_zero_velocity():
     assert oracle.wf_utau(0.0, 2.0, 1e-5) == 0.0
+
+
+def test_nishimura_slip_follows_eq31():
+    # Sec 3.1.5, eq 31: u_W = u_R - u_tau^2 d_WR / (nu + nu_t)|_R with d_WR = 1.75.  Above the
+    # flat top of a plate a linear velocity profile makes the LSQ value at R exact and a
+    # uniform chi makes (nu_t)_R = nu chi f_v1(chi); u_tau comes from eq 22 at R.
+    from paper_2601_18443_gb300 import workloads as W
+    nx0, ny0, top = 48, 32, 12.375
+    nu_lat = 0.01
+    U = 0.1 * math.sqrt(1.0 / 3.0)
+    cfg = W.base_config(levels=1, nx0=nx0, ny0=ny0, h0=1.0, Re=U / nu_lat, Ma=0.1, wall_model=1,
+                        turbulence=1, d_wr=1.75)
+    s = oracle.Solver(cfg)
+    s.set_geometry([W.rectangle(8.0, 6.0, 40.0, top)])
+    y = np.arange(ny0) + 0.5
+    a, b, chi = 0.004, 0.003, 4.0
+    ux = np.tile((a + b * (y - top))[:, None], (1, nx0))
+    s.set_fields(0, rho=np.ones((ny0, nx0)), ux=ux, uy=np.zeros((ny0, nx0)), chi=np.full((ny0, nx0), chi))
+    ij, geo, ns = s.wall_records()
+    st = s.wall_state()
+    # records on the top face, away from the corners (their stencils see only the profile)
+    sel = (geo[:, 3] > 0.999) & (ij[:, 0] > 12) & (ij[:, 0] < 36)
+    assert sel.sum() >= 20
+    fv1 = chi**3 / (chi**3 + CV1_3)
+    for r in np.nonzero(sel)[0]:
+        uR = a + b * (geo[r, 6] - top)              # R y in lattice units from the box origin
+        utau = oracle.wf_utau(uR, 1.75, nu_lat)
+        expect = uR - utau**2 * 1.75 / (nu_lat + nu_lat * chi * fv1)
+        assert st[r, 3] == pytest.approx(utau, rel=1e-12)
+        assert st[r, 1] == pytest.approx(expect, rel=1e-9, abs=1e-15)
+        assert st[r, 2] == pytest.approx(0.0, abs=1e-12)
