@@ -245,9 +245,10 @@ def gpu_arm(args, rank, world, dist):
         mlups_c, cores, sample, _ = run_oracle_sample(args.cpu_steps, 2)
         cpu = {"value": round(mlups_c, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample}
 
-    hbm = None
+    hbm = hbm_sc = None
     if rank == 0 and not args.no_hbm_grid:
         hbm = hbm_grid_roofline(pkg, stream, peak, peak_kind)
+        hbm_sc = hbm_grid_roofline(pkg, stream, peak, peak_kind, turbulence=0)
 
     # precision forms: the same workload with populations stored in FP16 / BF16
     forms = None
@@ -307,6 +308,7 @@ def gpu_arm(args, rank, world, dist):
             line["cpu_baseline"] = cpu
         if hbm is not None:
             line["roofline_hbm_grid"] = hbm
+            line["roofline_stream_collide"] = hbm_sc
         if forms is not None:
             line["precision_forms"] = forms
         print(json.dumps(line), flush=True)
@@ -314,11 +316,12 @@ def gpu_arm(args, rank, world, dist):
     return 0
 
 
-def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096):
-    """Stream-collide on one periodic 4096 x 4096 level (1.5 GB of traffic per launch,
-    far beyond L2): the kernel's HBM roofline without multilevel effects."""
+def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096, turbulence=1):
+    """The level kernel on one periodic 4096 x 4096 level (1.4-1.7 GB of traffic per
+    launch, far beyond L2): its HBM roofline without multilevel effects; turbulence=0
+    leaves the stream-collide alone (84 B per node update)."""
     cfg = W.base_config(levels=1, nx0=n, ny0=n, h0=1.0, Re=1000.0, Ma=0.1, periodic=1, solid_walls=0,
-                        turbulence=1, wall_model=3)
+                        turbulence=turbulence, wall_model=3)
     s = pkg.Solver(cfg, stream=stream)
     s.set_geometry([])
     s.step(3)
@@ -330,7 +333,8 @@ def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096):
     s.close()
     ach = bpl / (avg * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-            "kernel": "k_level", "grid": f"{n}x{n} periodic, 1 level, SA on", "bytes_per_launch": int(bpl),
+            "kernel": "k_level", "grid": f"{n}x{n} periodic, 1 level, SA {'on' if turbulence else 'off'}",
+            "bytes_per_launch": int(bpl),
             "avg_launch_ms": round(avg, 4), "mlups": round(info["cells_active"][0] / avg / 1e3, 1),
             "peak_kind": peak_kind}
 

@@ -55,10 +55,13 @@ typedef struct {
     double chi_inf;         /* inlet and initial nu_tilde / nu (Sec 3.1.1: 3)                        */
     double d_wr, d_wv;      /* reference / virtual node wall distances in finest cells (Sec 2.3: 2, 1) */
     int turbulence;         /* 0 laminar, 1 SA-neg                                                   */
-    int wall_model;         /* 0 virtual-node slip (Sec 2.3), 2 prescribed slip per loop, 3 no-slip  */
+    int wall_model;         /* 0 virtual-node slip (Sec 2.3), 1 Nishimura slip (Sec 3.1.5, eq 31; use
+                               d_wr = 1.75), 2 prescribed slip per loop, 3 no-slip                   */
     int periodic;           /* 1: periodic level-0 box without domain BCs (nx0 % 32 == 0, ny0 % 8 == 0) */
     int solid_walls;        /* 1: loops are walls; 0: loops only drive the refinement                */
-    int store;              /* population storage: 0 FP32 shifted (f - w_i); 1 FP16 and 2 BF16 reserved */
+    int store;              /* population storage, FP32 arithmetic: 0 FP32 (f - w_i); 1 FP16, 2 BF16
+                               (f - f_eq(1, U, 0), the free-stream equilibrium)                      */
+    int sa_convection;      /* SA-neg convection: 0 Lax-Wendroff (Sec 2.2), 1 first-order upwind (Sec 3.3) */
     void *cuda_stream;      /* cudaStream_t to run on, or NULL for a library-owned stream            */
     void *(*dev_alloc)(size_t bytes, void *stream, void *ctx); /* optional device allocator          */
     void (*dev_free)(void *ptr, void *stream, void *ctx);      /* its matching free                  */

@@ -1022,22 +1022,14 @@ static void wall_function(oracle_solver *s)
             R0->chiB = SA_KAPPA * utau * R0->dwb / nu;
         } else if (c->wall_model == 1) {
             /* Nishimura's slip adapted to RANS (Sec 3.1.5, eq 31).  Readings: u_tau from eq 22 at
-               R (step 3 kept: eq 31 needs it; the VN steps 4-5 are the ones replaced, as Sec 2.3
-               states); (nu_t)_R = IDW of the SA-neg eddy viscosity nu chi f_v1 over the R
-               stencil; slip along t = u_Rt/|u_Rt|; the SA Dirichlet value as in the VN method. */
+               R (step 3 kept: eq 31 needs it; Sec 2.3 names the VN steps 4-5 as the ones
+               Nishimura's approach lacks, so Sec 3.1.5's 'steps 3 and 4' are read as those);
+               (nu_t)_R is the eddy viscosity of the SA log layer at R, nu kappa y+_R (eq 20; the
+               mixing-length value Nishimura et al. use at R, and the value the VN method takes at
+               V); slip along t = u_Rt/|u_Rt|; the SA Dirichlet value as in the VN method. */
             double utau = oracle_wf_utau(ut, c->d_wr, nu);
-            double swn = 0, swt = 0;
-            for (int m = 0; m < R0->ns; m++) {
-                long kk = cidx(F, R0->si[m], R0->sj[m]);
-                double dx = R0->si[m] + 0.5 - R0->r[0], dy = R0->sj[m] + 0.5 - R0->r[1];
-                double d2 = dx * dx + dy * dy;
-                double w = 1.0 / (d2 > 1e-20 ? d2 : 1e-20);
-                double ch = F->chi[kk];
-                swn += w * (ch > 0 ? ch : 0.0) * nu * sa_fv1(ch);
-                swt += w;
-            }
-            double nutR = swt > 0 ? swn / swt : 0.0;
-            double uW = ut - utau * utau * c->d_wr / (nu + nutR);
+            double ypr = utau * c->d_wr / nu;
+            double uW = ut - utau * utau * c->d_wr / (nu * (1.0 + SA_KAPPA * ypr));
             R0->utau = utau;
             R0->uW[0] = uW * R0->t[0];
             R0->uW[1] = uW * R0->t[1];

@@ -23,7 +23,7 @@ struct LevelView {
     const int *work_tiles;        // tiles with active or ghost fluid cells (the level kernel's grid)
     int n_work_tiles;
     const uint32_t *flags;        // per slot
-    const float *dist;            // wall distance (level lattice units)
+    const float *inv_d2;          // 1 / d^2, d the wall distance in level lattice units (SA-neg)
     const int *rec;               // wall record of a B node (finest level) or nullptr
     void *f[2];                   // populations f - w, [q * ns + slot], two lattices (storage type: store)
     int store;                    // 0 FP32, 1 FP16, 2 BF16 population storage (arithmetic is FP32)
@@ -53,6 +53,7 @@ struct StepConsts {
     int nx0, ny0, ntx0; // level-0 cells and tiles per row
     int turbulence;
     int wall_model;
+    int sa_convection;  // 0 Lax-Wendroff, 1 first-order upwind
     float U;            // inlet lattice velocity
     float chi_inf;
     float d_wr, d_wv;

@@ -210,7 +210,7 @@ static void alloc_level(Level &Lv, int i0, int j0, int nx, int ny)
     Lv.bi0 = i0; Lv.bj0 = j0; Lv.bnx = nx; Lv.bny = ny;
     size_t n = (size_t)nx * ny;
     Lv.kind.assign(n, KIND_ABSENT); Lv.solid.assign(n, 0); Lv.band.assign(n, 0); Lv.bnode.assign(n, 0);
-    Lv.coal.assign(n, 0); Lv.cut.assign(n, 0); Lv.dist.assign(n, 0.f); Lv.rec.assign(n, -1);
+    Lv.coal.assign(n, 0); Lv.cut.assign(n, 0); Lv.dist.assign(n, 0.0); Lv.rec.assign(n, -1);
 }
 
 // centre of level cell (i, j) in fixed units
@@ -435,7 +435,7 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                     dd = T.nearest(px, py, kb, cx, cy) / (double)P.scale;
                     if (dd > DCAP) dd = DCAP;
                 }
-                P.dist[c] = (float)dd;
+                P.dist[c] = dd;
             }
     }
     // wall records in (j, i) order at the finest level
@@ -468,11 +468,11 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                 for (int a = -1; a <= 2; a++) {
                     long cc = Fn.idx(ic + a, jc + b);
                     bool act = cc >= 0 && Fn.kind[cc] == KIND_ACTIVE;
-                    if (sp.wall_model == 0 && !act) return failmsg(msg, "reference point stencil leaves the finest active level");
+                    if (sp.wall_model <= 1 && !act) return failmsg(msg, "reference point stencil leaves the finest active level");
                     if (!act || Fn.solid[cc] || Fn.bnode[cc]) continue;
                     rc.si[rc.ns] = ic + a; rc.sj[rc.ns] = jc + b; rc.ns++;
                 }
-            if (sp.wall_model == 0 && rc.ns == 0) return failmsg(msg, "empty reference stencil");
+            if (sp.wall_model <= 1 && rc.ns == 0) return failmsg(msg, "empty reference stencil");
             Fn.rec[c] = (int)g.recs.size();
             g.recs.push_back(rc);
         }

@@ -28,7 +28,7 @@ struct Level {
     std::vector<uint8_t> kind;      // KIND_* over the box
     std::vector<uint8_t> solid, band, bnode;
     std::vector<uint16_t> coal, cut;
-    std::vector<float> dist;        // wall distance, level lattice units
+    std::vector<double> dist;       // wall distance, level lattice units
     std::vector<int> rec;           // wall record of a B node
     // present-cell box
     int pi0 = 0, pj0 = 0, pnx = 0, pny = 0;

@@ -266,8 +266,10 @@ __device__ __forceinline__ float sa_diff_coef(float chi)
     return 1.0f + chi * fn;
 }
 
-// explicit Euler + Lax-Wendroff step of eqs 12 / 16 written for chi = nu_t~ / nu
-__device__ float sa_update(const Stencil &S, float d, float nu)
+// explicit Euler step of eqs 12 / 16 written for chi = nu_t~ / nu, with Lax-Wendroff
+// (conv = 0, Sec 2.2) or first-order upwind (conv = 1, Sec 3.3) convection;
+// id2 = 1 / d^2 (wall distance d in level lattice units)
+__device__ float sa_update(const Stencil &S, float id2, float nu, int conv)
 {
     float dudx, dudy, dvdx, dvdy;
     lsq_grad(S.ux, dudx, dudy);
@@ -278,7 +280,9 @@ __device__ float sa_update(const Stencil &S, float d, float nu)
     const float gxx = x[1] - 2.0f * x[0] + x[2], gyy = x[3] - 2.0f * x[0] + x[4];
     const float gxy = 0.25f * (x[5] - x[8] - x[7] + x[6]);
     const float u = S.ux[0], v = S.uy[0];
-    const float conv = -(u * gx + v * gy) + 0.5f * (u * u * gxx + 2.0f * u * v * gxy + v * v * gyy);
+    const float cv = conv == 1
+                         ? -(u * (u > 0.0f ? x[0] - x[2] : x[1] - x[0]) + v * (v > 0.0f ? x[0] - x[4] : x[3] - x[0]))
+                         : -(u * gx + v * gy) + 0.5f * (u * u * gxx + 2.0f * u * v * gxy + v * v * gyy);
     float Dc, De, Dw, Dn, Ds;
     if (fminf(fminf(x[0], x[1]), fminf(fminf(x[2], x[3]), x[4])) >= 0.0f) {
         // nu_t~ >= 0 on the whole stencil: f_n = 1
@@ -293,7 +297,6 @@ __device__ float sa_update(const Stencil &S, float d, float nu)
     const float div = De * (x[1] - x[0]) - Dw * (x[0] - x[2]) + Dn * (x[3] - x[0]) - Ds * (x[0] - x[4]);
     const float diff = nu * (div + SA_CB2 * (gx * gx + gy * gy)) * (1.0f / SA_SIGMA);
     const float chi = x[0];
-    const float id2 = __fdividef(1.0f, d * d);                    // 1 / d^2
     const float ikd2 = id2 * (1.0f / (SA_KAPPA * SA_KAPPA));      // 1 / (kappa d)^2
     float src;
     if (chi >= 0.0f) {
@@ -314,7 +317,7 @@ __device__ float sa_update(const Stencil &S, float d, float nu)
     } else {
         src = SA_CB1 * (1.0f - SA_CT3) * vort * chi + SA_CW1 * nu * chi * chi * id2;
     }
-    return chi + conv + src + diff;
+    return chi + cv + src + diff;
 }
 
 // ------------------------------------------------------------------ wall function (Sec 2.3 steps 1-5)
@@ -404,6 +407,17 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
         const float uV = utau * wf_uplus(ypv);                              // step 4
         const float uW = uV - utau * utau * k.d_wv / (nu * (1.0f + SA_KAPPA * ypv));   // eq 28
         uWx = uW * tx; uWy = uW * ty;                                       // step 5
+        chiB = SA_KAPPA * utau * R.dwb[r] / nu;
+    } else if (k.wall_model == 1) {
+        // Nishimura's slip adapted to RANS (Sec 3.1.5, eq 31): u_tau from eq 22 at R and the
+        // slip extrapolated linearly from R with the SA log-layer eddy viscosity
+        // (nu_t)_R = nu kappa y+_R (eq 20)
+        const float nu = P.nu;
+        utau = wf_utau(ut, k.d_wr, nu, R.utau_start[r]);
+        if (keep_start) R.utau_start[r] = utau;
+        const float ypr = utau * k.d_wr / nu;
+        const float uW = ut - utau * utau * k.d_wr / (nu * (1.0f + SA_KAPPA * ypr));
+        uWx = uW * tx; uWy = uW * ty;
         chiB = SA_KAPPA * utau * R.dwb[r] / nu;
     } else if (k.wall_model == 2) {
         uWx = R.slip[2 * R.loop[r]]; uWy = R.slip[2 * R.loop[r] + 1];
@@ -499,7 +513,7 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
                     const int ic = (fl & FL_OUTLET) ? k.nx0 - 2 : i;     // outlet: copy of its neighbour
                     Stencil S;
                     gather0(P.chi[p], P.ux[p], P.uy[p], k, ic, j, S);
-                    chin = sa_update(S, P.dist[slot0(k, ic, j)], P.nu);
+                    chin = sa_update(S, P.inv_d2[slot0(k, ic, j)], P.nu, k.sa_convection);
                 }
             } else {
                 Stencil S;
@@ -508,7 +522,7 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
                 for (int q = 0; q < 9; q++) {
                     S.chi[q] = __ldg(xc + nbs[q]); S.ux[q] = __ldg(xu + nbs[q]); S.uy[q] = __ldg(xv + nbs[q]);
                 }
-                chin = sa_update(S, __ldg(P.dist + slot), P.nu);
+                chin = sa_update(S, __ldg(P.inv_d2 + slot), P.nu, k.sa_convection);
             }
             P.chi[p ^ 1][slot] = chin;
         } else {

@@ -301,7 +301,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
     if (cfg->levels < 1 || cfg->levels > LBM_MAXL || cfg->nx0 < 4 || cfg->ny0 < 4 || !(cfg->h0 > 0) ||
         cfg->layers < 3 || !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->chord > 0) || cfg->store < 0 || cfg->store > 2 ||
         (cfg->periodic && (cfg->nx0 % LBM_TX || cfg->ny0 % LBM_TY)) || (!cfg->periodic && (cfg->nx0 < 8)) ||
-        (cfg->wall_model != 0 && cfg->wall_model != 2 && cfg->wall_model != 3) || (!cfg->dev_alloc != !cfg->dev_free))
+        cfg->wall_model < 0 || cfg->wall_model > 3 || cfg->sa_convection < 0 || cfg->sa_convection > 1 ||
+        (!cfg->dev_alloc != !cfg->dev_free))
         return LBM_ERR_INVALID_ARG;
     lbm_solver *s = new (std::nothrow) lbm_solver();
     if (!s) return LBM_ERR_OOM;
@@ -354,7 +355,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         const long long ns = (long long)G.ntiles * LBM_TILE;
         if (9 * ns >= (1LL << 31)) { free_all(s); return fail(s, LBM_ERR_INVALID_ARG, "level too large for 32-bit slot indices"); }
         H.flags.assign(ns, 0);
-        std::vector<float> dist(ns, 0.f);
+        std::vector<float> inv_d2(ns, 0.f);
         std::vector<int> rec(l == L - 1 ? ns : 1, -1);
         for (int t = 0; t < G.ntiles; t++)
             for (int c2 = 0; c2 < LBM_TILE; c2++) {
@@ -377,7 +378,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
                 }
                 long long sl = (long long)t * LBM_TILE + c2;
                 H.flags[sl] = f;
-                dist[sl] = G.dist[b];
+                inv_d2[sl] = (float)(1.0 / ((double)G.dist[b] * (double)G.dist[b]));
                 if (l == L - 1) rec[sl] = G.rec[b];
             }
         LevelView &v = H.v;
@@ -394,7 +395,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.work_tiles = upload(s, G.work_tiles, ok);
         v.n_work_tiles = (int)G.work_tiles.size();
         v.flags = upload(s, H.flags, ok);
-        v.dist = upload(s, dist, ok);
+        v.inv_d2 = upload(s, inv_d2, ok);
         v.rec = (l == L - 1) ? upload(s, rec, ok) : nullptr;
         for (int b = 0; b < 2; b++) {
             v.f[b] = dalloc(s, 9 * ns * pop_bytes(c.store));
@@ -485,7 +486,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     // constants and initial state: equilibrium of rho = 1, u = (U, 0), chi = chi_inf
     s->k.level0_edges = !c.periodic;
     s->k.nx0 = c.nx0; s->k.ny0 = c.ny0; s->k.ntx0 = s->g.lv[0].ntx;
-    s->k.turbulence = c.turbulence; s->k.wall_model = c.wall_model;
+    s->k.turbulence = c.turbulence; s->k.wall_model = c.wall_model; s->k.sa_convection = c.sa_convection;
     s->k.U = (float)s->U; s->k.chi_inf = (float)c.chi_inf;
     s->k.d_wr = (float)c.d_wr; s->k.d_wv = (float)c.d_wv;
     {

@@ -351,3 +351,28 @@ def test_queries_leave_the_trajectory_unchanged():
         fa, fb = a.get_fields(l), b.get_fields(l)
         for key in ("rho", "ux", "uy", "chi"):
             assert np.array_equal(fa[key], fb[key], equal_nan=True), (l, key)
+
+
+# --------------------------------------------------------------------------- paper variants
+
+VARIANTS = {
+    "upwind-sa": dict(sa_convection=1),                 # Sec 3.3
+    "nishimura": dict(wall_model=1, d_wr=1.75),         # Sec 3.1.5, eq 31
+}
+
+
+@pytest.mark.parametrize("name", list(VARIANTS))
+def test_paper_variants_on_the_turbulent_airfoil(name):
+    cfg, loops = __import__("__graft_entry__").smoke_case()
+    cfg.update(VARIANTS[name])
+    g, r = pair(cfg, loops)
+    g.step(10); r.step(10)
+    sg, sr = g.wall_state(), r.wall_state()
+    for col, key in enumerate(["rhoW", "uWx", "uWy", "utau", "chiB"]):
+        e = rel(sg[:, col], sr[:, col])
+        assert e <= TOL_FIELD, (key, e)
+    g.step(40); r.step(40)
+    assert_fields(g, r, cfg["levels"])
+    lg, lr = g.get_loads(), r.get_loads()
+    for key in ("CL", "CD"):
+        assert abs(lg[key] - lr[key]) <= TOL_LOADS * abs(lr[key]), (key, lg[key], lr[key])

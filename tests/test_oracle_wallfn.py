@@ -65,9 +65,9 @@ def test_inversion_zero_velocity():
 
 
 def test_nishimura_slip_follows_eq31():
-    # Sec 3.1.5, eq 31: u_W = u_R - u_tau^2 d_WR / (nu + nu_t)|_R with d_WR = 1.75.  Above the
-    # flat top of a plate a linear velocity profile makes the LSQ value at R exact and a
-    # uniform chi makes (nu_t)_R = nu chi f_v1(chi); u_tau comes from eq 22 at R.
+    # Sec 3.1.5, eq 31: u_W = u_R - u_tau^2 d_WR / (nu + nu_t)|_R with d_WR = 1.75 and the SA
+    # log-layer eddy viscosity (nu_t)_R = nu kappa y+_R (eq 20).  Above the flat top of a plate
+    # a linear velocity profile makes the LSQ value at R exact; u_tau comes from eq 22 at R.
     from paper_2601_18443_gb300 import workloads as W
     nx0, ny0, top = 48, 32, 12.375
     nu_lat = 0.01
@@ -85,11 +85,10 @@ def test_nishimura_slip_follows_eq31():
     # records on the top face, away from the corners (their stencils see only the profile)
     sel = (geo[:, 3] > 0.999) & (ij[:, 0] > 12) & (ij[:, 0] < 36)
     assert sel.sum() >= 20
-    fv1 = chi**3 / (chi**3 + CV1_3)
     for r in np.nonzero(sel)[0]:
         uR = a + b * (geo[r, 6] - top)              # R y in lattice units from the box origin
         utau = oracle.wf_utau(uR, 1.75, nu_lat)
-        expect = uR - utau**2 * 1.75 / (nu_lat + nu_lat * chi * fv1)
+        expect = uR - utau**2 * 1.75 / (nu_lat * (1.0 + KAPPA * utau * 1.75 / nu_lat))
         assert st[r, 3] == pytest.approx(utau, rel=1e-12)
         assert st[r, 1] == pytest.approx(expect, rel=1e-9, abs=1e-15)
         assert st[r, 2] == pytest.approx(0.0, abs=1e-12)
