@@ -41,6 +41,26 @@ WORKLOAD = "naca0012_a10_re6e6_ma015_6lvl_c4096"
 CPU_SAMPLE = "naca0012_a0_re1e6_ma01_6lvl_c256"
 
 
+def ncu_traffic(key):
+    """DRAM bytes of one launch from the committed ncu summary, or None when the kernel
+    source changed since the capture."""
+    import hashlib
+    try:
+        vals = {}
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
+            for ln in f:
+                if ln.strip() and not ln.startswith("#"):
+                    k, v = ln.split()
+                    vals[k] = v
+        src = os.path.join(ROOT, "paper_2601_18443_gb300", "csrc", "kernels.cu")
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != vals["kernels_cu_sha256"]:
+                return None
+        return int(vals[key])
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -293,7 +313,7 @@ def gpu_arm(args, rank, world, dist):
                        "replicas": world, "parallelism": f"replicas{world}"},
             "gbs_full_step_algorithmic": round(value * 1e6 * bpn / 1e9, 1),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "frac": round(achieved / peak, 4), "traffic": ncu_traffic("workload_finest_launch"),
                          "kernel": "k_level (finest level: wall function + SA-neg + stream-collide)", "peak_kind": peak_kind,
                          "bytes_per_launch": int(act_fin * bpn), "avg_launch_ms": round(avg_ms, 5),
                          "share_of_step": round(fin["ms"] / total_kt, 3) if total_kt > 0 else None},
@@ -333,7 +353,7 @@ def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096, turbulence=1):
     s.close()
     ach = bpl / (avg * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-            "kernel": "k_level", "grid": f"{n}x{n} periodic, 1 level, SA {'on' if turbulence else 'off'}",
+            "traffic": ncu_traffic("hbm_grid_launch") if turbulence else None, "kernel": "k_level", "grid": f"{n}x{n} periodic, 1 level, SA {'on' if turbulence else 'off'}",
             "bytes_per_launch": int(bpl),
             "avg_launch_ms": round(avg, 4), "mlups": round(info["cells_active"][0] / avg / 1e3, 1),
             "peak_kind": peak_kind}
