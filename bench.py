@@ -174,6 +174,21 @@ def reference_arm(args, rank, world):
     return 0
 
 
+# --------------------------------------------------------------------------- replicas
+
+def replica_totals(ms, units, dist, device):
+    """Whole-job timing of independent replicas: the slowest rank's time and the sum of
+    the node updates of all ranks (no collective touches the solver's data)."""
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def gpu_arm(args, rank, world, dist):
@@ -222,11 +237,8 @@ def gpu_arm(args, rank, world, dist):
     clk = clocks.stop()
     s.synchronize()          # status word: non-finite fields raise here
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nu_step * K * world / (ms * 1e-3) / 1e6
+    ms, units = replica_totals(ms, nu_step * K, dist, dev)
+    value = units / (ms * 1e-3) / 1e6
 
     # dominant kernel: per-launch CUDA events on the solver stream over the same workload
     kt = s.time_kernels(max(2, min(10, K)))

@@ -136,6 +136,12 @@ lbm_status lbm_get_level_box(lbm_solver *s, int level, int *i0, int *j0, int *nx
 lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, double *uy,
                           double *nu_tilde_ratio, unsigned char *mask, int cap);
 
+/* Copy a level's populations f_i (eq 1, index i = 0..8 in the order of eq 2) to the host:
+ * pop[i * nx * ny + (j - j0) * nx + (i - i0)] over the box of lbm_get_level_box, the
+ * post-collision values the next step streams.  Cells without populations of their own
+ * (absent, solid, covered) hold NaN.  cap: element capacity (>= 9 nx ny). */
+lbm_status lbm_get_populations(lbm_solver *s, int level, double *pop, long long cap);
+
 /* Set the macroscopic fields of the active fluid cells of a level (NULL = keep) and
  * reset their populations to the equilibrium of eq 4; the interfaces are re-synchronised
  * (restriction, explosion, ghost reconstruction).  Arrays as in lbm_get_fields. */

@@ -78,6 +78,9 @@ def lib():
             L.oracle_get_wall_records.argtypes = [C.c_void_p, ip, dp, ip, C.c_int, ip]
             L.oracle_get_wall_state.argtypes = [C.c_void_p, dp, C.c_int, ip]
             L.oracle_get_wall_distance.argtypes = [C.c_void_p, C.c_int, dp, C.c_int]
+            L.oracle_set_walls.argtypes = [C.c_void_p, dp, ip, C.c_int]
+            L.oracle_probe_cells.argtypes = [C.c_void_p, C.c_int, ip, C.c_int, C.c_void_p, C.c_void_p, dp]
+            L.oracle_probe_links.argtypes = [C.c_void_p, ip, C.c_int, dp]
             L.oracle_mass.argtypes = [C.c_void_p]
             L.oracle_mass.restype = C.c_double
             L.oracle_wf_uplus.argtypes = [C.c_double]
@@ -190,6 +193,32 @@ class Solver:
         off[1:] = np.cumsum([len(p) for p in loops])
         self._check(self._lib.oracle_set_geometry(self._h, _dp(xy), _ip(off), len(loops)))
         self.n_loops = len(loops)
+
+    def set_walls(self, loops):
+        """Snap the wall polylines without building the levels (for the point probes)."""
+        xy = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64) for p in loops])
+                                  if loops else np.zeros((0, 2)))
+        off = np.zeros(len(loops) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([len(p) for p in loops])
+        self._check(self._lib.oracle_set_walls(self._h, _dp(xy), _ip(off), len(loops)))
+
+    def probe_cells(self, level, ij):
+        """solid flag, refinement test of level + 1, and wall distance of level cells ij (n, 2)."""
+        ij = np.ascontiguousarray(ij, dtype=np.int32)
+        n = len(ij)
+        solid = np.zeros(n, dtype=np.uint8)
+        near = np.zeros(n, dtype=np.uint8)
+        dist = np.zeros(n)
+        self._check(self._lib.oracle_probe_cells(self._h, level, _ip(ij), n, solid.ctypes.data_as(C.c_void_p),
+                                                 near.ctypes.data_as(C.c_void_p), _dp(dist)))
+        return solid, near, dist
+
+    def probe_links(self, ijd):
+        """wall fraction q of finest-level links ijd (n, 3) = (i, j, pulled direction)."""
+        ijd = np.ascontiguousarray(ijd, dtype=np.int32)
+        q = np.zeros(len(ijd))
+        self._check(self._lib.oracle_probe_links(self._h, _ip(ijd), len(ijd), _dp(q)))
+        return q
 
     def set_wall_slip(self, uw):
         uw = np.ascontiguousarray(uw, dtype=np.float64).reshape(-1)

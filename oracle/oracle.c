@@ -608,10 +608,9 @@ static int alloc_level(olevel *L, int i0, int j0, int nx, int ny)
 
 static void init_state(oracle_solver *s);
 
-int oracle_set_geometry(oracle_solver *s, const double *xy, const int *loop_off, int nloops)
+/* the wall polylines: vertices snapped to the fixed-point grid, segments of non-zero length */
+static int setup_walls(oracle_solver *s, const double *xy, const int *loop_off, int nloops)
 {
-    if (!s || (nloops > 0 && (!xy || !loop_off)) || nloops < 0) return -1;
-    free_geometry(s);
     const oracle_config *c = &s->cfg;
     const int L = s->L;
     double hfin = c->h0 / (double)(1LL << (L - 1));
@@ -651,6 +650,17 @@ int oracle_set_geometry(oracle_solver *s, const double *xy, const int *loop_off,
         if (area2 == 0 || nl < 3) return fail(s, -5, "degenerate loop");
         s->loop_ccw[lp] = area2 > 0;
     }
+    return 0;
+}
+
+int oracle_set_geometry(oracle_solver *s, const double *xy, const int *loop_off, int nloops)
+{
+    if (!s || (nloops > 0 && (!xy || !loop_off)) || nloops < 0) return -1;
+    free_geometry(s);
+    const oracle_config *c = &s->cfg;
+    const int L = s->L;
+    int rc = setup_walls(s, xy, loop_off, nloops);
+    if (rc) return rc;
     /* level 0: every cell of the box is present and active */
     olevel *lv = s->lv;
     for (int l = 0; l < L; l++) lv[l].scale = 1LL << (L - 1 - l);
@@ -1255,6 +1265,65 @@ int oracle_step(oracle_solver *s, int n)
         for (long k = 0; k < m; k++)
             if (P->kind[k] == K_ACTIVE && !P->solid[k] && !(isfinite(P->rho[k]) && isfinite(P->ux[k])))
                 return fail(s, -6, "diverged (non-finite field)");
+    }
+    return 0;
+}
+
+/* ===========================================================================
+ * Point probes of the geometry predicates (for sampled checks of grids too large
+ * to build here): the walls only, no levels
+ * ========================================================================= */
+
+int oracle_set_walls(oracle_solver *s, const double *xy, const int *loop_off, int nloops)
+{
+    if (!s || (nloops > 0 && (!xy || !loop_off)) || nloops < 0) return -1;
+    free_geometry(s);
+    return setup_walls(s, xy, loop_off, nloops);
+}
+
+/* For level-l cells (ij[2k], ij[2k+1]): solid (centre inside or on a loop), near (centre
+ * within R_{l+1} of a wall, the refinement test of level l+1; 0 on the finest level) and
+ * the exact distance to the nearest segment in level-l lattice units. */
+int oracle_probe_cells(const oracle_solver *s, int level, const int *ij, int n, unsigned char *solid,
+                       unsigned char *near, double *dist)
+{
+    if (!s || level < 0 || level >= s->L || n < 0) return -1;
+    const oracle_config *c = &s->cfg;
+    const int L = s->L;
+    olevel P;
+    memset(&P, 0, sizeof P);
+    P.scale = 1LL << (L - 1 - level);
+    long long R = 0;
+    if (level < L - 1) {
+        R = (long long)c->layers * FIX_ONE;
+        for (int m = L - 2; m >= level + 1; m--) R += (long long)c->layers * (1LL << (L - 1 - m)) * FIX_ONE;
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < n; k++) {
+        ipt p = centre_fix(&P, ij[2 * k], ij[2 * k + 1]);
+        if (solid) solid[k] = (unsigned char)point_solid(s, p);
+        if (near) near[k] = (unsigned char)(level < L - 1 ? near_wall(s, p, R) : 0);
+        if (dist) {
+            double px = (ij[2 * k] + 0.5) * P.scale, py = (ij[2 * k + 1] + 0.5) * P.scale;
+            dist[k] = wall_distance(s, px, py, NULL, NULL, NULL) / (double)P.scale;
+        }
+    }
+    return 0;
+}
+
+/* wall fraction q of eq 27 for finest-level links (ijd[3k], ijd[3k+1]) -> pulled direction ijd[3k+2] */
+int oracle_probe_links(const oracle_solver *s, const int *ijd, int n, double *q)
+{
+    if (!s || n < 0) return -1;
+    olevel F;
+    memset(&F, 0, sizeof F);
+    F.scale = 1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < n; k++) {
+        int d = ijd[3 * k + 2];
+        ipt pb = centre_fix(&F, ijd[3 * k], ijd[3 * k + 1]);
+        ipt dv = {-CX[d] * FIX_ONE, -CY[d] * FIX_ONE};
+        q[k] = link_fraction(s, pb, dv);
     }
     return 0;
 }

@@ -59,6 +59,11 @@ int  oracle_get_wall_records(const oracle_solver *s, int *ij, double *geo, int *
 int  oracle_get_wall_state(oracle_solver *s, double *state, int cap, int *n);
 int  oracle_get_wall_distance(const oracle_solver *s, int level, double *d, int cap);
 double oracle_mass(const oracle_solver *s);
+/* point probes of the geometry predicates, for sampled checks of large grids */
+int  oracle_set_walls(oracle_solver *s, const double *xy, const int *loop_offsets, int n_loops);
+int  oracle_probe_cells(const oracle_solver *s, int level, const int *ij, int n, unsigned char *solid,
+                        unsigned char *near, double *dist);
+int  oracle_probe_links(const oracle_solver *s, const int *ijd, int n, double *q);
 int  oracle_threads(void);
 
 /* building blocks exported for the closed-form pins */

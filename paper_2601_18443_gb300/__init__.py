@@ -84,6 +84,7 @@ def library():
         "lbm_get_level_box": ([vp, C.c_int, ip, ip, ip, ip], C.c_int),
         "lbm_get_fields": ([vp, C.c_int, dp, dp, dp, dp, vp, C.c_int], C.c_int),
         "lbm_set_fields": ([vp, C.c_int, dp, dp, dp, dp], C.c_int),
+        "lbm_get_populations": ([vp, C.c_int, dp, C.c_longlong], C.c_int),
         "lbm_get_loads": ([vp, C.POINTER(lbm_loads), dp, dp, C.c_int, ip], C.c_int),
         "lbm_get_cut_links": ([vp, ip, dp, C.c_int, ip], C.c_int),
         "lbm_get_wall_records": ([vp, ip, dp, ip, C.c_int, ip], C.c_int),
@@ -197,6 +198,13 @@ class Solver:
         self._check(self._lib.lbm_get_fields(self._h, level, _dp(rho), _dp(ux), _dp(uy), _dp(chi),
                                              mask.ctypes.data_as(C.c_void_p), nx * ny))
         return dict(rho=rho, ux=ux, uy=uy, chi=chi, mask=mask, i0=i0, j0=j0)
+
+    def get_populations(self, level):
+        """Populations f_i of a level's box as an array (9, ny, nx); NaN where a cell has none."""
+        i0, j0, nx, ny = self.level_box(level)
+        pop = np.zeros((9, ny, nx))
+        self._check(self._lib.lbm_get_populations(self._h, level, _dp(pop), pop.size))
+        return pop
 
     def set_fields(self, level, rho=None, ux=None, uy=None, chi=None):
         i0, j0, nx, ny = self.level_box(level)

@@ -610,6 +610,41 @@ lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, dou
     return LBM_OK;
 }
 
+// one stored population of a host copy of a lattice, as f - w (storage shift undone)
+static double get_pop(int store, const unsigned char *base, size_t idx)
+{
+    if (store == 1) return (double)__half2float(reinterpret_cast<const __half *>(base)[idx]);
+    if (store == 2) return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[idx]);
+    return (double)reinterpret_cast<const float *>(base)[idx];
+}
+
+lbm_status lbm_get_populations(lbm_solver *s, int level, double *pop, long long cap)
+{
+    int i0, j0, nx, ny;
+    lbm_status st = lbm_get_level_box(s, level, &i0, &j0, &nx, &ny);
+    if (st != LBM_OK) return st;
+    const long long ncell = (long long)nx * ny;
+    if (!pop || 9 * ncell > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    const LevelView &v = s->lv[level].v;
+    const size_t pb = pop_bytes(s->cfg.store);
+    std::vector<unsigned char> f(9 * (size_t)v.ns * pb);
+    CK(cudaMemcpyAsync(f.data(), v.f[s->parity[level]], f.size(), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const lbmgrid::Level &G = s->g.lv[level];
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            const long b = G.idx(i0 + i, j0 + j);
+            const long sl = G.slot(i0 + i, j0 + j);
+            const unsigned char m = mask_of(G, b);
+            const bool has = sl >= 0 && (m == 1 || m == 2 || m == 4);
+            for (int q = 0; q < 9; q++) {
+                const double g = has ? get_pop(s->cfg.store, f.data(), (size_t)q * v.ns + sl) + s->k.pshift[q] : NAN;
+                pop[q * ncell + (long long)j * nx + i] = has ? g + WQh[q] : NAN;
+            }
+        }
+    return LBM_OK;
+}
+
 lbm_status lbm_get_wall_distance(lbm_solver *s, int level, double *d, int cap)
 {
     int i0, j0, nx, ny;

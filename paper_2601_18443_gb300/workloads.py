@@ -109,3 +109,47 @@ def noise_field(shape, amplitude, seed):
     """Seeded uniform noise in [-amplitude, amplitude]."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-amplitude, amplitude, size=shape)
+
+
+def highlift_loops(h_finest, alpha_deg=8.0, gap=0.02, overlap=0.02):
+    """Synthetic three-element high-lift section (chord c = 1 of the main element):
+    slat NACA 2412 of chord 0.15 deflected 30 deg nose-down, main NACA 4412, flap NACA
+    2412 of chord 0.3 deflected 30 deg trailing-edge-down, the whole set rotated to
+    alpha about the main element's quarter chord.
+
+    Placement: the slat trailing edge sits `overlap` aft of the main leading edge and
+    `gap` above the main upper surface there; the flap leading edge sits `overlap` ahead
+    of the main trailing edge and `gap` below the main trailing edge plus the flap's
+    own half-thickness near its nose (so that the slot is about `gap` wide)."""
+    main = naca_loop("4412", h_finest)
+    # slat: rotate about its own trailing edge, then move that edge to its station
+    slat = naca_loop("2412", h_finest / 0.15, chord=1.0) * 0.15
+    slat = transform(slat, 1.0, -30.0, pivot=(slat[0, 0], slat[0, 1]))
+    xs = overlap
+    m, p, t = 0.04, 0.4, 0.12
+    yt = 5 * t * (0.2969 * xs**0.5 - 0.1260 * xs - 0.3516 * xs**2 + 0.2843 * xs**3 - 0.1036 * xs**4)
+    yc = m / p**2 * (2 * p * xs - xs**2)
+    slat = slat + (np.array([xs, yc + yt + gap]) - slat[0])
+    # flap: rotate about its own leading edge, then move that edge to its station
+    flap = naca_loop("2412", h_finest / 0.3, chord=1.0) * 0.3
+    le = flap[np.argmin(flap[:, 0])]
+    flap = transform(flap, 1.0, 30.0, pivot=(le[0], le[1]))
+    le = flap[np.argmin(flap[:, 0])]
+    half = 0.3 * 0.12 * 0.5
+    flap = flap + (np.array([1.0 - overlap, -gap - half]) - le)
+    loops = [slat, main, flap]
+    return [transform(lp, 1.0, alpha_deg) for lp in loops]
+
+
+def highlift_3element(levels=8, layers=128, box=(16.0, 8.0), h0=1.0 / 64.0):
+    """Synthetic three-element high-lift case: alpha 8 deg, Re 9e6, Ma 0.2, SA-neg, the
+    virtual-node wall function; `levels` 2:1 levels from h0 (finest h0 / 2^(levels-1)).
+    Defaults: 8 levels from c/64 to c/8192 over a 16c x 8c box, 128 cells per band:
+    7.46M active nodes, 555M node updates per coarse step."""
+    nx0, ny0 = int(round(box[0] / h0)), int(round(box[1] / h0))
+    nx0 -= nx0 % 32
+    ny0 -= ny0 % 8
+    cfg = base_config(levels=levels, nx0=nx0, ny0=ny0, x0=-0.35 * box[0], y0=-0.5 * box[1], h0=h0, layers=layers,
+                      chord=1.0, Re=9.0e6, Ma=0.2, turbulence=1, wall_model=0, periodic=0, solid_walls=1)
+    hf = h0 / 2 ** (levels - 1)
+    return cfg, highlift_loops(hf)

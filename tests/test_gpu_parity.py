@@ -376,3 +376,21 @@ def test_paper_variants_on_the_turbulent_airfoil(name):
     lg, lr = g.get_loads(), r.get_loads()
     for key in ("CL", "CD"):
         assert abs(lg[key] - lr[key]) <= TOL_LOADS * abs(lr[key]), (key, lg[key], lr[key])
+
+
+def test_three_element_high_lift_at_oracle_size():
+    # the synthetic three-element section (slat, main, flap: three wall loops with 0.02c
+    # slots) on 4 levels to c/512 over a 4c x 2c box: grid tables bit-exact, fields and
+    # loads after 10 coarse steps
+    cfg, loops = W.highlift_3element(levels=4, layers=16, box=(4.0, 2.0), h0=1.0 / 64.0)
+    g, r = pair(cfg, loops)
+    for l in range(cfg["levels"]):
+        assert np.array_equal(g.get_fields(l)["mask"], r.get_fields(l)["mask"])
+    ijd_g, q_g = g.cut_links()
+    ijd_r, q_r = r.cut_links()
+    assert np.array_equal(ijd_g, ijd_r) and np.array_equal(q_g, q_r)
+    g.step(10); r.step(10)
+    assert_fields(g, r, cfg["levels"])
+    lg, lr = g.get_loads(), r.get_loads()
+    for key in ("CL", "CD"):
+        assert abs(lg[key] - lr[key]) <= TOL_LOADS * abs(lr[key]), (key, lg[key], lr[key])

@@ -190,3 +190,31 @@ def test_coincident_vertices_are_merged():
     assert len(la["cp"]) == len(lb["cp"]) == 4
     for key in ("CL", "CD", "CDp", "CDf"):
         assert np.isfinite(lb[key]) and lb[key] == la[key]
+
+
+def test_point_probes_agree_with_the_built_grid():
+    # the probes serve sampled checks of grids too large to build; on a small grid they must
+    # reproduce the full build: solid flags, refinement of level l+1 (covered cells), wall
+    # distances and cut-link fractions
+    cfg, loops = W.naca0012_small(levels=4)
+    full = oracle.Solver(cfg)
+    full.set_geometry(loops)
+    probe = oracle.Solver(cfg)
+    probe.set_walls(loops)
+    for l in range(cfg["levels"]):
+        F = full.get_fields(l)
+        m = F["mask"]
+        jj, ii = np.nonzero(m > 0)
+        ij = np.stack([ii + F["i0"], jj + F["j0"]], axis=1)
+        solid, near, dist = probe.probe_cells(l, ij)
+        assert np.array_equal(solid.astype(bool), m[jj, ii] == 5)
+        if l < cfg["levels"] - 1:
+            # among the fluid cells that are not ghosts (which never refine), the covered ones
+            # are exactly those within R_{l+1} of a wall
+            sel = np.isin(m[jj, ii], (1, 2, 3))
+            assert np.array_equal(near.astype(bool)[sel], m[jj, ii][sel] == 3)
+        d = full.wall_distance(l)[jj, ii]
+        fin = np.isfinite(d)
+        assert np.array_equal(d[fin], dist[fin])
+    ijd, q = full.cut_links()
+    assert np.array_equal(probe.probe_links(ijd), q)
