@@ -110,6 +110,23 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out);
  * LBM_ERR_OOM, LBM_ERR_CUDA. */
 lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_offsets, int n_loops);
 
+/* Memory plan of a geometry without a GPU: builds the grid on the host exactly as
+ * lbm_set_geometry does and reports the device bytes a solver would hold (allocations
+ * rounded to 256 bytes) and the active cells per level.  No CUDA call is made; all
+ * arguments are host memory.  Used to admit solves against a device-memory budget.
+ * Errors: as lbm_create and lbm_set_geometry (LBM_ERR_INVALID_ARG, LBM_ERR_GEOMETRY);
+ * on error, reason holds the message lbm_last_error would give (NUL-terminated). */
+typedef struct {
+    int levels;
+    long long cells_active[16];     /* active fluid cells per level                     */
+    long long node_updates_per_step;/* sum over levels of cells_active[l] * 2^l         */
+    long long wall_records;         /* boundary nodes of the finest level               */
+    double device_bytes;            /* device memory the solver would allocate           */
+    char reason[128];               /* error message, empty on success                  */
+} lbm_plan;
+lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int *loop_offsets, int n_loops,
+                             lbm_plan *out);
+
 /* Prescribed wall slip velocity per loop for wall_model 2 (lattice units): uw_xy holds
  * 2 * n_loops doubles.  Errors: LBM_ERR_INVALID_ARG, LBM_ERR_NO_GEOMETRY. */
 lbm_status lbm_set_wall_slip(lbm_solver *s, const double *uw_xy, int n_loops);

@@ -56,6 +56,11 @@ class lbm_info(C.Structure):
                 ("device_bytes", C.c_double)]
 
 
+class lbm_plan(C.Structure):
+    _fields_ = [("levels", C.c_int), ("cells_active", C.c_longlong * 16), ("node_updates_per_step", C.c_longlong),
+                ("wall_records", C.c_longlong), ("device_bytes", C.c_double), ("reason", C.c_char * 128)]
+
+
 class lbm_kernel_times(C.Structure):
     _fields_ = [("n_classes", C.c_int), ("name", (C.c_char * 32) * 8), ("total_ms", C.c_double * 8),
                 ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
@@ -78,6 +83,7 @@ def library():
         "lbm_create": ([C.POINTER(lbm_config), C.POINTER(vp)], C.c_int),
         "lbm_set_geometry": ([vp, dp, ip, C.c_int], C.c_int),
         "lbm_set_wall_slip": ([vp, dp, C.c_int], C.c_int),
+        "lbm_plan_geometry": ([C.POINTER(lbm_config), dp, ip, C.c_int, C.POINTER(lbm_plan)], C.c_int),
         "lbm_step": ([vp, C.c_int], C.c_int),
         "lbm_step_async": ([vp, C.c_int], C.c_int),
         "lbm_synchronize": ([vp], C.c_int),
@@ -110,6 +116,36 @@ def _dp(a):
 
 def _ip(a):
     return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _config_struct(cfg):
+    c = lbm_config()
+    for name, _ in lbm_config._fields_:
+        if name in ("cuda_stream", "dev_alloc", "dev_free", "alloc_ctx"):
+            continue
+        setattr(c, name, cfg.get(name, 0))
+    return c
+
+
+def _loops_arrays(loops):
+    xy = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64) for p in loops])
+                              if loops else np.zeros((0, 2)))
+    off = np.zeros(len(loops) + 1, dtype=np.int32)
+    off[1:] = np.cumsum([len(p) for p in loops])
+    return xy, off
+
+
+def plan(cfg: dict, loops) -> dict:
+    """lbm_plan_geometry: device bytes and active cells of a solve, without a GPU."""
+    c = _config_struct(cfg)
+    xy, off = _loops_arrays(loops)
+    out = lbm_plan()
+    rc = library().lbm_plan_geometry(C.byref(c), _dp(xy), _ip(off), len(loops), C.byref(out))
+    if rc != 0:
+        raise LBMError(rc, "lbm_plan_geometry: " + out.reason.decode())
+    L = out.levels
+    return dict(levels=L, cells_active=list(out.cells_active[:L]), node_updates_per_step=out.node_updates_per_step,
+                wall_records=out.wall_records, device_bytes=out.device_bytes)
 
 
 class Solver:

@@ -111,6 +111,9 @@ struct lbm_solver {
     bool have_cl = false;
     long long kernels_per_step = 0;
     int n_loops = 0;
+    // memory plan (lbm_plan_geometry): allocations are counted, not made
+    bool planning = false;
+    size_t plan_cursor = 1 << 20;
     // eager timing (lbm_time_kernels)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -139,6 +142,14 @@ static lbm_status cuda_fail(lbm_solver *s, cudaError_t e, const char *where)
 static void *dalloc(lbm_solver *s, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
+    if (s->planning) {
+        // memory plan only: count the bytes (rounded as cudaMalloc aligns them), hand back
+        // a distinct placeholder that is never dereferenced
+        bytes = (bytes + 255) & ~(size_t)255;
+        s->device_bytes += (double)bytes;
+        s->plan_cursor += bytes;
+        return (void *)(uintptr_t)s->plan_cursor;
+    }
     void *p = nullptr;
     if (s->cfg.dev_alloc) {
         p = s->cfg.dev_alloc(bytes, (void *)s->stream, s->cfg.alloc_ctx);
@@ -151,12 +162,17 @@ static void *dalloc(lbm_solver *s, size_t bytes)
         if (s->cfg.dev_free) s->cfg.dev_free(p, (void *)s->stream, s->cfg.alloc_ctx);
         return nullptr;
     }
-    if (p) { s->allocs.push_back(p); s->device_bytes += (double)bytes; }
+    if (p) { s->allocs.push_back(p); s->device_bytes += (double)((bytes + 255) & ~(size_t)255); }
     return p;
 }
 
 static void free_all(lbm_solver *s)
 {
+    if (s->planning) {
+        s->device_bytes = 0;
+        s->plan_cursor = 1 << 20;
+        return;
+    }
     for (int b = 0; b < 2; b++)
         if (s->graph[b]) { cudaGraphExecDestroy(s->graph[b]); s->graph[b] = nullptr; }
     if (s->stream) cudaStreamSynchronize(s->stream);
@@ -176,7 +192,7 @@ static T *upload(lbm_solver *s, const std::vector<T> &h, bool &ok)
 {
     T *d = (T *)dalloc(s, h.size() * sizeof(T));
     if (!d) { ok = false; return nullptr; }
-    if (!h.empty() && cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    if (!s->planning && !h.empty() && cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
         ok = false;
     return d;
 }
@@ -294,16 +310,20 @@ static lbm_status check_status(lbm_solver *s)
 // ---------------------------------------------------------------- API
 extern "C" {
 
+static bool config_ok(const lbm_config *cfg)
+{
+    return !(cfg->levels < 1 || cfg->levels > LBM_MAXL || cfg->nx0 < 4 || cfg->ny0 < 4 || !(cfg->h0 > 0) ||
+        cfg->layers < 3 || !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->chord > 0) || cfg->store < 0 || cfg->store > 2 ||
+        (cfg->periodic && (cfg->nx0 % LBM_TX || cfg->ny0 % LBM_TY)) || (!cfg->periodic && (cfg->nx0 < 8)) ||
+        cfg->wall_model < 0 || cfg->wall_model > 3 || cfg->sa_convection < 0 || cfg->sa_convection > 1 ||
+        (!cfg->dev_alloc != !cfg->dev_free));
+}
+
 lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
 {
     if (!cfg || !out) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
-    if (cfg->levels < 1 || cfg->levels > LBM_MAXL || cfg->nx0 < 4 || cfg->ny0 < 4 || !(cfg->h0 > 0) ||
-        cfg->layers < 3 || !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->chord > 0) || cfg->store < 0 || cfg->store > 2 ||
-        (cfg->periodic && (cfg->nx0 % LBM_TX || cfg->ny0 % LBM_TY)) || (!cfg->periodic && (cfg->nx0 < 8)) ||
-        cfg->wall_model < 0 || cfg->wall_model > 3 || cfg->sa_convection < 0 || cfg->sa_convection > 1 ||
-        (!cfg->dev_alloc != !cfg->dev_free))
-        return LBM_ERR_INVALID_ARG;
+    if (!config_ok(cfg)) return LBM_ERR_INVALID_ARG;
     lbm_solver *s = new (std::nothrow) lbm_solver();
     if (!s) return LBM_ERR_OOM;
     s->cfg = *cfg;
@@ -448,8 +468,10 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         float **outs[9] = {&v.drhoW, &v.uWx, &v.uWy, &v.utau, &v.chiB, &v.tx, &v.ty, &v.ut, &v.utau_start};
         for (auto o : outs) { *o = (float *)dalloc(s, (size_t)std::max(nr, 1) * sizeof(float)); ok = ok && *o; }
         if (!ok || !s->d_slip) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
-        CK(cudaMemsetAsync(s->d_slip, 0, 2 * (size_t)std::max(n_loops, 1) * sizeof(float), s->stream));
-        for (auto o : outs) CK(cudaMemsetAsync(*o, 0, (size_t)std::max(nr, 1) * sizeof(float), s->stream));
+        if (!s->planning) {
+            CK(cudaMemsetAsync(s->d_slip, 0, 2 * (size_t)std::max(n_loops, 1) * sizeof(float), s->stream));
+            for (auto o : outs) CK(cudaMemsetAsync(*o, 0, (size_t)std::max(nr, 1) * sizeof(float), s->stream));
+        }
     }
     // surface segments for the loads
     {
@@ -482,6 +504,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     s->d_status = (int *)dalloc(s, 16);
     s->d_acc = (double *)dalloc(s, 8 * sizeof(double));
     if (!s->d_status || !s->d_acc) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
+    if (s->planning) return LBM_OK;
     CK(cudaMemsetAsync(s->d_status, 0, 16, s->stream));
     // constants and initial state: equilibrium of rho = 1, u = (U, 0), chi = chi_inf
     s->k.level0_edges = !c.periodic;
@@ -510,6 +533,39 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     s->n_loops = n_loops;
     s->geometry = true;
     return LBM_OK;
+}
+
+lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int *loop_offsets, int n_loops,
+                             lbm_plan *out)
+{
+    if (!cfg || !out) return LBM_ERR_INVALID_ARG;
+    if (!config_ok(cfg)) return LBM_ERR_INVALID_ARG;
+    lbm_solver *s = new (std::nothrow) lbm_solver();
+    if (!s) return LBM_ERR_OOM;
+    s->cfg = *cfg;
+    s->L = cfg->levels;
+    s->U = cfg->Ma * std::sqrt(1.0 / 3.0);
+    s->planning = true;
+    lbm_status st = lbm_set_geometry(s, xy, loop_offsets, n_loops);
+    std::memset(out, 0, sizeof *out);
+    if (st != LBM_OK) std::snprintf(out->reason, sizeof out->reason, "%s", s->err.c_str());
+    if (st == LBM_OK) {
+        out->levels = s->L;
+        out->device_bytes = s->device_bytes;
+        long long nu = 0;
+        for (int l = 0; l < s->L; l++) {
+            const lbmgrid::Level &G = s->g.lv[l];
+            long long act = 0;
+            for (size_t b = 0; b < G.kind.size(); b++)
+                if (G.kind[b] == KIND_ACTIVE && !G.solid[b]) act++;
+            out->cells_active[l] = act;
+            nu += act << l;
+        }
+        out->node_updates_per_step = nu;
+        out->wall_records = (long long)s->g.recs.size();
+    }
+    delete s;
+    return st;
 }
 
 lbm_status lbm_set_wall_slip(lbm_solver *s, const double *uw, int n_loops)

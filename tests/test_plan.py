@@ -1,0 +1,40 @@
+"""lbm_plan_geometry runs the host grid build without a GPU: its active-cell counts
+equal the oracle's, and its memory plan grows with the grid."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2601_18443_gb300 as pkg
+from paper_2601_18443_gb300 import workloads as W
+
+
+def test_plan_counts_match_the_oracle():
+    pkg.build()
+    cfg, loops = __import__("__graft_entry__").smoke_case()
+    p = pkg.plan(cfg, loops)
+    r = oracle.Solver(cfg)
+    r.set_geometry(loops)
+    for l in range(cfg["levels"]):
+        m = r.get_fields(l)["mask"]
+        assert p["cells_active"][l] == int(((m == 1) | (m == 2)).sum())
+    assert p["node_updates_per_step"] == sum(n << l for l, n in enumerate(p["cells_active"]))
+    assert p["wall_records"] == len(r.wall_records()[0])
+    assert p["device_bytes"] > 0
+
+
+def test_plan_memory_grows_with_the_grid_and_the_storage():
+    pkg.build()
+    small = pkg.plan(*W.naca0012_small(levels=4))
+    big = pkg.plan(*W.naca0012_small(levels=6))
+    assert big["device_bytes"] > small["device_bytes"]
+    cfg, loops = W.naca0012_small(levels=6)
+    half = pkg.plan(dict(cfg, store=1), loops)
+    assert half["device_bytes"] < big["device_bytes"]
+
+
+def test_plan_reports_geometry_errors():
+    pkg.build()
+    cfg = W.base_config(levels=3, nx0=32, ny0=32, h0=1.0, layers=3)
+    with pytest.raises(pkg.LBMError) as e:
+        pkg.plan(cfg, [W.rectangle(0.5, 0.5, 5.0, 5.0)])     # refinement reaches the box edge
+    assert e.value.code == -5 and "box edge" in str(e.value)
