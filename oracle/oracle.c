@@ -71,6 +71,12 @@ static const double WQ[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
 #define FIX_BITS 12               /* fixed-point unit = finest cell / 2^12 */
 #define FIX_ONE (1LL << FIX_BITS)
 #define D_CAP 1.0e12              /* wall distance used where there is no wall */
+/* Smallest wall distance the SA-neg terms of eqs 11-17 see at a fluid node, in lattice
+ * units of the node's level.  The paper does not treat a fluid node (no cut link) lying
+ * closer than half a spacing to the wall; that happens only beside a wall sliver thinner
+ * than the lattice (a sharp trailing edge passing between nodes), where d -> 0 makes the
+ * explicit destruction rate 2 c_w1 nu~ / d^2 exceed one per step. */
+#define SA_D_MIN 0.5
 
 enum { K_ABSENT = 0, K_ACTIVE = 1, K_COVERED = 2, K_GHOST = 3 };
 
@@ -1083,7 +1089,7 @@ static void sa_level(oracle_solver *s, int l)
                 if (kn < 0 || P->kind[kn] == K_ABSENT) { kn = k; sgn = 1.0; }   /* never taken on a valid grid */
                 ch[q] = P->chi[kn]; u[q] = P->ux[kn]; v[q] = sgn * P->uy[kn];
             }
-            P->chin[k] = oracle_sa_update_point(ch, u, v, P->d[k], P->nu, c->sa_convection);
+            P->chin[k] = oracle_sa_update_point(ch, u, v, fmax(P->d[k], SA_D_MIN), P->nu, c->sa_convection);
         }
     if (edge) {
         for (int j = 0; j < c->ny0; j++) {

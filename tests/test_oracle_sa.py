@@ -152,3 +152,53 @@ def test_sa_update_uses_the_requested_convection():
     up = oracle.sa_update_point(chi, u9, v9, FAR, nu, 1)
     assert lw - 3.0 == pytest.approx(0.5 * 0.01 * 0.4, rel=1e-9)
     assert up - 3.0 == pytest.approx(-0.1 * (0.0 - 0.2), rel=1e-9)
+
+
+def _sliver_case():
+    """Periodic 32 x 32 box (one level) with a wall sliver 0.004 cells thick lying 0.003-0.007
+    cells above the row of cell centres y = 16.5: no centre is inside it, so no link is cut and
+    the sixteen nodes beside it are plain fluid nodes at d < 1/2 from the wall."""
+    from paper_2601_18443_gb300 import workloads as W
+
+    cfg = W.base_config(levels=1, nx0=32, ny0=32, periodic=1, solid_walls=1, turbulence=1, wall_model=0, Re=100.0)
+    sliver = np.array([[8.0, 16.505], [24.0, 16.503], [24.0, 16.507]])
+    return cfg, [sliver]
+
+
+def test_sa_sees_at_least_half_a_spacing_of_wall_distance():
+    # From a uniform state the first SA-neg update of every node is the point update of a
+    # uniform stencil; beside the sliver it must be taken at d = 1/2, elsewhere at the node's d
+    cfg, loops = _sliver_case()
+    r = oracle.Solver(cfg)
+    r.set_geometry(loops)
+    assert len(r.cut_links()[0]) == 0
+    d = r.wall_distance(0)
+    f0 = r.get_fields(0)
+    U = f0["ux"][0, 0]
+    assert np.all(f0["chi"] == 3.0) and np.all(f0["ux"] == U) and np.all(f0["uy"] == 0.0)
+    nu = cfg["Ma"] * math.sqrt(1.0 / 3.0) / cfg["Re"]
+    r.step(1)
+    chi1 = r.get_fields(0)["chi"]
+    ch, u, v = np.full(9, 3.0), np.full(9, U), np.zeros(9)
+    near = d < 0.5
+    assert near.sum() == 16
+    for j, i in zip(*np.nonzero(np.ones_like(d, dtype=bool))):
+        want = oracle.sa_update_point(ch, u, v, max(d[j, i], 0.5), nu)
+        assert chi1[j, i] == pytest.approx(want, rel=1e-14, abs=1e-14)
+    # the update at the true distance would have driven nu~ far below zero in one step
+    j, i = np.argwhere(near)[0]
+    assert oracle.sa_update_point(ch, u, v, d[j, i], nu) < -100.0
+    assert chi1[near].min() > 2.5
+
+
+def test_sliver_run_stays_finite_and_the_flow_uniform():
+    # no cut links: the populations stay at the uniform equilibrium whatever nu_t does, and
+    # nu~ stays bounded beside the sliver over many steps
+    cfg, loops = _sliver_case()
+    r = oracle.Solver(cfg)
+    r.set_geometry(loops)
+    r.step(300)
+    f = r.get_fields(0)
+    assert np.all(np.isfinite(f["chi"]))
+    assert np.abs(f["ux"] - f["ux"][0, 0]).max() < 1e-15 and np.abs(f["uy"]).max() < 1e-15
+    assert f["chi"].min() > 0.0 and f["chi"].max() <= 3.0 + 1e-12
