@@ -1208,14 +1208,16 @@ static void stream_collide_level(oracle_solver *s, int l)
                     out[7] = out[8] + 0.5 * (out[3] - out[4]) + rho * U / 6.0;
                 }
             }
-        /* outlet (Yu): f_q(N-1) = 2 f_q(N-2) - f_q(N-3) for q = 2, 6, 8 (post-stream values) */
+        /* outlet: zero-gradient extrapolation f_q(N-1) = f_q(N-2) for q = 2, 6, 8 (post-stream
+         * values).  The linear form 2 f_q(N-2) - f_q(N-3) amplifies the wake's vortices as
+         * they cross the last columns and the disturbance then spreads upstream. */
         const int qs[3] = {2, 6, 8};
         for (int j = 0; j < c->ny0; j++) {
             long k = cidx(P, c->nx0 - 1, j);
             if (P->solid[k]) continue;
             for (int m = 0; m < 3; m++) {
                 int q = qs[m];
-                P->fn[9 * k + q] = 2.0 * P->fn[9 * cidx(P, c->nx0 - 2, j) + q] - P->fn[9 * cidx(P, c->nx0 - 3, j) + q];
+                P->fn[9 * k + q] = P->fn[9 * cidx(P, c->nx0 - 2, j) + q];
             }
         }
     }
