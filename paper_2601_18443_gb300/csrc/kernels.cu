@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
                 }
             }
         } else {
-            // level-0 box edge: in-box pulls, symmetry planes, Zou-He inlet, extrapolated outlet (Sec 3.1.1)
+            // level-0 box edge: in-box pulls, symmetry planes, Zou-He inlet, zero-gradient outlet (Sec 3.1.1)
             const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
 #pragma unroll
             for (int q = 1; q < 9; q++) {
@@ -588,17 +588,14 @@ __global__ void __launch_bounds__(256, 5) k_level(LevelView P, LevelView F, Leve
                 g[7] = g[8] + 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
             }
             if (i == k.nx0 - 1) {
+                // outlet: zero-gradient extrapolation, g_q(N-1) = g_q(N-2) for the pulled-in
+                // directions 2, 6, 8 (the post-stream values of the neighbour column)
 #pragma unroll
                 for (int m = 0; m < 3; m++) {
                     const int q = m == 0 ? 2 : (m == 1 ? 6 : 8);
-                    float v[2];
-#pragma unroll
-                    for (int b = 0; b < 2; b++) {
-                        const int ii = k.nx0 - 2 - b, si = ii - cxq(q), sj = j - cyq(q);
-                        v[b] = (sj >= 0 && sj < k.ny0) ? IO.ld(fc + q * ns + slot0(k, si, sj), q)
-                                                       : IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
-                    }
-                    g[q] = 2.0f * v[0] - v[1];
+                    const int si = k.nx0 - 2 - cxq(q), sj = j - cyq(q);
+                    g[q] = (sj >= 0 && sj < k.ny0) ? IO.ld(fc + q * ns + slot0(k, si, sj), q)
+                                                   : IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
                 }
             }
         }

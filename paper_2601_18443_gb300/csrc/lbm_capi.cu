@@ -398,7 +398,11 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
                 }
                 long long sl = (long long)t * LBM_TILE + c2;
                 H.flags[sl] = f;
-                inv_d2[sl] = (float)(1.0 / ((double)G.dist[b] * (double)G.dist[b]));
+                // SA-neg sees d >= 1/2 (level units): a fluid node closer to the wall than that
+                // lies beside a wall sliver thinner than the lattice (a sharp trailing edge
+                // between nodes), where d -> 0 makes the explicit destruction term unstable
+                const double dsa = G.dist[b] > 0.5 ? (double)G.dist[b] : 0.5;
+                inv_d2[sl] = (float)(1.0 / (dsa * dsa));
                 if (l == L - 1) rec[sl] = G.rec[b];
             }
         LevelView &v = H.v;

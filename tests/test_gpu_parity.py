@@ -179,6 +179,22 @@ def test_periodic_sa_random_state():
     assert_fields(g, r, 1)
 
 
+def test_sa_distance_floor_beside_a_wall_sliver():
+    # a wall sliver thinner than the lattice between two rows of nodes: no cut links, sixteen
+    # fluid nodes at d < 1/2, where SA-neg takes d = 1/2 (seeded velocity so chi varies)
+    cfg = W.base_config(levels=1, nx0=32, ny0=32, periodic=1, solid_walls=1, turbulence=1, wall_model=0, Re=100.0)
+    loops = [np.array([[8.0, 16.505], [24.0, 16.503], [24.0, 16.507]])]
+    g, r = pair(cfg, loops)
+    assert len(g.cut_links()[0]) == 0 and len(r.cut_links()[0]) == 0
+    (rho, ux, uy, chi), = seeded_fields(r, 1, 32, seed=23)
+    for s in (g, r):
+        s.set_fields(0, rho=rho, ux=ux, uy=uy, chi=chi)
+    g.step(1); r.step(1)
+    assert_fields(g, r, 1)
+    g.step(100); r.step(100)
+    assert_fields(g, r, 1)
+
+
 def _channel(qb, model, nx0=32, N=16):
     yb = 2.5 - qb
     yt = yb + N
