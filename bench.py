@@ -393,6 +393,66 @@ def profile_case(args):
     return 0
 
 
+def serving_arm(args):
+    """Continuous batching of the seeded polar-request stream (NACA 4-digit sections,
+    4..7 levels, Poisson arrivals) against the same stream served one solve at a time."""
+    import torch
+
+    import paper_2601_18443_gb300 as pkg
+    from paper_2601_18443_gb300.serve import GpuBackend, Service, SolveRequest, summarize
+
+    pkg.library()
+    torch.cuda.set_device(0)
+    rate = args.serving_rate
+    reqs = []
+    for q in W.polar_requests(args.serving, rate_per_s=rate if rate > 0 else 2.0):
+        cfg, loops = W.polar_case(q)
+        reqs.append(SolveRequest(rid=q["rid"], arrival=q["arrival"] if rate > 0 else 0.0, cfg=cfg, loops=loops,
+                                 max_steps=args.serving_max_steps, min_steps=args.serving_min_steps,
+                                 check_every=100, window=args.serving_window, tol=args.serving_tol, patience=2))
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        pass
+    out = {}
+    arms = [("batched", args.serving_slots)] + ([] if args.serving_no_baseline else [("one_at_a_time", 1)])
+    clk = None
+    for name, slots in arms:
+        clocks = ClockSampler(uuid)
+        clocks.start()
+        svc = Service(max_slots=slots, backend=GpuBackend())
+        res = svc.run(reqs)
+        c = clocks.stop()
+        if name == "batched":
+            clk = c
+        sm = summarize(res)
+        if args.serving_dump:
+            with open(f"{args.serving_dump}.{name}.json", "w") as fh:
+                json.dump([dict(rid=r.rid, status=r.status, levels=q.cfg["levels"], arrival=r.arrival,
+                                admitted=r.admitted, started=r.started, finished=r.finished, steps=r.steps,
+                                history=r.history, message=r.message) for r, q in zip(res, reqs)], fh)
+        sm["max_resident"] = max((n for *_, n in svc.trace), default=0)
+        sm["clocks"] = c
+        out[name] = sm
+        by_levels = {}
+        for r, q in zip(res, reqs):
+            by_levels.setdefault(q.cfg["levels"], []).append(r)
+        sm["by_levels"] = {L: dict(n=len(v), steps_mean=float(np.mean([r.steps for r in v])),
+                                   latency_p50_s=float(np.median([r.latency for r in v])))
+                           for L, v in sorted(by_levels.items())}
+    b = out["batched"]
+    line = {"metric": "solves_per_hour", "value": b.get("solves_per_hour"), "unit": "solves/h", "n_gpus": 1,
+            "higher_is_better": True, "impl": "ours", "dtype": "f16-store/f32",
+            "data": "synthetic", "config": {"workload": f"polar_stream_{args.serving}req_seed2026",
+                                           "rate_per_s": rate, "slots": args.serving_slots,
+                                           "max_steps": args.serving_max_steps, "min_steps": args.serving_min_steps,
+                                           "window_steps": 100 * args.serving_window, "tol_window_mean_CL": args.serving_tol},
+            "serving": out, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,9 +464,20 @@ def main():
     ap.add_argument("--no-hbm-grid", action="store_true")
     ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--profile-case", choices=["hbm_grid", "workload"], default=None)
+    ap.add_argument("--serving", type=int, default=0, help="serve this many requests of the polar stream")
+    ap.add_argument("--serving-slots", type=int, default=16)
+    ap.add_argument("--serving-rate", type=float, default=2.0, help="mean arrivals per second (0: all at once)")
+    ap.add_argument("--serving-max-steps", type=int, default=8000)
+    ap.add_argument("--serving-min-steps", type=int, default=1600)
+    ap.add_argument("--serving-window", type=int, default=8, help="chunks of 100 level-0 steps per CL window")
+    ap.add_argument("--serving-tol", type=float, default=5e-3, help="|change of the window-mean CL|")
+    ap.add_argument("--serving-no-baseline", action="store_true")
+    ap.add_argument("--serving-dump", default=None, help="write per-request results to <path>.<arm>.json")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case(args)
+    if args.serving:
+        return serving_arm(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

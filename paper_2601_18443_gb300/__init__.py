@@ -259,6 +259,13 @@ class Solver:
         d["cp"], d["cf"] = cp[:cap], cf[:cap]
         return d
 
+    def coefficients(self):
+        """CL, CD, CDp, CDf, mass, dCL and step from one lbm_get_loads call (no per-segment arrays)."""
+        out = lbm_loads()
+        n = C.c_int()
+        self._check(self._lib.lbm_get_loads(self._h, C.byref(out), None, None, 0, C.byref(n)))
+        return {k: getattr(out, k) for k, _ in lbm_loads._fields_}
+
     def cut_links(self):
         n = C.c_int()
         self._check(self._lib.lbm_get_cut_links(self._h, None, None, 0, C.byref(n)))

@@ -160,7 +160,7 @@ def highlift_3element(levels=8, layers=128, box=(16.0, 8.0), h0=1.0 / 64.0):
 def polar_requests(n=256, seed=2026, rate_per_s=2.0):
     """Seeded polar-solve requests: Poisson arrivals (mean rate_per_s), NACA 4-digit
     sections with m in 0..4, p in 2..5 (tenths), t in 09..18, alpha ~ U[-4, 16] deg,
-    Re ~ logU[1e6, 1e7], 4..7 levels; FP32 population storage, Ma 0.15."""
+    Re ~ logU[1e6, 1e7], 4..7 levels; FP16 (shifted) population storage, Ma 0.15."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
     out = []
@@ -170,7 +170,7 @@ def polar_requests(n=256, seed=2026, rate_per_s=2.0):
         th = int(rng.integers(9, 19))
         code = f"{m}{p if m else 0}{th:02d}"
         out.append(dict(rid=k, arrival=float(t[k]), code=code, alpha=float(rng.uniform(-4.0, 16.0)),
-                        Re=float(10.0 ** rng.uniform(6.0, 7.0)), levels=int(rng.integers(4, 8)), Ma=0.15, store=0))
+                        Re=float(10.0 ** rng.uniform(6.0, 7.0)), levels=int(rng.integers(4, 8)), Ma=0.15, store=1))
     return out
 
 
@@ -183,6 +183,6 @@ def polar_case(req, h0=1.0 / 16.0, box=(16.0, 8.0)):
     nx0, ny0 = int(round(box[0] / h0)), int(round(box[1] / h0))
     cfg = base_config(levels=levels, nx0=nx0, ny0=ny0, x0=-0.375 * box[0] + 0.25, y0=-0.5 * box[1], h0=h0,
                       layers=layers, chord=1.0, Re=req["Re"], Ma=req["Ma"], turbulence=1, wall_model=0, periodic=0,
-                      solid_walls=1, store=req.get("store", 0))
+                      solid_walls=1, store=req.get("store", 1))
     hf = h0 / 2 ** (levels - 1)
     return cfg, [naca_loop(req["code"], hf, alpha_deg=req["alpha"])]

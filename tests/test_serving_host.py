@@ -1,0 +1,171 @@
+"""Host logic of the continuous-batching service, driven by a simulated backend (no GPU):
+admission in arrival order under the slot and memory limits, rejection of solves that
+cannot fit, convergence and divergence handling, memory release, and the summary."""
+import math
+import threading
+import time
+
+import pytest
+
+from paper_2601_18443_gb300.serve import Service, SolveRequest, summarize
+
+
+class FakeHandle:
+    def __init__(self, be, req):
+        self.be, self.req = be, req
+        self.ready_at = 0.0
+        self.steps = 0
+        self.closed = False
+
+    def enqueue(self, n):
+        self.steps += n
+        self.ready_at = time.perf_counter() + n * self.req.cfg["cost"]
+
+    def ready(self):
+        return time.perf_counter() >= self.ready_at
+
+    def read(self):
+        if self.req.cfg.get("diverge_at") and self.steps >= self.req.cfg["diverge_at"]:
+            raise RuntimeError("lbm status -6: non-finite populations")
+        if self.req.cfg.get("shedding"):     # periodic lift: never converges
+            return dict(CL=0.5 + 0.1 * math.sin(self.steps / 70.0), CD=0.01)
+        tau = self.req.cfg["tau"]
+        cl = self.req.cfg["cl"] * (1.0 - math.exp(-self.steps / tau))
+        return dict(CL=cl, CD=0.01)
+
+    def close(self):
+        assert not self.closed
+        self.closed = True
+        with self.be.lock:
+            self.be.live -= 1
+
+
+class FakeBackend:
+    def __init__(self, free=1 << 30):
+        self.free = free
+        self.lock = threading.Lock()
+        self.live = 0
+        self.max_live = 0
+        self.handles = []
+
+    def plan(self, cfg, loops):
+        if cfg.get("bad"):
+            raise RuntimeError("lbm status -5: refinement reaches the level-0 box edge")
+        return dict(device_bytes=cfg["bytes"], node_updates_per_step=cfg["updates"])
+
+    def build(self, req):
+        time.sleep(0.002)
+        h = FakeHandle(self, req)
+        with self.lock:
+            self.live += 1
+            self.max_live = max(self.max_live, self.live)
+            self.handles.append(h)
+        return h
+
+    def free_bytes(self):
+        return self.free
+
+
+def make(rid, arrival, nbytes, cost=2e-5, tau=300.0, **kw):
+    cfg = dict(bytes=nbytes, updates=1000 * (rid + 1), cost=cost, tau=tau, cl=0.5, **kw)
+    return SolveRequest(rid=rid, arrival=arrival, cfg=cfg, loops=[], max_steps=4000, min_steps=200,
+                        check_every=100, tol=2e-3, patience=2)
+
+
+def check_trace(svc, budget, slots):
+    for t, ev, rid, used, resident in svc.trace:
+        assert used <= budget + 1e-6
+        assert resident <= slots
+
+
+def test_memory_budget_and_slots_are_never_exceeded():
+    be = FakeBackend()
+    reqs = [make(k, 0.001 * k, (3 + k % 4) << 20) for k in range(12)]
+    budget = 16 << 20
+    svc = Service(max_slots=3, mem_budget=budget, overhead=0, backend=be)
+    res = svc.run(reqs)
+    assert all(r.status == "converged" for r in res)
+    check_trace(svc, budget, 3)
+    assert be.max_live <= 3
+    assert be.live == 0 and all(h.closed for h in be.handles)
+
+
+def test_admission_follows_arrival_order():
+    be = FakeBackend()
+    # a large solve at the head holds back the small ones behind it until memory frees
+    reqs = [make(0, 0.0, 6 << 20), make(1, 0.001, 9 << 20), make(2, 0.002, 1 << 20), make(3, 0.003, 1 << 20)]
+    svc = Service(max_slots=4, mem_budget=10 << 20, overhead=0, backend=be)
+    res = svc.run(reqs)
+    order = [rid for _, ev, rid, _, _ in svc.trace if ev == "admit"]
+    assert order == [0, 1, 2, 3]
+    assert res[1].admitted >= res[0].finished
+    assert all(r.status == "converged" for r in res)
+
+
+def test_solves_that_cannot_fit_or_fail_to_plan_are_rejected():
+    be = FakeBackend()
+    reqs = [make(0, 0.0, 64 << 20), make(1, 0.0, 1 << 20, bad=True), make(2, 0.0, 1 << 20)]
+    res = Service(max_slots=2, mem_budget=32 << 20, overhead=0, backend=be).run(reqs)
+    assert [r.status for r in res] == ["rejected", "rejected", "converged"]
+    assert "budget" in res[0].message and "box edge" in res[1].message
+
+
+def test_divergence_ends_the_solve_and_frees_its_memory():
+    be = FakeBackend()
+    reqs = [make(0, 0.0, 4 << 20, diverge_at=300), make(1, 0.0, 4 << 20)]
+    svc = Service(max_slots=1, mem_budget=8 << 20, overhead=0, backend=be)
+    res = svc.run(reqs)
+    assert res[0].status == "diverged" and res[0].steps == 300
+    assert res[1].status == "converged"
+    assert be.live == 0
+
+
+def test_convergence_rule_and_step_cap():
+    be = FakeBackend()
+    fast, slow = make(0, 0.0, 1 << 20, tau=100.0), make(1, 0.0, 1 << 20, shedding=True)
+    slow.max_steps = 500
+    res = Service(max_slots=2, mem_budget=8 << 20, overhead=0, backend=be).run([fast, slow])
+    # tau = 100: |dCL| over the chunk ending at n is 0.5 (e - 1) e^(-n/100), <= 2e-3 from n = 700;
+    # two calm chunks in a row end the solve at n = 800
+    assert res[0].status == "converged" and res[0].steps == 800
+    assert [h[0] for h in res[0].history] == list(range(100, 900, 100))
+    assert res[1].status == "max_steps" and res[1].steps == 500
+
+
+def test_concurrent_slots_shorten_the_makespan_and_summary():
+    reqs = [make(k, 0.0, 1 << 20, cost=5e-5) for k in range(6)]
+    one = Service(max_slots=1, mem_budget=64 << 20, overhead=0, backend=FakeBackend()).run(reqs)
+    many = Service(max_slots=6, mem_budget=64 << 20, overhead=0, backend=FakeBackend()).run(reqs)
+    s1, s6 = summarize(one), summarize(many)
+    assert s1["converged"] == s6["converged"] == 6
+    assert s6["makespan_s"] < 0.6 * s1["makespan_s"]
+    assert s6["p99_s"] < s1["p99_s"] and s6["solves_per_hour"] > s1["solves_per_hour"]
+    assert s1["node_updates"] == sum(r.node_updates_per_step * r.steps for r in one)
+    assert s1["p50_s"] <= s1["p99_s"]
+    for a, b in zip(one, many):
+        assert a.history == b.history
+
+
+def test_window_mean_convergence_ignores_a_steady_oscillation():
+    # CL = 0.8 + 0.05 sin(2 pi n / 400): chunk-to-chunk changes stay near 0.07, but the mean over
+    # a 400-step window (4 chunks) is 0.8 exactly, so the windowed rule converges
+    class Osc(FakeHandle):
+        def read(self):
+            return dict(CL=0.8 + 0.05 * math.sin(2 * math.pi * self.steps / 400.0), CD=0.01)
+
+    class OscBackend(FakeBackend):
+        def build(self, req):
+            h = super().build(req)
+            o = Osc(self, req)
+            self.handles[-1] = o
+            return o
+
+    plain = make(0, 0.0, 1 << 20)
+    plain.max_steps = 2000
+    windowed = make(1, 0.0, 1 << 20)
+    windowed.max_steps, windowed.window = 2000, 4
+    be = OscBackend()
+    res = Service(max_slots=2, mem_budget=8 << 20, overhead=0, backend=be).run([plain, windowed])
+    assert res[0].status == "max_steps"
+    assert res[1].status == "converged" and res[1].steps == 900
+    assert res[1].CL == pytest.approx(0.8, abs=1e-12)
