@@ -13,6 +13,9 @@ Arms:
   default            the CUDA library (one replica per rank under torchrun, no collective)
   --impl reference   the FP64 CPU oracle on the host cores (rank 0 only)
 
+Launch variant: lbm_autotune picks each level's kernel variant and PDL on/off from timed
+steps before the warm-up (--no-autotune keeps the default variant).
+
 Timing: W untimed warm-up steps, then K steps timed with CUDA events on the solver's
 stream; a 512 MB buffer is written between timed steps to flush L2 (the flush is
 outside the events).  The dominant kernel's roofline comes from a per-launch event
@@ -207,6 +210,8 @@ def gpu_arm(args, rank, world, dist):
     cfg, loops = W.naca0012_large()
     s = pkg.Solver(cfg, stream=stream)
     s.set_geometry(loops)
+    # launch autotuner (per-level kernel variant, PDL on/off); its steps are untimed
+    tune = None if args.no_autotune else s.autotune(10)
     info = s.info()
     nu_step = info["node_updates_per_step"]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -279,8 +284,8 @@ def gpu_arm(args, rank, world, dist):
 
     hbm = hbm_sc = None
     if rank == 0 and not args.no_hbm_grid:
-        hbm = hbm_grid_roofline(pkg, stream, peak, peak_kind)
-        hbm_sc = hbm_grid_roofline(pkg, stream, peak, peak_kind, turbulence=0)
+        hbm = hbm_grid_roofline(pkg, stream, peak, peak_kind, tune=not args.no_autotune)
+        hbm_sc = hbm_grid_roofline(pkg, stream, peak, peak_kind, turbulence=0, tune=not args.no_autotune)
 
     # precision forms: the same workload with populations stored in FP16 / BF16
     forms = None
@@ -335,6 +340,10 @@ def gpu_arm(args, rank, world, dist):
             "clocks": clk,
             "loads": {"CL": loads["CL"], "CD": loads["CD"], "step": loads["step"]},
             "e2e": e2e,
+            "autotune": None if tune is None else {
+                "min_blocks_per_level": tune["min_blocks"], "stage_per_level": tune["stage"], "pdl": tune["pdl"],
+                "step_us_default": round(tune["default_step_us"], 2),
+                "step_us_tuned": round(min(tune["step_us"].values()), 2)},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
@@ -348,7 +357,7 @@ def gpu_arm(args, rank, world, dist):
     return 0
 
 
-def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096, turbulence=1):
+def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096, turbulence=1, tune=True):
     """The level kernel on one periodic 4096 x 4096 level (1.4-1.7 GB of traffic per
     launch, far beyond L2): its HBM roofline without multilevel effects; turbulence=0
     leaves the stream-collide alone (84 B per node update)."""
@@ -356,6 +365,8 @@ def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096, turbulence=1):
                         turbulence=turbulence, wall_model=3)
     s = pkg.Solver(cfg, stream=stream)
     s.set_geometry([])
+    if tune:
+        s.autotune(3)
     s.step(3)
     kt = s.time_kernels(5)
     info = s.info()
@@ -387,7 +398,12 @@ def profile_case(args):
         cfg, loops = W.naca0012_large()
     s = pkg.Solver(cfg)
     s.set_geometry(loops)
+    if not args.no_autotune:
+        s.autotune(2)
+    # the steps to profile sit in an NVTX range ("steps"): ncu --nvtx --nvtx-include steps/
+    torch.cuda.nvtx.range_push("steps")
     s.step(args.steps)
+    torch.cuda.nvtx.range_pop()
     print("profile case", args.profile_case, "ok", flush=True)
     s.close()
     return 0
@@ -464,6 +480,7 @@ def main():
     ap.add_argument("--no-hbm-grid", action="store_true")
     ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--profile-case", choices=["hbm_grid", "workload"], default=None)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch variant")
     ap.add_argument("--serving", type=int, default=0, help="serve this many requests of the polar stream")
     ap.add_argument("--serving-slots", type=int, default=16)
     ap.add_argument("--serving-rate", type=float, default=2.0, help="mean arrivals per second (0: all at once)")

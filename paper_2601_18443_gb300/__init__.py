@@ -66,6 +66,17 @@ class lbm_kernel_times(C.Structure):
                 ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
 
 
+TUNE_CANDIDATES = 8
+
+
+class lbm_tune_report(C.Structure):
+    _fields_ = [("levels", C.c_int), ("candidate_min_blocks", C.c_int * TUNE_CANDIDATES),
+                ("candidate_stage", C.c_int * TUNE_CANDIDATES),
+                ("level_us", (C.c_double * 16) * TUNE_CANDIDATES), ("min_blocks", C.c_int * 16),
+                ("stage", C.c_int * 16), ("default_step_us", C.c_double), ("step_us", C.c_double * 2),
+                ("pdl", C.c_int), ("steps_taken", C.c_longlong)]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     return _build_ext.build(force=force, verbose=verbose)
 
@@ -98,6 +109,7 @@ def library():
         "lbm_get_wall_distance": ([vp, C.c_int, dp, C.c_int], C.c_int),
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
+        "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
         "lbm_level_mass_noalloc": ([vp, vp, vp, vp, vp, C.c_longlong, C.c_double, vp, vp, vp], C.c_int),
         "lbm_last_error": ([vp], C.c_char_p),
         "lbm_destroy": ([vp], None),
@@ -305,11 +317,29 @@ class Solver:
                     surface_segments=out.surface_segments, kernels_per_step=out.kernels_per_step,
                     bytes_per_node_update=out.bytes_per_node_update, device_bytes=out.device_bytes)
 
+    def autotune(self, steps=10):
+        """lbm_autotune: per-level kernel variant and PDL choice by timing; advances the
+        solve by the returned steps_taken coarse steps."""
+        out = lbm_tune_report()
+        self._check(self._lib.lbm_autotune(self._h, int(steps), C.byref(out)))
+        return _tune_dict(out)
+
     def time_kernels(self, n=1):
         out = lbm_kernel_times()
         self._check(self._lib.lbm_time_kernels(self._h, int(n), C.byref(out)))
         return {out.name[i].value.decode(): dict(ms=out.total_ms[i], launches=out.launches[i], cells=out.cells[i])
                 for i in range(out.n_classes)}
+
+
+def _tune_dict(out):
+    L = out.levels
+    cand = list(zip(out.candidate_min_blocks, out.candidate_stage))
+    return dict(levels=L, candidates=cand,
+                level_us={c: list(out.level_us[i][:L]) for i, c in enumerate(cand)},
+                min_blocks=list(out.min_blocks[:L]), stage=list(out.stage[:L]),
+                default_step_us=out.default_step_us,
+                step_us={"pdl_off": out.step_us[0], "pdl_on": out.step_us[1]}, pdl=out.pdl,
+                steps_taken=out.steps_taken)
 
 
 def level_mass_noalloc(flags, drho, ux, uy, chi, n_cells, area, mass_out, nonfinite_out, stream=0):

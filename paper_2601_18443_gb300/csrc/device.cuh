@@ -77,10 +77,20 @@ struct LevelStep {
     int *status;        // device status word (LBM_STATUS_* bits)
 };
 
+// Launch variant of a level's kernels (chosen by lbm_autotune): the register budget of the
+// fused level kernel, as the minimum resident blocks per SM (3, 4, 5 or 6), whether its
+// SA-neg stencil is staged in shared memory, and whether launches use programmatic
+// dependent launch.  Every variant computes the same numbers.
+struct LevelTune {
+    int min_blocks;
+    int stage;
+    int pdl;
+};
+
 // launchers (kernels.cu); all enqueue on the given stream
 void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,
-                  const StepConsts &k, const LevelStep &ls);
-void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p);
+                  const StepConsts &k, const LevelStep &ls, const LevelTune &tu);
+void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pdl);
 int level_blocks_per_sm();
 void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k);
 void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pp, int pf);

@@ -100,6 +100,9 @@ struct lbm_solver {
     LoadsView segs;
     StepConsts k;
     int parity[LBM_MAXL];
+    int min_blocks[LBM_MAXL];     // register budget of each level's kernel (lbm_autotune)
+    int stage[LBM_MAXL];          // SA-neg stencil staged in shared memory (lbm_autotune)
+    int pdl = 1;                  // programmatic dependent launch (lbm_autotune)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<void *> allocs;
     double device_bytes = 0;
@@ -119,6 +122,7 @@ struct lbm_solver {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, int>> ev_marks;   // (class, event index pair start)
     std::vector<long long> ev_cells;
+    std::vector<int> ev_level;
     int ev_used = 0;
 };
 
@@ -215,12 +219,13 @@ static void mark_begin(lbm_solver *s)
     cudaEventRecord(s->ev_pool[s->ev_used], s->stream);
 }
 
-static void mark_end(lbm_solver *s, int cls, long long cells)
+static void mark_end(lbm_solver *s, int cls, long long cells, int level)
 {
     if (!s->timing) return;
     cudaEventRecord(s->ev_pool[s->ev_used + 1], s->stream);
     s->ev_marks.push_back({cls, s->ev_used});
     s->ev_cells.push_back(cells);
+    s->ev_level.push_back(level);
     s->ev_used += 2;
 }
 
@@ -237,8 +242,8 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     const LevelView *C = (l > 0) ? &s->lv[l - 1].v : nullptr;
     if (F) {
         mark_begin(s);
-        lbmdev::launch_prolong(st, P, *F, s->parity[l]);
-        mark_end(s, KC_PROLONG, (long long)P.n_band_tiles * LBM_TILE);
+        lbmdev::launch_prolong(st, P, *F, s->parity[l], s->pdl);
+        mark_end(s, KC_PROLONG, (long long)P.n_band_tiles * LBM_TILE, l);
         nk += P.n_band_tiles > 0;
         advance(s, st, l + 1, 0, nk);
         advance(s, st, l + 1, 1, nk);
@@ -253,15 +258,22 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     ls.pp = C ? s->parity[l - 1] : 0;
     ls.status = s->d_status;
     mark_begin(s);
-    lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls);
-    mark_end(s, l == L - 1 ? KC_LEVEL_FINEST : KC_LEVEL_COARSE, P.ns);
+    const lbmdev::LevelTune tu{s->min_blocks[l], s->stage[l], s->pdl};
+    lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls, tu);
+    mark_end(s, l == L - 1 ? KC_LEVEL_FINEST : KC_LEVEL_COARSE, P.ns, l);
     nk++;
     s->parity[l] ^= 1;
 }
 
+// one graph per level-0 parity; the graph of the current parity is captured first, and
+// the two captures leave every level's parity as it was
 static lbm_status capture_graphs(lbm_solver *s)
 {
-    for (int b = 0; b < 2; b++) {
+    for (int b = 0; b < 2; b++)
+        if (s->graph[b]) { cudaGraphExecDestroy(s->graph[b]); s->graph[b] = nullptr; }
+    const int b0 = s->parity[0];
+    for (int bi = 0; bi < 2; bi++) {
+        const int b = b0 ^ bi;
         if (s->parity[0] != b) return fail(s, LBM_ERR_CUDA, "internal: parity mismatch at capture");
         cudaGraph_t gr;
         long long nk = 0;
@@ -329,7 +341,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
     s->cfg = *cfg;
     s->L = cfg->levels;
     s->U = cfg->Ma * std::sqrt(1.0 / 3.0);
-    for (int l = 0; l < LBM_MAXL; l++) s->parity[l] = 0;
+    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; s->stage[l] = 0; }
     if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LBM_ERR_CUDA; }
     if (cfg->cuda_stream) {
         s->stream = (cudaStream_t)cfg->cuda_stream;
@@ -906,6 +918,7 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n, lbm_kernel_times *out)
         s->ev_used = 0;
         s->ev_marks.clear();
         s->ev_cells.clear();
+        s->ev_level.clear();
         long long nk = 0;
         advance(s, s->stream, 0, 0, nk);
         s->timing = false;
@@ -921,6 +934,101 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n, lbm_kernel_times *out)
             out->cells[cls] += s->ev_cells[m];
         }
     }
+    return check_status(s);
+}
+
+// mean per-launch time (us) of each level's fused kernel over n eager coarse steps
+static lbm_status level_launch_times(lbm_solver *s, int n, double *us)
+{
+    double tot[LBM_MAXL] = {0};
+    long long cnt[LBM_MAXL] = {0};
+    for (int it = 0; it < n; it++) {
+        s->timing = true;
+        s->ev_used = 0;
+        s->ev_marks.clear();
+        s->ev_cells.clear();
+        s->ev_level.clear();
+        long long nk = 0;
+        advance(s, s->stream, 0, 0, nk);
+        s->timing = false;
+        s->step++;
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s->stream));
+        for (size_t m = 0; m < s->ev_marks.size(); m++) {
+            if (s->ev_marks[m].first == KC_PROLONG) continue;
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, s->ev_pool[s->ev_marks[m].second], s->ev_pool[s->ev_marks[m].second + 1]));
+            tot[s->ev_level[m]] += 1e3 * ms;
+            cnt[s->ev_level[m]]++;
+        }
+    }
+    for (int l = 0; l < s->L; l++) us[l] = cnt[l] ? tot[l] / (double)cnt[l] : 0.0;
+    return LBM_OK;
+}
+
+// mean time (us) of one coarse step through the captured graphs, over n steps
+static lbm_status graph_step_time(lbm_solver *s, int n, double *us)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return fail(s, LBM_ERR_CUDA, "cudaEventCreate"); }
+    cudaEventRecord(a, s->stream);
+    lbm_status st = enqueue_steps(s, n);
+    cudaEventRecord(b, s->stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != LBM_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(s, e, "graph step timing");
+    *us = 1e3 * ms / (double)n;
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
+{
+    if (!s || !out || steps < 1) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {3, 4, 5, 6, 3, 4, 5, 6};
+    static const int CAND_ST[LBM_TUNE_CANDIDATES] = {0, 0, 0, 0, 1, 1, 1, 1};
+    std::memset(out, 0, sizeof *out);
+    const int L = s->L;
+    out->levels = L;
+    lbm_status st;
+    if ((st = graph_step_time(s, steps, &out->default_step_us)) != LBM_OK) return st;
+    int keep_mb[LBM_MAXL], keep_st[LBM_MAXL];
+    for (int l = 0; l < L; l++) { keep_mb[l] = s->min_blocks[l]; keep_st[l] = s->stage[l]; }
+    // 1: kernel variant per level (register budget, stencil staging), from per-launch
+    //    event timings of every candidate
+    for (int c = 0; c < LBM_TUNE_CANDIDATES; c++) {
+        for (int l = 0; l < L; l++) { s->min_blocks[l] = CAND_MB[c]; s->stage[l] = CAND_ST[c]; }
+        out->candidate_min_blocks[c] = CAND_MB[c];
+        out->candidate_stage[c] = CAND_ST[c];
+        if ((st = level_launch_times(s, steps, out->level_us[c])) != LBM_OK) {
+            for (int l = 0; l < L; l++) { s->min_blocks[l] = keep_mb[l]; s->stage[l] = keep_st[l]; }
+            return st;
+        }
+    }
+    for (int l = 0; l < L; l++) {
+        int best = 0;
+        for (int c = 1; c < LBM_TUNE_CANDIDATES; c++)
+            if (out->level_us[c][l] < out->level_us[best][l]) best = c;
+        s->min_blocks[l] = CAND_MB[best];
+        s->stage[l] = CAND_ST[best];
+        out->min_blocks[l] = CAND_MB[best];
+        out->stage[l] = CAND_ST[best];
+    }
+    // 2: programmatic dependent launch on or off, from whole graph steps
+    for (int pdl = 0; pdl < 2; pdl++) {
+        s->pdl = pdl;
+        if ((st = capture_graphs(s)) != LBM_OK) return st;
+        if ((st = graph_step_time(s, steps, &out->step_us[pdl])) != LBM_OK) return st;
+    }
+    s->pdl = out->step_us[1] <= out->step_us[0] ? 1 : 0;
+    out->pdl = s->pdl;
+    if ((st = capture_graphs(s)) != LBM_OK) return st;
+    out->steps_taken = (long long)steps * (3 + LBM_TUNE_CANDIDATES);
     return check_status(s);
 }
 
