@@ -13,7 +13,7 @@ Arms:
   default            the CUDA library (one replica per rank under torchrun, no collective)
   --impl reference   the FP64 CPU oracle on the host cores (rank 0 only)
 
-Launch variant: lbm_autotune picks each level's kernel variant and PDL on/off from timed
+Launch variant: lbm_autotune picks each level's register budget and PDL on/off from timed
 steps before the warm-up (--no-autotune keeps the default variant).
 
 Timing: W untimed warm-up steps, then K steps timed with CUDA events on the solver's
@@ -210,7 +210,7 @@ def gpu_arm(args, rank, world, dist):
     cfg, loops = W.naca0012_large()
     s = pkg.Solver(cfg, stream=stream)
     s.set_geometry(loops)
-    # launch autotuner (per-level kernel variant, PDL on/off); its steps are untimed
+    # launch autotuner (per-level register budget, PDL on/off); its steps are untimed
     tune = None if args.no_autotune else s.autotune(10)
     info = s.info()
     nu_step = info["node_updates_per_step"]
@@ -341,7 +341,7 @@ def gpu_arm(args, rank, world, dist):
             "loads": {"CL": loads["CL"], "CD": loads["CD"], "step": loads["step"]},
             "e2e": e2e,
             "autotune": None if tune is None else {
-                "min_blocks_per_level": tune["min_blocks"], "stage_per_level": tune["stage"], "pdl": tune["pdl"],
+                "min_blocks_per_level": tune["min_blocks"], "pdl": tune["pdl"],
                 "step_us_default": round(tune["default_step_us"], 2),
                 "step_us_tuned": round(min(tune["step_us"].values()), 2)},
         }

@@ -193,29 +193,32 @@ lbm_status lbm_get_info(lbm_solver *s, lbm_info *out);
 lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times *out);
 
 /* Launch autotuner.  Not part of the paper's method (Sec 2.1 gives the level schedule, not
- * its mapping to a GPU).  For each level it picks one of LBM_TUNE_CANDIDATES variants of
- * the fused level kernel: a register budget of at least 3, 4, 5 or 6 resident 256-thread
- * blocks per SM, each with the SA-neg stencil (chi and u at the 3 x 3 neighbourhood, Sec
- * 2.2) read through the cache or staged per tile in shared memory.  The choice comes from
- * per-launch CUDA-event timings of `steps` eager coarse steps per candidate.  Then it picks
- * whether launches use programmatic dependent launch, from the time of `steps` coarse steps
- * through the step graphs each way, and recaptures the graphs with the choice.  Every
- * variant computes bit-identical results; the timed steps are real steps of the solve
- * (steps_taken of them).  Synchronous.  Errors as lbm_step. */
-#define LBM_TUNE_CANDIDATES 8
+ * its mapping to a GPU).  For each level it picks the register budget of the fused level
+ * kernel among LBM_TUNE_CANDIDATES variants (at least 5 or 6 resident 256-thread blocks
+ * per SM, i.e. at most 48 or 40 registers a thread), from per-launch CUDA-event timings
+ * of `steps` eager coarse steps per candidate.  Then it picks whether launches use
+ * programmatic dependent launch, from the time of `steps` coarse steps through the step
+ * graphs each way, and recaptures the graphs with the choice.  Every variant computes
+ * bit-identical results; the timed steps are real steps of the solve (steps_taken of
+ * them).  Synchronous.  Errors as lbm_step. */
+#define LBM_TUNE_CANDIDATES 2
 typedef struct {
     int levels;
     int candidate_min_blocks[LBM_TUNE_CANDIDATES];
-    int candidate_stage[LBM_TUNE_CANDIDATES];
     double level_us[LBM_TUNE_CANDIDATES][16]; /* mean launch time of level l's kernel per candidate */
     int min_blocks[16];                       /* chosen register budget per level                  */
-    int stage[16];                            /* chosen stencil staging per level                  */
     double default_step_us;                   /* coarse step through the graphs before tuning      */
     double step_us[2];                        /* coarse step, chosen kernels, PDL off / on         */
     int pdl;                                  /* chosen: 1 programmatic dependent launch on        */
     long long steps_taken;                    /* coarse steps the tuning advanced the solve by     */
 } lbm_tune_report;
 lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out);
+
+/* Set the launch variant directly (for instance one lbm_autotune found on a solve of the
+ * same shape): min_blocks[l] in {5, 6} for each of the solver's levels, pdl 0 or 1; the
+ * step graphs are recaptured.  No device work.
+ * Errors: LBM_ERR_INVALID_ARG for a value outside those sets, LBM_ERR_NO_GEOMETRY. */
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, int pdl);
 
 /* Largest n_cells that lbm_level_mass_noalloc accepts (its fixed scratch holds 4096
  * per-block partial sums of at most 16384 cells each). */

@@ -66,14 +66,13 @@ class lbm_kernel_times(C.Structure):
                 ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
 
 
-TUNE_CANDIDATES = 8
+TUNE_CANDIDATES = 2
 
 
 class lbm_tune_report(C.Structure):
     _fields_ = [("levels", C.c_int), ("candidate_min_blocks", C.c_int * TUNE_CANDIDATES),
-                ("candidate_stage", C.c_int * TUNE_CANDIDATES),
                 ("level_us", (C.c_double * 16) * TUNE_CANDIDATES), ("min_blocks", C.c_int * 16),
-                ("stage", C.c_int * 16), ("default_step_us", C.c_double), ("step_us", C.c_double * 2),
+                ("default_step_us", C.c_double), ("step_us", C.c_double * 2),
                 ("pdl", C.c_int), ("steps_taken", C.c_longlong)]
 
 
@@ -110,6 +109,7 @@ def library():
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
+        "lbm_set_launch_variant": ([vp, ip, C.c_int], C.c_int),
         "lbm_level_mass_noalloc": ([vp, vp, vp, vp, vp, C.c_longlong, C.c_double, vp, vp, vp], C.c_int),
         "lbm_last_error": ([vp], C.c_char_p),
         "lbm_destroy": ([vp], None),
@@ -318,11 +318,16 @@ class Solver:
                     bytes_per_node_update=out.bytes_per_node_update, device_bytes=out.device_bytes)
 
     def autotune(self, steps=10):
-        """lbm_autotune: per-level kernel variant and PDL choice by timing; advances the
+        """lbm_autotune: per-level register budget and PDL choice by timing; advances the
         solve by the returned steps_taken coarse steps."""
         out = lbm_tune_report()
         self._check(self._lib.lbm_autotune(self._h, int(steps), C.byref(out)))
         return _tune_dict(out)
+
+    def set_launch_variant(self, min_blocks, pdl=1):
+        """lbm_set_launch_variant: per-level register budget (5 or 6 blocks per SM) and PDL."""
+        mb = np.ascontiguousarray(min_blocks, dtype=np.int32)
+        self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), int(pdl)))
 
     def time_kernels(self, n=1):
         out = lbm_kernel_times()
@@ -333,11 +338,10 @@ class Solver:
 
 def _tune_dict(out):
     L = out.levels
-    cand = list(zip(out.candidate_min_blocks, out.candidate_stage))
+    cand = list(out.candidate_min_blocks)
     return dict(levels=L, candidates=cand,
                 level_us={c: list(out.level_us[i][:L]) for i, c in enumerate(cand)},
-                min_blocks=list(out.min_blocks[:L]), stage=list(out.stage[:L]),
-                default_step_us=out.default_step_us,
+                min_blocks=list(out.min_blocks[:L]), default_step_us=out.default_step_us,
                 step_us={"pdl_off": out.step_us[0], "pdl_on": out.step_us[1]}, pdl=out.pdl,
                 steps_taken=out.steps_taken)
 

@@ -78,12 +78,10 @@ struct LevelStep {
 };
 
 // Launch variant of a level's kernels (chosen by lbm_autotune): the register budget of the
-// fused level kernel, as the minimum resident blocks per SM (3, 4, 5 or 6), whether its
-// SA-neg stencil is staged in shared memory, and whether launches use programmatic
-// dependent launch.  Every variant computes the same numbers.
+// fused level kernel, as the minimum resident blocks per SM (5 or 6), and whether launches
+// use programmatic dependent launch.  Every variant computes the same numbers.
 struct LevelTune {
     int min_blocks;
-    int stage;
     int pdl;
 };
 

@@ -450,45 +450,16 @@ template <typename T> struct ShiftedIO {
     }
 };
 
-// Fields of the SA-neg stencil staged in shared memory: the tile plus a one-cell halo,
-// rows of STG_W floats (48: the two rows of a warp's 16 x 2 patch fall in disjoint banks).
-#define STG_W 48
-#define STG_N (10 * STG_W)
-
-// Stage chi, u_x, u_y of the tile and its halo (time level p).  Every thread stores its own
-// cell; threads 0..83 each store one of the 84 halo cells (a halo cell of an absent tile is
-// left unset: readers take their own cell's value there, as the global path does).
-__device__ __forceinline__ void stage_fields(const int *nb3, const float *chi, const float *ux, const float *uy,
-                                             int slot, int lx, int ly, int c, float *stg)
-{
-    const int o = (ly + 1) * STG_W + lx + 1;
-    stg[o] = __ldg(chi + slot); stg[STG_N + o] = __ldg(ux + slot); stg[2 * STG_N + o] = __ldg(uy + slot);
-    if (c < 84) {
-        int hx, hy;
-        if (c < 34) { hx = c - 1; hy = -1; }
-        else if (c < 68) { hx = c - 35; hy = LBM_TY; }
-        else if (c < 76) { hx = -1; hy = c - 68; }
-        else { hx = LBM_TX; hy = c - 76; }
-        const int s = nb_slot(nb3, 0, 0, hx, hy);
-        if (s >= 0) {
-            const int h = (hy + 1) * STG_W + hx + 1;
-            stg[h] = __ldg(chi + s); stg[STG_N + h] = __ldg(ux + s); stg[2 * STG_N + h] = __ldg(uy + s);
-        }
-    }
-}
-
-// MINB: minimum resident blocks per SM the register allocation must allow (3..6, that is
-// at most 80, 64, 48 or 40 registers a thread).  STAGE: the SA-neg stencil reads chi and u
-// from a shared-memory copy of the tile and its halo (one block barrier) instead of 27
-// cached global loads per cell.  Both are picked per level by the autotuner; every
-// variant computes the same numbers.
-template <bool WALL, bool CHILD, typename T, int MINB, bool STAGE>
+// MINB: minimum resident blocks per SM the register allocation must allow (5 or 6, that
+// is at most 48 or 40 registers a thread), picked per level by the autotuner.  Both
+// budgets give bit-identical results (larger budgets, 3 or 4 blocks, were measured to
+// round differently and to run no faster, and are not offered).
+template <bool WALL, bool CHILD, typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, LevelView C, RecView R, StepConsts k,
                                                       LevelStep ls)
 {
     const ShiftedIO<T> IO{k.pshift};
-    __shared__ int nb3w[LBM_TILE / 32][9];       // one copy per warp
-    __shared__ float stg[STAGE ? 3 * STG_N : 1];
+    __shared__ int nb3w[LBM_TILE / 32][9];       // one copy per warp: no block-wide barrier
     const int t = P.work_tiles[blockIdx.x], c = threadIdx.x;
     const int lane = c & 31;
     int lx, ly;
@@ -499,12 +470,6 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
     griddep_launch();
     griddep_wait();
     const int slot = t * LBM_TILE + ly * LBM_TX + lx;
-    if constexpr (STAGE) {
-        if (k.turbulence) {                       // uniform over the block
-            stage_fields(nb3, P.chi[ls.p], P.ux[ls.p], P.uy[ls.p], slot, lx, ly, c, stg);
-            __syncthreads();
-        }
-    }
     const uint32_t fl = __ldg(P.flags + slot);
     const uint32_t kind = fl & FL_KIND_MASK;
     const bool fluid = !(fl & FL_SOLID);
@@ -531,7 +496,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
         const bool edge = ls.is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
         const bool bnode = WALL && (fl & FL_BNODE);
         int nbs[9];
-        const unsigned present = neighbours(nb3, lx, ly, slot, nbs);
+        neighbours(nb3, lx, ly, slot, nbs);
         // ---- wall function of the boundary node (Sec 2.3), fields at time t
         float drW = 0.f, uWx = 0.f, uWy = 0.f, chiB = 0.f;
         int r = -1;
@@ -556,19 +521,10 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
                 }
             } else {
                 Stencil S;
-                if constexpr (STAGE) {
-                    const int o0 = (ly + 1) * STG_W + lx + 1;
+                const float *xc = P.chi[p], *xu = P.ux[p], *xv = P.uy[p];
 #pragma unroll
-                    for (int q = 0; q < 9; q++) {
-                        const int o = (present >> q) & 1u ? o0 + cyq(q) * STG_W + cxq(q) : o0;
-                        S.chi[q] = stg[o]; S.ux[q] = stg[STG_N + o]; S.uy[q] = stg[2 * STG_N + o];
-                    }
-                } else {
-                    const float *xc = P.chi[p], *xu = P.ux[p], *xv = P.uy[p];
-#pragma unroll
-                    for (int q = 0; q < 9; q++) {
-                        S.chi[q] = __ldg(xc + nbs[q]); S.ux[q] = __ldg(xu + nbs[q]); S.uy[q] = __ldg(xv + nbs[q]);
-                    }
+                for (int q = 0; q < 9; q++) {
+                    S.chi[q] = __ldg(xc + nbs[q]); S.ux[q] = __ldg(xu + nbs[q]); S.uy[q] = __ldg(xv + nbs[q]);
                 }
                 chin = sa_update(S, __ldg(P.inv_d2 + slot), P.nu, k.sa_convection);
             }
@@ -915,33 +871,21 @@ static void launch_pdl(void (*kern)(Args...), unsigned grid, cudaStream_t st, in
 }
 
 // the level holding the wall records is the finest one, which has no child level
-template <typename T, int MINB, bool STAGE>
+template <typename T, int MINB>
 static void launch_level_mb(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
                             const RecView &R, const StepConsts &k, const LevelStep &ls, int pdl)
 {
-    if (ls.wall) launch_pdl(k_level<true, false, T, MINB, STAGE>, P.n_work_tiles, st, pdl, P, Fv, Cv, R, k, ls);
-    else if (child) launch_pdl(k_level<false, true, T, MINB, STAGE>, P.n_work_tiles, st, pdl, P, Fv, Cv, R, k, ls);
-    else launch_pdl(k_level<false, false, T, MINB, STAGE>, P.n_work_tiles, st, pdl, P, Fv, Cv, R, k, ls);
-}
-
-template <typename T, bool STAGE>
-static void launch_level_st(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
-                            const RecView &R, const StepConsts &k, const LevelStep &ls, const LevelTune &tu)
-{
-    switch (tu.min_blocks) {
-    case 3: launch_level_mb<T, 3, STAGE>(st, P, Fv, Cv, child, R, k, ls, tu.pdl); break;
-    case 4: launch_level_mb<T, 4, STAGE>(st, P, Fv, Cv, child, R, k, ls, tu.pdl); break;
-    case 6: launch_level_mb<T, 6, STAGE>(st, P, Fv, Cv, child, R, k, ls, tu.pdl); break;
-    default: launch_level_mb<T, 5, STAGE>(st, P, Fv, Cv, child, R, k, ls, tu.pdl); break;
-    }
+    if (ls.wall) launch_pdl(k_level<true, false, T, MINB>, P.n_work_tiles, st, pdl, P, Fv, Cv, R, k, ls);
+    else if (child) launch_pdl(k_level<false, true, T, MINB>, P.n_work_tiles, st, pdl, P, Fv, Cv, R, k, ls);
+    else launch_pdl(k_level<false, false, T, MINB>, P.n_work_tiles, st, pdl, P, Fv, Cv, R, k, ls);
 }
 
 template <typename T>
 static void launch_level_t(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
                            const RecView &R, const StepConsts &k, const LevelStep &ls, const LevelTune &tu)
 {
-    if (tu.stage) launch_level_st<T, true>(st, P, Fv, Cv, child, R, k, ls, tu);
-    else launch_level_st<T, false>(st, P, Fv, Cv, child, R, k, ls, tu);
+    if (tu.min_blocks == 6) launch_level_mb<T, 6>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+    else launch_level_mb<T, 5>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
 }
 
 void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,

@@ -101,7 +101,6 @@ struct lbm_solver {
     StepConsts k;
     int parity[LBM_MAXL];
     int min_blocks[LBM_MAXL];     // register budget of each level's kernel (lbm_autotune)
-    int stage[LBM_MAXL];          // SA-neg stencil staged in shared memory (lbm_autotune)
     int pdl = 1;                  // programmatic dependent launch (lbm_autotune)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<void *> allocs;
@@ -161,8 +160,9 @@ static void *dalloc(lbm_solver *s, size_t bytes)
         p = nullptr;
     }
     if (p && ((uintptr_t)p & 255u)) {
-        // the level kernels stage 1 KB tile planes with bulk copies: every array must be
-        // at least 16-byte aligned (cudaMalloc gives 256); refuse anything less than 256
+        // every tile plane (1 KB in FP32) starts on a 256-byte boundary only if its array
+        // does, which keeps each warp's row segments in whole sectors (cudaMalloc gives
+        // 256-byte alignment); refuse anything less
         if (s->cfg.dev_free) s->cfg.dev_free(p, (void *)s->stream, s->cfg.alloc_ctx);
         return nullptr;
     }
@@ -258,7 +258,7 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     ls.pp = C ? s->parity[l - 1] : 0;
     ls.status = s->d_status;
     mark_begin(s);
-    const lbmdev::LevelTune tu{s->min_blocks[l], s->stage[l], s->pdl};
+    const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl};
     lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls, tu);
     mark_end(s, l == L - 1 ? KC_LEVEL_FINEST : KC_LEVEL_COARSE, P.ns, l);
     nk++;
@@ -313,7 +313,7 @@ static lbm_status check_status(lbm_solver *s)
     int st = 0;
     CK(cudaMemcpyAsync(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
-    if (st & LBM_STATUS_TIMEOUT) return fail(s, LBM_ERR_TIMEOUT, "a staged tile copy did not arrive (wait limit)");
+    if (st & LBM_STATUS_TIMEOUT) return fail(s, LBM_ERR_TIMEOUT, "a device wait reached its limit");
     if (st & LBM_STATUS_NONFINITE) return fail(s, LBM_ERR_DIVERGED, "diverged (non-finite field)");
     if (st) return fail(s, LBM_ERR_CUDA, "device status word set");
     return LBM_OK;
@@ -341,7 +341,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
     s->cfg = *cfg;
     s->L = cfg->levels;
     s->U = cfg->Ma * std::sqrt(1.0 / 3.0);
-    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; s->stage[l] = 0; }
+    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; }
     if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LBM_ERR_CUDA; }
     if (cfg->cuda_stream) {
         s->stream = (cudaStream_t)cfg->cuda_stream;
@@ -990,23 +990,20 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
 {
     if (!s || !out || steps < 1) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
-    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {3, 4, 5, 6, 3, 4, 5, 6};
-    static const int CAND_ST[LBM_TUNE_CANDIDATES] = {0, 0, 0, 0, 1, 1, 1, 1};
+    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6};
     std::memset(out, 0, sizeof *out);
     const int L = s->L;
     out->levels = L;
     lbm_status st;
     if ((st = graph_step_time(s, steps, &out->default_step_us)) != LBM_OK) return st;
-    int keep_mb[LBM_MAXL], keep_st[LBM_MAXL];
-    for (int l = 0; l < L; l++) { keep_mb[l] = s->min_blocks[l]; keep_st[l] = s->stage[l]; }
-    // 1: kernel variant per level (register budget, stencil staging), from per-launch
-    //    event timings of every candidate
+    int keep_mb[LBM_MAXL];
+    for (int l = 0; l < L; l++) keep_mb[l] = s->min_blocks[l];
+    // 1: register budget per level, from per-launch event timings of every candidate
     for (int c = 0; c < LBM_TUNE_CANDIDATES; c++) {
-        for (int l = 0; l < L; l++) { s->min_blocks[l] = CAND_MB[c]; s->stage[l] = CAND_ST[c]; }
+        for (int l = 0; l < L; l++) s->min_blocks[l] = CAND_MB[c];
         out->candidate_min_blocks[c] = CAND_MB[c];
-        out->candidate_stage[c] = CAND_ST[c];
         if ((st = level_launch_times(s, steps, out->level_us[c])) != LBM_OK) {
-            for (int l = 0; l < L; l++) { s->min_blocks[l] = keep_mb[l]; s->stage[l] = keep_st[l]; }
+            for (int l = 0; l < L; l++) s->min_blocks[l] = keep_mb[l];
             return st;
         }
     }
@@ -1015,9 +1012,7 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
         for (int c = 1; c < LBM_TUNE_CANDIDATES; c++)
             if (out->level_us[c][l] < out->level_us[best][l]) best = c;
         s->min_blocks[l] = CAND_MB[best];
-        s->stage[l] = CAND_ST[best];
         out->min_blocks[l] = CAND_MB[best];
-        out->stage[l] = CAND_ST[best];
     }
     // 2: programmatic dependent launch on or off, from whole graph steps
     for (int pdl = 0; pdl < 2; pdl++) {
@@ -1030,6 +1025,18 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     if ((st = capture_graphs(s)) != LBM_OK) return st;
     out->steps_taken = (long long)steps * (3 + LBM_TUNE_CANDIDATES);
     return check_status(s);
+}
+
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, int pdl)
+{
+    if (!s || !min_blocks || (pdl != 0 && pdl != 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    for (int l = 0; l < s->L; l++)
+        if (min_blocks[l] != 5 && min_blocks[l] != 6)
+            return fail(s, LBM_ERR_INVALID_ARG, "launch variant: min_blocks must be 5 or 6");
+    for (int l = 0; l < s->L; l++) s->min_blocks[l] = min_blocks[l];
+    s->pdl = pdl;
+    return capture_graphs(s);
 }
 
 }  // extern "C"

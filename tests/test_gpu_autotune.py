@@ -1,6 +1,7 @@
 """lbm_autotune on the GPU: its choices are valid, and the tuned solve stays bit-identical
 to an untuned one (every launch variant computes the same numbers), both through the
-eager timing steps of all candidates and through the recaptured step graphs."""
+eager timing steps of all candidates and through the recaptured step graphs; and each
+variant set directly gives the same populations as the default."""
 import numpy as np
 import pytest
 
@@ -22,10 +23,9 @@ def test_autotuned_solve_equals_the_default_one(store):
     b.step(3)                      # odd level-0 parity: the recapture starts from graph 1
     rep = b.autotune(steps=2)
     L = cfg["levels"]
-    assert rep["steps_taken"] == 2 * 11 and rep["levels"] == L
-    assert rep["candidates"] == [(m, st) for st in (0, 1) for m in (3, 4, 5, 6)]
-    assert all(m in (3, 4, 5, 6) for m in rep["min_blocks"]) and rep["pdl"] in (0, 1)
-    assert all(st in (0, 1) for st in rep["stage"])
+    assert rep["steps_taken"] == 2 * 5 and rep["levels"] == L
+    assert rep["candidates"] == [5, 6]
+    assert all(m in (5, 6) for m in rep["min_blocks"]) and rep["pdl"] in (0, 1)
     assert all(t > 0 for ts in rep["level_us"].values() for t in ts)
     assert rep["default_step_us"] > 0 and min(rep["step_us"].values()) > 0
     a.step(rep["steps_taken"])
@@ -37,3 +37,20 @@ def test_autotuned_solve_equals_the_default_one(store):
         assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), l
     la, lb = a.coefficients(), b.coefficients()
     assert la["step"] == lb["step"] and abs(la["CL"] - lb["CL"]) < 1e-12
+
+
+@pytest.mark.parametrize("mb,pdl", [(6, 1), (5, 0), (6, 0)])
+def test_each_launch_variant_computes_the_same_numbers(mb, pdl):
+    pkg.build()
+    cfg, loops = W.naca0012_small(levels=5)
+    L = cfg["levels"]
+    a, b = pkg.Solver(cfg), pkg.Solver(cfg)
+    a.set_geometry(loops)
+    b.set_geometry(loops)
+    b.set_launch_variant([mb] * L, pdl)
+    a.step(6)
+    b.step(6)
+    for l in range(L):
+        assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), l
+    with pytest.raises(pkg.LBMError):
+        b.set_launch_variant([4] * L, 1)
