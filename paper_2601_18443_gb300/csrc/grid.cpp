@@ -15,6 +15,7 @@
 #include "grid.hpp"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -148,6 +149,51 @@ struct SegTree {
             }
         }
         return best;
+    }
+    // distance from p to the nearest segment, searching only within `bound` (an upper bound
+    // of that distance, or infinity); squared distances throughout, so that the result
+    // equals the sqrt of the smallest squared distance nearest() evaluates: bit for bit
+    // the distance nearest() returns.  Infinity if no segment lies within bound.
+    double nearest_dist(double px, double py, double bound, int &kfound) const
+    {
+        double best2 = bound * bound;
+        bool found = false;
+        kfound = -1;
+        if (root < 0) return std::numeric_limits<double>::infinity();
+        int stack[128];
+        int sp = 0;
+        stack[sp++] = root;
+        while (sp) {
+            const Node &nd = nodes[stack[--sp]];
+            if (box_dist2(nd, px, py) > best2) continue;
+            if (nd.left < 0) {
+                for (int k = nd.lo; k < nd.hi; k++) {
+                    const double d2 = seg_dist2(k, px, py);
+                    if (d2 <= best2) { best2 = d2; found = true; kfound = k; }
+                }
+            } else {
+                double dl = box_dist2(nodes[nd.left], px, py), dr = box_dist2(nodes[nd.right], px, py);
+                if (dl <= dr) { stack[sp++] = nd.right; stack[sp++] = nd.left; }
+                else { stack[sp++] = nd.left; stack[sp++] = nd.right; }
+            }
+        }
+        return found ? std::sqrt(best2) : std::numeric_limits<double>::infinity();
+    }
+    double seg_dist2(int k, double px, double py) const
+    {
+        double dx = bx[k] - ax[k], dy = by[k] - ay[k];
+        double len2 = dx * dx + dy * dy;
+        double t = len2 > 0 ? ((px - ax[k]) * dx + (py - ay[k]) * dy) / len2 : 0.0;
+        if (t < 0) t = 0;
+        if (t > 1) t = 1;
+        const double qx = ax[k] + t * dx, qy = ay[k] + t * dy;
+        return (px - qx) * (px - qx) + (py - qy) * (py - qy);
+    }
+    static double box_dist2(const Node &nd, double px, double py)
+    {
+        double dx = std::max(0.0, std::max(nd.x0 - px, px - nd.x1));
+        double dy = std::max(0.0, std::max(nd.y0 - py, py - nd.y1));
+        return dx * dx + dy * dy;
     }
     void overlapping(double x0, double y0, double x1, double y1, std::vector<int> &out) const
     {
@@ -318,19 +364,47 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
     R[L - 1] = (long long)sp.layers * FIXU;
     for (int l = L - 2; l >= 1; l--) R[l] = R[l + 1] + (long long)sp.layers * g.lv[l].scale * FIXU;
 
+    // runs of consecutive segments whose joint bounding box stays within the smallest band
+    // radius: one pass over a run's candidate cells tests all of its segments
+    std::vector<int> run_start;
+    {
+        const long long lim = R[L - 1];
+        long long x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        for (int k = 0; k < (int)g.sa.size(); k++) {
+            IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
+            const long long ax = std::min(a.x, b.x), bx = std::max(a.x, b.x);
+            const long long ay = std::min(a.y, b.y), by = std::max(a.y, b.y);
+            if (run_start.empty() || std::max(bx, x1) - std::min(ax, x0) > lim || std::max(by, y1) - std::min(ay, y0) > lim ||
+                k - run_start.back() >= 64) {
+                run_start.push_back(k);
+                x0 = ax; x1 = bx; y0 = ay; y1 = by;
+            } else {
+                x0 = std::min(x0, ax); x1 = std::max(x1, bx); y0 = std::min(y0, ay); y1 = std::max(y1, by);
+            }
+        }
+        run_start.push_back((int)g.sa.size());
+    }
+    const long nruns = (long)run_start.size() - 1;
+
     for (int l = 1; l < L; l++) {
         Level &P = g.lv[l - 1];
         const long long hh = P.scale * FIXU / 2;
-        // refinement: candidate cells around each segment, exact distance test (segments
-        // in parallel; a cell found near any segment is marked, marks only go 0 -> 1)
+        // refinement: candidate cells around each run of segments, exact distance test
+        // (runs in parallel; a cell found near any segment is marked, marks only go 0 -> 1)
         std::vector<uint8_t> near(P.kind.size(), 0);
-#pragma omp parallel for schedule(dynamic, 64)
-        for (long k = 0; k < (long)g.sa.size(); k++) {
-            IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
-            long long il = cdiv((i128)std::min(a.x, b.x) - R[l] - hh, 2 * (i128)hh);
-            long long ih = fdiv((i128)std::max(a.x, b.x) + R[l] - hh, 2 * (i128)hh);
-            long long jl = cdiv((i128)std::min(a.y, b.y) - R[l] - hh, 2 * (i128)hh);
-            long long jh = fdiv((i128)std::max(a.y, b.y) + R[l] - hh, 2 * (i128)hh);
+#pragma omp parallel for schedule(dynamic, 4)
+        for (long ru = 0; ru < nruns; ru++) {
+            const int k0 = run_start[ru], k1 = run_start[ru + 1];
+            long long x0 = LLONG_MAX, x1 = LLONG_MIN, y0 = LLONG_MAX, y1 = LLONG_MIN;
+            for (int k = k0; k < k1; k++) {
+                IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
+                x0 = std::min({x0, a.x, b.x}); x1 = std::max({x1, a.x, b.x});
+                y0 = std::min({y0, a.y, b.y}); y1 = std::max({y1, a.y, b.y});
+            }
+            long long il = cdiv((i128)x0 - R[l] - hh, 2 * (i128)hh);
+            long long ih = fdiv((i128)x1 + R[l] - hh, 2 * (i128)hh);
+            long long jl = cdiv((i128)y0 - R[l] - hh, 2 * (i128)hh);
+            long long jh = fdiv((i128)y1 + R[l] - hh, 2 * (i128)hh);
             il = std::max<long long>(il, P.bi0); jl = std::max<long long>(jl, P.bj0);
             ih = std::min<long long>(ih, (long long)P.bi0 + P.bnx - 1);
             jh = std::min<long long>(jh, (long long)P.bj0 + P.bny - 1);
@@ -340,7 +414,16 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                     uint8_t seen;
 #pragma omp atomic read
                     seen = near[c];
-                    if (seen || P.kind[c] != KIND_ACTIVE || !within_r(a, b, centre(P, i, j), R[l])) continue;
+                    if (seen || P.kind[c] != KIND_ACTIVE) continue;
+                    const IPt pc = centre(P, i, j);
+                    // every segment of the run lies in its bounding box: a centre farther
+                    // than R from the box is farther than R from all of them
+                    const i128 dx = pc.x < x0 ? (i128)x0 - pc.x : (pc.x > x1 ? (i128)pc.x - x1 : 0);
+                    const i128 dy = pc.y < y0 ? (i128)y0 - pc.y : (pc.y > y1 ? (i128)pc.y - y1 : 0);
+                    if (dx * dx + dy * dy > (i128)R[l] * R[l]) continue;
+                    bool hit = false;
+                    for (int k = k0; k < k1 && !hit; k++) hit = within_r(g.v[g.sa[k]], g.v[g.sb[k]], pc, R[l]);
+                    if (!hit) continue;
 #pragma omp atomic write
                     near[c] = 1;
                 }
@@ -423,20 +506,28 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
     for (int l = 0; l < L; l++) {
         Level &P = g.lv[l];
 #pragma omp parallel for schedule(dynamic, 4)
-        for (int r = 0; r < P.bny; r++)
+        for (int r = 0; r < P.bny; r++) {
+            // the nearest segment of the previous cell in the row bounds the search: the
+            // distance to that segment is at least the distance to the nearest one
+            int kprev = -1;
             for (int q = 0; q < P.bnx; q++) {
                 size_t c = (size_t)r * P.bnx + q;
                 if (P.kind[c] != KIND_ACTIVE || P.solid[c]) continue;
                 double dd = DCAP;
                 if (sp.solid_walls && !g.sa.empty()) {
-                    int kb;
-                    double cx, cy;
                     double px = (P.bi0 + q + 0.5) * (double)P.scale, py = (P.bj0 + r + 0.5) * (double)P.scale;
-                    dd = T.nearest(px, py, kb, cx, cy) / (double)P.scale;
+                    const double bound = kprev >= 0 ? std::sqrt(T.seg_dist2(kprev, px, py)) * (1.0 + 1e-9) + 1e-9
+                                                    : std::numeric_limits<double>::infinity();
+                    int kb;
+                    double d = T.nearest_dist(px, py, bound, kb);
+                    if (std::isinf(d)) d = T.nearest_dist(px, py, std::numeric_limits<double>::infinity(), kb);
+                    kprev = kb;
+                    dd = d / (double)P.scale;
                     if (dd > DCAP) dd = DCAP;
                 }
                 P.dist[c] = dd;
             }
+        }
     }
     // wall records in (j, i) order at the finest level
     Level &Fn = g.lv[L - 1];
