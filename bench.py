@@ -328,6 +328,10 @@ def gpu_arm(args, rank, world, dist):
                            "ms_per_step": round(msum / kk, 4), "bytes_per_node_update": bpn3,
                            "finest_kernel_gbs": round(act_fin * bpn3 / (avg3 * 1e-3) / 1e9, 1)}
             s3.close()
+            # the same storage on the HBM-bound 4096^2 level (SA on), against FP32 there
+            g16 = hbm_grid_roofline(pkg, stream, peak, peak_kind, tune=not args.no_autotune, store=store)
+            forms[name]["hbm_grid_mlups"] = g16["mlups"]
+            forms[name]["hbm_grid_frac"] = g16["frac"]
 
     if rank == 0:
         line = {
@@ -368,12 +372,12 @@ def gpu_arm(args, rank, world, dist):
     return 0
 
 
-def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096, turbulence=1, tune=True):
+def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096, turbulence=1, tune=True, store=0):
     """The level kernel on one periodic 4096 x 4096 level (1.4-1.7 GB of traffic per
     launch, far beyond L2): its HBM roofline without multilevel effects; turbulence=0
     leaves the stream-collide alone (84 B per node update)."""
     cfg = W.base_config(levels=1, nx0=n, ny0=n, h0=1.0, Re=1000.0, Ma=0.1, periodic=1, solid_walls=0,
-                        turbulence=turbulence, wall_model=3)
+                        turbulence=turbulence, wall_model=3, store=store)
     s = pkg.Solver(cfg, stream=stream)
     s.set_geometry([])
     if tune:
@@ -387,7 +391,7 @@ def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096, turbulence=1, tune=T
     s.close()
     ach = bpl / (avg * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-            "traffic": ncu_traffic("hbm_grid_launch") if turbulence else None, "kernel": "k_level", "grid": f"{n}x{n} periodic, 1 level, SA {'on' if turbulence else 'off'}",
+            "traffic": ncu_traffic("hbm_grid_launch") if turbulence and not store else None, "kernel": "k_level", "grid": f"{n}x{n} periodic, 1 level, SA {'on' if turbulence else 'off'}",
             "bytes_per_launch": int(bpl),
             "avg_launch_ms": round(avg, 4), "mlups": round(info["cells_active"][0] / avg / 1e3, 1),
             "peak_kind": peak_kind}
