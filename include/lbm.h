@@ -214,6 +214,21 @@ typedef struct {
 } lbm_tune_report;
 lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out);
 
+/* Checkpoint and resume.  Not in the paper.  lbm_get_state copies the solve's state at the
+ * current level-0 step into a host buffer: for every level its populations and its rho - 1,
+ * u, chi at the current time level (raw device layout), the wall records' Newton start
+ * values, the step count and the last C_L.  With buf NULL it only returns the size.  That
+ * is enough to continue bit for bit: lbm_set_state into a solver created with the same
+ * configuration and geometry (or into the same solver, to rewind) makes its next steps
+ * equal to those the saved solve would have taken.  The blob records the grid (a hash of
+ * the cell flags), and set_state rejects a blob from another configuration or grid with
+ * LBM_ERR_INVALID_ARG.  It also clears the device status word.  Both calls are
+ * synchronous.  The wall-function outputs (lbm_get_wall_state) are not part of the state;
+ * the next step or lbm_get_loads recomputes them.  Errors: LBM_ERR_INVALID_ARG,
+ * LBM_ERR_NO_GEOMETRY, LBM_ERR_CUDA. */
+lbm_status lbm_get_state(lbm_solver *s, void *buf, size_t cap, size_t *size);
+lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size);
+
 /* Set the launch variant directly (for instance one lbm_autotune found on a solve of the
  * same shape): min_blocks[l] in {5, 6} for each of the solver's levels, pdl 0 or 1; the
  * step graphs are recaptured.  No device work.

@@ -110,6 +110,8 @@ def library():
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
         "lbm_set_launch_variant": ([vp, ip, C.c_int], C.c_int),
+        "lbm_get_state": ([vp, vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
+        "lbm_set_state": ([vp, vp, C.c_size_t], C.c_int),
         "lbm_level_mass_noalloc": ([vp, vp, vp, vp, vp, C.c_longlong, C.c_double, vp, vp, vp], C.c_int),
         "lbm_last_error": ([vp], C.c_char_p),
         "lbm_destroy": ([vp], None),
@@ -323,6 +325,19 @@ class Solver:
         out = lbm_tune_report()
         self._check(self._lib.lbm_autotune(self._h, int(steps), C.byref(out)))
         return _tune_dict(out)
+
+    def get_state(self) -> np.ndarray:
+        """lbm_get_state: the solve's state at the current step as a uint8 array."""
+        n = C.c_size_t()
+        self._check(self._lib.lbm_get_state(self._h, None, 0, C.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        self._check(self._lib.lbm_get_state(self._h, buf.ctypes.data_as(C.c_void_p), buf.size, C.byref(n)))
+        return buf
+
+    def set_state(self, blob):
+        """lbm_set_state: continue from a blob of get_state (same configuration and grid)."""
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        self._check(self._lib.lbm_set_state(self._h, b.ctypes.data_as(C.c_void_p), b.size))
 
     def set_launch_variant(self, min_blocks, pdl=1):
         """lbm_set_launch_variant: per-level register budget (5 or 6 blocks per SM) and PDL."""

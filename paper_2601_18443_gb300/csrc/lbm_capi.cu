@@ -1027,6 +1027,97 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     return check_status(s);
 }
 
+// ---------------------------------------------------------------- checkpoint / resume
+struct StateHeader {
+    char magic[8];                 // "LBMSTAT1"
+    int levels, store, turbulence, have_cl;
+    long long step, nrec;
+    double last_cl;
+    long long ns[LBM_MAXL];
+    unsigned long long grid_hash;  // FNV-1a of every level's flag words
+};
+
+static unsigned long long grid_hash(const lbm_solver *s)
+{
+    unsigned long long h = 1469598103934665603ull;
+    for (int l = 0; l < s->L; l++)
+        for (uint32_t w : s->lv[l].flags)
+            for (int b = 0; b < 4; b++) { h ^= (w >> (8 * b)) & 0xFFu; h *= 1099511628211ull; }
+    return h;
+}
+
+static size_t state_bytes(const lbm_solver *s)
+{
+    size_t n = sizeof(StateHeader);
+    const size_t pb = pop_bytes(s->cfg.store);
+    for (int l = 0; l < s->L; l++) n += (size_t)s->lv[l].v.ns * (9 * pb + 4 * sizeof(float));
+    return n + (size_t)s->rec.n * sizeof(float);
+}
+
+lbm_status lbm_get_state(lbm_solver *s, void *buf, size_t cap, size_t *size)
+{
+    if (!s || !size) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    *size = state_bytes(s);
+    if (!buf) return LBM_OK;
+    if (cap < *size) return fail(s, LBM_ERR_INVALID_ARG, "state buffer too small");
+    CK(cudaStreamSynchronize(s->stream));
+    StateHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "LBMSTAT1", 8);
+    h.levels = s->L; h.store = s->cfg.store; h.turbulence = s->cfg.turbulence; h.have_cl = s->have_cl;
+    h.step = s->step; h.nrec = s->rec.n; h.last_cl = s->last_cl;
+    for (int l = 0; l < s->L; l++) h.ns[l] = s->lv[l].v.ns;
+    h.grid_hash = grid_hash(s);
+    unsigned char *o = (unsigned char *)buf;
+    std::memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    const size_t pb = pop_bytes(s->cfg.store);
+    for (int l = 0; l < s->L; l++) {
+        const LevelView &v = s->lv[l].v;
+        const int p = s->parity[l];
+        const size_t nf = 9 * (size_t)v.ns * pb, nm = (size_t)v.ns * sizeof(float);
+        CK(cudaMemcpyAsync(o, v.f[p], nf, cudaMemcpyDeviceToHost, s->stream)); o += nf;
+        const float *m[4] = {v.drho[p], v.ux[p], v.uy[p], v.chi[p]};
+        for (const float *a : m) { CK(cudaMemcpyAsync(o, a, nm, cudaMemcpyDeviceToHost, s->stream)); o += nm; }
+    }
+    if (s->rec.n > 0) CK(cudaMemcpyAsync(o, s->rec.utau_start, (size_t)s->rec.n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
+{
+    if (!s || !buf) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    StateHeader h;
+    if (size < sizeof h) return fail(s, LBM_ERR_INVALID_ARG, "state blob too short");
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, "LBMSTAT1", 8) != 0) return fail(s, LBM_ERR_INVALID_ARG, "not a state blob");
+    bool same = h.levels == s->L && h.store == s->cfg.store && h.turbulence == s->cfg.turbulence && h.nrec == s->rec.n;
+    for (int l = 0; same && l < s->L; l++) same = h.ns[l] == s->lv[l].v.ns;
+    if (!same || h.grid_hash != grid_hash(s)) return fail(s, LBM_ERR_INVALID_ARG, "state blob from another configuration or grid");
+    if (size != state_bytes(s)) return fail(s, LBM_ERR_INVALID_ARG, "state blob size differs");
+    const unsigned char *o = (const unsigned char *)buf + sizeof h;
+    const size_t pb = pop_bytes(s->cfg.store);
+    CK(cudaStreamSynchronize(s->stream));
+    for (int l = 0; l < s->L; l++) {
+        LevelView &v = s->lv[l].v;
+        const int p = s->parity[l];
+        const size_t nf = 9 * (size_t)v.ns * pb, nm = (size_t)v.ns * sizeof(float);
+        CK(cudaMemcpyAsync(v.f[p], o, nf, cudaMemcpyHostToDevice, s->stream)); o += nf;
+        float *m[4] = {v.drho[p], v.ux[p], v.uy[p], v.chi[p]};
+        for (float *a : m) { CK(cudaMemcpyAsync(a, o, nm, cudaMemcpyHostToDevice, s->stream)); o += nm; }
+    }
+    if (s->rec.n > 0) CK(cudaMemcpyAsync(s->rec.utau_start, o, (size_t)s->rec.n * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->step = h.step;
+    s->have_cl = h.have_cl != 0;
+    s->last_cl = h.last_cl;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, int pdl)
 {
     if (!s || !min_blocks || (pdl != 0 && pdl != 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
