@@ -356,7 +356,7 @@ def gpu_arm(args, rank, world, dist):
             "loads": {"CL": loads["CL"], "CD": loads["CD"], "step": loads["step"]},
             "e2e": e2e,
             "autotune": None if tune is None else {
-                "min_blocks_per_level": tune["min_blocks"], "pdl": tune["pdl"],
+                "min_blocks_per_level": tune["min_blocks"], "pdl": tune["pdl"], "wall_split": tune["wall_split"],
                 "step_us_default": round(tune["default_step_us"], 2),
                 "step_us_tuned": round(min(tune["step_us"].values()), 2)},
         }

@@ -102,6 +102,7 @@ struct lbm_solver {
     int parity[LBM_MAXL];
     int min_blocks[LBM_MAXL];     // register budget of each level's kernel (lbm_autotune)
     int pdl = 1;                  // programmatic dependent launch (lbm_autotune)
+    int wall_split = 0;           // wall function in its own launch (lbm_autotune)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<void *> allocs;
     double device_bytes = 0;
@@ -203,8 +204,8 @@ static T *upload(lbm_solver *s, const std::vector<T> &h, bool &ok)
 
 // ---------------------------------------------------------------- scheduler
 // Kernel classes for lbm_time_kernels.
-enum { KC_LEVEL_FINEST = 0, KC_LEVEL_COARSE = 1, KC_PROLONG = 2, KC_N = 3 };
-static const char *KC_NAME[KC_N] = {"level_step_finest", "level_step_coarse", "prolong"};
+enum { KC_LEVEL_FINEST = 0, KC_LEVEL_COARSE = 1, KC_PROLONG = 2, KC_WALLFN = 3, KC_N = 4 };
+static const char *KC_NAME[KC_N] = {"level_step_finest", "level_step_coarse", "prolong", "wall_function"};
 
 static void mark_begin(lbm_solver *s)
 {
@@ -257,6 +258,13 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     ls.restrict_up = restrict_up && C != nullptr;
     ls.pp = C ? s->parity[l - 1] : 0;
     ls.status = s->d_status;
+    ls.wall_pre = ls.wall && s->wall_split;
+    if (ls.wall_pre) {
+        mark_begin(s);
+        lbmdev::launch_wallfn_step(st, P, s->parity[l], s->rec, s->k, s->pdl);
+        mark_end(s, KC_WALLFN, s->rec.n, -1);
+        nk++;
+    }
     mark_begin(s);
     const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl};
     lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls, tu);
@@ -955,7 +963,8 @@ static lbm_status level_launch_times(lbm_solver *s, int n, double *us)
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(s->stream));
         for (size_t m = 0; m < s->ev_marks.size(); m++) {
-            if (s->ev_marks[m].first == KC_PROLONG) continue;
+            const int cls = s->ev_marks[m].first;
+            if (cls != KC_LEVEL_FINEST && cls != KC_LEVEL_COARSE) continue;
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, s->ev_pool[s->ev_marks[m].second], s->ev_pool[s->ev_marks[m].second + 1]));
             tot[s->ev_level[m]] += 1e3 * ms;
@@ -1022,8 +1031,19 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     }
     s->pdl = out->step_us[1] <= out->step_us[0] ? 1 : 0;
     out->pdl = s->pdl;
+    // 3: the finest level's wall function fused into its launch, or in a launch of its own
+    out->step_us_wall[0] = out->step_us[s->pdl];
+    long long extra = 0;
+    if (s->rec.n > 0) {
+        s->wall_split = 1;
+        if ((st = capture_graphs(s)) != LBM_OK) return st;
+        if ((st = graph_step_time(s, steps, &out->step_us_wall[1])) != LBM_OK) return st;
+        s->wall_split = out->step_us_wall[1] < out->step_us_wall[0] ? 1 : 0;
+        extra = steps;
+    }
+    out->wall_split = s->wall_split;
     if ((st = capture_graphs(s)) != LBM_OK) return st;
-    out->steps_taken = (long long)steps * (3 + LBM_TUNE_CANDIDATES);
+    out->steps_taken = (long long)steps * (3 + LBM_TUNE_CANDIDATES) + extra;
     return check_status(s);
 }
 
@@ -1118,15 +1138,17 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, int pdl)
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, int pdl, int wall_split)
 {
-    if (!s || !min_blocks || (pdl != 0 && pdl != 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s || !min_blocks || (pdl != 0 && pdl != 1) || (wall_split != 0 && wall_split != 1))
+        return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     for (int l = 0; l < s->L; l++)
         if (min_blocks[l] != 5 && min_blocks[l] != 6)
             return fail(s, LBM_ERR_INVALID_ARG, "launch variant: min_blocks must be 5 or 6");
     for (int l = 0; l < s->L; l++) s->min_blocks[l] = min_blocks[l];
     s->pdl = pdl;
+    s->wall_split = wall_split;
     return capture_graphs(s);
 }
 

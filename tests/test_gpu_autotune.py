@@ -23,7 +23,7 @@ def test_autotuned_solve_equals_the_default_one(store):
     b.step(3)                      # odd level-0 parity: the recapture starts from graph 1
     rep = b.autotune(steps=2)
     L = cfg["levels"]
-    assert rep["steps_taken"] == 2 * 5 and rep["levels"] == L
+    assert rep["steps_taken"] == 2 * 6 and rep["levels"] == L and rep["wall_split"] in (0, 1)
     assert rep["candidates"] == [5, 6]
     assert all(m in (5, 6) for m in rep["min_blocks"]) and rep["pdl"] in (0, 1)
     assert all(t > 0 for ts in rep["level_us"].values() for t in ts)
@@ -39,18 +39,23 @@ def test_autotuned_solve_equals_the_default_one(store):
     assert la["step"] == lb["step"] and abs(la["CL"] - lb["CL"]) < 1e-12
 
 
-@pytest.mark.parametrize("mb,pdl", [(6, 1), (5, 0), (6, 0)])
-def test_each_launch_variant_computes_the_same_numbers(mb, pdl):
+@pytest.mark.parametrize("mb,pdl,split", [(6, 1, 0), (5, 0, 0), (6, 0, 0), (5, 1, 1), (6, 0, 1)])
+def test_each_launch_variant_computes_the_same_numbers(mb, pdl, split):
     pkg.build()
     cfg, loops = W.naca0012_small(levels=5)
     L = cfg["levels"]
     a, b = pkg.Solver(cfg), pkg.Solver(cfg)
     a.set_geometry(loops)
     b.set_geometry(loops)
-    b.set_launch_variant([mb] * L, pdl)
+    b.set_launch_variant([mb] * L, pdl, split)
     a.step(6)
     b.step(6)
     for l in range(L):
         assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), l
     with pytest.raises(pkg.LBMError):
         b.set_launch_variant([4] * L, 1)
+    # queries in between leave the trajectory alone in either wall-function placement
+    a.coefficients(); b.coefficients()
+    a.step(3); b.step(3)
+    for l in range(L):
+        assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), l
