@@ -1007,6 +1007,7 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     if ((st = graph_step_time(s, steps, &out->default_step_us)) != LBM_OK) return st;
     int keep_mb[LBM_MAXL];
     for (int l = 0; l < L; l++) keep_mb[l] = s->min_blocks[l];
+    s->wall_split = 0;            // stages 1-2 time the fused form; stage 3 decides the placement
     // 1: register budget per level, from per-launch event timings of every candidate
     for (int c = 0; c < LBM_TUNE_CANDIDATES; c++) {
         for (int l = 0; l < L; l++) s->min_blocks[l] = CAND_MB[c];
