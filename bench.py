@@ -332,6 +332,9 @@ def gpu_arm(args, rank, world, dist):
             g16 = hbm_grid_roofline(pkg, stream, peak, peak_kind, tune=not args.no_autotune, store=store)
             forms[name]["hbm_grid_mlups"] = g16["mlups"]
             forms[name]["hbm_grid_frac"] = g16["frac"]
+            sc16 = hbm_grid_roofline(pkg, stream, peak, peak_kind, turbulence=0, tune=not args.no_autotune, store=store)
+            forms[name]["stream_collide_mlups"] = sc16["mlups"]
+            forms[name]["stream_collide_frac"] = sc16["frac"]
 
     if rank == 0:
         line = {
