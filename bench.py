@@ -359,7 +359,8 @@ def gpu_arm(args, rank, world, dist):
             "loads": {"CL": loads["CL"], "CD": loads["CD"], "step": loads["step"]},
             "e2e": e2e,
             "autotune": None if tune is None else {
-                "min_blocks_per_level": tune["min_blocks"], "pdl": tune["pdl"], "wall_split": tune["wall_split"],
+                "min_blocks_per_level": tune["min_blocks"], "persistent_per_level": tune["persistent"],
+                "pdl": tune["pdl"], "wall_split": tune["wall_split"],
                 "step_us_default": round(tune["default_step_us"], 2),
                 "step_us_tuned": round(min(tune["step_us"].values()), 2)},
         }
@@ -408,9 +409,9 @@ def profile_case(args):
     import paper_2601_18443_gb300 as pkg
 
     torch.cuda.set_device(0)
-    if args.profile_case == "hbm_grid":
+    if args.profile_case in ("hbm_grid", "hbm_grid_laminar"):
         cfg = W.base_config(levels=1, nx0=4096, ny0=4096, h0=1.0, Re=1000.0, Ma=0.1, periodic=1, solid_walls=0,
-                            turbulence=1, wall_model=3)
+                            turbulence=int(args.profile_case == "hbm_grid"), wall_model=3)
         loops = []
     else:
         cfg, loops = W.naca0012_large()
@@ -497,7 +498,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hbm-grid", action="store_true")
     ap.add_argument("--no-precision-forms", action="store_true")
-    ap.add_argument("--profile-case", choices=["hbm_grid", "workload"], default=None)
+    ap.add_argument("--profile-case", choices=["hbm_grid", "hbm_grid_laminar", "workload"], default=None)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch variant")
     ap.add_argument("--workload", choices=["naca0012", "highlift"], default="naca0012",
                     help="highlift: the three-element 8-level case (2 timed steps, no extra measurements)")

@@ -193,10 +193,12 @@ lbm_status lbm_get_info(lbm_solver *s, lbm_info *out);
 lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times *out);
 
 /* Launch autotuner.  Not part of the paper's method (Sec 2.1 gives the level schedule, not
- * its mapping to a GPU).  For each level it picks the register budget of the fused level
- * kernel among LBM_TUNE_CANDIDATES variants (at least 5 or 6 resident 256-thread blocks
- * per SM, i.e. at most 48 or 40 registers a thread), from per-launch CUDA-event timings
- * of `steps` eager coarse steps per candidate.  Then it picks whether launches use
+ * its mapping to a GPU).  For each level it picks one of LBM_TUNE_CANDIDATES launch forms
+ * of the fused level kernel: a register budget of at least 5 or 6 resident 256-thread
+ * blocks per SM (at most 48 or 40 registers a thread), each either with one block per
+ * tile or with a persistent grid (2 x SMs x that budget) whose blocks stride over the
+ * level's tiles.  The choice comes from per-launch CUDA-event timings of `steps` eager
+ * coarse steps per candidate.  Then it picks whether launches use
  * programmatic dependent launch, from the time of `steps` coarse steps through the step
  * graphs each way; and, when the solve has wall records, whether the finest level's wall
  * function (Sec 2.3 steps 1-5) runs inside the fused level launch or in a compact launch
@@ -204,12 +206,14 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times 
  * then recaptures the graphs with the choice.  Every variant computes bit-identical
  * results; the timed steps are real steps of the solve (steps_taken of them).
  * Synchronous.  Errors as lbm_step. */
-#define LBM_TUNE_CANDIDATES 2
+#define LBM_TUNE_CANDIDATES 4
 typedef struct {
     int levels;
     int candidate_min_blocks[LBM_TUNE_CANDIDATES];
+    int candidate_persistent[LBM_TUNE_CANDIDATES];
     double level_us[LBM_TUNE_CANDIDATES][16]; /* mean launch time of level l's kernel per candidate */
     int min_blocks[16];                       /* chosen register budget per level                  */
+    int persistent[16];                       /* chosen grid schedule per level (1 persistent)     */
     double default_step_us;                   /* coarse step through the graphs before tuning      */
     double step_us[2];                        /* coarse step, chosen kernels, PDL off / on         */
     int pdl;                                  /* chosen: 1 programmatic dependent launch on        */
@@ -235,10 +239,11 @@ lbm_status lbm_get_state(lbm_solver *s, void *buf, size_t cap, size_t *size);
 lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size);
 
 /* Set the launch variant directly (for instance one lbm_autotune found on a solve of the
- * same shape): min_blocks[l] in {5, 6} for each of the solver's levels, pdl 0 or 1,
- * wall_split 0 or 1; the step graphs are recaptured.  No device work.
- * Errors: LBM_ERR_INVALID_ARG for a value outside those sets, LBM_ERR_NO_GEOMETRY. */
-lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, int pdl, int wall_split);
+ * same shape): min_blocks[l] in {5, 6} and persistent[l] in {0, 1} for each of the
+ * solver's levels, pdl 0 or 1, wall_split 0 or 1; the step graphs are recaptured.  No
+ * device work.  Errors: LBM_ERR_INVALID_ARG for a value outside those sets,
+ * LBM_ERR_NO_GEOMETRY. */
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, int pdl, int wall_split);
 
 /* Largest n_cells that lbm_level_mass_noalloc accepts (its fixed scratch holds 4096
  * per-block partial sums of at most 16384 cells each). */

@@ -66,12 +66,14 @@ class lbm_kernel_times(C.Structure):
                 ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
 
 
-TUNE_CANDIDATES = 2
+TUNE_CANDIDATES = 4
 
 
 class lbm_tune_report(C.Structure):
     _fields_ = [("levels", C.c_int), ("candidate_min_blocks", C.c_int * TUNE_CANDIDATES),
+                ("candidate_persistent", C.c_int * TUNE_CANDIDATES),
                 ("level_us", (C.c_double * 16) * TUNE_CANDIDATES), ("min_blocks", C.c_int * 16),
+                ("persistent", C.c_int * 16),
                 ("default_step_us", C.c_double), ("step_us", C.c_double * 2),
                 ("pdl", C.c_int), ("step_us_wall", C.c_double * 2), ("wall_split", C.c_int),
                 ("steps_taken", C.c_longlong)]
@@ -110,7 +112,7 @@ def library():
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
-        "lbm_set_launch_variant": ([vp, ip, C.c_int, C.c_int], C.c_int),
+        "lbm_set_launch_variant": ([vp, ip, ip, C.c_int, C.c_int], C.c_int),
         "lbm_get_state": ([vp, vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
         "lbm_set_state": ([vp, vp, C.c_size_t], C.c_int),
         "lbm_level_mass_noalloc": ([vp, vp, vp, vp, vp, C.c_longlong, C.c_double, vp, vp, vp], C.c_int),
@@ -340,11 +342,12 @@ class Solver:
         b = np.ascontiguousarray(blob, dtype=np.uint8)
         self._check(self._lib.lbm_set_state(self._h, b.ctypes.data_as(C.c_void_p), b.size))
 
-    def set_launch_variant(self, min_blocks, pdl=1, wall_split=0):
-        """lbm_set_launch_variant: per-level register budget (5 or 6 blocks per SM), PDL and
-        whether the wall function runs in its own launch."""
+    def set_launch_variant(self, min_blocks, pdl=1, wall_split=0, persistent=None):
+        """lbm_set_launch_variant: per-level register budget (5 or 6 blocks per SM) and grid
+        schedule (persistent 0/1), PDL, and whether the wall function runs in its own launch."""
         mb = np.ascontiguousarray(min_blocks, dtype=np.int32)
-        self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), int(pdl), int(wall_split)))
+        pe = np.ascontiguousarray(persistent if persistent is not None else [0] * len(mb), dtype=np.int32)
+        self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), _ip(pe), int(pdl), int(wall_split)))
 
     def time_kernels(self, n=1):
         out = lbm_kernel_times()
@@ -355,10 +358,11 @@ class Solver:
 
 def _tune_dict(out):
     L = out.levels
-    cand = list(out.candidate_min_blocks)
+    cand = list(zip(out.candidate_min_blocks, out.candidate_persistent))
     return dict(levels=L, candidates=cand,
                 level_us={c: list(out.level_us[i][:L]) for i, c in enumerate(cand)},
-                min_blocks=list(out.min_blocks[:L]), default_step_us=out.default_step_us,
+                min_blocks=list(out.min_blocks[:L]), persistent=list(out.persistent[:L]),
+                default_step_us=out.default_step_us,
                 step_us={"pdl_off": out.step_us[0], "pdl_on": out.step_us[1]}, pdl=out.pdl,
                 step_us_wall={"fused": out.step_us_wall[0], "own_launch": out.step_us_wall[1]},
                 wall_split=out.wall_split, steps_taken=out.steps_taken)

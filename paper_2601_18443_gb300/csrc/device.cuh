@@ -57,7 +57,7 @@ struct StepConsts {
     float U;            // inlet lattice velocity
     float chi_inf;
     float d_wr, d_wv;
-    int resident_blocks; // persistent grid of the level kernel: SMs x blocks per SM
+    int sms;            // streaming multiprocessors of the device
     float pshift[9];    // 16-bit storage holds g_q - pshift_q (pshift = f_eq(1, U, 0) - w); 0 for FP32
 };
 
@@ -79,11 +79,13 @@ struct LevelStep {
 };
 
 // Launch variant of a level's kernels (chosen by lbm_autotune): the register budget of the
-// fused level kernel, as the minimum resident blocks per SM (5 or 6), and whether launches
-// use programmatic dependent launch.  Every variant computes the same numbers.
+// fused level kernel, as the minimum resident blocks per SM (5 or 6), whether its blocks
+// persist over several tiles, and whether launches use programmatic dependent launch.
+// Every variant computes the same numbers.
 struct LevelTune {
     int min_blocks;
     int pdl;
+    int persistent;     // grid of 2 x SMs x min_blocks blocks striding over the work tiles
 };
 
 // Wall function of every record in a launch of its own (one thread per record), ahead of
@@ -94,7 +96,6 @@ void launch_wallfn_step(cudaStream_t st, const LevelView &P, int p, const RecVie
 void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,
                   const StepConsts &k, const LevelStep &ls, const LevelTune &tu);
 void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pdl);
-int level_blocks_per_sm();
 void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k);
 void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pp, int pf);
 void launch_explode_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pf);

@@ -101,6 +101,7 @@ struct lbm_solver {
     StepConsts k;
     int parity[LBM_MAXL];
     int min_blocks[LBM_MAXL];     // register budget of each level's kernel (lbm_autotune)
+    int persistent[LBM_MAXL];     // persistent grid for each level's kernel (lbm_autotune)
     int pdl = 1;                  // programmatic dependent launch (lbm_autotune)
     int wall_split = 0;           // wall function in its own launch (lbm_autotune)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -266,7 +267,7 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
         nk++;
     }
     mark_begin(s);
-    const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl};
+    const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl, s->persistent[l]};
     lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls, tu);
     mark_end(s, l == L - 1 ? KC_LEVEL_FINEST : KC_LEVEL_COARSE, P.ns, l);
     nk++;
@@ -349,7 +350,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
     s->cfg = *cfg;
     s->L = cfg->levels;
     s->U = cfg->Ma * std::sqrt(1.0 / 3.0);
-    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; }
+    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; s->persistent[l] = 0; }
     if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LBM_ERR_CUDA; }
     if (cfg->cuda_stream) {
         s->stream = (cudaStream_t)cfg->cuda_stream;
@@ -539,7 +540,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     {
         int sms = 0;
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-        s->k.resident_blocks = sms * lbmdev::level_blocks_per_sm();
+        s->k.sms = sms;
     }
     float g9[9];
     feq_shifted(1.0, s->U, 0.0, g9);
@@ -999,21 +1000,24 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
 {
     if (!s || !out || steps < 1) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
-    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6};
+    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6, 5, 6};
+    static const int CAND_PE[LBM_TUNE_CANDIDATES] = {0, 0, 1, 1};
     std::memset(out, 0, sizeof *out);
     const int L = s->L;
     out->levels = L;
     lbm_status st;
     if ((st = graph_step_time(s, steps, &out->default_step_us)) != LBM_OK) return st;
-    int keep_mb[LBM_MAXL];
-    for (int l = 0; l < L; l++) keep_mb[l] = s->min_blocks[l];
+    int keep_mb[LBM_MAXL], keep_pe[LBM_MAXL];
+    for (int l = 0; l < L; l++) { keep_mb[l] = s->min_blocks[l]; keep_pe[l] = s->persistent[l]; }
     s->wall_split = 0;            // stages 1-2 time the fused form; stage 3 decides the placement
-    // 1: register budget per level, from per-launch event timings of every candidate
+    // 1: register budget and grid schedule per level, from per-launch event timings of
+    //    every candidate
     for (int c = 0; c < LBM_TUNE_CANDIDATES; c++) {
-        for (int l = 0; l < L; l++) s->min_blocks[l] = CAND_MB[c];
+        for (int l = 0; l < L; l++) { s->min_blocks[l] = CAND_MB[c]; s->persistent[l] = CAND_PE[c]; }
         out->candidate_min_blocks[c] = CAND_MB[c];
+        out->candidate_persistent[c] = CAND_PE[c];
         if ((st = level_launch_times(s, steps, out->level_us[c])) != LBM_OK) {
-            for (int l = 0; l < L; l++) s->min_blocks[l] = keep_mb[l];
+            for (int l = 0; l < L; l++) { s->min_blocks[l] = keep_mb[l]; s->persistent[l] = keep_pe[l]; }
             return st;
         }
     }
@@ -1022,7 +1026,9 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
         for (int c = 1; c < LBM_TUNE_CANDIDATES; c++)
             if (out->level_us[c][l] < out->level_us[best][l]) best = c;
         s->min_blocks[l] = CAND_MB[best];
+        s->persistent[l] = CAND_PE[best];
         out->min_blocks[l] = CAND_MB[best];
+        out->persistent[l] = CAND_PE[best];
     }
     // 2: programmatic dependent launch on or off, from whole graph steps
     for (int pdl = 0; pdl < 2; pdl++) {
@@ -1139,15 +1145,15 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, int pdl, int wall_split)
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, int pdl, int wall_split)
 {
-    if (!s || !min_blocks || (pdl != 0 && pdl != 1) || (wall_split != 0 && wall_split != 1))
+    if (!s || !min_blocks || !persistent || (pdl != 0 && pdl != 1) || (wall_split != 0 && wall_split != 1))
         return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     for (int l = 0; l < s->L; l++)
-        if (min_blocks[l] != 5 && min_blocks[l] != 6)
-            return fail(s, LBM_ERR_INVALID_ARG, "launch variant: min_blocks must be 5 or 6");
-    for (int l = 0; l < s->L; l++) s->min_blocks[l] = min_blocks[l];
+        if ((min_blocks[l] != 5 && min_blocks[l] != 6) || (persistent[l] != 0 && persistent[l] != 1))
+            return fail(s, LBM_ERR_INVALID_ARG, "launch variant: min_blocks must be 5 or 6, persistent 0 or 1");
+    for (int l = 0; l < s->L; l++) { s->min_blocks[l] = min_blocks[l]; s->persistent[l] = persistent[l]; }
     s->pdl = pdl;
     s->wall_split = wall_split;
     return capture_graphs(s);

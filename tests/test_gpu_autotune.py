@@ -23,8 +23,9 @@ def test_autotuned_solve_equals_the_default_one(store):
     b.step(3)                      # odd level-0 parity: the recapture starts from graph 1
     rep = b.autotune(steps=2)
     L = cfg["levels"]
-    assert rep["steps_taken"] == 2 * 6 and rep["levels"] == L and rep["wall_split"] in (0, 1)
-    assert rep["candidates"] == [5, 6]
+    assert rep["steps_taken"] == 2 * 8 and rep["levels"] == L and rep["wall_split"] in (0, 1)
+    assert rep["candidates"] == [(5, 0), (6, 0), (5, 1), (6, 1)]
+    assert all(pe in (0, 1) for pe in rep["persistent"])
     assert all(m in (5, 6) for m in rep["min_blocks"]) and rep["pdl"] in (0, 1)
     assert all(t > 0 for ts in rep["level_us"].values() for t in ts)
     assert rep["default_step_us"] > 0 and min(rep["step_us"].values()) > 0
@@ -39,15 +40,16 @@ def test_autotuned_solve_equals_the_default_one(store):
     assert la["step"] == lb["step"] and abs(la["CL"] - lb["CL"]) < 1e-12
 
 
-@pytest.mark.parametrize("mb,pdl,split", [(6, 1, 0), (5, 0, 0), (6, 0, 0), (5, 1, 1), (6, 0, 1)])
-def test_each_launch_variant_computes_the_same_numbers(mb, pdl, split):
+@pytest.mark.parametrize("mb,pdl,split,pe", [(6, 1, 0, 0), (5, 0, 0, 0), (6, 0, 0, 1), (5, 1, 1, 0), (6, 0, 1, 0),
+                                          (5, 1, 0, 1), (6, 1, 1, 1)])
+def test_each_launch_variant_computes_the_same_numbers(mb, pdl, split, pe):
     pkg.build()
     cfg, loops = W.naca0012_small(levels=5)
     L = cfg["levels"]
     a, b = pkg.Solver(cfg), pkg.Solver(cfg)
     a.set_geometry(loops)
     b.set_geometry(loops)
-    b.set_launch_variant([mb] * L, pdl, split)
+    b.set_launch_variant([mb] * L, pdl, split, [pe] * L)
     a.step(6)
     b.step(6)
     for l in range(L):
