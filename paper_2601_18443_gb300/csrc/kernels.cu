@@ -451,11 +451,215 @@ template <typename T> struct ShiftedIO {
     }
 };
 
+// One tile of the fused level step (the body of k_level): every thread updates its cell
+// of tile t.  nb3 holds the 3 x 3 neighbour tiles of t for this warp.
+template <bool WALL, bool CHILD, typename T>
+__device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &F, const LevelView &C, const RecView &R,
+                                           const StepConsts &k, const LevelStep &ls, const ShiftedIO<T> &IO, int t,
+                                           int lane, int lx, int ly, const int *nb3)
+{
+    const int slot = t * LBM_TILE + ly * LBM_TX + lx;
+    const uint32_t fl = __ldg(P.flags + slot);
+    const uint32_t kind = fl & FL_KIND_MASK;
+    const bool fluid = !(fl & FL_SOLID);
+    const int ns = P.ns, p = ls.p;
+    const T *fc = static_cast<const T *>(P.f[p]);
+    T *fn = static_cast<T *>(P.f[p ^ 1]);
+    bool valid = false;
+    float n_dr = 0.f, n_ux = 0.f, n_uy = 0.f, n_chi = 0.f;
+
+    if (kind == KIND_GHOST && fluid) {
+        // ghosts are streamed (relayed), never collided
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            const int s = q == 0 ? slot : nb_slot(nb3, lx, ly, -cxq(q), -cyq(q));
+            bool ok = false;
+            if (s >= 0) {
+                const uint32_t fs = __ldg(P.flags + s);
+                const uint32_t ks = fs & FL_KIND_MASK;
+                ok = (ks == KIND_ACTIVE || ks == KIND_GHOST) && !(fs & FL_SOLID);
+            }
+            IO.st(fn + q * ns + slot, q, IO.ld(fc + q * ns + (ok ? s : slot), q));
+        }
+    } else if (kind == KIND_ACTIVE && fluid) {
+        const bool edge = ls.is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
+        const bool bnode = WALL && (fl & FL_BNODE);
+        int nbs[9];
+        neighbours(nb3, lx, ly, slot, nbs);
+        // ---- wall function of the boundary node (Sec 2.3), fields at time t
+        float drW = 0.f, uWx = 0.f, uWy = 0.f, chiB = 0.f;
+        int r = -1;
+        if (bnode) {
+            r = P.rec[slot];
+            if (ls.wall_pre) {
+                drW = R.drhoW[r]; uWx = R.uWx[r]; uWy = R.uWy[r]; chiB = R.chiB[r];
+            } else {
+                wall_record(P, p, R, k, r, true, drW, uWx, uWy, chiB);
+            }
+        }
+        // ---- SA-neg update of chi (Sec 2.2), fields at time t
+        float chin;
+        if (k.turbulence) {
+            if (bnode) {
+                chin = chiB;                                        // Dirichlet nu_t~_B (Sec 2.2)
+            } else if (edge) {
+                const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
+                if (fl & FL_INLET) {
+                    chin = k.chi_inf;
+                } else {
+                    const int ic = (fl & FL_OUTLET) ? k.nx0 - 2 : i;     // outlet: copy of its neighbour
+                    Stencil S;
+                    gather0(P.chi[p], P.ux[p], P.uy[p], k, ic, j, S);
+                    chin = sa_update(S, P.inv_d2[slot0(k, ic, j)], P.nu, k.sa_convection);
+                }
+            } else {
+                Stencil S;
+                const float *xc = P.chi[p], *xu = P.ux[p], *xv = P.uy[p];
+#pragma unroll
+                for (int q = 0; q < 9; q++) {
+                    S.chi[q] = __ldg(xc + nbs[q]); S.ux[q] = __ldg(xu + nbs[q]); S.uy[q] = __ldg(xv + nbs[q]);
+                }
+                chin = sa_update(S, __ldg(P.inv_d2 + slot), P.nu, k.sa_convection);
+            }
+            P.chi[p ^ 1][slot] = chin;
+        } else {
+            chin = __ldg(P.chi[p] + slot);
+        }
+        // ---- pull streaming (eq 1) with coalescence, cut links and box edges
+        float g[9];
+        g[0] = IO.ld(fc + slot, 0);
+        const uint32_t special = fl & (0xFFu << FL_COAL_SHIFT | 0xFFu << FL_CUT_SHIFT);
+        if (!edge && !special) {
+            // plain cell: every direction is pulled from its upstream neighbour
+#pragma unroll
+            for (int q = 1; q < 9; q++) g[q] = IO.ld(fc + q * ns + nbs[oppq(q)], q);
+        } else if (!edge) {
+            int cb = -1;
+            if (CHILD && (fl & FL_BAND)) cb = child_base(P, t, lx, ly);
+#pragma unroll
+            for (int q = 1; q < 9; q++) {
+                if (CHILD && (fl & (1u << (FL_COAL_SHIFT + q - 1)))) {
+                    // coalescence: mean of the four ghost children after the two fine sub-steps
+                    const T *ff = static_cast<const T *>(F.f[ls.pf]) + q * F.ns;
+                    g[q] = cb >= 0 ? 0.25f * (IO.ldp(ff + cb, q) + IO.ldp(ff + cb + 1, q) + IO.ldp(ff + cb + LBM_TX, q) +
+                                              IO.ldp(ff + cb + LBM_TX + 1, q))
+                                   : IO.ld(fc + q * ns + slot, q);
+                } else if (WALL && (fl & (1u << (FL_CUT_SHIFT + q - 1)))) {
+                    // Yu interpolated bounce-back with the slip velocity of the wall record (eq 27)
+                    const int qo = oppq(q);
+                    const float qf = R.q[r * 9 + q];
+                    const float mom = 6.0f * wq(q) * (1.0f + drW) * (cxq(q) * uWx + cyq(q) * uWy);
+                    const int sf = nbs[q];
+                    bool ok = false;
+                    if (sf != slot) {
+                        const uint32_t ff = __ldg(P.flags + sf);
+                        ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
+                    }
+                    if (ok)
+                        g[q] = ((1.0f - qf) * IO.ld(fc + qo * ns + sf, qo) + qf * IO.ld(fc + qo * ns + slot, qo) + mom) /
+                                   (1.0f + qf) +
+                               qf / (1.0f + qf) * IO.ld(fc + q * ns + slot, q);
+                    else
+                        g[q] = IO.ld(fc + qo * ns + slot, qo) + mom;        // half-way form, eq 24
+                } else {
+                    g[q] = IO.ld(fc + q * ns + nbs[oppq(q)], q);
+                }
+            }
+        } else {
+            // level-0 box edge: in-box pulls, symmetry planes, Zou-He inlet, zero-gradient outlet (Sec 3.1.1)
+            const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
+#pragma unroll
+            for (int q = 1; q < 9; q++) {
+                const int si = i - cxq(q), sj = j - cyq(q);
+                const bool xin = si >= 0 && si < k.nx0, yin = sj >= 0 && sj < k.ny0;
+                if (xin && yin) g[q] = IO.ld(fc + q * ns + slot0(k, si, sj), q);
+                else if (xin) g[q] = IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
+                else g[q] = 0.0f;
+            }
+            if (i == 0) {
+                const float U = k.U;
+                const float S = g[0] + g[3] + g[4] + 2.0f * (g[2] + g[6] + g[8]);   // sum of w over these is 1
+                const float rho = (1.0f + S) / (1.0f - U);
+                g[1] = g[2] + (2.0f / 3.0f) * rho * U;
+                g[5] = g[6] - 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
+                g[7] = g[8] + 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
+            }
+            if (i == k.nx0 - 1) {
+                // outlet: zero-gradient extrapolation, g_q(N-1) = g_q(N-2) for the pulled-in
+                // directions 2, 6, 8 (the post-stream values of the neighbour column)
+#pragma unroll
+                for (int m = 0; m < 3; m++) {
+                    const int q = m == 0 ? 2 : (m == 1 ? 6 : 8);
+                    const int si = k.nx0 - 2 - cxq(q), sj = j - cyq(q);
+                    g[q] = (sj >= 0 && sj < k.ny0) ? IO.ld(fc + q * ns + slot0(k, si, sj), q)
+                                                   : IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
+                }
+            }
+        }
+        // ---- macroscopic fields (eq 3) and central-moment collision (eqs 5-11)
+        const float drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+        const float jx = g[1] - g[2] + g[5] - g[6] + g[7] - g[8];
+        const float jy = g[3] - g[4] + g[5] - g[6] - g[7] + g[8];
+        const float irho = 1.0f / (1.0f + drho);
+        const float ux = jx * irho, uy = jy * irho;
+        P.drho[p ^ 1][slot] = drho; P.ux[p ^ 1][slot] = ux; P.uy[p ^ 1][slot] = uy;
+        float o[9];
+        collide_cm(g, drho, jx, jy, ux, uy, delta_of(P.nu, chin, k.turbulence), o);
+#pragma unroll
+        for (int q = 0; q < 9; q++) IO.st(fn + q * ns + slot, q, o[q]);
+        if (CHILD && (fl & FL_BAND)) {
+            // explosion: post-collision populations copied to the four ghost children
+            const int cb = child_base(P, t, lx, ly);
+            if (cb >= 0) {
+#pragma unroll
+                for (int q = 0; q < 9; q++) {
+                    T *ff = static_cast<T *>(F.f[ls.pf]) + q * F.ns;
+                    IO.st(ff + cb, q, o[q]); IO.st(ff + cb + 1, q, o[q]);
+                    IO.st(ff + cb + LBM_TX, q, o[q]); IO.st(ff + cb + LBM_TX + 1, q, o[q]);
+                }
+            }
+        }
+        valid = true;
+        n_dr = drho; n_ux = ux; n_uy = uy; n_chi = chin;
+    }
+
+    if (ls.restrict_up) {
+        // restriction into the covered parents (their children are this level's active
+        // cells; a 2 x 2 group of children lies inside one warp, lanes l, l+1, l+16, l+17):
+        // rho and chi are the means over the fluid children, u is mass-weighted (Rohde
+        // transfers, Sec 2.1)
+        const float rr = valid ? 1.0f + n_dr : 0.0f;
+        float a0 = valid ? n_dr : 0.0f, a1 = rr, a2 = rr * n_ux, a3 = rr * n_uy, a4 = valid ? n_chi : 0.0f;
+        float a5 = valid ? 1.0f : 0.0f;
+        // sum over (l, l+1) then over (l, l+16)
+#pragma unroll
+        for (int d = 1; d <= 16; d <<= 4) {
+            a0 += __shfl_down_sync(0xffffffffu, a0, d); a1 += __shfl_down_sync(0xffffffffu, a1, d);
+            a2 += __shfl_down_sync(0xffffffffu, a2, d); a3 += __shfl_down_sync(0xffffffffu, a3, d);
+            a4 += __shfl_down_sync(0xffffffffu, a4, d); a5 += __shfl_down_sync(0xffffffffu, a5, d);
+        }
+        if (!(lane & 1) && lane < 16 && kind == KIND_ACTIVE) {
+            const int pt = P.parent[t];
+            const int n = (int)a5;
+            if (pt >= 0 && n > 0) {
+                const int px = (P.tile_x[t] & 1) * (LBM_TX / 2) + (lx >> 1);
+                const int py = (P.tile_y[t] & 1) * (LBM_TY / 2) + (ly >> 1);
+                const int ps = pt * LBM_TILE + py * LBM_TX + px;
+                const int q1 = ls.pp ^ 1;
+                C.drho[q1][ps] = a0 / n; C.ux[q1][ps] = a2 / a1; C.uy[q1][ps] = a3 / a1;
+                C.chi[q1][ps] = a4 / n;
+            }
+        }
+    }
+}
+
 // MINB: minimum resident blocks per SM the register allocation must allow (5 or 6, that
-// is at most 48 or 40 registers a thread), picked per level by the autotuner.  Both
-// budgets give bit-identical results (larger budgets, 3 or 4 blocks, were measured to
-// round differently and to run no faster, and are not offered).
-template <bool WALL, bool CHILD, typename T, int MINB>
+// is at most 48 or 40 registers a thread).  PERSIST: the grid (2 x SMs x MINB blocks)
+// strides over the level's work tiles instead of one block per tile.  Both are picked
+// per level by the autotuner.  Every variant computes bit-identical results (larger
+// budgets, 3 or 4 blocks, were measured to round differently and to run no faster, and
+// are not offered).
+template <bool WALL, bool CHILD, typename T, int MINB, bool PERSIST>
 __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, LevelView C, RecView R, StepConsts k,
                                                       LevelStep ls)
 {
@@ -466,214 +670,31 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
     int lx, ly;
     cell_of_thread(c, lx, ly);
     int *nb3 = nb3w[c >> 5];
-    // one tile per block (grid = work tiles), or a persistent grid striding over the
-    // work tiles; the first tile's neighbour table is read before the wait
-    int wt = blockIdx.x;
-    if (wt < P.n_work_tiles && lane < 9) nb3[lane] = P.nbr[P.work_tiles[wt] * 9 + dir_of3(lane)];
-    __syncwarp();
-    griddep_launch();
-    griddep_wait();
-    for (; wt < P.n_work_tiles; wt += gridDim.x) {
-        const int t = P.work_tiles[wt];
-        if (wt != (int)blockIdx.x) {
-            __syncwarp();
-            if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
-            __syncwarp();
-        }
-        const int slot = t * LBM_TILE + ly * LBM_TX + lx;
-        const uint32_t fl = __ldg(P.flags + slot);
-        const uint32_t kind = fl & FL_KIND_MASK;
-        const bool fluid = !(fl & FL_SOLID);
-        const int ns = P.ns, p = ls.p;
-        const T *fc = static_cast<const T *>(P.f[p]);
-        T *fn = static_cast<T *>(P.f[p ^ 1]);
-        bool valid = false;
-        float n_dr = 0.f, n_ux = 0.f, n_uy = 0.f, n_chi = 0.f;
-
-        if (kind == KIND_GHOST && fluid) {
-            // ghosts are streamed (relayed), never collided
-#pragma unroll
-            for (int q = 0; q < 9; q++) {
-                const int s = q == 0 ? slot : nb_slot(nb3, lx, ly, -cxq(q), -cyq(q));
-                bool ok = false;
-                if (s >= 0) {
-                    const uint32_t fs = __ldg(P.flags + s);
-                    const uint32_t ks = fs & FL_KIND_MASK;
-                    ok = (ks == KIND_ACTIVE || ks == KIND_GHOST) && !(fs & FL_SOLID);
-                }
-                IO.st(fn + q * ns + slot, q, IO.ld(fc + q * ns + (ok ? s : slot), q));
+    if constexpr (!PERSIST) {
+        const int t = P.work_tiles[blockIdx.x];
+        if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
+        __syncwarp();
+        griddep_launch();
+        griddep_wait();
+        level_tile<WALL, CHILD, T>(P, F, C, R, k, ls, IO, t, lane, lx, ly, nb3);
+    } else {
+        // the first tile's neighbour table is read before the wait
+        int wt = blockIdx.x;
+        if (wt < P.n_work_tiles && lane < 9) nb3[lane] = P.nbr[P.work_tiles[wt] * 9 + dir_of3(lane)];
+        __syncwarp();
+        griddep_launch();
+        griddep_wait();
+        for (; wt < P.n_work_tiles; wt += gridDim.x) {
+            const int t = P.work_tiles[wt];
+            if (wt != (int)blockIdx.x) {
+                __syncwarp();
+                if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
+                __syncwarp();
             }
-        } else if (kind == KIND_ACTIVE && fluid) {
-            const bool edge = ls.is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
-            const bool bnode = WALL && (fl & FL_BNODE);
-            int nbs[9];
-            neighbours(nb3, lx, ly, slot, nbs);
-            // ---- wall function of the boundary node (Sec 2.3), fields at time t
-            float drW = 0.f, uWx = 0.f, uWy = 0.f, chiB = 0.f;
-            int r = -1;
-            if (bnode) {
-                r = P.rec[slot];
-                if (ls.wall_pre) {
-                    drW = R.drhoW[r]; uWx = R.uWx[r]; uWy = R.uWy[r]; chiB = R.chiB[r];
-                } else {
-                    wall_record(P, p, R, k, r, true, drW, uWx, uWy, chiB);
-                }
-            }
-            // ---- SA-neg update of chi (Sec 2.2), fields at time t
-            float chin;
-            if (k.turbulence) {
-                if (bnode) {
-                    chin = chiB;                                        // Dirichlet nu_t~_B (Sec 2.2)
-                } else if (edge) {
-                    const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
-                    if (fl & FL_INLET) {
-                        chin = k.chi_inf;
-                    } else {
-                        const int ic = (fl & FL_OUTLET) ? k.nx0 - 2 : i;     // outlet: copy of its neighbour
-                        Stencil S;
-                        gather0(P.chi[p], P.ux[p], P.uy[p], k, ic, j, S);
-                        chin = sa_update(S, P.inv_d2[slot0(k, ic, j)], P.nu, k.sa_convection);
-                    }
-                } else {
-                    Stencil S;
-                    const float *xc = P.chi[p], *xu = P.ux[p], *xv = P.uy[p];
-#pragma unroll
-                    for (int q = 0; q < 9; q++) {
-                        S.chi[q] = __ldg(xc + nbs[q]); S.ux[q] = __ldg(xu + nbs[q]); S.uy[q] = __ldg(xv + nbs[q]);
-                    }
-                    chin = sa_update(S, __ldg(P.inv_d2 + slot), P.nu, k.sa_convection);
-                }
-                P.chi[p ^ 1][slot] = chin;
-            } else {
-                chin = __ldg(P.chi[p] + slot);
-            }
-            // ---- pull streaming (eq 1) with coalescence, cut links and box edges
-            float g[9];
-            g[0] = IO.ld(fc + slot, 0);
-            const uint32_t special = fl & (0xFFu << FL_COAL_SHIFT | 0xFFu << FL_CUT_SHIFT);
-            if (!edge && !special) {
-                // plain cell: every direction is pulled from its upstream neighbour
-#pragma unroll
-                for (int q = 1; q < 9; q++) g[q] = IO.ld(fc + q * ns + nbs[oppq(q)], q);
-            } else if (!edge) {
-                int cb = -1;
-                if (CHILD && (fl & FL_BAND)) cb = child_base(P, t, lx, ly);
-#pragma unroll
-                for (int q = 1; q < 9; q++) {
-                    if (CHILD && (fl & (1u << (FL_COAL_SHIFT + q - 1)))) {
-                        // coalescence: mean of the four ghost children after the two fine sub-steps
-                        const T *ff = static_cast<const T *>(F.f[ls.pf]) + q * F.ns;
-                        g[q] = cb >= 0 ? 0.25f * (IO.ldp(ff + cb, q) + IO.ldp(ff + cb + 1, q) + IO.ldp(ff + cb + LBM_TX, q) +
-                                                  IO.ldp(ff + cb + LBM_TX + 1, q))
-                                       : IO.ld(fc + q * ns + slot, q);
-                    } else if (WALL && (fl & (1u << (FL_CUT_SHIFT + q - 1)))) {
-                        // Yu interpolated bounce-back with the slip velocity of the wall record (eq 27)
-                        const int qo = oppq(q);
-                        const float qf = R.q[r * 9 + q];
-                        const float mom = 6.0f * wq(q) * (1.0f + drW) * (cxq(q) * uWx + cyq(q) * uWy);
-                        const int sf = nbs[q];
-                        bool ok = false;
-                        if (sf != slot) {
-                            const uint32_t ff = __ldg(P.flags + sf);
-                            ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
-                        }
-                        if (ok)
-                            g[q] = ((1.0f - qf) * IO.ld(fc + qo * ns + sf, qo) + qf * IO.ld(fc + qo * ns + slot, qo) + mom) /
-                                       (1.0f + qf) +
-                                   qf / (1.0f + qf) * IO.ld(fc + q * ns + slot, q);
-                        else
-                            g[q] = IO.ld(fc + qo * ns + slot, qo) + mom;        // half-way form, eq 24
-                    } else {
-                        g[q] = IO.ld(fc + q * ns + nbs[oppq(q)], q);
-                    }
-                }
-            } else {
-                // level-0 box edge: in-box pulls, symmetry planes, Zou-He inlet, zero-gradient outlet (Sec 3.1.1)
-                const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
-#pragma unroll
-                for (int q = 1; q < 9; q++) {
-                    const int si = i - cxq(q), sj = j - cyq(q);
-                    const bool xin = si >= 0 && si < k.nx0, yin = sj >= 0 && sj < k.ny0;
-                    if (xin && yin) g[q] = IO.ld(fc + q * ns + slot0(k, si, sj), q);
-                    else if (xin) g[q] = IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
-                    else g[q] = 0.0f;
-                }
-                if (i == 0) {
-                    const float U = k.U;
-                    const float S = g[0] + g[3] + g[4] + 2.0f * (g[2] + g[6] + g[8]);   // sum of w over these is 1
-                    const float rho = (1.0f + S) / (1.0f - U);
-                    g[1] = g[2] + (2.0f / 3.0f) * rho * U;
-                    g[5] = g[6] - 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
-                    g[7] = g[8] + 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
-                }
-                if (i == k.nx0 - 1) {
-                    // outlet: zero-gradient extrapolation, g_q(N-1) = g_q(N-2) for the pulled-in
-                    // directions 2, 6, 8 (the post-stream values of the neighbour column)
-#pragma unroll
-                    for (int m = 0; m < 3; m++) {
-                        const int q = m == 0 ? 2 : (m == 1 ? 6 : 8);
-                        const int si = k.nx0 - 2 - cxq(q), sj = j - cyq(q);
-                        g[q] = (sj >= 0 && sj < k.ny0) ? IO.ld(fc + q * ns + slot0(k, si, sj), q)
-                                                       : IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
-                    }
-                }
-            }
-            // ---- macroscopic fields (eq 3) and central-moment collision (eqs 5-11)
-            const float drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
-            const float jx = g[1] - g[2] + g[5] - g[6] + g[7] - g[8];
-            const float jy = g[3] - g[4] + g[5] - g[6] - g[7] + g[8];
-            const float irho = 1.0f / (1.0f + drho);
-            const float ux = jx * irho, uy = jy * irho;
-            P.drho[p ^ 1][slot] = drho; P.ux[p ^ 1][slot] = ux; P.uy[p ^ 1][slot] = uy;
-            float o[9];
-            collide_cm(g, drho, jx, jy, ux, uy, delta_of(P.nu, chin, k.turbulence), o);
-#pragma unroll
-            for (int q = 0; q < 9; q++) IO.st(fn + q * ns + slot, q, o[q]);
-            if (CHILD && (fl & FL_BAND)) {
-                // explosion: post-collision populations copied to the four ghost children
-                const int cb = child_base(P, t, lx, ly);
-                if (cb >= 0) {
-#pragma unroll
-                    for (int q = 0; q < 9; q++) {
-                        T *ff = static_cast<T *>(F.f[ls.pf]) + q * F.ns;
-                        IO.st(ff + cb, q, o[q]); IO.st(ff + cb + 1, q, o[q]);
-                        IO.st(ff + cb + LBM_TX, q, o[q]); IO.st(ff + cb + LBM_TX + 1, q, o[q]);
-                    }
-                }
-            }
-            valid = true;
-            n_dr = drho; n_ux = ux; n_uy = uy; n_chi = chin;
-        }
-
-        if (ls.restrict_up) {
-            // restriction into the covered parents (their children are this level's active
-            // cells; a 2 x 2 group of children lies inside one warp, lanes l, l+1, l+16, l+17):
-            // rho and chi are the means over the fluid children, u is mass-weighted (Rohde
-            // transfers, Sec 2.1)
-            const float rr = valid ? 1.0f + n_dr : 0.0f;
-            float a0 = valid ? n_dr : 0.0f, a1 = rr, a2 = rr * n_ux, a3 = rr * n_uy, a4 = valid ? n_chi : 0.0f;
-            float a5 = valid ? 1.0f : 0.0f;
-            // sum over (l, l+1) then over (l, l+16)
-#pragma unroll
-            for (int d = 1; d <= 16; d <<= 4) {
-                a0 += __shfl_down_sync(0xffffffffu, a0, d); a1 += __shfl_down_sync(0xffffffffu, a1, d);
-                a2 += __shfl_down_sync(0xffffffffu, a2, d); a3 += __shfl_down_sync(0xffffffffu, a3, d);
-                a4 += __shfl_down_sync(0xffffffffu, a4, d); a5 += __shfl_down_sync(0xffffffffu, a5, d);
-            }
-            if (!(lane & 1) && lane < 16 && kind == KIND_ACTIVE) {
-                const int pt = P.parent[t];
-                const int n = (int)a5;
-                if (pt >= 0 && n > 0) {
-                    const int px = (P.tile_x[t] & 1) * (LBM_TX / 2) + (lx >> 1);
-                    const int py = (P.tile_y[t] & 1) * (LBM_TY / 2) + (ly >> 1);
-                    const int ps = pt * LBM_TILE + py * LBM_TX + px;
-                    const int q1 = ls.pp ^ 1;
-                    C.drho[q1][ps] = a0 / n; C.ux[q1][ps] = a2 / a1; C.uy[q1][ps] = a3 / a1;
-                    C.chi[q1][ps] = a4 / n;
-                }
-            }
+            level_tile<WALL, CHILD, T>(P, F, C, R, k, ls, IO, t, lane, lx, ly, nb3);
         }
     }
+
 }
 
 // ------------------------------------------------------------------ prolongation (Sec 2.2)
@@ -891,23 +912,28 @@ static void launch_pdl(void (*kern)(Args...), unsigned grid, cudaStream_t st, in
 }
 
 // the level holding the wall records is the finest one, which has no child level
-template <typename T, int MINB>
+template <typename T, int MINB, bool PERSIST>
 static void launch_level_mb(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
-                            const RecView &R, const StepConsts &k, const LevelStep &ls, const LevelTune &tu)
+                            const RecView &R, const StepConsts &k, const LevelStep &ls, int pdl)
 {
     // persistent: two rounds of the resident blocks stride over the work tiles
-    const unsigned grid = tu.persistent ? (unsigned)std::min(P.n_work_tiles, 2 * k.sms * MINB) : (unsigned)P.n_work_tiles;
-    if (ls.wall) launch_pdl(k_level<true, false, T, MINB>, grid, st, tu.pdl, P, Fv, Cv, R, k, ls);
-    else if (child) launch_pdl(k_level<false, true, T, MINB>, grid, st, tu.pdl, P, Fv, Cv, R, k, ls);
-    else launch_pdl(k_level<false, false, T, MINB>, grid, st, tu.pdl, P, Fv, Cv, R, k, ls);
+    const unsigned grid = PERSIST ? (unsigned)std::min(P.n_work_tiles, 2 * k.sms * MINB) : (unsigned)P.n_work_tiles;
+    if (ls.wall) launch_pdl(k_level<true, false, T, MINB, PERSIST>, grid, st, pdl, P, Fv, Cv, R, k, ls);
+    else if (child) launch_pdl(k_level<false, true, T, MINB, PERSIST>, grid, st, pdl, P, Fv, Cv, R, k, ls);
+    else launch_pdl(k_level<false, false, T, MINB, PERSIST>, grid, st, pdl, P, Fv, Cv, R, k, ls);
 }
 
 template <typename T>
 static void launch_level_t(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
                            const RecView &R, const StepConsts &k, const LevelStep &ls, const LevelTune &tu)
 {
-    if (tu.min_blocks == 6) launch_level_mb<T, 6>(st, P, Fv, Cv, child, R, k, ls, tu);
-    else launch_level_mb<T, 5>(st, P, Fv, Cv, child, R, k, ls, tu);
+    if (tu.min_blocks == 6) {
+        if (tu.persistent) launch_level_mb<T, 6, true>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        else launch_level_mb<T, 6, false>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+    } else {
+        if (tu.persistent) launch_level_mb<T, 5, true>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        else launch_level_mb<T, 5, false>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+    }
 }
 
 void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,
