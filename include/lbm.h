@@ -198,7 +198,9 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times 
  * blocks per SM (at most 48 or 40 registers a thread), each either with one block per
  * tile or with a persistent grid (2 x SMs x that budget) whose blocks stride over the
  * level's tiles.  The choice comes from per-launch CUDA-event timings of `steps` eager
- * coarse steps per candidate.  Then it picks whether launches use
+ * coarse steps per candidate, and is kept only if `steps` coarse steps through the step
+ * graphs confirm it (against the same choice without persistent grids, and against the
+ * form before tuning), since launches overlap inside the graphs.  Then it picks whether launches use
  * programmatic dependent launch, from the time of `steps` coarse steps through the step
  * graphs each way; and, when the solve has wall records, whether the finest level's wall
  * function (Sec 2.3 steps 1-5) runs inside the fused level launch or in a compact launch
@@ -214,6 +216,8 @@ typedef struct {
     double level_us[LBM_TUNE_CANDIDATES][16]; /* mean launch time of level l's kernel per candidate */
     int min_blocks[16];                       /* chosen register budget per level                  */
     int persistent[16];                       /* chosen grid schedule per level (1 persistent)     */
+    double step_us_confirm[3];                /* coarse step: per-level pick, pick without
+                                                 persistent grids, form before tuning            */
     double default_step_us;                   /* coarse step through the graphs before tuning      */
     double step_us[2];                        /* coarse step, chosen kernels, PDL off / on         */
     int pdl;                                  /* chosen: 1 programmatic dependent launch on        */

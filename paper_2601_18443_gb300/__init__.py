@@ -73,7 +73,7 @@ class lbm_tune_report(C.Structure):
     _fields_ = [("levels", C.c_int), ("candidate_min_blocks", C.c_int * TUNE_CANDIDATES),
                 ("candidate_persistent", C.c_int * TUNE_CANDIDATES),
                 ("level_us", (C.c_double * 16) * TUNE_CANDIDATES), ("min_blocks", C.c_int * 16),
-                ("persistent", C.c_int * 16),
+                ("persistent", C.c_int * 16), ("step_us_confirm", C.c_double * 3),
                 ("default_step_us", C.c_double), ("step_us", C.c_double * 2),
                 ("pdl", C.c_int), ("step_us_wall", C.c_double * 2), ("wall_split", C.c_int),
                 ("steps_taken", C.c_longlong)]
@@ -362,6 +362,8 @@ def _tune_dict(out):
     return dict(levels=L, candidates=cand,
                 level_us={c: list(out.level_us[i][:L]) for i, c in enumerate(cand)},
                 min_blocks=list(out.min_blocks[:L]), persistent=list(out.persistent[:L]),
+                step_us_confirm={"pick": out.step_us_confirm[0], "pick_no_persistent": out.step_us_confirm[1],
+                                 "before": out.step_us_confirm[2]},
                 default_step_us=out.default_step_us,
                 step_us={"pdl_off": out.step_us[0], "pdl_on": out.step_us[1]}, pdl=out.pdl,
                 step_us_wall={"fused": out.step_us_wall[0], "own_launch": out.step_us_wall[1]},

@@ -1030,6 +1030,33 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
         out->min_blocks[l] = CAND_MB[best];
         out->persistent[l] = CAND_PE[best];
     }
+    // 1b: per-launch timings miss how launches overlap inside the graph (a persistent grid
+    //     occupies every SM while the next launch would start): keep the per-level choice
+    //     only if whole graph steps confirm it, against the same choice without persistent
+    //     grids and against the default form
+    {
+        int pick_mb[LBM_MAXL], pick_pe[LBM_MAXL];
+        for (int l = 0; l < L; l++) { pick_mb[l] = s->min_blocks[l]; pick_pe[l] = s->persistent[l]; }
+        double best_us = 0.0;
+        int best = 0;
+        for (int v = 0; v < 3; v++) {
+            for (int l = 0; l < L; l++) {
+                s->min_blocks[l] = v == 2 ? keep_mb[l] : pick_mb[l];
+                s->persistent[l] = v == 0 ? pick_pe[l] : (v == 1 ? 0 : keep_pe[l]);
+            }
+            double us = 0.0;
+            if ((st = capture_graphs(s)) != LBM_OK) return st;
+            if ((st = graph_step_time(s, steps, &us)) != LBM_OK) return st;
+            out->step_us_confirm[v] = us;
+            if (v == 0 || us < best_us) { best_us = us; best = v; }
+        }
+        for (int l = 0; l < L; l++) {
+            s->min_blocks[l] = best == 2 ? keep_mb[l] : pick_mb[l];
+            s->persistent[l] = best == 0 ? pick_pe[l] : (best == 1 ? 0 : keep_pe[l]);
+            out->min_blocks[l] = s->min_blocks[l];
+            out->persistent[l] = s->persistent[l];
+        }
+    }
     // 2: programmatic dependent launch on or off, from whole graph steps
     for (int pdl = 0; pdl < 2; pdl++) {
         s->pdl = pdl;
@@ -1050,7 +1077,7 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     }
     out->wall_split = s->wall_split;
     if ((st = capture_graphs(s)) != LBM_OK) return st;
-    out->steps_taken = (long long)steps * (3 + LBM_TUNE_CANDIDATES) + extra;
+    out->steps_taken = (long long)steps * (6 + LBM_TUNE_CANDIDATES) + extra;
     return check_status(s);
 }
 

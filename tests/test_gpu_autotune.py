@@ -23,7 +23,8 @@ def test_autotuned_solve_equals_the_default_one(store):
     b.step(3)                      # odd level-0 parity: the recapture starts from graph 1
     rep = b.autotune(steps=2)
     L = cfg["levels"]
-    assert rep["steps_taken"] == 2 * 8 and rep["levels"] == L and rep["wall_split"] in (0, 1)
+    assert rep["steps_taken"] == 2 * 11 and rep["levels"] == L and rep["wall_split"] in (0, 1)
+    assert min(rep["step_us_confirm"].values()) > 0
     assert rep["candidates"] == [(5, 0), (6, 0), (5, 1), (6, 1)]
     assert all(pe in (0, 1) for pe in rep["persistent"])
     assert all(m in (5, 6) for m in rep["min_blocks"]) and rep["pdl"] in (0, 1)
