@@ -202,10 +202,7 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times 
  * graphs confirm it (against the same choice without persistent grids, and against the
  * form before tuning), since launches overlap inside the graphs.  Then it picks whether launches use
  * programmatic dependent launch, from the time of `steps` coarse steps through the step
- * graphs each way; and, when the solve has wall records, whether the finest level's wall
- * function (Sec 2.3 steps 1-5) runs inside the fused level launch or in a compact launch
- * of its own (one thread per record) just before it, again from graph step timings.  It
- * then recaptures the graphs with the choice.  Every variant computes bit-identical
+ * graphs each way, and recaptures the graphs with the choice.  Every variant computes bit-identical
  * results; the timed steps are real steps of the solve (steps_taken of them).
  * Synchronous.  Errors as lbm_step. */
 #define LBM_TUNE_CANDIDATES 4
@@ -221,8 +218,6 @@ typedef struct {
     double default_step_us;                   /* coarse step through the graphs before tuning      */
     double step_us[2];                        /* coarse step, chosen kernels, PDL off / on         */
     int pdl;                                  /* chosen: 1 programmatic dependent launch on        */
-    double step_us_wall[2];                   /* coarse step, wall function fused / own launch     */
-    int wall_split;                           /* chosen: 1 wall function in its own launch         */
     long long steps_taken;                    /* coarse steps the tuning advanced the solve by     */
 } lbm_tune_report;
 lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out);
@@ -244,10 +239,9 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size);
 
 /* Set the launch variant directly (for instance one lbm_autotune found on a solve of the
  * same shape): min_blocks[l] in {5, 6} and persistent[l] in {0, 1} for each of the
- * solver's levels, pdl 0 or 1, wall_split 0 or 1; the step graphs are recaptured.  No
- * device work.  Errors: LBM_ERR_INVALID_ARG for a value outside those sets,
- * LBM_ERR_NO_GEOMETRY. */
-lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, int pdl, int wall_split);
+ * solver's levels, pdl 0 or 1; the step graphs are recaptured.  No device work.
+ * Errors: LBM_ERR_INVALID_ARG for a value outside those sets, LBM_ERR_NO_GEOMETRY. */
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, int pdl);
 
 /* Largest n_cells that lbm_level_mass_noalloc accepts (its fixed scratch holds 4096
  * per-block partial sums of at most 16384 cells each). */

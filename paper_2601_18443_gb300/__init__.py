@@ -75,8 +75,7 @@ class lbm_tune_report(C.Structure):
                 ("level_us", (C.c_double * 16) * TUNE_CANDIDATES), ("min_blocks", C.c_int * 16),
                 ("persistent", C.c_int * 16), ("step_us_confirm", C.c_double * 3),
                 ("default_step_us", C.c_double), ("step_us", C.c_double * 2),
-                ("pdl", C.c_int), ("step_us_wall", C.c_double * 2), ("wall_split", C.c_int),
-                ("steps_taken", C.c_longlong)]
+                ("pdl", C.c_int), ("steps_taken", C.c_longlong)]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -112,7 +111,7 @@ def library():
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
-        "lbm_set_launch_variant": ([vp, ip, ip, C.c_int, C.c_int], C.c_int),
+        "lbm_set_launch_variant": ([vp, ip, ip, C.c_int], C.c_int),
         "lbm_get_state": ([vp, vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
         "lbm_set_state": ([vp, vp, C.c_size_t], C.c_int),
         "lbm_level_mass_noalloc": ([vp, vp, vp, vp, vp, C.c_longlong, C.c_double, vp, vp, vp], C.c_int),
@@ -342,12 +341,12 @@ class Solver:
         b = np.ascontiguousarray(blob, dtype=np.uint8)
         self._check(self._lib.lbm_set_state(self._h, b.ctypes.data_as(C.c_void_p), b.size))
 
-    def set_launch_variant(self, min_blocks, pdl=1, wall_split=0, persistent=None):
-        """lbm_set_launch_variant: per-level register budget (5 or 6 blocks per SM) and grid
-        schedule (persistent 0/1), PDL, and whether the wall function runs in its own launch."""
+    def set_launch_variant(self, min_blocks, pdl=1, persistent=None):
+        """lbm_set_launch_variant: per-level register budget (5 or 6 blocks per SM), grid
+        schedule (persistent 0/1) and PDL."""
         mb = np.ascontiguousarray(min_blocks, dtype=np.int32)
         pe = np.ascontiguousarray(persistent if persistent is not None else [0] * len(mb), dtype=np.int32)
-        self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), _ip(pe), int(pdl), int(wall_split)))
+        self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), _ip(pe), int(pdl)))
 
     def time_kernels(self, n=1):
         out = lbm_kernel_times()
@@ -366,8 +365,7 @@ def _tune_dict(out):
                                  "before": out.step_us_confirm[2]},
                 default_step_us=out.default_step_us,
                 step_us={"pdl_off": out.step_us[0], "pdl_on": out.step_us[1]}, pdl=out.pdl,
-                step_us_wall={"fused": out.step_us_wall[0], "own_launch": out.step_us_wall[1]},
-                wall_split=out.wall_split, steps_taken=out.steps_taken)
+                steps_taken=out.steps_taken)
 
 
 def level_mass_noalloc(flags, drho, ux, uy, chi, n_cells, area, mass_out, nonfinite_out, stream=0):

@@ -75,7 +75,6 @@ struct LevelStep {
     int restrict_up;    // write the restriction of this level's new fields into level l-1
     int pp;             // time level of level l-1 (restriction writes [pp ^ 1])
     int *status;        // device status word (LBM_STATUS_* bits)
-    int wall_pre;       // the wall function ran in its own launch before this one: read its results
 };
 
 // Launch variant of a level's kernels (chosen by lbm_autotune): the register budget of the
@@ -88,9 +87,6 @@ struct LevelTune {
     int persistent;     // grid of 2 x SMs x min_blocks blocks striding over the work tiles
 };
 
-// Wall function of every record in a launch of its own (one thread per record), ahead of
-// the finest-level launch; keeps the Newton result as the next step's start.
-void launch_wallfn_step(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k, int pdl);
 
 // launchers (kernels.cu); all enqueue on the given stream
 void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,

@@ -491,11 +491,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         int r = -1;
         if (bnode) {
             r = P.rec[slot];
-            if (ls.wall_pre) {
-                drW = R.drhoW[r]; uWx = R.uWx[r]; uWy = R.uWy[r]; chiB = R.chiB[r];
-            } else {
-                wall_record(P, p, R, k, r, true, drW, uWx, uWy, chiB);
-            }
+            wall_record(P, p, R, k, r, true, drW, uWx, uWy, chiB);
         }
         // ---- SA-neg update of chi (Sec 2.2), fields at time t
         float chin;
@@ -735,16 +731,12 @@ __global__ void __launch_bounds__(256) k_prolong(LevelView P, LevelView F, int p
 }
 
 // ------------------------------------------------------------------ wall-state query
-// keep_start = 0: a query (lbm_get_loads / lbm_get_wall_state), the trajectory is untouched;
-// keep_start = 1: the step's own wall function, launched ahead of the finest-level launch
-__global__ void __launch_bounds__(128) k_wallfn(LevelView P, int p, RecView R, StepConsts k, int keep_start)
+__global__ void __launch_bounds__(128) k_wallfn(LevelView P, int p, RecView R, StepConsts k)
 {
-    griddep_launch();
-    griddep_wait();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R.n) return;
     float drW, uWx, uWy, chiB;
-    wall_record(P, p, R, k, r, keep_start != 0, drW, uWx, uWy, chiB);
+    wall_record(P, p, R, k, r, false, drW, uWx, uWy, chiB);
 }
 
 // ------------------------------------------------------------------ interface sync (set_fields)
@@ -956,22 +948,7 @@ void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int
 void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k)
 {
     if (R.n <= 0) return;
-    k_wallfn<<<(R.n + 127) / 128, 128, 0, st>>>(P, p, R, k, 0);
-}
-
-void launch_wallfn_step(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k, int pdl)
-{
-    if (R.n <= 0) return;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((R.n + 127) / 128);
-    cfg.blockDim = dim3(128);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k_wallfn, P, p, R, k, 1);
+    k_wallfn<<<(R.n + 127) / 128, 128, 0, st>>>(P, p, R, k);
 }
 
 void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pp, int pf)

@@ -103,7 +103,6 @@ struct lbm_solver {
     int min_blocks[LBM_MAXL];     // register budget of each level's kernel (lbm_autotune)
     int persistent[LBM_MAXL];     // persistent grid for each level's kernel (lbm_autotune)
     int pdl = 1;                  // programmatic dependent launch (lbm_autotune)
-    int wall_split = 0;           // wall function in its own launch (lbm_autotune)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<void *> allocs;
     double device_bytes = 0;
@@ -205,8 +204,8 @@ static T *upload(lbm_solver *s, const std::vector<T> &h, bool &ok)
 
 // ---------------------------------------------------------------- scheduler
 // Kernel classes for lbm_time_kernels.
-enum { KC_LEVEL_FINEST = 0, KC_LEVEL_COARSE = 1, KC_PROLONG = 2, KC_WALLFN = 3, KC_N = 4 };
-static const char *KC_NAME[KC_N] = {"level_step_finest", "level_step_coarse", "prolong", "wall_function"};
+enum { KC_LEVEL_FINEST = 0, KC_LEVEL_COARSE = 1, KC_PROLONG = 2, KC_N = 3 };
+static const char *KC_NAME[KC_N] = {"level_step_finest", "level_step_coarse", "prolong"};
 
 static void mark_begin(lbm_solver *s)
 {
@@ -259,13 +258,6 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     ls.restrict_up = restrict_up && C != nullptr;
     ls.pp = C ? s->parity[l - 1] : 0;
     ls.status = s->d_status;
-    ls.wall_pre = ls.wall && s->wall_split;
-    if (ls.wall_pre) {
-        mark_begin(s);
-        lbmdev::launch_wallfn_step(st, P, s->parity[l], s->rec, s->k, s->pdl);
-        mark_end(s, KC_WALLFN, s->rec.n, -1);
-        nk++;
-    }
     mark_begin(s);
     const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl, s->persistent[l]};
     lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls, tu);
@@ -1009,7 +1001,6 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     if ((st = graph_step_time(s, steps, &out->default_step_us)) != LBM_OK) return st;
     int keep_mb[LBM_MAXL], keep_pe[LBM_MAXL];
     for (int l = 0; l < L; l++) { keep_mb[l] = s->min_blocks[l]; keep_pe[l] = s->persistent[l]; }
-    s->wall_split = 0;            // stages 1-2 time the fused form; stage 3 decides the placement
     // 1: register budget and grid schedule per level, from per-launch event timings of
     //    every candidate
     for (int c = 0; c < LBM_TUNE_CANDIDATES; c++) {
@@ -1065,19 +1056,8 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     }
     s->pdl = out->step_us[1] <= out->step_us[0] ? 1 : 0;
     out->pdl = s->pdl;
-    // 3: the finest level's wall function fused into its launch, or in a launch of its own
-    out->step_us_wall[0] = out->step_us[s->pdl];
-    long long extra = 0;
-    if (s->rec.n > 0) {
-        s->wall_split = 1;
-        if ((st = capture_graphs(s)) != LBM_OK) return st;
-        if ((st = graph_step_time(s, steps, &out->step_us_wall[1])) != LBM_OK) return st;
-        s->wall_split = out->step_us_wall[1] < out->step_us_wall[0] ? 1 : 0;
-        extra = steps;
-    }
-    out->wall_split = s->wall_split;
     if ((st = capture_graphs(s)) != LBM_OK) return st;
-    out->steps_taken = (long long)steps * (6 + LBM_TUNE_CANDIDATES) + extra;
+    out->steps_taken = (long long)steps * (6 + LBM_TUNE_CANDIDATES);
     return check_status(s);
 }
 
@@ -1172,17 +1152,15 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, int pdl, int wall_split)
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, int pdl)
 {
-    if (!s || !min_blocks || !persistent || (pdl != 0 && pdl != 1) || (wall_split != 0 && wall_split != 1))
-        return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s || !min_blocks || !persistent || (pdl != 0 && pdl != 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     for (int l = 0; l < s->L; l++)
         if ((min_blocks[l] != 5 && min_blocks[l] != 6) || (persistent[l] != 0 && persistent[l] != 1))
             return fail(s, LBM_ERR_INVALID_ARG, "launch variant: min_blocks must be 5 or 6, persistent 0 or 1");
     for (int l = 0; l < s->L; l++) { s->min_blocks[l] = min_blocks[l]; s->persistent[l] = persistent[l]; }
     s->pdl = pdl;
-    s->wall_split = wall_split;
     return capture_graphs(s);
 }
 

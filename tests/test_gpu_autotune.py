@@ -23,7 +23,7 @@ def test_autotuned_solve_equals_the_default_one(store):
     b.step(3)                      # odd level-0 parity: the recapture starts from graph 1
     rep = b.autotune(steps=2)
     L = cfg["levels"]
-    assert rep["steps_taken"] == 2 * 11 and rep["levels"] == L and rep["wall_split"] in (0, 1)
+    assert rep["steps_taken"] == 2 * 10 and rep["levels"] == L
     assert min(rep["step_us_confirm"].values()) > 0
     assert rep["candidates"] == [(5, 0), (6, 0), (5, 1), (6, 1)]
     assert all(pe in (0, 1) for pe in rep["persistent"])
@@ -41,23 +41,22 @@ def test_autotuned_solve_equals_the_default_one(store):
     assert la["step"] == lb["step"] and abs(la["CL"] - lb["CL"]) < 1e-12
 
 
-@pytest.mark.parametrize("mb,pdl,split,pe", [(6, 1, 0, 0), (5, 0, 0, 0), (6, 0, 0, 1), (5, 1, 1, 0), (6, 0, 1, 0),
-                                          (5, 1, 0, 1), (6, 1, 1, 1)])
-def test_each_launch_variant_computes_the_same_numbers(mb, pdl, split, pe):
+@pytest.mark.parametrize("mb,pdl,pe", [(6, 1, 0), (5, 0, 0), (6, 0, 1), (5, 1, 1), (6, 1, 1)])
+def test_each_launch_variant_computes_the_same_numbers(mb, pdl, pe):
     pkg.build()
     cfg, loops = W.naca0012_small(levels=5)
     L = cfg["levels"]
     a, b = pkg.Solver(cfg), pkg.Solver(cfg)
     a.set_geometry(loops)
     b.set_geometry(loops)
-    b.set_launch_variant([mb] * L, pdl, split, [pe] * L)
+    b.set_launch_variant([mb] * L, pdl, [pe] * L)
     a.step(6)
     b.step(6)
     for l in range(L):
         assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), l
     with pytest.raises(pkg.LBMError):
         b.set_launch_variant([4] * L, 1)
-    # queries in between leave the trajectory alone in either wall-function placement
+    # queries in between leave the trajectory alone
     a.coefficients(); b.coefficients()
     a.step(3); b.step(3)
     for l in range(L):
