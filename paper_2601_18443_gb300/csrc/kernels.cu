@@ -452,14 +452,15 @@ template <typename T> struct ShiftedIO {
 };
 
 // One tile of the fused level step (the body of k_level): every thread updates its cell
-// of tile t.  nb3 holds the 3 x 3 neighbour tiles of t for this warp.
-template <bool WALL, bool CHILD, typename T>
+// of tile t.  nb3 holds the 3 x 3 neighbour tiles of t for this warp.  The cell's flag
+// word is read here, or passed in (FL_GIVEN) when the caller has fetched it ahead.
+template <bool WALL, bool CHILD, typename T, bool FL_GIVEN>
 __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &F, const LevelView &C, const RecView &R,
                                            const StepConsts &k, const LevelStep &ls, const ShiftedIO<T> &IO, int t,
-                                           int lane, int lx, int ly, const int *nb3)
+                                           int lane, int lx, int ly, const int *nb3, uint32_t fl_given)
 {
     const int slot = t * LBM_TILE + ly * LBM_TX + lx;
-    const uint32_t fl = __ldg(P.flags + slot);
+    const uint32_t fl = FL_GIVEN ? fl_given : __ldg(P.flags + slot);
     const uint32_t kind = fl & FL_KIND_MASK;
     const bool fluid = !(fl & FL_SOLID);
     const int ns = P.ns, p = ls.p;
@@ -672,22 +673,32 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
         __syncwarp();
         griddep_launch();
         griddep_wait();
-        level_tile<WALL, CHILD, T>(P, F, C, R, k, ls, IO, t, lane, lx, ly, nb3);
+        level_tile<WALL, CHILD, T, false>(P, F, C, R, k, ls, IO, t, lane, lx, ly, nb3, 0u);
     } else {
-        // the first tile's neighbour table is read before the wait
+        // the grid tables are static: the first tile's neighbour table and flag word are
+        // read before the wait, and each tile's flag word one tile ahead
+        const int cell = ly * LBM_TX + lx;
         int wt = blockIdx.x;
-        if (wt < P.n_work_tiles && lane < 9) nb3[lane] = P.nbr[P.work_tiles[wt] * 9 + dir_of3(lane)];
+        uint32_t fl_next = 0;
+        if (wt < P.n_work_tiles) {
+            const int t0 = P.work_tiles[wt];
+            if (lane < 9) nb3[lane] = P.nbr[t0 * 9 + dir_of3(lane)];
+            fl_next = __ldg(P.flags + t0 * LBM_TILE + cell);
+        }
         __syncwarp();
         griddep_launch();
         griddep_wait();
         for (; wt < P.n_work_tiles; wt += gridDim.x) {
             const int t = P.work_tiles[wt];
+            const uint32_t fl = fl_next;
+            if (wt + (int)gridDim.x < P.n_work_tiles)
+                fl_next = __ldg(P.flags + P.work_tiles[wt + gridDim.x] * LBM_TILE + cell);
             if (wt != (int)blockIdx.x) {
                 __syncwarp();
                 if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
                 __syncwarp();
             }
-            level_tile<WALL, CHILD, T>(P, F, C, R, k, ls, IO, t, lane, lx, ly, nb3);
+            level_tile<WALL, CHILD, T, true>(P, F, C, R, k, ls, IO, t, lane, lx, ly, nb3, fl);
         }
     }
 
