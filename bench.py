@@ -417,7 +417,9 @@ def profile_case(args):
         cfg, loops = W.naca0012_large()
     s = pkg.Solver(cfg)
     s.set_geometry(loops)
-    if not args.no_autotune:
+    if args.profile_persistent:
+        s.set_launch_variant([6] * cfg["levels"], 1, [1] * cfg["levels"])
+    elif not args.no_autotune:
         s.autotune(2)
     # the steps to profile sit in an NVTX range ("steps"): ncu --nvtx --nvtx-include steps/
     torch.cuda.nvtx.range_push("steps")
@@ -500,6 +502,8 @@ def main():
     ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--profile-case", choices=["hbm_grid", "hbm_grid_laminar", "workload"], default=None)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch variant")
+    ap.add_argument("--profile-persistent", action="store_true",
+                    help="profile case: persistent grid, 6 blocks/SM on every level instead of autotuning")
     ap.add_argument("--workload", choices=["naca0012", "highlift"], default="naca0012",
                     help="highlift: the three-element 8-level case (2 timed steps, no extra measurements)")
     ap.add_argument("--serving", type=int, default=0, help="serve this many requests of the polar stream")
