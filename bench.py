@@ -395,7 +395,7 @@ def hbm_grid_roofline(pkg, stream, peak, peak_kind, n=4096, turbulence=1, tune=T
     s.close()
     ach = bpl / (avg * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-            "traffic": ncu_traffic("hbm_grid_launch") if turbulence and not store else None, "kernel": "k_level", "grid": f"{n}x{n} periodic, 1 level, SA {'on' if turbulence else 'off'}",
+            "traffic": (ncu_traffic("hbm_grid_launch" if turbulence else "stream_collide_launch") if not store else None), "kernel": "k_level", "grid": f"{n}x{n} periodic, 1 level, SA {'on' if turbulence else 'off'}",
             "bytes_per_launch": int(bpl),
             "avg_launch_ms": round(avg, 4), "mlups": round(info["cells_active"][0] / avg / 1e3, 1),
             "peak_kind": peak_kind}
