@@ -169,7 +169,10 @@ def reference_arm(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": 0,
         "steps": steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": CPU_SAMPLE, "arm": "FP64 CPU oracle on host cores (bounded sample)"},
+        "config": {"workload": WORKLOAD, "arm": "FP64 CPU oracle on host cores (bounded sample)",
+                   "sample": f"each step is one coarse step of {CPU_SAMPLE} (the same multilevel method at "
+                             f"c/256, 207k node updates): the oracle's node-update rate stands for the workload's, "
+                             f"whose 21.4M node updates per coarse step would take seconds each"},
         "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
