@@ -38,3 +38,14 @@ def test_plan_reports_geometry_errors():
     with pytest.raises(pkg.LBMError) as e:
         pkg.plan(cfg, [W.rectangle(0.5, 0.5, 5.0, 5.0)])     # refinement reaches the box edge
     assert e.value.code == -5 and "box edge" in str(e.value)
+
+
+def test_plan_rejects_degenerate_loops():
+    pkg.build()
+    cfg = W.base_config(levels=2, nx0=64, ny0=64, h0=1.0, layers=4)
+    with pytest.raises(pkg.LBMError) as e:
+        pkg.plan(cfg, [np.array([[20.0, 20.0], [30.0, 30.0]])])          # two vertices
+    assert e.value.code == -5 and "3 vertices" in str(e.value)
+    with pytest.raises(pkg.LBMError) as e:
+        pkg.plan(cfg, [np.array([[20.0, 20.0], [30.0, 30.0], [40.0, 40.0]])])   # zero area
+    assert e.value.code == -5 and "degenerate" in str(e.value)
