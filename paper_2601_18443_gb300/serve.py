@@ -128,12 +128,13 @@ class GpuBackend:
 
 
 class _Slot:
-    __slots__ = ("req", "res", "handle", "need", "calm", "enqueued")
+    __slots__ = ("req", "res", "handle", "need", "calm", "enqueued", "released")
 
     def __init__(self, req, res, handle, need):
         self.req, self.res, self.handle, self.need = req, res, handle, need
         self.calm = 0
         self.enqueued = 0
+        self.released = False
 
 
 class Service:
@@ -176,90 +177,112 @@ class Service:
             self.trace.append((now(), ev, rid, used, resident))
 
         with ThreadPoolExecutor(max_workers=self.builders) as pool:
-            while pending or waiting or building or active:
-                moved = False
-                t = now()
-                while pending and pending[0].arrival * time_scale <= t:
-                    r = pending.popleft()
-                    waiting.append((r, pool.submit(self.backend.plan, r.cfg, r.loops)))
-                    moved = True
-
-                # admission: arrival order; the head waits for memory (no overtaking)
-                while waiting and resident < self.max_slots:
-                    r, pf = waiting[0]
-                    if not pf.done():
-                        break
-                    res = results[r.rid]
-                    try:
-                        p = pf.result()
-                    except Exception as e:   # geometry the grid builder rejects
-                        waiting.popleft()
-                        res.status, res.message, res.finished = "rejected", str(e), now()
+            try:
+                while pending or waiting or building or active:
+                    moved = False
+                    t = now()
+                    while pending and pending[0].arrival * time_scale <= t:
+                        r = pending.popleft()
+                        waiting.append((r, pool.submit(self.backend.plan, r.cfg, r.loops)))
                         moved = True
-                        continue
-                    need = float(p["device_bytes"]) + self.overhead
-                    res.device_bytes = float(p["device_bytes"])
-                    res.node_updates_per_step = int(p["node_updates_per_step"])
-                    if need > budget:
+
+                    # admission: arrival order; the head waits for memory (no overtaking)
+                    while waiting and resident < self.max_slots:
+                        r, pf = waiting[0]
+                        if not pf.done():
+                            break
+                        res = results[r.rid]
+                        try:
+                            p = pf.result()
+                        except Exception as e:   # geometry the grid builder rejects
+                            waiting.popleft()
+                            res.status, res.message, res.finished = "rejected", str(e), now()
+                            moved = True
+                            continue
+                        need = float(p["device_bytes"]) + self.overhead
+                        res.device_bytes = float(p["device_bytes"])
+                        res.node_updates_per_step = int(p["node_updates_per_step"])
+                        if need > budget:
+                            waiting.popleft()
+                            res.status, res.finished = "rejected", now()
+                            res.message = f"needs {need:.3e} B, budget {budget:.3e} B"
+                            moved = True
+                            continue
+                        if used + need > budget:
+                            break
                         waiting.popleft()
-                        res.status, res.finished = "rejected", now()
-                        res.message = f"needs {need:.3e} B, budget {budget:.3e} B"
+                        used += need
+                        resident += 1
+                        res.admitted = now()
+                        building.append((r, need, pool.submit(self.backend.build, r)))
+                        note("admit", r.rid)
                         moved = True
-                        continue
-                    if used + need > budget:
-                        break
-                    waiting.popleft()
-                    used += need
-                    resident += 1
-                    res.admitted = now()
-                    building.append((r, need, pool.submit(self.backend.build, r)))
-                    note("admit", r.rid)
-                    moved = True
 
-                # finished builds start stepping
-                still = []
-                for r, need, bf in building:
-                    if not bf.done():
-                        still.append((r, need, bf))
-                        continue
-                    res = results[r.rid]
-                    moved = True
-                    try:
-                        h = bf.result()
-                    except Exception as e:
-                        used -= need
-                        resident -= 1
-                        res.status, res.message, res.finished = "error", str(e), now()
-                        note("error", r.rid)
-                        continue
-                    slot = _Slot(r, res, h, need)
-                    active.append(slot)
-                    res.started = now()
-                    self._enqueue(slot)
-                    note("start", r.rid)
-                building = still
+                    # finished builds start stepping
+                    still = []
+                    for r, need, bf in building:
+                        if not bf.done():
+                            still.append((r, need, bf))
+                            continue
+                        res = results[r.rid]
+                        moved = True
+                        try:
+                            h = bf.result()
+                        except Exception as e:
+                            used -= need
+                            resident -= 1
+                            res.status, res.message, res.finished = "error", str(e), now()
+                            note("error", r.rid)
+                            continue
+                        slot = _Slot(r, res, h, need)
+                        res.started = now()
+                        try:
+                            self._enqueue(slot)
+                        except Exception as e:   # the solve could not be stepped: release it
+                            h.close()
+                            used -= need
+                            resident -= 1
+                            res.status, res.message, res.finished = "error", str(e), now()
+                            note("error", r.rid)
+                            continue
+                        active.append(slot)
+                        note("start", r.rid)
+                    building = still
 
-                # chunks that completed: read CL, test convergence, continue or finish
-                keep = []
+                    # chunks that completed: read CL, test convergence, continue or finish
+                    keep = []
+                    for slot in active:
+                        if not slot.handle.ready():
+                            keep.append(slot)
+                            continue
+                        moved = True
+                        if self._advance(slot):
+                            keep.append(slot)
+                            continue
+                        slot.res.finished = now()
+                        try:
+                            if on_finish is not None:
+                                on_finish(slot.res, slot.handle)
+                        finally:
+                            slot.handle.close()
+                            slot.released = True
+                            used -= slot.need
+                            resident -= 1
+                            note("finish", slot.req.rid)
+                    active = keep
+
+                    if not moved:
+                        time.sleep(self.poll_s)
+            finally:
+                # on an exception, release every solve still holding device memory
                 for slot in active:
-                    if not slot.handle.ready():
-                        keep.append(slot)
-                        continue
-                    moved = True
-                    if self._advance(slot):
-                        keep.append(slot)
-                        continue
-                    slot.res.finished = now()
-                    if on_finish is not None:
-                        on_finish(slot.res, slot.handle)
-                    slot.handle.close()
-                    used -= slot.need
-                    resident -= 1
-                    note("finish", slot.req.rid)
-                active = keep
-
-                if not moved:
-                    time.sleep(self.poll_s)
+                    if not slot.released:
+                        slot.handle.close()
+                for _, _, bf in building:
+                    try:
+                        bf.result().close()
+                    except Exception:
+                        pass
         return [results[r.rid] for r in requests]
 
     def _enqueue(self, slot):

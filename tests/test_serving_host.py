@@ -169,3 +169,39 @@ def test_window_mean_convergence_ignores_a_steady_oscillation():
     assert res[0].status == "max_steps"
     assert res[1].status == "converged" and res[1].steps == 900
     assert res[1].CL == pytest.approx(0.8, abs=1e-12)
+
+
+def test_a_solve_that_cannot_be_stepped_is_released():
+    class Broken(FakeHandle):
+        def enqueue(self, n):
+            raise RuntimeError("lbm status -3: launch failed")
+
+    class BrokenBackend(FakeBackend):
+        def build(self, req):
+            h = super().build(req)
+            if req.cfg.get("broken"):
+                b = Broken(self, req)
+                self.handles[-1] = b
+                return b
+            return h
+
+    be = BrokenBackend()
+    reqs = [make(0, 0.0, 4 << 20, broken=True), make(1, 0.0, 4 << 20)]
+    svc = Service(max_slots=1, mem_budget=8 << 20, overhead=0, backend=be)
+    res = svc.run(reqs)
+    assert res[0].status == "error" and "launch failed" in res[0].message
+    assert res[1].status == "converged"
+    assert be.live == 0 and all(h.closed for h in be.handles)
+
+
+def test_an_exception_in_the_caller_hook_still_releases_every_solve():
+    be = FakeBackend()
+    reqs = [make(k, 0.0, 1 << 20, cost=1e-5 * (k + 1)) for k in range(4)]
+
+    def boom(res, handle):
+        raise ValueError("caller hook failed")
+
+    with pytest.raises(ValueError):
+        Service(max_slots=4, mem_budget=64 << 20, overhead=0, backend=be).run(reqs, on_finish=boom)
+    time.sleep(0.05)
+    assert be.live == 0
