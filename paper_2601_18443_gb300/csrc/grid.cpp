@@ -73,7 +73,9 @@ static bool on_seg(IPt a, IPt b, IPt p)
 
 // ---------------------------------------------------------------- segment tree
 struct SegTree {
-    struct Node { double x0, y0, x1, y1; int lo, hi, left, right; };
+    // node: bounding box, and a capsule (the chord from the range's first to its last vertex,
+    // with a radius covering every endpoint) of the segments [lo, hi)
+    struct Node { double x0, y0, x1, y1, c0x, c0y, c1x, c1y, rad; int lo, hi, left, right; };
     std::vector<Node> nodes;
     std::vector<double> ax, ay, bx, by;   // finest lattice units
     int root = -1;
@@ -88,6 +90,16 @@ struct SegTree {
             nd.x0 = std::min(nd.x0, std::min(ax[k], bx[k])); nd.x1 = std::max(nd.x1, std::max(ax[k], bx[k]));
             nd.y0 = std::min(nd.y0, std::min(ay[k], by[k])); nd.y1 = std::max(nd.y1, std::max(ay[k], by[k]));
         }
+        nd.c0x = ax[lo]; nd.c0y = ay[lo]; nd.c1x = bx[hi - 1]; nd.c1y = by[hi - 1];
+        double r2 = 0.0;
+        for (int k = lo; k < hi; k++) {
+            r2 = std::max(r2, pt_seg2(nd.c0x, nd.c0y, nd.c1x, nd.c1y, ax[k], ay[k]));
+            r2 = std::max(r2, pt_seg2(nd.c0x, nd.c0y, nd.c1x, nd.c1y, bx[k], by[k]));
+        }
+        // every segment lies inside the capsule (it is convex and holds both endpoints); the
+        // margin keeps the bound below the true distance whatever the rounding
+        const double span = std::fabs(nd.x1 - nd.x0) + std::fabs(nd.y1 - nd.y0);
+        nd.rad = std::sqrt(r2) * (1.0 + 1e-9) + 1e-9 * (span + 1.0);
         int id = (int)nodes.size();
         nodes.push_back(nd);
         if (hi - lo > 8) {
@@ -96,6 +108,25 @@ struct SegTree {
             nodes[id].left = l; nodes[id].right = r;
         }
         return id;
+    }
+    static double pt_seg2(double ax_, double ay_, double bx_, double by_, double px, double py)
+    {
+        const double dx = bx_ - ax_, dy = by_ - ay_;
+        const double len2 = dx * dx + dy * dy;
+        double t = len2 > 0 ? ((px - ax_) * dx + (py - ay_) * dy) / len2 : 0.0;
+        if (t < 0) t = 0;
+        if (t > 1) t = 1;
+        const double qx = ax_ + t * dx - px, qy = ay_ + t * dy - py;
+        return qx * qx + qy * qy;
+    }
+    // lower bound of the squared distance from p to the node's segments
+    static double node_lb2(const Node &nd, double px, double py)
+    {
+        double dx = std::max(0.0, std::max(nd.x0 - px, px - nd.x1));
+        double dy = std::max(0.0, std::max(nd.y0 - py, py - nd.y1));
+        const double box2 = dx * dx + dy * dy;
+        const double cap = std::sqrt(pt_seg2(nd.c0x, nd.c0y, nd.c1x, nd.c1y, px, py)) - nd.rad;
+        return cap > 0.0 ? std::max(box2, cap * cap) : box2;
     }
     void init(const Grid &g)
     {
@@ -165,14 +196,14 @@ struct SegTree {
         stack[sp++] = root;
         while (sp) {
             const Node &nd = nodes[stack[--sp]];
-            if (box_dist2(nd, px, py) > best2) continue;
+            if (node_lb2(nd, px, py) > best2) continue;
             if (nd.left < 0) {
                 for (int k = nd.lo; k < nd.hi; k++) {
                     const double d2 = seg_dist2(k, px, py);
                     if (d2 <= best2) { best2 = d2; found = true; kfound = k; }
                 }
             } else {
-                double dl = box_dist2(nodes[nd.left], px, py), dr = box_dist2(nodes[nd.right], px, py);
+                double dl = node_lb2(nodes[nd.left], px, py), dr = node_lb2(nodes[nd.right], px, py);
                 if (dl <= dr) { stack[sp++] = nd.right; stack[sp++] = nd.left; }
                 else { stack[sp++] = nd.left; stack[sp++] = nd.right; }
             }
