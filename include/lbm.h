@@ -43,7 +43,7 @@ typedef enum {
     LBM_ERR_NO_GEOMETRY = -4,
     LBM_ERR_GEOMETRY = -5,
     LBM_ERR_DIVERGED = -6,
-    LBM_ERR_TIMEOUT = -7
+    LBM_ERR_TIMEOUT = -7    /* a device-side wait reached its limit (reserved: no kernel waits) */
 } lbm_status;
 
 typedef struct {

@@ -61,7 +61,8 @@ struct StepConsts {
     float pshift[9];    // 16-bit storage holds g_q - pshift_q (pshift = f_eq(1, U, 0) - w); 0 for FP32
 };
 
-// device status word bits (lbm_step maps them to lbm_status codes)
+// device status word bits (lbm_step maps them to lbm_status codes).  TIMEOUT is reserved
+// for a kernel that waits on a flag with an iteration limit; no kernel here waits.
 #define LBM_STATUS_NONFINITE 1
 #define LBM_STATUS_TIMEOUT 2
 
