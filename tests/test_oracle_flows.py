@@ -173,3 +173,16 @@ def test_vortex_leaves_through_the_outlet():
     e = ((f["ux"] - U) ** 2 + f["uy"] ** 2).sum()
     assert e < 1e-3 * e0
     assert np.abs(f["rho"] - 1).max() < 1e-3
+
+
+def test_zou_he_inlet_imposes_the_velocity_exactly():
+    # Sec 3.1.1: the inlet column's unknown populations are closed so that the post-stream
+    # velocity there is (U, 0) whatever arrives from the interior (here the vortex state)
+    r, U = _vortex_box()
+    r.step(150)                     # the vortex's pressure pulse has reached the inlet by now
+    for _ in range(3):
+        r.step(1)
+        f = r.get_fields(0)
+        assert np.abs(f["uy"][:, 1]).max() > 1e-7          # the next column is disturbed ...
+        assert np.abs(f["ux"][:, 0] - U).max() < 1e-14     # ... the inlet column is not
+        assert np.abs(f["uy"][:, 0]).max() < 1e-14
