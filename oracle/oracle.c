@@ -334,11 +334,14 @@ double oracle_sa_update_point(const double *chi9, const double *ux9, const doubl
     for (int k = 0; k < 9; k++) Dk[k] = sa_diffusivity(chi9[k], nu);
     double De = 0.5 * (Dk[0] + Dk[1]), Dw = 0.5 * (Dk[0] + Dk[2]);
     double Dn = 0.5 * (Dk[0] + Dk[3]), Ds = 0.5 * (Dk[0] + Dk[4]);
-    double div = De * (e - c) - Dw * (c - w) + Dn * (n - c) - Ds * (c - s);
-    double diff = (div + SA_CB2 * (gx * gx + gy * gy)) / SA_SIGMA;
+    /* diffusion with its diagonal taken at the new time level (point-implicit): the
+     * explicit form diverges once (nu + nu~)/sigma passes 1/4 per step; this one has the
+     * same steady states and keeps the diffusion a weighted mean at any nu~ */
+    double a = (De + Dw + Dn + Ds) / SA_SIGMA;
+    double off = (De * e + Dw * w + Dn * n + Ds * s + SA_CB2 * (gx * gx + gy * gy)) / SA_SIGMA;
     double P, D;
     oracle_sa_source(chi9[0], nu, vort, d, &P, &D);
-    double nnew = c + conv + P - D + diff;
+    double nnew = (c + conv + P - D + off) / (1.0 + a);
     return nnew / nu;
 }
 

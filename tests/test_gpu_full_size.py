@@ -105,7 +105,7 @@ def test_full_size_grid_and_one_step(name):
         chi9 = np.array([F0["chi"][j + CY[q], i + CX[q]] for q in range(9)])
         u9 = np.array([F0["ux"][j + CY[q], i + CX[q]] for q in range(9)])
         v9 = np.array([F0["uy"][j + CY[q], i + CX[q]] for q in range(9)])
-        chi_new = oracle.sa_update_point(chi9, u9, v9, d0[j, i], nu0, cfg.get("sa_convection", 0))
+        chi_new = oracle.sa_update_point(chi9, u9, v9, max(d0[j, i], 0.5), nu0, cfg.get("sa_convection", 0))
         chi_err.append(abs(F1["chi"][j, i] - chi_new) / max(abs(chi_new), 1.0))
         pulled = np.array([pop0[q, j - CY[q], i - CX[q]] for q in range(9)])
         c3 = max(chi_new, 0.0) ** 3

@@ -89,8 +89,11 @@ def test_lsq_vorticity_exact_for_linear_velocity(grad):
     uy = _stencil(lambda x, y: -0.05 + c * x + e * y)
     # constant velocity offset is removed from convection because chi is uniform
     chi0 = 2.0
-    new = oracle.sa_update_point(np.full(9, chi0), ux, uy, FAR, 1e-6)
-    assert (new - chi0) / (CB1 * chi0) == pytest.approx(abs(c - b), rel=1e-9, abs=1e-15)
+    nu = 1e-6
+    new = oracle.sa_update_point(np.full(9, chi0), ux, uy, FAR, nu)
+    # the diffusion's diagonal is implicit: the source enters divided by 1 + sum_f D_f / sigma
+    a = 4.0 * nu * (1.0 + chi0) / SIGMA
+    assert (new - chi0) * (1.0 + a) / (CB1 * chi0) == pytest.approx(abs(c - b), rel=1e-9, abs=1e-15)
 
 
 def test_diffusion_second_order():
@@ -101,6 +104,10 @@ def test_diffusion_second_order():
         f = lambda x, y: 1.0 + 0.5 * math.sin(0.7 + x) * math.cos(0.3 + 2 * y)
         chi = _stencil(lambda i, j: f(i * h, j * h))
         new = oracle.sa_update_point(chi, np.zeros(9), np.zeros(9), FAR, nu)
+        # the diagonal of the diffusion is implicit: the increment is the explicit one
+        # divided by 1 + sum_f D_f / sigma, D_f the face means of nu + nu~ (nu~ = chi nu)
+        D = nu * (1.0 + chi)
+        a = sum(0.5 * (D[0] + D[k]) for k in (1, 2, 3, 4)) / SIGMA
         # analytic right-hand side in physical units, scaled by h^2 for the unit lattice
         x, y = 0.0, 0.0
         nt = f(x, y)
@@ -109,7 +116,7 @@ def test_diffusion_second_order():
         fxx = -0.5 * math.sin(0.7 + x) * math.cos(0.3 + 2 * y)
         fyy = -2.0 * math.sin(0.7 + x) * math.cos(0.3 + 2 * y)
         rhs = ((1 + nt) * (fxx + fyy) + (fx * fx + fy * fy) + CB2 * (fx * fx + fy * fy)) / SIGMA
-        errs.append(abs((new - chi[0]) / h**2 - rhs))
+        errs.append(abs((new - chi[0]) * (1.0 + a) / h**2 - rhs))
     assert math.log2(errs[0] / errs[1]) > 1.8
     assert math.log2(errs[1] / errs[2]) > 1.8
 
@@ -202,3 +209,20 @@ def test_sliver_run_stays_finite_and_the_flow_uniform():
     assert np.all(np.isfinite(f["chi"]))
     assert np.abs(f["ux"] - f["ux"][0, 0]).max() < 1e-15 and np.abs(f["uy"]).max() < 1e-15
     assert f["chi"].min() > 0.0 and f["chi"].max() <= 3.0 + 1e-12
+
+
+def test_implicit_diagonal_keeps_the_diffusion_a_weighted_mean():
+    # nu~ so large that explicit diffusion (factor (nu + nu~)/sigma per step, well above 1/4)
+    # would overshoot: with the diagonal implicit, a stencil without source, convection or
+    # cb2 term (gradient zero by symmetry) updates to a weighted mean of its values
+    nu = 1e-3
+    chi = np.array([5.0e4, 9.0e4, 9.0e4, 2.0e4, 2.0e4, 7.0e4, 7.0e4, 7.0e4, 7.0e4])
+    new = oracle.sa_update_point(chi, np.zeros(9), np.zeros(9), FAR, nu)
+    assert chi.min() <= new <= chi.max()
+    D = nu * (1.0 + chi)
+    Df = [0.5 * (D[0] + D[k]) for k in (1, 2, 3, 4)]
+    explicit = chi[0] + sum(f * (chi[k] - chi[0]) for f, k in zip(Df, (1, 2, 3, 4))) / SIGMA
+    assert not (chi.min() <= explicit <= chi.max())      # the explicit step leaves the range
+    # and the same fixed point: a stencil in balance does not move
+    flat = np.full(9, 7.0e4)
+    assert oracle.sa_update_point(flat, np.zeros(9), np.zeros(9), FAR, nu) == pytest.approx(7.0e4, rel=1e-14)
