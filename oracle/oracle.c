@@ -338,10 +338,12 @@ double oracle_sa_update_point(const double *chi9, const double *ux9, const doubl
      * explicit form diverges once (nu + nu~)/sigma passes 1/4 per step; this one has the
      * same steady states and keeps the diffusion a weighted mean at any nu~ */
     double a = (De + Dw + Dn + Ds) / SA_SIGMA;
-    double off = (De * e + Dw * w + Dn * n + Ds * s + SA_CB2 * (gx * gx + gy * gy)) / SA_SIGMA;
+    double div = De * (e - c) - Dw * (c - w) + Dn * (n - c) - Ds * (c - s);
+    double diff = (div + SA_CB2 * (gx * gx + gy * gy)) / SA_SIGMA;
     double P, D;
     oracle_sa_source(chi9[0], nu, vort, d, &P, &D);
-    double nnew = (c + conv + P - D + off) / (1.0 + a);
+    /* (c + conv + P - D + diff + a c) / (1 + a), written as an increment of c */
+    double nnew = c + (conv + P - D + diff) / (1.0 + a);
     return nnew / nu;
 }
 

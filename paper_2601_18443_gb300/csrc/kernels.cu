@@ -267,8 +267,9 @@ __device__ __forceinline__ float sa_diff_coef(float chi)
     return 1.0f + chi * fn;
 }
 
-// explicit Euler step of eqs 12 / 16 written for chi = nu_t~ / nu, with Lax-Wendroff
-// (conv = 0, Sec 2.2) or first-order upwind (conv = 1, Sec 3.3) convection;
+// Euler step of eqs 12 / 16 written for chi = nu_t~ / nu (explicit, with the diagonal of the
+// diffusion at the new time level), with Lax-Wendroff (conv = 0, Sec 2.2) or first-order
+// upwind (conv = 1, Sec 3.3) convection;
 // id2 = 1 / d^2 (wall distance d in level lattice units)
 __device__ float sa_update(const Stencil &S, float id2, float nu, int conv)
 {
@@ -318,7 +319,10 @@ __device__ float sa_update(const Stencil &S, float id2, float nu, int conv)
     } else {
         src = SA_CB1 * (1.0f - SA_CT3) * vort * chi + SA_CW1 * nu * chi * chi * id2;
     }
-    return chi + cv + src + diff;
+    // the diffusion's diagonal at the new time level (point-implicit): the explicit increment
+    // divided by 1 + sum_f D_f / sigma; unconditionally stable diffusion, same steady states
+    const float a = nu * (De + Dw + Dn + Ds) * (1.0f / SA_SIGMA);
+    return chi + (cv + src + diff) / (1.0f + a);
 }
 
 // ------------------------------------------------------------------ wall function (Sec 2.3 steps 1-5)
