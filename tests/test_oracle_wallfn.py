@@ -92,3 +92,42 @@ def test_nishimura_slip_follows_eq31():
         assert st[r, 3] == pytest.approx(utau, rel=1e-12)
         assert st[r, 1] == pytest.approx(expect, rel=1e-9, abs=1e-15)
         assert st[r, 2] == pytest.approx(0.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("nu_lat", [0.01, 2e-7])
+def test_virtual_node_slip_follows_eq28(nu_lat):
+    # Sec 2.3 steps 3-5: u_tau from eq 22 at R (d_WR = 2), u_V = u_tau u+(y+_V) at the virtual
+    # node (d_WV = 1), the slip of eq 28 u_W = u_V - u_tau^2 d_WV / (nu (1 + kappa y+_V)) along
+    # t, and the Dirichlet chi_B = kappa u_tau d_WB / nu.  Linear profile above a plate top, as
+    # in the eq 31 pin.  At the small viscosity y+_V is in the log layer, where eq 28 tends to
+    # u_W = u_tau (u+(y+_V) - 1/kappa).
+    from paper_2601_18443_gb300 import workloads as W
+    nx0, ny0, top = 48, 32, 12.375
+    U = 0.1 * math.sqrt(1.0 / 3.0)
+    cfg = W.base_config(levels=1, nx0=nx0, ny0=ny0, h0=1.0, Re=U / nu_lat, Ma=0.1, wall_model=0,
+                        turbulence=1, d_wr=2.0, d_wv=1.0)
+    s = oracle.Solver(cfg)
+    s.set_geometry([W.rectangle(8.0, 6.0, 40.0, top)])
+    y = np.arange(ny0) + 0.5
+    a, b = 0.004, 0.003
+    ux = np.tile((a + b * (y - top))[:, None], (1, nx0))
+    s.set_fields(0, rho=np.ones((ny0, nx0)), ux=ux, uy=np.zeros((ny0, nx0)), chi=np.full((ny0, nx0), 4.0))
+    ij, geo, ns = s.wall_records()
+    st = s.wall_state()
+    sel = (geo[:, 3] > 0.999) & (ij[:, 0] > 12) & (ij[:, 0] < 36)
+    assert sel.sum() >= 20
+    n_log = 0
+    for r in np.nonzero(sel)[0]:
+        uR = a + b * (geo[r, 6] - top)
+        utau = oracle.wf_utau(uR, 2.0, nu_lat)
+        ypv = utau * 1.0 / nu_lat
+        uV = utau * oracle.wf_uplus(ypv)
+        uW = uV - utau**2 * 1.0 / (nu_lat * (1.0 + KAPPA * ypv))
+        assert st[r, 3] == pytest.approx(utau, rel=1e-12)
+        assert st[r, 1] == pytest.approx(uW, rel=1e-9, abs=1e-15)
+        assert st[r, 2] == pytest.approx(0.0, abs=1e-12)
+        assert st[r, 4] == pytest.approx(KAPPA * utau * geo[r, 4] / nu_lat, rel=1e-12)
+        if ypv > 200.0:
+            n_log += 1
+            assert uW == pytest.approx(utau * (oracle.wf_uplus(ypv) - 1.0 / KAPPA), rel=2e-2)
+    assert n_log == (sel.sum() if nu_lat < 1e-6 else 0)
