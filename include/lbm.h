@@ -105,8 +105,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out);
  * to the equilibrium of rho = 1, u = (U, 0), chi = chi_inf.  xy: 2 * n_points doubles
  * (x, y) in chord units; loop_offsets: n_loops + 1 ints, loop k = points
  * [loop_offsets[k], loop_offsets[k+1]), first vertex not repeated, any orientation.
- * Errors: LBM_ERR_GEOMETRY (refinement breaks 2:1 nesting or reaches the box edge, a
- * wall touches a non-finest cell, a reference stencil leaves the finest level),
+ * Errors: LBM_ERR_GEOMETRY (a loop with fewer than 3 vertices or zero area, wall
+ * segments that cross, refinement that breaks 2:1 nesting or reaches the box edge, a
+ * wall touching a non-finest cell, a reference stencil leaving the finest level),
  * LBM_ERR_OOM, LBM_ERR_CUDA. */
 lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_offsets, int n_loops);
 

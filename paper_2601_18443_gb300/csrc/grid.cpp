@@ -71,6 +71,19 @@ static bool on_seg(IPt a, IPt b, IPt p)
     return dot >= 0 && dot <= ex * ex + ey * ey;
 }
 
+// exact test whether segments ab and cd cross properly (each strictly separates the other's
+// ends); touching, a shared end and collinear overlap are not crossings
+static int orient(IPt a, IPt b, IPt c)
+{
+    const i128 v = (i128)(b.x - a.x) * (c.y - a.y) - (i128)(b.y - a.y) * (c.x - a.x);
+    return v > 0 ? 1 : (v < 0 ? -1 : 0);
+}
+
+static bool segs_cross(IPt a, IPt b, IPt c, IPt d)
+{
+    return orient(a, b, c) * orient(a, b, d) < 0 && orient(c, d, a) * orient(c, d, b) < 0;
+}
+
 // ---------------------------------------------------------------- segment tree
 struct SegTree {
     // node: bounding box, and a capsule (the chord from the range's first to its last vertex,
@@ -385,6 +398,33 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
     if (!sp.solid_walls) g.loop_ccw.assign(std::max(n_loops, 1), 1);
     SegTree T;
     T.init(g);
+    // no two wall segments may cross: a loop that crosses itself or another loop has no
+    // consistent inside.  Contacts without crossing (the zero-width tip a closed trailing
+    // edge can leave after snapping, loops sharing an edge) are accepted.
+    if (sp.solid_walls) {
+        const long nseg = (long)g.sa.size();
+        int bad = 0;
+#pragma omp parallel
+        {
+        std::vector<int> cand;
+#pragma omp for schedule(dynamic, 256)
+        for (long k = 0; k < nseg; k++) {
+            int flag;
+#pragma omp atomic read
+            flag = bad;
+            if (flag) continue;
+            const IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
+            T.overlapping((double)std::min(a.x, b.x) / FIXU - 1e-9, (double)std::min(a.y, b.y) / FIXU - 1e-9,
+                          (double)std::max(a.x, b.x) / FIXU + 1e-9, (double)std::max(a.y, b.y) / FIXU + 1e-9, cand);
+            for (int m : cand)
+                if (m > k && segs_cross(a, b, g.v[g.sa[m]], g.v[g.sb[m]])) {
+#pragma omp atomic write
+                    bad = 1;
+                }
+        }
+        }
+        if (bad) return failmsg(msg, "wall loops cross themselves or each other");
+    }
 
     g.lv.resize(L);
     for (int l = 0; l < L; l++) { g.lv[l].l = l; g.lv[l].scale = 1LL << (L - 1 - l); }

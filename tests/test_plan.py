@@ -49,3 +49,20 @@ def test_plan_rejects_degenerate_loops():
     with pytest.raises(pkg.LBMError) as e:
         pkg.plan(cfg, [np.array([[20.0, 20.0], [30.0, 30.0], [40.0, 40.0]])])   # zero area
     assert e.value.code == -5 and "degenerate" in str(e.value)
+
+
+def test_plan_rejects_crossing_loops_and_accepts_touching_ones():
+    pkg.build()
+    cfg = W.base_config(levels=2, nx0=64, ny0=64, h0=1.0, layers=4)
+    # two overlapping squares: their edges cross
+    with pytest.raises(pkg.LBMError) as e:
+        pkg.plan(cfg, [W.rectangle(20.0, 20.0, 30.0, 30.0), W.rectangle(25.0, 25.0, 35.0, 35.0)])
+    assert e.value.code == -5 and "cross" in str(e.value)
+    # a figure eight with lobes of different size (nonzero signed area, one self-crossing)
+    eight = np.array([[20.0, 20.0], [36.0, 32.0], [36.0, 20.0], [20.0, 28.0]])
+    with pytest.raises(pkg.LBMError) as e:
+        pkg.plan(cfg, [eight])
+    assert e.value.code == -5 and "cross" in str(e.value)
+    # loops that only touch along an edge, and separate loops, are valid geometry
+    pkg.plan(cfg, [W.rectangle(20.0, 20.0, 30.0, 30.0), W.rectangle(30.0, 22.0, 38.0, 28.0)])
+    pkg.plan(cfg, [W.rectangle(18.0, 18.0, 26.0, 26.0), W.rectangle(32.0, 32.0, 42.0, 42.0)])
