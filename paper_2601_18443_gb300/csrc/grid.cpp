@@ -88,7 +88,7 @@ static bool segs_cross(IPt a, IPt b, IPt c, IPt d)
 struct SegTree {
     // node: bounding box, and a capsule (the chord from the range's first to its last vertex,
     // with a radius covering every endpoint) of the segments [lo, hi)
-    struct Node { double x0, y0, x1, y1, c0x, c0y, c1x, c1y, rad; int lo, hi, left, right; };
+    struct Node { double x0, y0, x1, y1, c0x, c0y, c1x, c1y, rad, ux, uy, il2; int lo, hi, left, right; };
     std::vector<Node> nodes;
     std::vector<double> ax, ay, bx, by;   // finest lattice units
     int root = -1;
@@ -113,6 +113,9 @@ struct SegTree {
         // margin keeps the bound below the true distance whatever the rounding
         const double span = std::fabs(nd.x1 - nd.x0) + std::fabs(nd.y1 - nd.y0);
         nd.rad = std::sqrt(r2) * (1.0 + 1e-9) + 1e-9 * (span + 1.0);
+        nd.ux = nd.c1x - nd.c0x; nd.uy = nd.c1y - nd.c0y;
+        const double l2 = nd.ux * nd.ux + nd.uy * nd.uy;
+        nd.il2 = l2 > 0 ? 1.0 / l2 : 0.0;
         int id = (int)nodes.size();
         nodes.push_back(nd);
         if (hi - lo > 8) {
@@ -132,13 +135,19 @@ struct SegTree {
         const double qx = ax_ + t * dx - px, qy = ay_ + t * dy - py;
         return qx * qx + qy * qy;
     }
-    // lower bound of the squared distance from p to the node's segments
+    // lower bound of the squared distance from p to the node's segments.  The capsule term
+    // measures p against a point of the chord (the projection, with the chord's reciprocal
+    // squared length precomputed): any point of the chord is at least as far as the chord,
+    // and the rounding of the projection is far below the radius margin
     static double node_lb2(const Node &nd, double px, double py)
     {
-        double dx = std::max(0.0, std::max(nd.x0 - px, px - nd.x1));
-        double dy = std::max(0.0, std::max(nd.y0 - py, py - nd.y1));
+        const double dx = std::max(0.0, std::max(nd.x0 - px, px - nd.x1));
+        const double dy = std::max(0.0, std::max(nd.y0 - py, py - nd.y1));
         const double box2 = dx * dx + dy * dy;
-        const double cap = std::sqrt(pt_seg2(nd.c0x, nd.c0y, nd.c1x, nd.c1y, px, py)) - nd.rad;
+        double t = ((px - nd.c0x) * nd.ux + (py - nd.c0y) * nd.uy) * nd.il2;
+        t = t < 0 ? 0 : (t > 1 ? 1 : t);
+        const double qx = nd.c0x + t * nd.ux - px, qy = nd.c0y + t * nd.uy - py;
+        const double cap = std::sqrt(qx * qx + qy * qy) - nd.rad;
         return cap > 0.0 ? std::max(box2, cap * cap) : box2;
     }
     void init(const Grid &g)
@@ -204,21 +213,28 @@ struct SegTree {
         bool found = false;
         kfound = -1;
         if (root < 0) return std::numeric_limits<double>::infinity();
+        // each stacked node carries its lower bound, evaluated once when it is pushed and
+        // tested again when it is popped, against the best distance found by then
         int stack[128];
+        double slb2[128];
         int sp = 0;
-        stack[sp++] = root;
+        stack[sp] = root; slb2[sp++] = 0.0;
         while (sp) {
-            const Node &nd = nodes[stack[--sp]];
-            if (node_lb2(nd, px, py) > best2) continue;
+            --sp;
+            if (slb2[sp] > best2) continue;
+            const Node &nd = nodes[stack[sp]];
             if (nd.left < 0) {
                 for (int k = nd.lo; k < nd.hi; k++) {
                     const double d2 = seg_dist2(k, px, py);
                     if (d2 <= best2) { best2 = d2; found = true; kfound = k; }
                 }
             } else {
-                double dl = node_lb2(nodes[nd.left], px, py), dr = node_lb2(nodes[nd.right], px, py);
-                if (dl <= dr) { stack[sp++] = nd.right; stack[sp++] = nd.left; }
-                else { stack[sp++] = nd.left; stack[sp++] = nd.right; }
+                const double dl = node_lb2(nodes[nd.left], px, py), dr = node_lb2(nodes[nd.right], px, py);
+                // the nearer child is popped first
+                const int first = dl <= dr ? nd.left : nd.right, second = dl <= dr ? nd.right : nd.left;
+                const double lf = std::min(dl, dr), ls = std::max(dl, dr);
+                if (ls <= best2) { stack[sp] = second; slb2[sp++] = ls; }
+                if (lf <= best2) { stack[sp] = first; slb2[sp++] = lf; }
             }
         }
         return found ? std::sqrt(best2) : std::numeric_limits<double>::infinity();
@@ -298,9 +314,14 @@ static int failmsg(std::string &msg, const char *m)
 static void alloc_level(Level &Lv, int i0, int j0, int nx, int ny)
 {
     Lv.bi0 = i0; Lv.bj0 = j0; Lv.bnx = nx; Lv.bny = ny;
-    size_t n = (size_t)nx * ny;
-    Lv.kind.assign(n, KIND_ABSENT); Lv.solid.assign(n, 0); Lv.band.assign(n, 0); Lv.bnode.assign(n, 0);
-    Lv.coal.assign(n, 0); Lv.cut.assign(n, 0); Lv.dist.assign(n, 0.0); Lv.rec.assign(n, -1);
+    const long n = (long)nx * ny;
+    Lv.kind.resize(n); Lv.solid.resize(n); Lv.band.resize(n); Lv.bnode.resize(n);
+    Lv.coal.resize(n); Lv.cut.resize(n); Lv.dist.resize(n); Lv.rec.resize(n);
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; c++) {
+        Lv.kind[c] = KIND_ABSENT; Lv.solid[c] = 0; Lv.band[c] = 0; Lv.bnode[c] = 0;
+        Lv.coal[c] = 0; Lv.cut[c] = 0; Lv.dist[c] = 0.0; Lv.rec[c] = -1;
+    }
 }
 
 // centre of level cell (i, j) in fixed units
@@ -360,7 +381,8 @@ static void paint_solid(const Grid &g, Level &Lv)
                 if (c >= 0 && on_seg(a, b, centre(Lv, i, j))) Lv.solid[c] = 1;
             }
     }
-    for (size_t c = 0; c < Lv.solid.size(); c++)
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < (long)Lv.solid.size(); c++)
         if (Lv.kind[c] == KIND_ABSENT) Lv.solid[c] = 0;
 }
 
@@ -499,28 +521,38 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                     near[c] = 1;
                 }
         }
-        for (size_t c = 0; c < near.size(); c++)
+#pragma omp parallel for schedule(static)
+        for (long c = 0; c < (long)near.size(); c++)
             if (near[c]) P.kind[c] = KIND_COVERED;
-        // nesting checks, band, child box
+        // nesting checks, band, child box.  Rows run in parallel; each notes its first
+        // violation, and the first row with one names the error (as a row-major scan would)
         long long ci0 = (1LL << 40), cj0 = (1LL << 40), ci1 = -(1LL << 40), cj1 = -(1LL << 40);
+        std::vector<uint8_t> row_err(P.bny, 0);
+#pragma omp parallel for schedule(dynamic, 8) reduction(min : ci0, cj0) reduction(max : ci1, cj1)
         for (int r = 0; r < P.bny; r++)
-            for (int q = 0; q < P.bnx; q++) {
+            for (int q = 0; q < P.bnx && !row_err[r]; q++) {
                 if (P.kind[(size_t)r * P.bnx + q] != KIND_COVERED) continue;
                 long long i = P.bi0 + q, j = P.bj0 + r;
-                if (l == 1 && (i < 2 || j < 2 || i >= sp.nx0 - 2 || j >= sp.ny0 - 2))
-                    return failmsg(msg, "refinement reaches the level-0 box edge");
+                if (l == 1 && (i < 2 || j < 2 || i >= sp.nx0 - 2 || j >= sp.ny0 - 2)) { row_err[r] = 1; break; }
                 for (int d = 1; d < 9; d++) {
                     long c = P.idx(i + CX[d], j + CY[d]);
-                    if (c < 0 || (P.kind[c] != KIND_ACTIVE && P.kind[c] != KIND_COVERED))
-                        return failmsg(msg, "refinement band violates 2:1 nesting (increase layers)");
-                    if (P.kind[c] == KIND_ACTIVE) P.band[c] = 1;
+                    if (c < 0 || (P.kind[c] != KIND_ACTIVE && P.kind[c] != KIND_COVERED)) { row_err[r] = 2; break; }
+                    if (P.kind[c] == KIND_ACTIVE) {
+#pragma omp atomic write
+                        P.band[c] = 1;
+                    }
                 }
                 ci0 = std::min(ci0, i - 1); cj0 = std::min(cj0, j - 1);
                 ci1 = std::max(ci1, i + 1); cj1 = std::max(cj1, j + 1);
             }
+        for (int r = 0; r < P.bny; r++) {
+            if (row_err[r] == 1) return failmsg(msg, "refinement reaches the level-0 box edge");
+            if (row_err[r] == 2) return failmsg(msg, "refinement band violates 2:1 nesting (increase layers)");
+        }
         if (ci1 < ci0) return failmsg(msg, "level has no cells (wall far from the box?)");
         Level &F = g.lv[l];
         alloc_level(F, (int)(2 * ci0 - 1), (int)(2 * cj0 - 1), (int)(2 * (ci1 - ci0 + 1) + 2), (int)(2 * (cj1 - cj0 + 1) + 2));
+#pragma omp parallel for schedule(static)
         for (long long j = cj0; j <= cj1; j++)
             for (long long i = ci0; i <= ci1; i++) {
                 long c = P.idx(i, j);
@@ -554,6 +586,8 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
     // cut links; walls may only touch active cells of the finest level
     for (int l = 0; l < L; l++) {
         Level &P = g.lv[l];
+        int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
         for (int r = 0; r < P.bny; r++)
             for (int q = 0; q < P.bnx; q++) {
                 size_t c = (size_t)r * P.bnx + q;
@@ -567,11 +601,11 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                     if (cc >= 0 && P.kind[cc] != KIND_ABSENT && P.solid[cc]) m |= (uint16_t)(1u << d);
                 }
                 if (!m) continue;
-                if (l != L - 1 || P.kind[c] != KIND_ACTIVE)
-                    return failmsg(msg, "wall reaches a cell that is not on the finest active level");
+                if (l != L - 1 || P.kind[c] != KIND_ACTIVE) { bad = 1; continue; }
                 P.cut[c] = m;
                 P.bnode[c] = 1;
             }
+        if (bad) return failmsg(msg, "wall reaches a cell that is not on the finest active level");
     }
     // wall distance of active fluid cells
     for (int l = 0; l < L; l++) {
@@ -600,44 +634,66 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
             }
         }
     }
-    // wall records in (j, i) order at the finest level
+    // wall records in (j, i) order at the finest level: the boundary nodes are listed row by
+    // row, then each record is built independently; an error is reported for the first
+    // record, in that order, that has one (the same one a sequential build meets first)
     Level &Fn = g.lv[L - 1];
-    for (int r = 0; r < Fn.bny; r++)
-        for (int q = 0; q < Fn.bnx; q++) {
-            size_t c = (size_t)r * Fn.bnx + q;
-            if (!Fn.bnode[c]) continue;
-            Record rc;
-            std::memset(&rc, 0, sizeof rc);
-            rc.i = Fn.bi0 + q; rc.j = Fn.bj0 + r;
-            double bx = rc.i + 0.5, by = rc.j + 0.5, cx, cy;
-            int kb;
-            double dwb = T.nearest(bx, by, kb, cx, cy);
-            rc.seg = kb; rc.loop = g.sloop[kb];
-            rc.iw[0] = cx; rc.iw[1] = cy; rc.dwb = dwb;
-            rc.n[0] = (bx - cx) / dwb; rc.n[1] = (by - cy) / dwb;
-            rc.r[0] = cx + sp.d_wr * rc.n[0]; rc.r[1] = cy + sp.d_wr * rc.n[1];
-            IPt pb = centre(Fn, rc.i, rc.j);
-            for (int d = 1; d < 9; d++) {
-                if (!(Fn.cut[c] >> d & 1)) continue;
-                double t = link_q(g, T, pb, IPt{-CX[d] * FIXU, -CY[d] * FIXU});
-                if (t > 1.0) return failmsg(msg, "cut link without a wall crossing");
-                rc.q[d] = t;
-                g.n_cut++;
-            }
-            int ic = (int)std::floor(rc.r[0] - 0.5), jc = (int)std::floor(rc.r[1] - 0.5);
-            rc.ns = 0;
-            for (int b = -1; b <= 2; b++)
-                for (int a = -1; a <= 2; a++) {
-                    long cc = Fn.idx(ic + a, jc + b);
-                    bool act = cc >= 0 && Fn.kind[cc] == KIND_ACTIVE;
-                    if (sp.wall_model <= 1 && !act) return failmsg(msg, "reference point stencil leaves the finest active level");
-                    if (!act || Fn.solid[cc] || Fn.bnode[cc]) continue;
-                    rc.si[rc.ns] = ic + a; rc.sj[rc.ns] = jc + b; rc.ns++;
-                }
-            if (sp.wall_model <= 1 && rc.ns == 0) return failmsg(msg, "empty reference stencil");
-            Fn.rec[c] = (int)g.recs.size();
-            g.recs.push_back(rc);
+    std::vector<long> bcell;
+    {
+        std::vector<std::vector<long>> per_row(Fn.bny);
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int r = 0; r < Fn.bny; r++)
+            for (int q = 0; q < Fn.bnx; q++)
+                if (Fn.bnode[(size_t)r * Fn.bnx + q]) per_row[r].push_back((long)r * Fn.bnx + q);
+        for (auto &v : per_row) bcell.insert(bcell.end(), v.begin(), v.end());
+    }
+    const long nrec = (long)bcell.size();
+    g.recs.resize(nrec);
+    std::vector<int> rec_err(nrec, 0);
+    long long n_cut = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : n_cut)
+    for (long k = 0; k < nrec; k++) {
+        const long c = bcell[k];
+        const int r = (int)(c / Fn.bnx), q = (int)(c % Fn.bnx);
+        Record &rc = g.recs[k];
+        std::memset(&rc, 0, sizeof rc);
+        rc.i = Fn.bi0 + q; rc.j = Fn.bj0 + r;
+        double bx = rc.i + 0.5, by = rc.j + 0.5, cx, cy;
+        int kb;
+        double dwb = T.nearest(bx, by, kb, cx, cy);
+        rc.seg = kb; rc.loop = g.sloop[kb];
+        rc.iw[0] = cx; rc.iw[1] = cy; rc.dwb = dwb;
+        rc.n[0] = (bx - cx) / dwb; rc.n[1] = (by - cy) / dwb;
+        rc.r[0] = cx + sp.d_wr * rc.n[0]; rc.r[1] = cy + sp.d_wr * rc.n[1];
+        IPt pb = centre(Fn, rc.i, rc.j);
+        int err = 0;
+        for (int d = 1; d < 9 && !err; d++) {
+            if (!(Fn.cut[c] >> d & 1)) continue;
+            double t = link_q(g, T, pb, IPt{-CX[d] * FIXU, -CY[d] * FIXU});
+            if (t > 1.0) { err = 1; break; }
+            rc.q[d] = t;
+            n_cut++;
         }
+        int ic = (int)std::floor(rc.r[0] - 0.5), jc = (int)std::floor(rc.r[1] - 0.5);
+        rc.ns = 0;
+        for (int b = -1; b <= 2 && !err; b++)
+            for (int a = -1; a <= 2; a++) {
+                long cc = Fn.idx(ic + a, jc + b);
+                bool act = cc >= 0 && Fn.kind[cc] == KIND_ACTIVE;
+                if (sp.wall_model <= 1 && !act) { err = 2; break; }
+                if (!act || Fn.solid[cc] || Fn.bnode[cc]) continue;
+                rc.si[rc.ns] = ic + a; rc.sj[rc.ns] = jc + b; rc.ns++;
+            }
+        if (!err && sp.wall_model <= 1 && rc.ns == 0) err = 3;
+        rec_err[k] = err;
+        Fn.rec[c] = (int)k;
+    }
+    for (long k = 0; k < nrec; k++) {
+        if (rec_err[k] == 1) return failmsg(msg, "cut link without a wall crossing");
+        if (rec_err[k] == 2) return failmsg(msg, "reference point stencil leaves the finest active level");
+        if (rec_err[k] == 3) return failmsg(msg, "empty reference stencil");
+    }
+    g.n_cut = n_cut;
     // surface element centroid -> two nearest boundary nodes (ties: lower record index)
     size_t nseg = g.sa.size();
     g.seg_b1.assign(nseg, -1); g.seg_b2.assign(nseg, -1); g.seg_w1.assign(nseg, 0); g.seg_w2.assign(nseg, 0);
@@ -682,6 +738,7 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
     for (int l = 0; l < L; l++) {
         Level &P = g.lv[l];
         int a0 = 1 << 30, b0 = 1 << 30, a1 = -(1 << 30), b1 = -(1 << 30);
+#pragma omp parallel for schedule(static) reduction(min : a0, b0) reduction(max : a1, b1)
         for (int r = 0; r < P.bny; r++)
             for (int q = 0; q < P.bnx; q++)
                 if (P.kind[(size_t)r * P.bnx + q] != KIND_ABSENT) {
@@ -698,7 +755,10 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
         // present cell -- solid cells carry no state: no population is ever pulled from
         // them and no stencil reads them -- and list tiles with boundary nodes first, so
         // that their wall-function work starts in the first wave of every launch.
-        std::vector<int> cand_x[2], cand_y[2];
+        // tile classes of each tile row (0 wall tiles, 1 the others, 2 none), then the two
+        // lists in row-major order
+        std::vector<uint8_t> tcls((size_t)P.ntx * P.nty, 2);
+#pragma omp parallel for schedule(dynamic, 4)
         for (int ty = 0; ty < P.nty; ty++)
             for (int tx = 0; tx < P.ntx; tx++) {
                 bool any = false, wall = false;
@@ -710,37 +770,38 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                         if (l == 0 || !P.solid[c]) any = true;
                         if (P.bnode[c]) wall = true;
                     }
-                if (!any) continue;
-                int cls = (l > 0 && wall) ? 0 : 1;
-                cand_x[cls].push_back(P.tx0 + tx); cand_y[cls].push_back(P.ty0 + ty);
+                if (any) tcls[(size_t)ty * P.ntx + tx] = (l > 0 && wall) ? 0 : 1;
             }
-        P.n_wall_tiles = (int)cand_x[0].size();
-        for (int cls = 0; cls < 2; cls++)
-            for (size_t m = 0; m < cand_x[cls].size(); m++) {
-                int tx = cand_x[cls][m] - P.tx0, ty = cand_y[cls][m] - P.ty0;
-                P.tile_of[(size_t)ty * P.ntx + tx] = (int)P.tile_x.size();
-                P.tile_x.push_back(cand_x[cls][m]); P.tile_y.push_back(cand_y[cls][m]);
-            }
-        P.ntiles = (int)P.tile_x.size();
-        P.band_tiles.clear();
-        for (int t = 0; t < P.ntiles; t++) {
-            bool band = false;
-            for (int y = 0; y < LBM_TY && !band; y++)
-                for (int x = 0; x < LBM_TX && !band; x++) {
-                    long c = P.idx(P.tile_x[t] * LBM_TX + x, P.tile_y[t] * LBM_TY + y);
-                    band = c >= 0 && P.band[c] && !P.solid[c];
+        for (int cls = 0; cls < 2; cls++) {
+            for (int ty = 0; ty < P.nty; ty++)
+                for (int tx = 0; tx < P.ntx; tx++) {
+                    if (tcls[(size_t)ty * P.ntx + tx] != cls) continue;
+                    P.tile_of[(size_t)ty * P.ntx + tx] = (int)P.tile_x.size();
+                    P.tile_x.push_back(P.tx0 + tx); P.tile_y.push_back(P.ty0 + ty);
                 }
-            if (band) P.band_tiles.push_back(t);
+            if (cls == 0) P.n_wall_tiles = (int)P.tile_x.size();
         }
+        P.ntiles = (int)P.tile_x.size();
+        // tiles with a non-solid band cell (explosion, prolongation) and tiles with a
+        // non-solid active or ghost cell (the level kernel's work list)
+        std::vector<uint8_t> tband(P.ntiles, 0), twork(P.ntiles, 0);
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int t = 0; t < P.ntiles; t++) {
+            bool band = false, work = false;
+            for (int y = 0; y < LBM_TY; y++)
+                for (int x = 0; x < LBM_TX; x++) {
+                    long c = P.idx(P.tile_x[t] * LBM_TX + x, P.tile_y[t] * LBM_TY + y);
+                    if (c < 0 || P.solid[c]) continue;
+                    band = band || P.band[c];
+                    work = work || P.kind[c] == KIND_ACTIVE || P.kind[c] == KIND_GHOST;
+                }
+            tband[t] = band; twork[t] = work;
+        }
+        P.band_tiles.clear();
         P.work_tiles.clear();
         for (int t = 0; t < P.ntiles; t++) {
-            bool work = false;
-            for (int y = 0; y < LBM_TY && !work; y++)
-                for (int x = 0; x < LBM_TX && !work; x++) {
-                    long c = P.idx(P.tile_x[t] * LBM_TX + x, P.tile_y[t] * LBM_TY + y);
-                    work = c >= 0 && !P.solid[c] && (P.kind[c] == KIND_ACTIVE || P.kind[c] == KIND_GHOST);
-                }
-            if (work) P.work_tiles.push_back(t);
+            if (tband[t]) P.band_tiles.push_back(t);
+            if (twork[t]) P.work_tiles.push_back(t);
         }
         P.nbr.assign((size_t)P.ntiles * 9, -1);
         const bool wrap = (l == 0 && sp.periodic);

@@ -4,12 +4,27 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "layout.hpp"
 
 namespace lbmgrid {
+
+// allocator whose value-less construct leaves elements uninitialised: the large per-cell
+// tables are sized first and then filled in parallel, so that their pages are first
+// touched by the threads that fill them instead of being zeroed by one thread
+template <class T>
+struct NoInit : std::allocator<T> {
+    template <class U> struct rebind { using other = NoInit<U>; };
+    NoInit() = default;
+    template <class U> NoInit(const NoInit<U> &) noexcept {}
+    template <class U> void construct(U *p) noexcept { ::new ((void *)p) U; }
+    template <class U, class... A> void construct(U *p, A &&...a) { ::new ((void *)p) U(std::forward<A>(a)...); }
+};
+template <class T> using cellvec = std::vector<T, NoInit<T>>;
 
 struct Spec {
     int levels, nx0, ny0, layers;
@@ -25,11 +40,11 @@ struct Level {
     long long scale = 1;            // finest cells per cell edge: 2^(L-1-l)
     // dense build-time box (global level indices)
     int bi0 = 0, bj0 = 0, bnx = 0, bny = 0;
-    std::vector<uint8_t> kind;      // KIND_* over the box
-    std::vector<uint8_t> solid, band, bnode;
-    std::vector<uint16_t> coal, cut;
-    std::vector<double> dist;       // wall distance, level lattice units
-    std::vector<int> rec;           // wall record of a B node
+    cellvec<uint8_t> kind;          // KIND_* over the box
+    cellvec<uint8_t> solid, band, bnode;
+    cellvec<uint16_t> coal, cut;
+    cellvec<double> dist;           // wall distance, level lattice units
+    cellvec<int> rec;               // wall record of a B node
     // present-cell box
     int pi0 = 0, pj0 = 0, pnx = 0, pny = 0;
     // tiles

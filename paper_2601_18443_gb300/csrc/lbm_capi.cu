@@ -390,6 +390,8 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         H.flags.assign(ns, 0);
         std::vector<float> inv_d2(ns, 0.f);
         std::vector<int> rec(l == L - 1 ? ns : 1, -1);
+        // every slot is written by the thread of its tile
+#pragma omp parallel for schedule(static)
         for (int t = 0; t < G.ntiles; t++)
             for (int c2 = 0; c2 < LBM_TILE; c2++) {
                 long long i = (long long)G.tile_x[t] * LBM_TX + (c2 & 31), j = (long long)G.tile_y[t] * LBM_TY + (c2 >> 5);
