@@ -88,15 +88,16 @@ static bool segs_cross(IPt a, IPt b, IPt c, IPt d)
 struct SegTree {
     // node: bounding box, and a capsule (the chord from the range's first to its last vertex,
     // with a radius covering every endpoint) of the segments [lo, hi)
-    struct Node { double x0, y0, x1, y1, c0x, c0y, c1x, c1y, rad, ux, uy, il2; int lo, hi, left, right; };
+    struct Node { double x0, y0, x1, y1, c0x, c0y, c1x, c1y, rad, ux, uy, il2; int lo, hi, left, right, up; };
     std::vector<Node> nodes;
     std::vector<double> ax, ay, bx, by;   // finest lattice units
+    std::vector<int> leaf_of;             // leaf node holding each segment
     int root = -1;
 
     int make(int lo, int hi)
     {
         Node nd;
-        nd.lo = lo; nd.hi = hi; nd.left = nd.right = -1;
+        nd.lo = lo; nd.hi = hi; nd.left = nd.right = nd.up = -1;
         nd.x0 = nd.y0 = std::numeric_limits<double>::infinity();
         nd.x1 = nd.y1 = -std::numeric_limits<double>::infinity();
         for (int k = lo; k < hi; k++) {
@@ -122,6 +123,9 @@ struct SegTree {
             int mid = (lo + hi) / 2;
             int l = make(lo, mid), r = make(mid, hi);
             nodes[id].left = l; nodes[id].right = r;
+            nodes[l].up = id; nodes[r].up = id;
+        } else {
+            for (int k = lo; k < hi; k++) leaf_of[k] = id;
         }
         return id;
     }
@@ -159,6 +163,7 @@ struct SegTree {
             bx[k] = (double)g.v[g.sb[k]].x / FIXU; by[k] = (double)g.v[g.sb[k]].y / FIXU;
         }
         nodes.clear();
+        leaf_of.assign(n, -1);
         root = n ? make(0, (int)n) : -1;
     }
     // distance from p to segment k and the foot of the perpendicular
@@ -238,6 +243,47 @@ struct SegTree {
             }
         }
         return found ? std::sqrt(best2) : std::numeric_limits<double>::infinity();
+    }
+    // distance from p to the nearest segment, searched outwards from the leaf of segment
+    // `kstart` (the nearest segment of a neighbouring point): that leaf first, then the
+    // sibling of each of its ancestors, each subtree pruned by the best distance found so
+    // far.  Every segment is either evaluated or pruned by a valid lower bound, so the
+    // result is the smallest squared distance over all segments, as in nearest_dist.
+    double nearest_dist_from(double px, double py, int kstart, int &kfound) const
+    {
+        double best2 = std::numeric_limits<double>::infinity();
+        int node = leaf_of[kstart];
+        for (int k = nodes[node].lo; k < nodes[node].hi; k++) {
+            const double d2 = seg_dist2(k, px, py);
+            if (d2 <= best2) { best2 = d2; kfound = k; }
+        }
+        int stack[128];
+        double slb2[128];
+        while (nodes[node].up >= 0) {
+            const Node &pa = nodes[nodes[node].up];
+            const int sib = pa.left == node ? pa.right : pa.left;
+            node = nodes[node].up;
+            int sp = 0;
+            stack[sp] = sib; slb2[sp++] = node_lb2(nodes[sib], px, py);
+            while (sp) {
+                --sp;
+                if (slb2[sp] > best2) continue;
+                const Node &nd = nodes[stack[sp]];
+                if (nd.left < 0) {
+                    for (int k = nd.lo; k < nd.hi; k++) {
+                        const double d2 = seg_dist2(k, px, py);
+                        if (d2 <= best2) { best2 = d2; kfound = k; }
+                    }
+                } else {
+                    const double dl = node_lb2(nodes[nd.left], px, py), dr = node_lb2(nodes[nd.right], px, py);
+                    const int first = dl <= dr ? nd.left : nd.right, second = dl <= dr ? nd.right : nd.left;
+                    const double lf = std::min(dl, dr), ls = std::max(dl, dr);
+                    if (ls <= best2) { stack[sp] = second; slb2[sp++] = ls; }
+                    if (lf <= best2) { stack[sp] = first; slb2[sp++] = lf; }
+                }
+            }
+        }
+        return std::sqrt(best2);
     }
     double seg_dist2(int k, double px, double py) const
     {
@@ -612,8 +658,8 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
         Level &P = g.lv[l];
 #pragma omp parallel for schedule(dynamic, 4)
         for (int r = 0; r < P.bny; r++) {
-            // the nearest segment of the previous cell in the row bounds the search: the
-            // distance to that segment is at least the distance to the nearest one
+            // the search for a cell starts from the nearest segment of the previous cell in
+            // the row, whose leaf usually holds or neighbours the new nearest segment
             int kprev = -1;
             for (int q = 0; q < P.bnx; q++) {
                 size_t c = (size_t)r * P.bnx + q;
@@ -621,11 +667,9 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                 double dd = DCAP;
                 if (sp.solid_walls && !g.sa.empty()) {
                     double px = (P.bi0 + q + 0.5) * (double)P.scale, py = (P.bj0 + r + 0.5) * (double)P.scale;
-                    const double bound = kprev >= 0 ? std::sqrt(T.seg_dist2(kprev, px, py)) * (1.0 + 1e-9) + 1e-9
-                                                    : std::numeric_limits<double>::infinity();
-                    int kb;
-                    double d = T.nearest_dist(px, py, bound, kb);
-                    if (std::isinf(d)) d = T.nearest_dist(px, py, std::numeric_limits<double>::infinity(), kb);
+                    int kb = -1;
+                    const double d = kprev >= 0 ? T.nearest_dist_from(px, py, kprev, kb)
+                                                : T.nearest_dist(px, py, std::numeric_limits<double>::infinity(), kb);
                     kprev = kb;
                     dd = d / (double)P.scale;
                     if (dd > DCAP) dd = DCAP;
