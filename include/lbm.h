@@ -128,6 +128,15 @@ typedef struct {
 lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int *loop_offsets, int n_loops,
                              lbm_plan *out);
 
+/* Digest of the host-built grid, without a GPU: 64-bit FNV-1a over every per-cell level
+ * table (kind, solid, band, boundary node, coalescence and cut-link bits, wall distance,
+ * record index), the tile tables, the wall records and the surface-segment tables, built
+ * exactly as lbm_set_geometry builds them.  The builder runs on host threads; the digest
+ * of an input does not depend on their number.  *digest (host) is set to 0 on error.
+ * Errors: as lbm_plan_geometry (LBM_ERR_INVALID_ARG, LBM_ERR_GEOMETRY). */
+lbm_status lbm_grid_digest(const lbm_config *cfg, const double *xy, const int *loop_offsets, int n_loops,
+                           unsigned long long *digest);
+
 /* Prescribed wall slip velocity per loop for wall_model 2 (lattice units): uw_xy holds
  * 2 * n_loops doubles.  Errors: LBM_ERR_INVALID_ARG, LBM_ERR_NO_GEOMETRY. */
 lbm_status lbm_set_wall_slip(lbm_solver *s, const double *uw_xy, int n_loops);

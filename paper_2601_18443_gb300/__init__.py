@@ -96,6 +96,7 @@ def library():
         "lbm_set_geometry": ([vp, dp, ip, C.c_int], C.c_int),
         "lbm_set_wall_slip": ([vp, dp, C.c_int], C.c_int),
         "lbm_plan_geometry": ([C.POINTER(lbm_config), dp, ip, C.c_int, C.POINTER(lbm_plan)], C.c_int),
+        "lbm_grid_digest": ([C.POINTER(lbm_config), dp, ip, C.c_int, C.POINTER(C.c_ulonglong)], C.c_int),
         "lbm_step": ([vp, C.c_int], C.c_int),
         "lbm_step_async": ([vp, C.c_int], C.c_int),
         "lbm_synchronize": ([vp], C.c_int),
@@ -162,6 +163,17 @@ def plan(cfg: dict, loops) -> dict:
     L = out.levels
     return dict(levels=L, cells_active=list(out.cells_active[:L]), node_updates_per_step=out.node_updates_per_step,
                 wall_records=out.wall_records, device_bytes=out.device_bytes)
+
+
+def grid_digest(cfg: dict, loops) -> int:
+    """lbm_grid_digest: 64-bit digest of the host-built grid tables, without a GPU."""
+    c = _config_struct(cfg)
+    xy, off = _loops_arrays(loops)
+    out = C.c_ulonglong(0)
+    rc = library().lbm_grid_digest(C.byref(c), _dp(xy), _ip(off), len(loops), C.byref(out))
+    if rc != 0:
+        raise LBMError(rc, "lbm_grid_digest")
+    return int(out.value)
 
 
 class Solver:

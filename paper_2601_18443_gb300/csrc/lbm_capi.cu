@@ -320,6 +320,25 @@ static lbm_status check_status(lbm_solver *s)
     return LBM_OK;
 }
 
+// 64-bit FNV-1a over raw bytes (grid digest)
+namespace {
+struct Fnv {
+    unsigned long long h = 1469598103934665603ull;
+    void bytes(const void *p, size_t n)
+    {
+        const unsigned char *c = (const unsigned char *)p;
+        for (size_t i = 0; i < n; i++) { h ^= c[i]; h *= 1099511628211ull; }
+    }
+    template <class T> void val(const T &v) { bytes(&v, sizeof v); }
+    template <class V> void vec(const V &v)
+    {
+        const size_t n = v.size();
+        val(n);
+        if (n) bytes(v.data(), n * sizeof(v[0]));
+    }
+};
+}  // namespace
+
 // ---------------------------------------------------------------- API
 extern "C" {
 
@@ -585,6 +604,41 @@ lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int 
     }
     delete s;
     return st;
+}
+
+
+lbm_status lbm_grid_digest(const lbm_config *cfg, const double *xy, const int *loop_offsets, int n_loops,
+                           unsigned long long *digest)
+{
+    if (!digest) return LBM_ERR_INVALID_ARG;
+    *digest = 0;
+    if (!cfg || !config_ok(cfg) || n_loops < 0 || (n_loops > 0 && (!xy || !loop_offsets))) return LBM_ERR_INVALID_ARG;
+    const lbm_config &c = *cfg;
+    lbmgrid::Spec sp{c.levels, c.nx0, c.ny0, c.layers, c.x0, c.y0, c.h0, c.d_wr, c.d_wv, c.periodic, c.solid_walls, c.wall_model};
+    lbmgrid::Grid g;
+    std::string msg;
+    const int rc = lbmgrid::build(sp, xy, loop_offsets, n_loops, g, msg);
+    if (rc != 0) return (lbm_status)rc;
+    Fnv f;
+    for (const lbmgrid::Level &G : g.lv) {
+        const int box[15] = {G.l, G.bi0, G.bj0, G.bnx, G.bny, G.pi0, G.pj0, G.pnx, G.pny,
+                             G.tx0, G.ty0, G.ntx, G.nty, G.ntiles, G.n_wall_tiles};
+        f.bytes(box, sizeof box);
+        f.val(G.scale);
+        f.vec(G.kind); f.vec(G.solid); f.vec(G.band); f.vec(G.bnode); f.vec(G.coal); f.vec(G.cut);
+        f.vec(G.dist); f.vec(G.rec);
+        f.vec(G.tile_of); f.vec(G.tile_x); f.vec(G.tile_y); f.vec(G.nbr); f.vec(G.child); f.vec(G.parent);
+        f.vec(G.band_tiles); f.vec(G.work_tiles);
+    }
+    for (const lbmgrid::Record &r : g.recs) {
+        f.val(r.i); f.val(r.j); f.val(r.seg); f.val(r.loop);
+        f.bytes(r.iw, sizeof r.iw); f.bytes(r.n, sizeof r.n); f.val(r.dwb); f.bytes(r.r, sizeof r.r);
+        f.val(r.ns); f.bytes(r.si, sizeof(int) * r.ns); f.bytes(r.sj, sizeof(int) * r.ns); f.bytes(r.q, sizeof r.q);
+    }
+    f.vec(g.seg_b1); f.vec(g.seg_b2); f.vec(g.seg_w1); f.vec(g.seg_w2); f.val(g.n_cut);
+    f.vec(g.sa); f.vec(g.sb); f.vec(g.sloop); f.vec(g.loop_ccw);
+    *digest = f.h;
+    return LBM_OK;
 }
 
 lbm_status lbm_set_wall_slip(lbm_solver *s, const double *uw, int n_loops)

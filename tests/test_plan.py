@@ -66,3 +66,45 @@ def test_plan_rejects_crossing_loops_and_accepts_touching_ones():
     # loops that only touch along an edge, and separate loops, are valid geometry
     pkg.plan(cfg, [W.rectangle(20.0, 20.0, 30.0, 30.0), W.rectangle(30.0, 22.0, 38.0, 28.0)])
     pkg.plan(cfg, [W.rectangle(18.0, 18.0, 26.0, 26.0), W.rectangle(32.0, 32.0, 42.0, 42.0)])
+
+
+_DIGEST_SCRIPT = r"""
+import sys
+import paper_2601_18443_gb300 as pkg
+from paper_2601_18443_gb300 import workloads as W
+cases = [W.naca0012_small(levels=6), W.highlift_3element(levels=4, layers=16, box=(4.0, 2.0), h0=1.0 / 64.0)]
+cases += [W.polar_case(r) for r in W.polar_requests(3)]
+cases.append((W.base_config(levels=2, nx0=64, ny0=64, h0=1.0, layers=4),
+              [W.rectangle(10, 10, 15, 15), W.rectangle(30.0, 30.0, 44.0, 38.0)]))
+print(" ".join(str(pkg.grid_digest(c, l)) for c, l in cases))
+"""
+
+
+def test_grid_build_does_not_depend_on_the_host_thread_count():
+    # the builder's parallel passes (table fill, nesting checks, cut links, wall records,
+    # tiles, wall distance) must give the same tables byte for byte with 1, 3 or 8 threads
+    import os
+    import subprocess
+    import sys
+    pkg.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for nt in ("1", "3", "8"):
+        env = dict(os.environ, OMP_NUM_THREADS=nt, PYTHONPATH=root)
+        r = subprocess.run([sys.executable, "-c", _DIGEST_SCRIPT], capture_output=True, text=True, env=env,
+                           cwd=root, timeout=300)
+        assert r.returncode == 0, r.stderr
+        outs.append(r.stdout.split())
+    assert len(outs[0]) == 6 and all(int(d) != 0 for d in outs[0])
+    assert outs[0] == outs[1] == outs[2]
+    # the digest sees a change of the input
+    cfg, loops = W.naca0012_small(levels=3)
+    assert pkg.grid_digest(cfg, loops) != pkg.grid_digest(cfg, [loops[0] + 1e-3])
+
+
+def test_grid_digest_reports_geometry_errors():
+    pkg.build()
+    cfg = W.base_config(levels=2, nx0=64, ny0=64, h0=1.0, layers=4)
+    with pytest.raises(pkg.LBMError) as e:
+        pkg.grid_digest(cfg, [W.rectangle(20.0, 20.0, 30.0, 30.0), W.rectangle(25.0, 25.0, 35.0, 35.0)])
+    assert e.value.code == -5
