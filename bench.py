@@ -276,8 +276,11 @@ def gpu_arm(args, rank, world, dist):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = pkg.Solver(cfg, stream=stream)
+        ta = time.perf_counter()
         s2.set_geometry(loops)
+        tb = time.perf_counter()
         s2.step(K)
+        tc = time.perf_counter()
         l2 = s2.get_loads()
         t1 = time.perf_counter()
         dev_b = s2.info()["device_bytes"]
@@ -288,7 +291,13 @@ def gpu_arm(args, rank, world, dist):
                "d2h_bytes_per_step": int((56 + 16 * n_seg) / K),
                "what": f"lbm_create + lbm_set_geometry (host grid build, table upload) + lbm_step({K}) + "
                        f"lbm_get_loads, wall clock; h2d counts the polyline plus the uploaded tables "
-                       f"(upper bound: device bytes held) spread over the K steps"}
+                       f"(upper bound: device bytes held) spread over the K steps",
+               "phases_s": {"create": round(ta - t0, 4), "set_geometry": round(tb - ta, 4),
+                            "steps": round(tc - tb, 4), "loads": round(t1 - tc, 4)}}
+        # the host-only part of set_geometry (grid build and table fill), timed apart
+        tp = time.perf_counter()
+        pkg.plan(cfg, loops)
+        e2e["host_grid_build_s"] = round(time.perf_counter() - tp, 4)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
