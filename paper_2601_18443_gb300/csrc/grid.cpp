@@ -94,10 +94,15 @@ struct SegTree {
     std::vector<int> leaf_of;             // leaf node holding each segment
     int root = -1;
 
-    int make(int lo, int hi)
+    // nodes of the subtree over n segments (a range splits in halves while it holds more
+    // than 8); the tree is stored in pre-order, so a node's right child follows its left
+    // subtree and every subtree can be built independently
+    static int tree_count(int n) { return n <= 8 ? 1 : 1 + tree_count(n / 2) + tree_count(n - n / 2); }
+
+    void make(int id, int lo, int hi, int up)
     {
         Node nd;
-        nd.lo = lo; nd.hi = hi; nd.left = nd.right = nd.up = -1;
+        nd.lo = lo; nd.hi = hi; nd.left = nd.right = -1; nd.up = up;
         nd.x0 = nd.y0 = std::numeric_limits<double>::infinity();
         nd.x1 = nd.y1 = -std::numeric_limits<double>::infinity();
         for (int k = lo; k < hi; k++) {
@@ -117,17 +122,25 @@ struct SegTree {
         nd.ux = nd.c1x - nd.c0x; nd.uy = nd.c1y - nd.c0y;
         const double l2 = nd.ux * nd.ux + nd.uy * nd.uy;
         nd.il2 = l2 > 0 ? 1.0 / l2 : 0.0;
-        int id = (int)nodes.size();
-        nodes.push_back(nd);
         if (hi - lo > 8) {
-            int mid = (lo + hi) / 2;
-            int l = make(lo, mid), r = make(mid, hi);
-            nodes[id].left = l; nodes[id].right = r;
-            nodes[l].up = id; nodes[r].up = id;
+            const int mid = (lo + hi) / 2;
+            nd.left = id + 1;
+            nd.right = id + 1 + tree_count(mid - lo);
+            nodes[id] = nd;
+            if (hi - lo > 8192) {
+#pragma omp task
+                make(nd.left, lo, mid, id);
+#pragma omp task
+                make(nd.right, mid, hi, id);
+#pragma omp taskwait
+            } else {
+                make(nd.left, lo, mid, id);
+                make(nd.right, mid, hi, id);
+            }
         } else {
+            nodes[id] = nd;
             for (int k = lo; k < hi; k++) leaf_of[k] = id;
         }
-        return id;
     }
     static double pt_seg2(double ax_, double ay_, double bx_, double by_, double px, double py)
     {
@@ -162,9 +175,14 @@ struct SegTree {
             ax[k] = (double)g.v[g.sa[k]].x / FIXU; ay[k] = (double)g.v[g.sa[k]].y / FIXU;
             bx[k] = (double)g.v[g.sb[k]].x / FIXU; by[k] = (double)g.v[g.sb[k]].y / FIXU;
         }
-        nodes.clear();
         leaf_of.assign(n, -1);
-        root = n ? make(0, (int)n) : -1;
+        nodes.assign(n ? tree_count((int)n) : 0, Node());
+        root = n ? 0 : -1;
+        if (n) {
+#pragma omp parallel
+#pragma omp single
+            make(0, 0, (int)n, -1);
+        }
     }
     // distance from p to segment k and the foot of the perpendicular
     double seg_dist(int k, double px, double py, double &qx, double &qy) const
@@ -382,23 +400,48 @@ static void paint_solid(const Grid &g, Level &Lv)
 {
     const long long hh = Lv.scale * FIXU / 2;     // half cell
     const size_t nseg = g.sa.size();
-    // rows crossed by each segment (half-open rule ymin <= Y < ymax)
-    std::vector<std::vector<int>> rows(Lv.bny);
-    for (size_t k = 0; k < nseg; k++) {
+    // rows crossed by each segment (half-open rule ymin <= Y < ymax), as lists per row
+    // (counted, then filled; the order inside a row does not matter, the parity is a XOR)
+    auto row_span = [&](long k, long long &jl, long long &jh) {
         IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
-        if (a.y == b.y) continue;
+        jl = jh = 0;
+        if (a.y == b.y) return;
         long long ymin = std::min(a.y, b.y), ymax = std::max(a.y, b.y);
-        long long jl = cdiv((i128)ymin - hh, 2 * (i128)hh), jh = cdiv((i128)ymax - hh, 2 * (i128)hh);
+        jl = cdiv((i128)ymin - hh, 2 * (i128)hh); jh = cdiv((i128)ymax - hh, 2 * (i128)hh);
         jl = std::max<long long>(jl, Lv.bj0);
         jh = std::min<long long>(jh, (long long)Lv.bj0 + Lv.bny);
-        for (long long j = jl; j < jh; j++) rows[j - Lv.bj0].push_back((int)k);
+    };
+    std::vector<long> row_off(Lv.bny + 1, 0);
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < (long)nseg; k++) {
+        long long jl, jh;
+        row_span(k, jl, jh);
+        for (long long j = jl; j < jh; j++) {
+#pragma omp atomic
+            row_off[j - Lv.bj0 + 1]++;
+        }
+    }
+    for (int r = 0; r < Lv.bny; r++) row_off[r + 1] += row_off[r];
+    std::vector<int> row_seg(row_off[Lv.bny]);
+    std::vector<long> fill(row_off.begin(), row_off.end() - 1);
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < (long)nseg; k++) {
+        long long jl, jh;
+        row_span(k, jl, jh);
+        for (long long j = jl; j < jh; j++) {
+            long at;
+#pragma omp atomic capture
+            at = fill[j - Lv.bj0]++;
+            row_seg[at] = (int)k;
+        }
     }
 #pragma omp parallel for schedule(dynamic, 8)
     for (int r = 0; r < Lv.bny; r++) {
         long long j = Lv.bj0 + r;
         long long Y = (2 * j + 1) * hh;
         std::vector<uint8_t> diff(Lv.bnx + 1, 0);
-        for (int k : rows[r]) {
+        for (long m = row_off[r]; m < row_off[r + 1]; m++) {
+            const int k = row_seg[m];
             IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
             if (a.y > b.y) std::swap(a, b);
             i128 den = (i128)(b.y - a.y);
@@ -417,14 +460,18 @@ static void paint_solid(const Grid &g, Level &Lv)
         }
     }
     // centres lying exactly on a segment are solid
-    for (size_t k = 0; k < nseg; k++) {
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < (long)nseg; k++) {
         IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
         long long il = cdiv((i128)std::min(a.x, b.x) - hh, 2 * (i128)hh), ih = fdiv((i128)std::max(a.x, b.x) - hh, 2 * (i128)hh);
         long long jl = cdiv((i128)std::min(a.y, b.y) - hh, 2 * (i128)hh), jh = fdiv((i128)std::max(a.y, b.y) - hh, 2 * (i128)hh);
         for (long long j = jl; j <= jh; j++)
             for (long long i = il; i <= ih; i++) {
                 long c = Lv.idx(i, j);
-                if (c >= 0 && on_seg(a, b, centre(Lv, i, j))) Lv.solid[c] = 1;
+                if (c >= 0 && on_seg(a, b, centre(Lv, i, j))) {
+#pragma omp atomic write
+                    Lv.solid[c] = 1;
+                }
             }
     }
 #pragma omp parallel for schedule(static)
@@ -504,8 +551,9 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
     for (int l = L - 2; l >= 1; l--) R[l] = R[l + 1] + (long long)sp.layers * g.lv[l].scale * FIXU;
 
     // runs of consecutive segments whose joint bounding box stays within the smallest band
-    // radius: one pass over a run's candidate cells tests all of its segments
+    // radius, and each run's bounding box
     std::vector<int> run_start;
+    std::vector<long long> run_box;     // x0, x1, y0, y1 per run
     {
         const long long lim = R[L - 1];
         long long x0 = 0, x1 = 0, y0 = 0, y1 = 0;
@@ -515,30 +563,86 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
             const long long ay = std::min(a.y, b.y), by = std::max(a.y, b.y);
             if (run_start.empty() || std::max(bx, x1) - std::min(ax, x0) > lim || std::max(by, y1) - std::min(ay, y0) > lim ||
                 k - run_start.back() >= 64) {
+                if (!run_start.empty()) run_box.insert(run_box.end(), {x0, x1, y0, y1});
                 run_start.push_back(k);
                 x0 = ax; x1 = bx; y0 = ay; y1 = by;
             } else {
                 x0 = std::min(x0, ax); x1 = std::max(x1, bx); y0 = std::min(y0, ay); y1 = std::max(y1, by);
             }
         }
+        if (!run_start.empty()) run_box.insert(run_box.end(), {x0, x1, y0, y1});
         run_start.push_back((int)g.sa.size());
     }
     const long nruns = (long)run_start.size() - 1;
+    // each run's capsule, in fixed units: the chord from its first to its last vertex and a
+    // radius holding every vertex (plus a margin far above the rounding of these doubles);
+    // every segment of the run lies in the capsule.  A run whose segments join end to end
+    // also comes within `rad` of every chord point (the chain runs from one chord end to
+    // the other), so a centre within R - rad of the chord is within R of a segment.
+    std::vector<double> run_cap(6 * std::max(nruns, 0L));
+    std::vector<uint8_t> run_chain(std::max(nruns, 0L));
+    for (long ru = 0; ru < nruns; ru++) {
+        const int k0 = run_start[ru], k1 = run_start[ru + 1];
+        const IPt a = g.v[g.sa[k0]], b = g.v[g.sb[k1 - 1]];
+        double *cp = &run_cap[6 * ru];
+        cp[0] = (double)a.x; cp[1] = (double)a.y;
+        cp[2] = (double)(b.x - a.x); cp[3] = (double)(b.y - a.y);
+        const double l2 = cp[2] * cp[2] + cp[3] * cp[3];
+        cp[4] = l2 > 0 ? 1.0 / l2 : 0.0;
+        double r2 = 0.0;
+        bool chain = true;
+        for (int k = k0; k < k1; k++) {
+            const IPt e0 = g.v[g.sa[k]], e1 = g.v[g.sb[k]];
+            for (const IPt &e : {e0, e1}) {
+                double t = (((double)e.x - cp[0]) * cp[2] + ((double)e.y - cp[1]) * cp[3]) * cp[4];
+                t = t < 0 ? 0 : (t > 1 ? 1 : t);
+                const double qx = cp[0] + t * cp[2] - (double)e.x, qy = cp[1] + t * cp[3] - (double)e.y;
+                r2 = std::max(r2, qx * qx + qy * qy);
+            }
+            if (k + 1 < k1) {
+                const IPt n0 = g.v[g.sa[k + 1]];
+                chain = chain && n0.x == e1.x && n0.y == e1.y;
+            }
+        }
+        cp[5] = std::sqrt(r2) + 1.0;
+        run_chain[ru] = chain;
+    }
 
     for (int l = 1; l < L; l++) {
         Level &P = g.lv[l - 1];
         const long long hh = P.scale * FIXU / 2;
-        // refinement: candidate cells around each run of segments, exact distance test
-        // (runs in parallel; a cell found near any segment is marked, marks only go 0 -> 1)
+        // refinement: a cell is covered iff its centre lies within R_l of a segment (exact
+        // test).  Consecutive runs are grouped while the group's bounding box stays within
+        // R_l / 2 (and at most 1/128 of the runs, to leave work for every thread), so that a
+        // group's candidate cells (its box grown by R_l) are enumerated once; each candidate
+        // is tested against the runs of the group whose box lies within R_l.  Groups run in
+        // parallel; marks only go 0 -> 1.
+        std::vector<long> group_start;
+        {
+            const long long glim = std::max(R[l] / 2, R[L - 1]);
+            const long gmax = std::max(1L, nruns / 128);
+            long long x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+            for (long ru = 0; ru < nruns; ru++) {
+                const long long *b = &run_box[4 * ru];
+                if (group_start.empty() || std::max(b[1], x1) - std::min(b[0], x0) > glim ||
+                    std::max(b[3], y1) - std::min(b[2], y0) > glim || ru - group_start.back() >= gmax) {
+                    group_start.push_back(ru);
+                    x0 = b[0]; x1 = b[1]; y0 = b[2]; y1 = b[3];
+                } else {
+                    x0 = std::min(x0, b[0]); x1 = std::max(x1, b[1]); y0 = std::min(y0, b[2]); y1 = std::max(y1, b[3]);
+                }
+            }
+            group_start.push_back(nruns);
+        }
+        const long ngroups = (long)group_start.size() - 1;
         std::vector<uint8_t> near(P.kind.size(), 0);
-#pragma omp parallel for schedule(dynamic, 4)
-        for (long ru = 0; ru < nruns; ru++) {
-            const int k0 = run_start[ru], k1 = run_start[ru + 1];
+#pragma omp parallel for schedule(dynamic, 1)
+        for (long gr = 0; gr < ngroups; gr++) {
+            const long r0 = group_start[gr], r1 = group_start[gr + 1];
             long long x0 = LLONG_MAX, x1 = LLONG_MIN, y0 = LLONG_MAX, y1 = LLONG_MIN;
-            for (int k = k0; k < k1; k++) {
-                IPt a = g.v[g.sa[k]], b = g.v[g.sb[k]];
-                x0 = std::min({x0, a.x, b.x}); x1 = std::max({x1, a.x, b.x});
-                y0 = std::min({y0, a.y, b.y}); y1 = std::max({y1, a.y, b.y});
+            for (long ru = r0; ru < r1; ru++) {
+                const long long *b = &run_box[4 * ru];
+                x0 = std::min(x0, b[0]); x1 = std::max(x1, b[1]); y0 = std::min(y0, b[2]); y1 = std::max(y1, b[3]);
             }
             long long il = cdiv((i128)x0 - R[l] - hh, 2 * (i128)hh);
             long long ih = fdiv((i128)x1 + R[l] - hh, 2 * (i128)hh);
@@ -555,13 +659,27 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
                     seen = near[c];
                     if (seen || P.kind[c] != KIND_ACTIVE) continue;
                     const IPt pc = centre(P, i, j);
-                    // every segment of the run lies in its bounding box: a centre farther
-                    // than R from the box is farther than R from all of them
-                    const i128 dx = pc.x < x0 ? (i128)x0 - pc.x : (pc.x > x1 ? (i128)pc.x - x1 : 0);
-                    const i128 dy = pc.y < y0 ? (i128)y0 - pc.y : (pc.y > y1 ? (i128)pc.y - y1 : 0);
-                    if (dx * dx + dy * dy > (i128)R[l] * R[l]) continue;
+                    const double Rd = (double)R[l];
                     bool hit = false;
-                    for (int k = k0; k < k1 && !hit; k++) hit = within_r(g.v[g.sa[k]], g.v[g.sb[k]], pc, R[l]);
+                    for (long ru = r0; ru < r1 && !hit; ru++) {
+                        // every segment of a run lies in its bounding box: a centre farther
+                        // than R from the box is farther than R from all of them
+                        const long long *b = &run_box[4 * ru];
+                        const i128 dx = pc.x < b[0] ? (i128)b[0] - pc.x : (pc.x > b[1] ? (i128)pc.x - b[1] : 0);
+                        const i128 dy = pc.y < b[2] ? (i128)b[2] - pc.y : (pc.y > b[3] ? (i128)pc.y - b[3] : 0);
+                        if (dx * dx + dy * dy > (i128)R[l] * R[l]) continue;
+                        // the capsule settles the run unless the centre lies within its
+                        // radius (plus a margin) of the distance R; the exact test does the rest
+                        const double *cp = &run_cap[6 * ru];
+                        double t = (((double)pc.x - cp[0]) * cp[2] + ((double)pc.y - cp[1]) * cp[3]) * cp[4];
+                        t = t < 0 ? 0 : (t > 1 ? 1 : t);
+                        const double qx = cp[0] + t * cp[2] - (double)pc.x, qy = cp[1] + t * cp[3] - (double)pc.y;
+                        const double dc = std::sqrt(qx * qx + qy * qy);
+                        if (dc - cp[5] > Rd + 1.0) continue;
+                        if (run_chain[ru] && dc + cp[5] < Rd - 1.0) { hit = true; break; }
+                        for (int k = run_start[ru]; k < run_start[ru + 1] && !hit; k++)
+                            hit = within_r(g.v[g.sa[k]], g.v[g.sb[k]], pc, R[l]);
+                    }
                     if (!hit) continue;
 #pragma omp atomic write
                     near[c] = 1;
@@ -612,6 +730,7 @@ int build(const Spec &sp, const double *xy, const int *loop_off, int n_loops, Gr
     // c - c_d, c - (c_dx, 0) or c - (0, c_dy) is covered
     for (int l = 0; l < L - 1; l++) {
         Level &P = g.lv[l];
+#pragma omp parallel for schedule(static)
         for (int r = 0; r < P.bny; r++)
             for (int q = 0; q < P.bnx; q++) {
                 size_t c = (size_t)r * P.bnx + q;
