@@ -594,7 +594,8 @@ lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int 
         for (int l = 0; l < s->L; l++) {
             const lbmgrid::Level &G = s->g.lv[l];
             long long act = 0;
-            for (size_t b = 0; b < G.kind.size(); b++)
+#pragma omp parallel for schedule(static) reduction(+ : act)
+            for (long b = 0; b < (long)G.kind.size(); b++)
                 if (G.kind[b] == KIND_ACTIVE && !G.solid[b]) act++;
             out->cells_active[l] = act;
             nu += act << l;
