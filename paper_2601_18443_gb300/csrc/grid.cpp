@@ -313,12 +313,6 @@ struct SegTree {
         const double qx = ax[k] + t * dx, qy = ay[k] + t * dy;
         return (px - qx) * (px - qx) + (py - qy) * (py - qy);
     }
-    static double box_dist2(const Node &nd, double px, double py)
-    {
-        double dx = std::max(0.0, std::max(nd.x0 - px, px - nd.x1));
-        double dy = std::max(0.0, std::max(nd.y0 - py, py - nd.y1));
-        return dx * dx + dy * dy;
-    }
     void overlapping(double x0, double y0, double x1, double y1, std::vector<int> &out) const
     {
         out.clear();
