@@ -100,6 +100,15 @@ typedef struct {
  * beyond creating the stream.  Errors: LBM_ERR_INVALID_ARG for a bad spec, LBM_ERR_CUDA. */
 lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out);
 
+/* Create a host-only handle: no CUDA call is ever made on it (it runs on machines
+ * without a GPU).  lbm_set_geometry builds the grid tables on the host exactly as on a
+ * device handle and allocates nothing on a device.  The host-table queries work:
+ * lbm_get_level_box, lbm_get_fields with only the mask requested (all field pointers
+ * NULL), lbm_get_wall_distance, lbm_get_cut_links, lbm_get_wall_records.  Every other
+ * call returns LBM_ERR_NO_GEOMETRY.  cuda_stream and the allocator hooks of cfg are
+ * ignored.  Release with lbm_destroy.  Errors: LBM_ERR_INVALID_ARG, LBM_ERR_OOM. */
+lbm_status lbm_create_host(const lbm_config *cfg, lbm_solver **out);
+
 /* Build the multilevel grid, cut links and wall records from closed wall polylines
  * (Sec 2.1 pre-processor, Sec 2.3 preprocessing), upload them and initialise the state
  * to the equilibrium of rho = 1, u = (U, 0), chi = chi_inf.  xy: 2 * n_points doubles
@@ -153,13 +162,15 @@ lbm_status lbm_step_async(lbm_solver *s, int n_coarse_steps);
 /* Wait for enqueued work and check the status word (as lbm_step). */
 lbm_status lbm_synchronize(lbm_solver *s);
 
-/* Present-cell box of a level: cells i in [i0, i0 + nx), j in [j0, j0 + ny). */
+/* Present-cell box of a level: cells i in [i0, i0 + nx), j in [j0, j0 + ny).  Works on
+ * host-only handles. */
 lbm_status lbm_get_level_box(lbm_solver *s, int level, int *i0, int *j0, int *nx, int *ny);
 
 /* Copy a level's macroscopic fields to the host (any pointer may be NULL).  cap is the
  * element capacity of each array (>= nx * ny).  rho, ux, uy in lattice units; nu_tilde_ratio
  * is nu_tilde / nu (chi).  Cells without values hold NaN.  mask: 0 absent, 1 active fluid,
- * 2 boundary node B, 3 covered, 4 ghost, 5 solid. */
+ * 2 boundary node B, 3 covered, 4 ghost, 5 solid.  On a host-only handle only the mask
+ * may be requested (LBM_ERR_NO_GEOMETRY otherwise). */
 lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, double *uy,
                           double *nu_tilde_ratio, unsigned char *mask, int cap);
 
@@ -187,12 +198,14 @@ lbm_status lbm_get_loads(lbm_solver *s, lbm_loads *out, double *cp_seg, double *
  * (j, i)): ij[2r]; geo[9r] = IW x, IW y, n x, n y, d_WB, R x, R y, loop, segment;
  * nstencil[r] = reference-stencil size.  Wall state (wall function on the current
  * state): st[8r] = rho_W, u_W x, u_W y, u_tau, chi_B, t x, t y, |u_Rt|.  Any pointer
- * may be NULL to query the count. */
+ * may be NULL to query the count.  Cut links and wall records also work on host-only
+ * handles; the wall state needs the device state. */
 lbm_status lbm_get_cut_links(lbm_solver *s, int *ij_dir, double *q, int cap, int *n);
 lbm_status lbm_get_wall_records(lbm_solver *s, int *ij, double *geo, int *nstencil, int cap, int *n);
 lbm_status lbm_get_wall_state(lbm_solver *s, double *st, int cap, int *n);
 
-/* Wall distance of the active fluid cells of a level (level lattice units, NaN elsewhere). */
+/* Wall distance of the active fluid cells of a level (level lattice units, NaN elsewhere).
+ * Works on host-only handles. */
 lbm_status lbm_get_wall_distance(lbm_solver *s, int level, double *d, int cap);
 
 /* Sizes, counts and the algorithmic bytes per node update. */

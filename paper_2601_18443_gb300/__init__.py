@@ -93,6 +93,7 @@ def library():
     vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
     sig = {
         "lbm_create": ([C.POINTER(lbm_config), C.POINTER(vp)], C.c_int),
+        "lbm_create_host": ([C.POINTER(lbm_config), C.POINTER(vp)], C.c_int),
         "lbm_set_geometry": ([vp, dp, ip, C.c_int], C.c_int),
         "lbm_set_wall_slip": ([vp, dp, C.c_int], C.c_int),
         "lbm_plan_geometry": ([C.POINTER(lbm_config), dp, ip, C.c_int, C.POINTER(lbm_plan)], C.c_int),
@@ -177,9 +178,13 @@ def grid_digest(cfg: dict, loops) -> int:
 
 
 class Solver:
-    """One LBM-RANS solve on the current CUDA device (see include/lbm.h)."""
+    """One LBM-RANS solve on the current CUDA device (see include/lbm.h).
 
-    def __init__(self, cfg: dict, stream=None, torch_allocator: bool = False):
+    host_only=True gives a handle without device state (lbm_create_host): it builds the
+    grid tables on the host and answers the table queries (level_box, mask,
+    wall_distance, cut_links, wall_records) on machines without a GPU."""
+
+    def __init__(self, cfg: dict, stream=None, torch_allocator: bool = False, host_only: bool = False):
         self._lib = library()
         c = lbm_config()
         for name, _ in lbm_config._fields_:
@@ -206,7 +211,8 @@ class Solver:
             self._keep += [a, f, blocks]
             c.dev_alloc, c.dev_free = a, f
         h = C.c_void_p()
-        rc = self._lib.lbm_create(C.byref(c), C.byref(h))
+        create = self._lib.lbm_create_host if host_only else self._lib.lbm_create
+        rc = create(C.byref(c), C.byref(h))
         if rc != 0:
             raise LBMError(rc, "lbm_create rejected the configuration")
         self._h = h
@@ -254,6 +260,14 @@ class Solver:
         v = [C.c_int() for _ in range(4)]
         self._check(self._lib.lbm_get_level_box(self._h, level, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def mask(self, level):
+        """Cell codes of a level over its box (also on host-only handles)."""
+        i0, j0, nx, ny = self.level_box(level)
+        mask = np.zeros((ny, nx), dtype=np.uint8)
+        self._check(self._lib.lbm_get_fields(self._h, level, None, None, None, None,
+                                             mask.ctypes.data_as(C.c_void_p), nx * ny))
+        return mask
 
     def get_fields(self, level):
         i0, j0, nx, ny = self.level_box(level)

@@ -93,7 +93,8 @@ struct lbm_solver {
     int device = 0;
     int L = 0;
     double U = 0;
-    bool geometry = false;
+    bool geometry = false;         // device state built (steps, fields, loads)
+    bool grid_ready = false;       // host grid tables built (also on host-only handles)
     lbmgrid::Grid g;
     HostLevelDev lv[LBM_MAXL];
     RecView rec;
@@ -378,6 +379,24 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
     return LBM_OK;
 }
 
+lbm_status lbm_create_host(const lbm_config *cfg, lbm_solver **out)
+{
+    if (!cfg || !out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!config_ok(cfg)) return LBM_ERR_INVALID_ARG;
+    lbm_solver *s = new (std::nothrow) lbm_solver();
+    if (!s) return LBM_ERR_OOM;
+    s->cfg = *cfg;
+    s->cfg.cuda_stream = nullptr;
+    s->cfg.dev_alloc = nullptr;
+    s->cfg.dev_free = nullptr;
+    s->L = cfg->levels;
+    s->U = cfg->Ma * std::sqrt(1.0 / 3.0);
+    s->planning = true;
+    *out = s;
+    return LBM_OK;
+}
+
 void lbm_destroy(lbm_solver *s)
 {
     if (!s) return;
@@ -393,6 +412,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
 {
     if (!s || n_loops < 0 || (n_loops > 0 && (!xy || !loop_off))) return fail(s, LBM_ERR_INVALID_ARG, "bad geometry arguments");
     free_all(s);
+    s->grid_ready = false;
     const lbm_config &c = s->cfg;
     lbmgrid::Spec sp{c.levels, c.nx0, c.ny0, c.layers, c.x0, c.y0, c.h0, c.d_wr, c.d_wv, c.periodic, c.solid_walls, c.wall_model};
     std::string msg;
@@ -542,7 +562,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     s->d_status = (int *)dalloc(s, 16);
     s->d_acc = (double *)dalloc(s, 8 * sizeof(double));
     if (!s->d_status || !s->d_acc) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
-    if (s->planning) return LBM_OK;
+    if (s->planning) { s->grid_ready = true; return LBM_OK; }
     CK(cudaMemsetAsync(s->d_status, 0, 16, s->stream));
     // constants and initial state: equilibrium of rho = 1, u = (U, 0), chi = chi_inf
     s->k.level0_edges = !c.periodic;
@@ -570,6 +590,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     s->have_cl = false;
     s->n_loops = n_loops;
     s->geometry = true;
+    s->grid_ready = true;
     return LBM_OK;
 }
 
@@ -682,7 +703,7 @@ lbm_status lbm_step(lbm_solver *s, int n)
 lbm_status lbm_get_level_box(lbm_solver *s, int level, int *i0, int *j0, int *nx, int *ny)
 {
     if (!s || !i0 || !j0 || !nx || !ny) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
-    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (!s->grid_ready) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     if (level < 0 || level >= s->L) return fail(s, LBM_ERR_INVALID_ARG, "level out of range");
     const lbmgrid::Level &G = s->g.lv[level];
     *i0 = G.pi0; *j0 = G.pj0; *nx = G.pnx; *ny = G.pny;
@@ -721,9 +742,13 @@ lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, dou
     lbm_status st = lbm_get_level_box(s, level, &i0, &j0, &nx, &ny);
     if (st != LBM_OK) return st;
     if ((long long)nx * ny > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    const bool fields = rho || ux || uy || chi;
+    if (fields && !s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no device state (host-only handle): only the mask");
     std::vector<float> dr, u, v, c2;
-    st = download_level(s, level, dr, u, v, c2);
-    if (st != LBM_OK) return st;
+    if (fields) {
+        st = download_level(s, level, dr, u, v, c2);
+        if (st != LBM_OK) return st;
+    }
     const lbmgrid::Level &G = s->g.lv[level];
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
@@ -750,6 +775,7 @@ static double get_pop(int store, const unsigned char *base, size_t idx)
 
 lbm_status lbm_get_populations(lbm_solver *s, int level, double *pop, long long cap)
 {
+    if (s && !s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     int i0, j0, nx, ny;
     lbm_status st = lbm_get_level_box(s, level, &i0, &j0, &nx, &ny);
     if (st != LBM_OK) return st;
@@ -794,6 +820,7 @@ lbm_status lbm_get_wall_distance(lbm_solver *s, int level, double *d, int cap)
 lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const double *ux, const double *uy,
                           const double *chi)
 {
+    if (s && !s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     int i0, j0, nx, ny;
     lbm_status st = lbm_get_level_box(s, level, &i0, &j0, &nx, &ny);
     if (st != LBM_OK) return st;
@@ -875,7 +902,7 @@ lbm_status lbm_get_loads(lbm_solver *s, lbm_loads *out, double *cp_seg, double *
 lbm_status lbm_get_cut_links(lbm_solver *s, int *ijd, double *q, int cap, int *n)
 {
     if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
-    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (!s->grid_ready) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     const lbmgrid::Level &G = s->g.lv[s->L - 1];
     int cnt = 0;
     for (const auto &R : s->g.recs) {
@@ -893,7 +920,7 @@ lbm_status lbm_get_cut_links(lbm_solver *s, int *ijd, double *q, int cap, int *n
 lbm_status lbm_get_wall_records(lbm_solver *s, int *ij, double *geo, int *nst, int cap, int *n)
 {
     if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
-    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (!s->grid_ready) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     const int nr = (int)s->g.recs.size();
     *n = nr;
     if (!ij) return LBM_OK;
