@@ -204,6 +204,15 @@ lbm_status lbm_get_cut_links(lbm_solver *s, int *ij_dir, double *q, int cap, int
 lbm_status lbm_get_wall_records(lbm_solver *s, int *ij, double *geo, int *nstencil, int cap, int *n);
 lbm_status lbm_get_wall_state(lbm_solver *s, double *st, int cap, int *n);
 
+/* Reference-point stencils of the wall records (step 1 of Sec 2.3), in record order:
+ * for record r and entry m < 16, sij[32r + 2m] = i, sij[32r + 2m + 1] = j of the
+ * finest-level stencil cell (-1 past the record's stencil size), and the FP64 weights
+ * the device applies: rho_R = sum wr[16r + m] rho_m (inverse squared distance, normalised)
+ * and u_R = sum wu[16r + m] u_m (intercept row of the linear least-squares fit, or the
+ * inverse-distance weights where the fit is undefined); 0 past the stencil size.  cap is
+ * the record capacity; sij NULL queries the count.  Works on host-only handles. */
+lbm_status lbm_get_wall_stencils(lbm_solver *s, int *sij, double *wr, double *wu, int cap, int *n);
+
 /* Wall distance of the active fluid cells of a level (level lattice units, NaN elsewhere).
  * Works on host-only handles. */
 lbm_status lbm_get_wall_distance(lbm_solver *s, int level, double *d, int cap);

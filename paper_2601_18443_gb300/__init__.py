@@ -109,6 +109,7 @@ def library():
         "lbm_get_cut_links": ([vp, ip, dp, C.c_int, ip], C.c_int),
         "lbm_get_wall_records": ([vp, ip, dp, ip, C.c_int, ip], C.c_int),
         "lbm_get_wall_state": ([vp, dp, C.c_int, ip], C.c_int),
+        "lbm_get_wall_stencils": ([vp, ip, dp, dp, C.c_int, ip], C.c_int),
         "lbm_get_wall_distance": ([vp, C.c_int, dp, C.c_int], C.c_int),
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
@@ -323,6 +324,15 @@ class Solver:
         ij, geo, ns = np.zeros((m, 2), dtype=np.int32), np.zeros((m, 9)), np.zeros(m, dtype=np.int32)
         self._check(self._lib.lbm_get_wall_records(self._h, _ip(ij), _dp(geo), _ip(ns), n.value, C.byref(n)))
         return ij[:n.value], geo[:n.value], ns[:n.value]
+
+    def wall_stencils(self):
+        """(sij [n, 16, 2], wr [n, 16], wu [n, 16]): reference-point stencils and weights."""
+        n = C.c_int()
+        self._check(self._lib.lbm_get_wall_stencils(self._h, None, None, None, 0, C.byref(n)))
+        sij = np.zeros((n.value, 16, 2), dtype=np.int32)
+        wr, wu = np.zeros((n.value, 16)), np.zeros((n.value, 16))
+        self._check(self._lib.lbm_get_wall_stencils(self._h, _ip(sij), _dp(wr), _dp(wu), n.value, C.byref(n)))
+        return sij, wr, wu
 
     def wall_state(self):
         n = C.c_int()

@@ -936,6 +936,29 @@ lbm_status lbm_get_wall_records(lbm_solver *s, int *ij, double *geo, int *nst, i
     return LBM_OK;
 }
 
+lbm_status lbm_get_wall_stencils(lbm_solver *s, int *sij, double *wr, double *wu, int cap, int *n)
+{
+    if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->grid_ready) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    const int nr = (int)s->g.recs.size();
+    *n = nr;
+    if (!sij) return LBM_OK;
+    if (nr > cap || !wr || !wu) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    for (int r = 0; r < nr; r++) {
+        const lbmgrid::Record &R = s->g.recs[r];
+        double a[16], b[16];
+        stencil_weights(R, a, b);
+        for (int m = 0; m < 16; m++) {
+            const bool in = m < R.ns;
+            sij[32 * r + 2 * m] = in ? R.si[m] : -1;
+            sij[32 * r + 2 * m + 1] = in ? R.sj[m] : -1;
+            wr[16 * r + m] = in ? a[m] : 0.0;
+            wu[16 * r + m] = in ? b[m] : 0.0;
+        }
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_get_wall_state(lbm_solver *s, double *st8, int cap, int *n)
 {
     if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");

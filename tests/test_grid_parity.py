@@ -83,3 +83,39 @@ def test_host_only_handle_refuses_device_work():
     assert g.mask(0).shape == g.level_box(0)[:1:-1]
     g.close()
     g.close()
+
+
+@pytest.mark.parametrize("name", ["naca0012-6lvl", "three-element-4lvl", "polar-3414-a14-5lvl"])
+def test_reference_point_stencils_and_weights(name):
+    # step 1 of Sec 2.3 as the device applies it: the stencil is the 4 x 4 block of finest
+    # cells around R without solid cells and boundary nodes (reading of the unspecified
+    # stencil); rho_R uses normalised inverse-squared-distance weights; u_R the intercept of
+    # the linear least-squares fit, recomputed here with numpy's pseudo-inverse
+    cfg, loops = CASES[name]()
+    g = pkg.Solver(cfg, host_only=True)
+    g.set_geometry(loops)
+    L = cfg["levels"]
+    i0, j0, nx, ny = g.level_box(L - 1)
+    mask = g.mask(L - 1)
+    sij, wr, wu = g.wall_stencils()
+    ij, geo, ns = g.wall_records()
+    assert len(sij) == len(ij) > 0
+    for r in range(len(ij)):
+        rx, ry = geo[r, 5], geo[r, 6]
+        ic, jc = int(np.floor(rx - 0.5)), int(np.floor(ry - 0.5))
+        want = [(ic + a, jc + b) for b in range(-1, 3) for a in range(-1, 3)
+                if mask[jc + b - j0, ic + a - i0] == 1]
+        n = ns[r]
+        got = [tuple(x) for x in sij[r, :n]]
+        assert got == want, r
+        assert np.all(sij[r, n:] == -1) and np.all(wr[r, n:] == 0) and np.all(wu[r, n:] == 0)
+        dx = np.array([i + 0.5 - rx for i, _ in got])
+        dy = np.array([j + 0.5 - ry for _, j in got])
+        inv = 1.0 / (dx * dx + dy * dy)
+        np.testing.assert_allclose(wr[r, :n], inv / inv.sum(), rtol=1e-12, atol=0)
+        phi = np.stack([np.ones(n), dx, dy], axis=1)
+        np.testing.assert_allclose(wu[r, :n], np.linalg.pinv(phi)[0], rtol=0, atol=1e-12)
+        # the intercept row reproduces any linear field at R
+        a, b, c = 0.7, -1.3, 2.1
+        assert abs(wu[r, :n] @ (a + b * dx + c * dy) - a) < 1e-12
+    g.close()
