@@ -213,6 +213,15 @@ lbm_status lbm_get_wall_state(lbm_solver *s, double *st, int cap, int *n);
  * the record capacity; sij NULL queries the count.  Works on host-only handles. */
 lbm_status lbm_get_wall_stencils(lbm_solver *s, int *sij, double *wr, double *wu, int cap, int *n);
 
+/* Surface-element map of the loads (Sec 3.1.3, eqs 29-30): for wall segment k (in loop
+ * order, zero-length segments of coincident snapped vertices dropped), mid[2k], mid[2k+1]
+ * = its midpoint in finest lattice units from the box origin; b12[2k], b12[2k+1] = the
+ * two nearest wall records (boundary-node centres; ties to the lower record index, -1
+ * if none) and w12 their inverse squared distances, the weights of the segment's C_p and
+ * C_f.  cap is the segment capacity; b12 NULL queries the count.  Works on host-only
+ * handles. */
+lbm_status lbm_get_segment_map(lbm_solver *s, double *mid, int *b12, double *w12, int cap, int *n);
+
 /* Wall distance of the active fluid cells of a level (level lattice units, NaN elsewhere).
  * Works on host-only handles. */
 lbm_status lbm_get_wall_distance(lbm_solver *s, int level, double *d, int cap);

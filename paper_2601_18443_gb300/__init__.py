@@ -110,6 +110,7 @@ def library():
         "lbm_get_wall_records": ([vp, ip, dp, ip, C.c_int, ip], C.c_int),
         "lbm_get_wall_state": ([vp, dp, C.c_int, ip], C.c_int),
         "lbm_get_wall_stencils": ([vp, ip, dp, dp, C.c_int, ip], C.c_int),
+        "lbm_get_segment_map": ([vp, dp, ip, dp, C.c_int, ip], C.c_int),
         "lbm_get_wall_distance": ([vp, C.c_int, dp, C.c_int], C.c_int),
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
@@ -333,6 +334,15 @@ class Solver:
         wr, wu = np.zeros((n.value, 16)), np.zeros((n.value, 16))
         self._check(self._lib.lbm_get_wall_stencils(self._h, _ip(sij), _dp(wr), _dp(wu), n.value, C.byref(n)))
         return sij, wr, wu
+
+    def segment_map(self):
+        """(mid [n, 2], b12 [n, 2], w12 [n, 2]): wall segments -> two nearest wall records."""
+        n = C.c_int()
+        self._check(self._lib.lbm_get_segment_map(self._h, None, None, None, 0, C.byref(n)))
+        mid, w12 = np.zeros((n.value, 2)), np.zeros((n.value, 2))
+        b12 = np.zeros((n.value, 2), dtype=np.int32)
+        self._check(self._lib.lbm_get_segment_map(self._h, _dp(mid), _ip(b12), _dp(w12), n.value, C.byref(n)))
+        return mid, b12, w12
 
     def wall_state(self):
         n = C.c_int()

@@ -959,6 +959,24 @@ lbm_status lbm_get_wall_stencils(lbm_solver *s, int *sij, double *wr, double *wu
     return LBM_OK;
 }
 
+lbm_status lbm_get_segment_map(lbm_solver *s, double *mid, int *b12, double *w12, int cap, int *n)
+{
+    if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->grid_ready) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    const int ns = (int)s->g.sa.size();
+    *n = ns;
+    if (!b12) return LBM_OK;
+    if (ns > cap || !mid || !w12) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    for (int k = 0; k < ns; k++) {
+        const lbmgrid::IPt a = s->g.v[s->g.sa[k]], b = s->g.v[s->g.sb[k]];
+        mid[2 * k] = 0.5 * (double)(a.x + b.x) / 4096.0;
+        mid[2 * k + 1] = 0.5 * (double)(a.y + b.y) / 4096.0;
+        b12[2 * k] = s->g.seg_b1[k]; b12[2 * k + 1] = s->g.seg_b2[k];
+        w12[2 * k] = s->g.seg_w1[k]; w12[2 * k + 1] = s->g.seg_w2[k];
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_get_wall_state(lbm_solver *s, double *st8, int cap, int *n)
 {
     if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");

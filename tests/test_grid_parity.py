@@ -119,3 +119,23 @@ def test_reference_point_stencils_and_weights(name):
         a, b, c = 0.7, -1.3, 2.1
         assert abs(wu[r, :n] @ (a + b * dx + c * dy) - a) < 1e-12
     g.close()
+
+
+@pytest.mark.parametrize("name", ["naca2412-3lvl", "three-element-4lvl", "square-L-diamond-3lvl"])
+def test_surface_elements_take_the_two_nearest_boundary_nodes(name):
+    # Sec 3.1.3 reading: each surface segment takes C_p, C_f from the two boundary nodes
+    # nearest to its midpoint (ties to the lower record index), weighted by 1/d^2;
+    # brute force over all records here
+    cfg, loops = CASES[name]()
+    g = pkg.Solver(cfg, host_only=True)
+    g.set_geometry(loops)
+    mid, b12, w12 = g.segment_map()
+    ij, _, _ = g.wall_records()
+    centres = ij.astype(np.float64) + 0.5
+    assert len(mid) > 0 and len(ij) >= 2
+    for k in range(len(mid)):
+        d2 = ((centres - mid[k]) ** 2).sum(axis=1)
+        order = np.lexsort((np.arange(len(d2)), d2))
+        assert tuple(b12[k]) == (order[0], order[1]), k
+        np.testing.assert_allclose(w12[k], 1.0 / d2[order[:2]], rtol=1e-12)
+    g.close()
