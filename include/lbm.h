@@ -137,6 +137,11 @@ typedef struct {
 lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int *loop_offsets, int n_loops,
                              lbm_plan *out);
 
+/* Host threads that grid builds started from the calling thread may use (the size of
+ * their OpenMP teams); n <= 0 gives every processor.  Callers that build several grids at
+ * once on their own threads give each a share of the processors. */
+void lbm_set_host_threads(int n);
+
 /* Digest of the host-built grid, without a GPU: 64-bit FNV-1a over every per-cell level
  * table (kind, solid, band, boundary node, coalescence and cut-link bits, wall distance,
  * record index), the tile tables, the wall records and the surface-segment tables, built

@@ -98,6 +98,7 @@ def library():
         "lbm_set_wall_slip": ([vp, dp, C.c_int], C.c_int),
         "lbm_plan_geometry": ([C.POINTER(lbm_config), dp, ip, C.c_int, C.POINTER(lbm_plan)], C.c_int),
         "lbm_grid_digest": ([C.POINTER(lbm_config), dp, ip, C.c_int, C.POINTER(C.c_ulonglong)], C.c_int),
+        "lbm_set_host_threads": ([C.c_int], None),
         "lbm_step": ([vp, C.c_int], C.c_int),
         "lbm_step_async": ([vp, C.c_int], C.c_int),
         "lbm_synchronize": ([vp], C.c_int),
@@ -166,6 +167,11 @@ def plan(cfg: dict, loops) -> dict:
     L = out.levels
     return dict(levels=L, cells_active=list(out.cells_active[:L]), node_updates_per_step=out.node_updates_per_step,
                 wall_records=out.wall_records, device_bytes=out.device_bytes)
+
+
+def set_host_threads(n: int) -> None:
+    """lbm_set_host_threads: host threads of the grid builds started from this thread."""
+    library().lbm_set_host_threads(int(n))
 
 
 def grid_digest(cfg: dict, loops) -> int:

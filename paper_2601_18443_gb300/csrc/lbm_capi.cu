@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <omp.h>
 
 #include <cmath>
 #include <cstdint>
@@ -628,6 +629,11 @@ lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int 
     return st;
 }
 
+
+void lbm_set_host_threads(int n)
+{
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+}
 
 lbm_status lbm_grid_digest(const lbm_config *cfg, const double *xy, const int *loop_offsets, int n_loops,
                            unsigned long long *digest)

@@ -27,6 +27,7 @@ without a GPU.
 from __future__ import annotations
 
 import math
+import os
 import time
 from collections import deque
 from concurrent.futures import ThreadPoolExecutor
@@ -126,6 +127,11 @@ class GpuBackend:
 
         return torch.cuda.mem_get_info()[0]
 
+    def host_threads(self, n):
+        from . import set_host_threads
+
+        set_host_threads(n)
+
 
 class _Slot:
     __slots__ = ("req", "res", "handle", "need", "calm", "enqueued", "released")
@@ -143,7 +149,9 @@ class Service:
     max_slots     solves resident at once (1 gives the one-solve-at-a-time baseline)
     mem_budget    device bytes the resident solves may hold (default: half the free memory)
     overhead      bytes added to each solve's plan (graphs, events, allocator rounding)
-    builders      worker threads for planning and grid building
+    builders      worker threads for planning and grid building; each build uses an equal
+                  share of the host processors (concurrent builds that each took all of
+                  them would oversubscribe the cores)
     """
 
     def __init__(self, max_slots=8, mem_budget=None, overhead=16 << 20, builders=4, poll_s=2e-4, backend=None):
@@ -176,6 +184,14 @@ class Service:
         def note(ev, rid):
             self.trace.append((now(), ev, rid, used, resident))
 
+        share = max(1, (os.cpu_count() or 1) // max(1, self.builders))
+        set_threads = getattr(self.backend, "host_threads", None)
+
+        def in_worker(fn, *args):
+            if set_threads is not None:
+                set_threads(share)
+            return fn(*args)
+
         with ThreadPoolExecutor(max_workers=self.builders) as pool:
             try:
                 while pending or waiting or building or active:
@@ -183,7 +199,7 @@ class Service:
                     t = now()
                     while pending and pending[0].arrival * time_scale <= t:
                         r = pending.popleft()
-                        waiting.append((r, pool.submit(self.backend.plan, r.cfg, r.loops)))
+                        waiting.append((r, pool.submit(in_worker, self.backend.plan, r.cfg, r.loops)))
                         moved = True
 
                     # admission: arrival order; the head waits for memory (no overtaking)
@@ -214,7 +230,7 @@ class Service:
                         used += need
                         resident += 1
                         res.admitted = now()
-                        building.append((r, need, pool.submit(self.backend.build, r)))
+                        building.append((r, need, pool.submit(in_worker, self.backend.build, r)))
                         note("admit", r.rid)
                         moved = True
 

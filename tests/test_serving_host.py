@@ -205,3 +205,41 @@ def test_an_exception_in_the_caller_hook_still_releases_every_solve():
         Service(max_slots=4, mem_budget=64 << 20, overhead=0, backend=be).run(reqs, on_finish=boom)
     time.sleep(0.05)
     assert be.live == 0
+
+
+def test_builders_share_the_host_processors():
+    # every plan and build runs on a worker thread that first limits its grid-build threads
+    # to an equal share of the processors
+    import os
+
+    class Recording(FakeBackend):
+        def __init__(self):
+            super().__init__()
+            self.calls = []
+
+        def host_threads(self, n):
+            with self.lock:
+                self.calls.append((threading.get_ident(), n))
+
+    be = Recording()
+    reqs = [make(k, 0.0, 1 << 20) for k in range(6)]
+    res = Service(max_slots=3, mem_budget=1 << 30, builders=3, backend=be).run(reqs)
+    assert all(r.status == "converged" for r in res)
+    share = max(1, (os.cpu_count() or 1) // 3)
+    assert len(be.calls) == 12 and all(n == share for _, n in be.calls)
+    assert threading.get_ident() not in {t for t, _ in be.calls}
+
+
+def test_host_thread_count_leaves_the_grid_unchanged():
+    import paper_2601_18443_gb300 as pkg
+    from paper_2601_18443_gb300 import workloads as W
+    pkg.build()
+    cfg, loops = W.naca0012_small(levels=4)
+    ref = pkg.grid_digest(cfg, loops)
+    try:
+        pkg.set_host_threads(1)
+        assert pkg.grid_digest(cfg, loops) == ref
+        pkg.set_host_threads(3)
+        assert pkg.grid_digest(cfg, loops) == ref
+    finally:
+        pkg.set_host_threads(0)
