@@ -138,8 +138,9 @@ lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int 
                              lbm_plan *out);
 
 /* Host threads that grid builds started from the calling thread may use (the size of
- * their OpenMP teams); n <= 0 gives every processor.  Callers that build several grids at
- * once on their own threads give each a share of the processors. */
+ * their OpenMP teams); n <= 0 restores the process default (OMP_NUM_THREADS, else every
+ * processor).  Callers that build several grids at once on their own threads give each a
+ * share of the processors. */
 void lbm_set_host_threads(int n);
 
 /* Digest of the host-built grid, without a GPU: 64-bit FNV-1a over every per-cell level

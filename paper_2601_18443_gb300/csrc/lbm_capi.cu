@@ -632,7 +632,8 @@ lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int 
 
 void lbm_set_host_threads(int n)
 {
-    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    static const int process_default = omp_get_max_threads();   // read before the first change
+    omp_set_num_threads(n > 0 ? n : process_default);
 }
 
 lbm_status lbm_grid_digest(const lbm_config *cfg, const double *xy, const int *loop_offsets, int n_loops,
