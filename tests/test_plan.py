@@ -77,6 +77,17 @@ cases += [W.polar_case(r) for r in W.polar_requests(3)]
 cases.append((W.base_config(levels=2, nx0=64, ny0=64, h0=1.0, layers=4),
               [W.rectangle(10, 10, 15, 15), W.rectangle(30.0, 30.0, 44.0, 38.0)]))
 print(" ".join(str(pkg.grid_digest(c, l)) for c, l in cases))
+# rejected inputs: the same message whatever the thread count (the first violation in scan order)
+bad = [(W.base_config(levels=3, nx0=32, ny0=32, h0=1.0, layers=3), [W.rectangle(0.5, 0.5, 5.0, 5.0)]),
+       (W.base_config(levels=3, nx0=64, ny0=64, h0=1.0, layers=1), [W.rectangle(28, 28, 36, 36)]),
+       (W.base_config(levels=2, nx0=64, ny0=64, h0=1.0, layers=4),
+        [W.rectangle(20.0, 20.0, 30.0, 30.0), W.rectangle(25.0, 25.0, 35.0, 35.0)])]
+for c, l in bad:
+    try:
+        pkg.plan(c, l)
+        print("accepted")
+    except pkg.LBMError as e:
+        print(str(e))
 """
 
 
@@ -94,8 +105,10 @@ def test_grid_build_does_not_depend_on_the_host_thread_count():
         r = subprocess.run([sys.executable, "-c", _DIGEST_SCRIPT], capture_output=True, text=True, env=env,
                            cwd=root, timeout=300)
         assert r.returncode == 0, r.stderr
-        outs.append(r.stdout.split())
-    assert len(outs[0]) == 6 and all(int(d) != 0 for d in outs[0])
+        outs.append(r.stdout.splitlines())
+    digests = outs[0][0].split()
+    assert len(digests) == 6 and all(int(d) != 0 for d in digests)
+    assert len(outs[0]) == 4 and all("accepted" not in m for m in outs[0][1:])
     assert outs[0] == outs[1] == outs[2]
     # the digest sees a change of the input
     cfg, loops = W.naca0012_small(levels=3)
