@@ -139,3 +139,32 @@ def test_surface_elements_take_the_two_nearest_boundary_nodes(name):
         assert tuple(b12[k]) == (order[0], order[1]), k
         np.testing.assert_allclose(w12[k], 1.0 / d2[order[:2]], rtol=1e-12)
     g.close()
+
+
+def test_host_only_handle_argument_checks():
+    import ctypes as C
+    lib = pkg.library()
+    cfg, loops = __import__("__graft_entry__").smoke_case()
+    # invalid configurations are refused before any work
+    bad = pkg._config_struct(dict(cfg, levels=0))
+    h = C.c_void_p()
+    assert lib.lbm_create_host(C.byref(bad), C.byref(h)) == -1 and not h.value
+    assert lib.lbm_create_host(None, C.byref(h)) == -1
+    g = pkg.Solver(cfg, host_only=True)
+    g.set_geometry(loops)
+    # capacities below the level box are refused; a level out of range too
+    i0, j0, nx, ny = g.level_box(0)
+    d = np.zeros(nx * ny - 1)
+    assert lib.lbm_get_wall_distance(g._h, 0, pkg._dp(d), nx * ny - 1) == -1
+    with pytest.raises(pkg.LBMError):
+        g.level_box(cfg["levels"])
+    # a second geometry replaces the first; a rejected one leaves no tables behind
+    before = g.mask(cfg["levels"] - 1).copy()
+    g.set_geometry(loops)
+    assert np.array_equal(g.mask(cfg["levels"] - 1), before)
+    with pytest.raises(pkg.LBMError):
+        g.set_geometry([np.array([[0.0, 0.0], [1.0, 1.0]])])
+    with pytest.raises(pkg.LBMError) as e:
+        g.level_box(0)
+    assert e.value.code == -4
+    g.close()
