@@ -629,7 +629,6 @@ lbm_status lbm_plan_geometry(const lbm_config *cfg, const double *xy, const int 
     return st;
 }
 
-
 void lbm_set_host_threads(int n)
 {
     static const int process_default = omp_get_max_threads();   // read before the first change
