@@ -152,10 +152,11 @@ struct SegTree {
         const double qx = ax_ + t * dx - px, qy = ay_ + t * dy - py;
         return qx * qx + qy * qy;
     }
-    // lower bound of the squared distance from p to the node's segments.  The capsule term
-    // measures p against a point of the chord (the projection, with the chord's reciprocal
-    // squared length precomputed): any point of the chord is at least as far as the chord,
-    // and the rounding of the projection is far below the radius margin
+    // lower bound of the squared distance from p to the node's segments: the larger of the
+    // box distance and the capsule distance (distance to the chord minus the radius).  The
+    // chord distance is measured to the computed projection of p (the chord's reciprocal
+    // squared length precomputed); rounding can only move that point off the nearest chord
+    // point and so overstate the distance, by far less than the radius margin
     static double node_lb2(const Node &nd, double px, double py)
     {
         const double dx = std::max(0.0, std::max(nd.x0 - px, px - nd.x1));
