@@ -228,6 +228,14 @@ lbm_status lbm_get_wall_stencils(lbm_solver *s, int *sij, double *wr, double *wu
  * handles. */
 lbm_status lbm_get_segment_map(lbm_solver *s, double *mid, int *b12, double *w12, int cap, int *n);
 
+/* The 32-bit flag word the level kernel reads for each cell of a level's box (0 where the
+ * cell has no slot): bits 0-1 kind (0 absent, 1 active, 2 covered, 3 ghost), bit 2 solid,
+ * bit 3 band (active, with ghost children on the next level), bit 4 boundary node,
+ * bits 5-12 coalesced pulled directions 1..8, bits 13-20 cut pulled directions 1..8,
+ * bits 21-24 level-0 inlet, outlet, bottom and top columns/rows (non-periodic boxes).
+ * Element (j - j0) * nx + (i - i0); cap >= nx * ny.  Works on host-only handles. */
+lbm_status lbm_get_flags(lbm_solver *s, int level, unsigned int *flags, int cap);
+
 /* Wall distance of the active fluid cells of a level (level lattice units, NaN elsewhere).
  * Works on host-only handles. */
 lbm_status lbm_get_wall_distance(lbm_solver *s, int level, double *d, int cap);

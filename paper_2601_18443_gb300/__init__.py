@@ -113,6 +113,7 @@ def library():
         "lbm_get_wall_stencils": ([vp, ip, dp, dp, C.c_int, ip], C.c_int),
         "lbm_get_segment_map": ([vp, dp, ip, dp, C.c_int, ip], C.c_int),
         "lbm_get_wall_distance": ([vp, C.c_int, dp, C.c_int], C.c_int),
+        "lbm_get_flags": ([vp, C.c_int, C.POINTER(C.c_uint), C.c_int], C.c_int),
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
@@ -356,6 +357,13 @@ class Solver:
         st = np.zeros((max(n.value, 1), 8))
         self._check(self._lib.lbm_get_wall_state(self._h, _dp(st), n.value, C.byref(n)))
         return st[:n.value]
+
+    def flags(self, level):
+        """The level kernel's 32-bit flag word per cell of the level box."""
+        i0, j0, nx, ny = self.level_box(level)
+        f = np.zeros((ny, nx), dtype=np.uint32)
+        self._check(self._lib.lbm_get_flags(self._h, level, f.ctypes.data_as(C.POINTER(C.c_uint)), nx * ny))
+        return f
 
     def wall_distance(self, level):
         i0, j0, nx, ny = self.level_box(level)

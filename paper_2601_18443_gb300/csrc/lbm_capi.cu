@@ -807,6 +807,22 @@ lbm_status lbm_get_populations(lbm_solver *s, int level, double *pop, long long 
     return LBM_OK;
 }
 
+lbm_status lbm_get_flags(lbm_solver *s, int level, unsigned int *flags, int cap)
+{
+    int i0, j0, nx, ny;
+    lbm_status st = lbm_get_level_box(s, level, &i0, &j0, &nx, &ny);
+    if (st != LBM_OK) return st;
+    if (!flags || (long long)nx * ny > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    const lbmgrid::Level &G = s->g.lv[level];
+    const std::vector<uint32_t> &fl = s->lv[level].flags;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++) {
+            const long sl = G.slot(i0 + i, j0 + j);
+            flags[(long long)j * nx + i] = sl >= 0 ? fl[sl] : 0u;
+        }
+    return LBM_OK;
+}
+
 lbm_status lbm_get_wall_distance(lbm_solver *s, int level, double *d, int cap)
 {
     int i0, j0, nx, ny;

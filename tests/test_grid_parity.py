@@ -168,3 +168,77 @@ def test_host_only_handle_argument_checks():
         g.level_box(0)
     assert e.value.code == -4
     g.close()
+
+
+CX = [0, 1, -1, 0, 0, 1, -1, 1, -1]
+CY = [0, 0, 0, 1, -1, 1, -1, -1, 1]
+
+
+@pytest.mark.parametrize("name", ["naca2412-3lvl", "naca0012-6lvl", "two-loops-periodic-3lvl"])
+def test_flag_words_encode_the_tables(name):
+    # the flag word the level kernel reads, decoded and checked against the cell codes, the
+    # cut links and the band / coalescence rules restated here (reading of the Rohde
+    # transfers: band = active cells beside a covered cell; pulled direction d of a band
+    # cell coalesces iff c - c_d, c - (c_dx, 0) or c - (0, c_dy) is covered)
+    cfg, loops = CASES[name]()
+    g = pkg.Solver(cfg, host_only=True)
+    g.set_geometry(loops)
+    L = cfg["levels"]
+    ijd, _ = g.cut_links()
+    for l in range(L):
+        i0, j0, nx, ny = g.level_box(l)
+        f = g.flags(l).astype(np.int64)
+        m = g.mask(l)
+        kind = f & 3
+        solid = (f >> 2) & 1
+        # cells without a slot: absent ones, and on finer levels the solid cells of tiles
+        # that hold nothing else (no state is kept for them)
+        slot = f != 0
+        assert np.all(m[~slot] == 0) if l == 0 else np.all(np.isin(m[~slot], (0, 5)))
+        assert np.array_equal(solid[slot] == 1, m[slot] == 5)
+        code = {1: 1, 2: 1, 3: 2, 4: 3}
+        for c, k in code.items():
+            assert np.all(kind[m == c] == k), (l, c)
+        assert np.array_equal((f >> 4) & 1 == 1, m == 2)
+        # band and coalescence, with kinds padded by absent cells around the box; checked
+        # where every cell they look at has a known kind
+        K = np.zeros((ny + 2, nx + 2), dtype=np.int64)
+        K[1:-1, 1:-1] = kind
+        known = np.ones((ny + 2, nx + 2), dtype=bool)
+        known[1:-1, 1:-1] = slot | (m == 0)
+        cov = K == 2
+        near_cov = np.zeros((ny, nx), dtype=bool)
+        seen = np.ones((ny, nx), dtype=bool)
+        for d in range(1, 9):
+            near_cov |= cov[1 + CY[d]:1 + CY[d] + ny, 1 + CX[d]:1 + CX[d] + nx]
+            seen &= known[1 + CY[d]:1 + CY[d] + ny, 1 + CX[d]:1 + CX[d] + nx]
+        seen &= slot
+        band = (f >> 3) & 1
+        if not (l == 0 and cfg.get("periodic")):
+            assert np.array_equal((band == 1)[seen], ((kind == 1) & near_cov)[seen]), l
+        coal = (f >> 5) & 0xFF
+        want = np.zeros((ny, nx), dtype=np.int64)
+        for d in range(1, 9):
+            hit = np.zeros((ny, nx), dtype=bool)
+            for sx, sy in ((CX[d], CY[d]), (CX[d], 0), (0, CY[d])):
+                hit |= cov[1 - sy:1 - sy + ny, 1 - sx:1 - sx + nx]
+            want |= np.where(hit & (band == 1), 1 << (d - 1), 0)
+        assert np.array_equal(coal[seen], want[seen]), l
+        assert np.all(coal[band == 0] == 0)
+        # cut links: finest level only, as listed by lbm_get_cut_links
+        cut = (f >> 13) & 0xFF
+        want = np.zeros((ny, nx), dtype=np.int64)
+        if l == L - 1:
+            for i, j, d in ijd:
+                want[j - j0, i - i0] |= 1 << (d - 1)
+        assert np.array_equal(cut, want), l
+        # level-0 edges of a box with domain boundaries
+        edges = (f >> 21) & 0xF
+        if l == 0 and not cfg.get("periodic"):
+            I, J = np.meshgrid(np.arange(i0, i0 + nx), np.arange(j0, j0 + ny))
+            pres = kind != 0
+            want = ((I == 0) * 1 + (I == cfg["nx0"] - 1) * 2 + (J == 0) * 4 + (J == cfg["ny0"] - 1) * 8) * pres
+            assert np.array_equal(edges, want)
+        else:
+            assert np.all(edges == 0)
+    g.close()
