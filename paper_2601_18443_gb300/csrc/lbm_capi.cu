@@ -322,6 +322,13 @@ static lbm_status check_status(lbm_solver *s)
     return LBM_OK;
 }
 
+// the grid builder's specification from a solver configuration
+static lbmgrid::Spec grid_spec(const lbm_config &c)
+{
+    return lbmgrid::Spec{c.levels, c.nx0, c.ny0, c.layers, c.x0, c.y0, c.h0, c.d_wr, c.d_wv,
+                         c.periodic, c.solid_walls, c.wall_model};
+}
+
 // 64-bit FNV-1a over raw bytes (grid digest)
 namespace {
 struct Fnv {
@@ -415,9 +422,8 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     free_all(s);
     s->grid_ready = false;
     const lbm_config &c = s->cfg;
-    lbmgrid::Spec sp{c.levels, c.nx0, c.ny0, c.layers, c.x0, c.y0, c.h0, c.d_wr, c.d_wv, c.periodic, c.solid_walls, c.wall_model};
     std::string msg;
-    int rc = lbmgrid::build(sp, xy, loop_off, n_loops, s->g, msg);
+    int rc = lbmgrid::build(grid_spec(c), xy, loop_off, n_loops, s->g, msg);
     if (rc != 0) return fail(s, (lbm_status)rc, msg);
     const int L = s->L;
     bool ok = true;
@@ -641,11 +647,9 @@ lbm_status lbm_grid_digest(const lbm_config *cfg, const double *xy, const int *l
     if (!digest) return LBM_ERR_INVALID_ARG;
     *digest = 0;
     if (!cfg || !config_ok(cfg) || n_loops < 0 || (n_loops > 0 && (!xy || !loop_offsets))) return LBM_ERR_INVALID_ARG;
-    const lbm_config &c = *cfg;
-    lbmgrid::Spec sp{c.levels, c.nx0, c.ny0, c.layers, c.x0, c.y0, c.h0, c.d_wr, c.d_wv, c.periodic, c.solid_walls, c.wall_model};
     lbmgrid::Grid g;
     std::string msg;
-    const int rc = lbmgrid::build(sp, xy, loop_offsets, n_loops, g, msg);
+    const int rc = lbmgrid::build(grid_spec(*cfg), xy, loop_offsets, n_loops, g, msg);
     if (rc != 0) return (lbm_status)rc;
     Fnv f;
     for (const lbmgrid::Level &G : g.lv) {
