@@ -108,3 +108,133 @@ def test_taylor_green_across_a_refined_patch():
         res.append(math.log((e1[a] ** 2).sum() / (e2[a] ** 2).sum()) / (2 * (T // 2)) / (2 * nu * k * k) - 1)
     assert abs(res[0]) < 2e-3
     assert abs(res[1]) < 2e-2
+
+
+# --------------------------------------------------------------------------- interface fields (Sec 2.2)
+# The ghost children of a band cell get chi and u from a linear least-squares fit over the
+# band cell's D2Q9 neighbourhood, evaluated at the child centre (offsets of a quarter of the
+# parent spacing); rho is copied from the parent.  A covered parent gets the mean rho and chi
+# of its fluid children and their mass-weighted velocity.  Linear fields pin both: the fit
+# reproduces a linear field exactly, and the mean of a linear field over the four children
+# is its value at the parent centre.
+
+LIN = dict(chi=(2.0, 0.031, -0.017), ux=(0.03, 2.5e-3, 1.5e-3), uy=(-0.01, -1e-3, 3e-3), rho=(1.0, 4e-3, -3e-3))
+
+
+def _lin(key, X, Y):
+    a, b, c = LIN[key]
+    return a + b * X + c * Y
+
+
+def _centres(s, l):
+    """Cell centres of level l in level-0 lattice units (h0 = 1, origin 0)."""
+    i0, j0, nx, ny = s.level_box(l)
+    x = (np.arange(i0, i0 + nx) + 0.5) / 2**l
+    y = (np.arange(j0, j0 + ny) + 0.5) / 2**l
+    return np.meshgrid(x, y)
+
+
+def _linear_solver(loops, levels, n, rho_linear, solid_walls=0, periodic=1):
+    cfg = W.base_config(levels=levels, nx0=n, ny0=n, h0=1.0, Re=U_LAT / 0.02, Ma=0.1, periodic=periodic,
+                        solid_walls=solid_walls, layers=3, wall_model=3, turbulence=1)
+    s = oracle.Solver(cfg)
+    s.set_geometry(loops)
+    for l in range(levels):
+        X, Y = _centres(s, l)
+        rho = _lin("rho", X, Y) if rho_linear else np.ones_like(X)
+        s.set_fields(l, rho=rho, ux=_lin("ux", X, Y), uy=_lin("uy", X, Y), chi=_lin("chi", X, Y))
+    return s
+
+
+@pytest.mark.parametrize("name", ["square-2lvl", "square-3lvl", "L-2lvl", "diamond-3lvl", "two-patches-3lvl"])
+def test_ghost_fields_reproduce_a_linear_field(name):
+    loops, levels, n = PATCHES[name]
+    s = _linear_solver(loops, levels, n, rho_linear=False)
+    for l in range(1, levels):
+        F = s.get_fields(l)
+        g = F["mask"] == 4
+        assert g.sum() > 0
+        X, Y = _centres(s, l)
+        for key in ("chi", "ux", "uy"):
+            err = np.abs(F[key][g] - _lin(key, X, Y)[g]).max()
+            assert err < 1e-13, (l, key, err)
+        assert np.abs(F["rho"][g] - 1.0).max() < 1e-15
+
+
+def test_ghost_density_is_the_parent_density():
+    loops, levels, n = PATCHES["square-2lvl"]
+    s = _linear_solver(loops, levels, n, rho_linear=True)
+    P, F = s.get_fields(0), s.get_fields(1)
+    i0p, j0p = s.level_box(0)[:2]
+    i0f, j0f = s.level_box(1)[:2]
+    jj, ii = np.nonzero(F["mask"] == 4)
+    parent = P["rho"][(jj + j0f) // 2 - j0p, (ii + i0f) // 2 - i0p]
+    assert np.array_equal(F["rho"][jj, ii], parent)
+
+
+@pytest.mark.parametrize("name", ["square-2lvl", "square-3lvl", "L-2lvl", "diamond-3lvl"])
+def test_covered_cells_hold_the_parent_centre_values(name):
+    # constant density: the mass weighting is a plain mean, so every restricted field of a
+    # linear state is its value at the parent centre
+    loops, levels, n = PATCHES[name]
+    s = _linear_solver(loops, levels, n, rho_linear=False)
+    for l in range(levels - 1):
+        F = s.get_fields(l)
+        c = F["mask"] == 3
+        assert c.sum() > 0
+        X, Y = _centres(s, l)
+        for key in ("chi", "ux", "uy"):
+            err = np.abs(F[key][c] - _lin(key, X, Y)[c]).max()
+            assert err < 1e-13, (l, key, err)
+
+
+def test_covered_velocity_is_mass_weighted():
+    # linear rho and u on two levels: the covered parent holds rho and chi at its centre and
+    # u = sum_c rho_c u_c / sum_c rho_c over its four children, which differs from the plain
+    # mean by about 3e-7 here (far above the rounding of the sums)
+    loops, levels, n = PATCHES["square-2lvl"]
+    s = _linear_solver(loops, levels, n, rho_linear=True)
+    F = s.get_fields(0)
+    c = F["mask"] == 3
+    X, Y = _centres(s, 0)
+    for key in ("rho", "chi"):
+        assert np.abs(F[key][c] - _lin(key, X, Y)[c]).max() < 1e-14
+    off = [(-0.25, -0.25), (0.25, -0.25), (-0.25, 0.25), (0.25, 0.25)]
+    rho_c = [_lin("rho", X + a, Y + b) for a, b in off]
+    for key in ("ux", "uy"):
+        mw = sum(r * _lin(key, X + a, Y + b) for r, (a, b) in zip(rho_c, off)) / sum(rho_c)
+        plain = _lin(key, X, Y)
+        assert np.abs(mw - plain)[c].min() > 1e-7          # the weighting is visible
+        assert np.abs(F[key][c] - mw[c]).max() < 1e-15, key
+
+
+def test_restriction_skips_solid_children():
+    # a wall inside the refined patch: covered parents with solid children hold the mean over
+    # their fluid children only (rho, chi) and the mass-weighted velocity over them
+    n = 32
+    cfg = W.base_config(levels=2, nx0=n, ny0=n, h0=1.0, Re=U_LAT / 0.02, Ma=0.1, periodic=1, solid_walls=1,
+                        layers=3, wall_model=3, turbulence=1)
+    s = oracle.Solver(cfg)
+    s.set_geometry([np.array([[13.3, 12.2], [19.1, 13.7], [17.6, 19.4], [12.4, 17.9]])])
+    for l in range(2):
+        X, Y = _centres(s, l)
+        s.set_fields(l, rho=_lin("rho", X, Y), ux=_lin("ux", X, Y), uy=_lin("uy", X, Y), chi=_lin("chi", X, Y))
+    P, F = s.get_fields(0), s.get_fields(1)
+    i0p, j0p = s.level_box(0)[:2]
+    i0f, j0f = s.level_box(1)[:2]
+    XF, YF = _centres(s, 1)
+    partial = 0
+    for j, i in zip(*np.nonzero(P["mask"] == 3)):
+        gi, gj = i + i0p, j + j0p
+        kids = [(2 * gj + b - j0f, 2 * gi + a - i0f) for b in (0, 1) for a in (0, 1)]
+        fluid = [(y, x) for y, x in kids if F["mask"][y, x] != 5]
+        if not fluid:
+            continue
+        partial += len(fluid) < 4
+        r = np.array([_lin("rho", XF[y, x], YF[y, x]) for y, x in fluid])
+        want = {"rho": r.mean(), "chi": np.mean([_lin("chi", XF[y, x], YF[y, x]) for y, x in fluid])}
+        for key in ("ux", "uy"):
+            want[key] = np.sum(r * np.array([_lin(key, XF[y, x], YF[y, x]) for y, x in fluid])) / r.sum()
+        for key, v in want.items():
+            assert abs(P[key][j, i] - v) < 1e-14, (key, i, j)
+    assert partial > 0
