@@ -62,6 +62,11 @@ typedef struct {
     int store;              /* population storage, FP32 arithmetic: 0 FP32 (f - w_i); 1 FP16, 2 BF16
                                (f - f_eq(1, U, 0), the free-stream equilibrium)                      */
     int sa_convection;      /* SA-neg convection: 0 Lax-Wendroff (Sec 2.2), 1 first-order upwind (Sec 3.3) */
+    int outlet;             /* level-0 outlet (Sec 3.1.1), on the post-stream values of the three
+                               populations entering from outside: 0 Yu's linear extrapolation
+                               f_q(N-1) = 2 f_q(N-2) - f_q(N-3), the form the paper names; 1 the
+                               zero-gradient copy f_q(N-1) = f_q(N-2), which lets wake vortices leave
+                               (the linear form amplifies them as they cross the last columns)    */
     void *cuda_stream;      /* cudaStream_t to run on, or NULL for a library-owned stream            */
     void *(*dev_alloc)(size_t bytes, void *stream, void *ctx); /* optional device allocator          */
     void (*dev_free)(void *ptr, void *stream, void *ctx);      /* its matching free                  */
@@ -316,8 +321,10 @@ lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const in
  * outputs after synchronising the stream.
  * Scratch: a fixed 48 KB array in device memory (file scope), held by every GPU that
  * loads the library until the process exits.  The first call on a device looks up that
- * array's device address (make it before any stream capture).  Every call on a device
- * shares the array: calls that overlap on the GPU (other streams, other threads) race.
+ * array's device address (make it before any stream capture) and keeps it for the process;
+ * after a cudaDeviceReset of that device the kept address is stale, so do not call this
+ * entry point on a device that has been reset.  Every call on a device shares the array:
+ * calls that overlap on the GPU (other streams, other threads) race.
  * Errors: LBM_ERR_INVALID_ARG for n_cells < 0, n_cells > LBM_NOALLOC_MAX_CELLS or a NULL
  * pointer (nothing is launched); LBM_ERR_CUDA if the device or the launch fails. */
 lbm_status lbm_level_mass_noalloc(const unsigned int *flags, const float *drho, const float *ux, const float *uy,

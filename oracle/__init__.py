@@ -46,7 +46,7 @@ class Config(C.Structure):
         ("chord", C.c_double), ("Re", C.c_double), ("Ma", C.c_double),
         ("chi_inf", C.c_double), ("d_wr", C.c_double), ("d_wv", C.c_double),
         ("turbulence", C.c_int), ("wall_model", C.c_int), ("periodic", C.c_int),
-        ("solid_walls", C.c_int), ("sa_convection", C.c_int),
+        ("solid_walls", C.c_int), ("sa_convection", C.c_int), ("outlet", C.c_int),
     ]
 
 

@@ -561,7 +561,8 @@ int oracle_create(const oracle_config *cfg, oracle_solver **out)
     if (!cfg || !out) return -1;
     *out = NULL;
     if (cfg->levels < 1 || cfg->levels > MAXL || cfg->nx0 < 4 || cfg->ny0 < 4 || !(cfg->h0 > 0) ||
-        cfg->layers < 3 || !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->chord > 0))
+        cfg->layers < 3 || !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->chord > 0) || cfg->outlet < 0 ||
+        cfg->outlet > 1 || (!cfg->periodic && cfg->nx0 < 8))
         return -1;
     oracle_solver *s = (oracle_solver *)calloc(1, sizeof *s);
     if (!s) return -2;
@@ -1213,16 +1214,18 @@ static void stream_collide_level(oracle_solver *s, int l)
                     out[7] = out[8] + 0.5 * (out[3] - out[4]) + rho * U / 6.0;
                 }
             }
-        /* outlet: zero-gradient extrapolation f_q(N-1) = f_q(N-2) for q = 2, 6, 8 (post-stream
-         * values).  The linear form 2 f_q(N-2) - f_q(N-3) amplifies the wake's vortices as
-         * they cross the last columns and the disturbance then spreads upstream. */
+        /* outlet, on the post-stream values of the three populations entering from outside
+         * (q = 2, 6, 8): Yu's linear extrapolation f_q(N-1) = 2 f_q(N-2) - f_q(N-3) (outlet 0,
+         * the form Sec 3.1.1 names), or the zero-gradient copy f_q(N-1) = f_q(N-2) (outlet 1).
+         * The linear form amplifies the wake's vortices as they cross the last columns. */
         const int qs[3] = {2, 6, 8};
         for (int j = 0; j < c->ny0; j++) {
             long k = cidx(P, c->nx0 - 1, j);
             if (P->solid[k]) continue;
+            const long k2 = cidx(P, c->nx0 - 2, j), k3 = cidx(P, c->nx0 - 3, j);
             for (int m = 0; m < 3; m++) {
                 int q = qs[m];
-                P->fn[9 * k + q] = P->fn[9 * cidx(P, c->nx0 - 2, j) + q];
+                P->fn[9 * k + q] = c->outlet == 0 ? 2.0 * P->fn[9 * k2 + q] - P->fn[9 * k3 + q] : P->fn[9 * k2 + q];
             }
         }
     }

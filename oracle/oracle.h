@@ -30,6 +30,8 @@ typedef struct {
     int periodic;          /* 1: periodic level-0 box, no domain BCs             */
     int solid_walls;       /* 1: loops are walls; 0: loops only drive refinement */
     int sa_convection;     /* 0 Lax-Wendroff (Sec 2.2), 1 first-order upwind (Sec 3.3) */
+    int outlet;            /* level-0 outlet (Sec 3.1.1): 0 Yu's linear extrapolation
+                              f_q(N-1) = 2 f_q(N-2) - f_q(N-3); 1 zero gradient f_q(N-1) = f_q(N-2) */
 } oracle_config;
 
 typedef struct oracle_solver oracle_solver;

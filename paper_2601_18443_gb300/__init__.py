@@ -38,7 +38,7 @@ class lbm_config(C.Structure):
         ("chi_inf", C.c_double), ("d_wr", C.c_double), ("d_wv", C.c_double),
         ("turbulence", C.c_int), ("wall_model", C.c_int), ("periodic", C.c_int),
         ("solid_walls", C.c_int), ("store", C.c_int), ("sa_convection", C.c_int),
-        ("cuda_stream", C.c_void_p),
+        ("outlet", C.c_int), ("cuda_stream", C.c_void_p),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
 

@@ -54,6 +54,7 @@ struct StepConsts {
     int turbulence;
     int wall_model;
     int sa_convection;  // 0 Lax-Wendroff, 1 first-order upwind
+    int outlet;         // 0 linear extrapolation (Yu), 1 zero gradient
     float U;            // inlet lattice velocity
     float chi_inf;
     float d_wr, d_wv;

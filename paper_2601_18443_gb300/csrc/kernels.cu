@@ -586,14 +586,18 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
                 g[7] = g[8] + 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
             }
             if (i == k.nx0 - 1) {
-                // outlet: zero-gradient extrapolation, g_q(N-1) = g_q(N-2) for the pulled-in
-                // directions 2, 6, 8 (the post-stream values of the neighbour column)
+                // outlet, for the directions 2, 6, 8 entering from outside, on the post-stream
+                // values of the columns N-2 and N-3 (in-box pull or symmetry reflection):
+                // Yu's linear extrapolation 2 g_q(N-2) - g_q(N-3), or the zero-gradient copy g_q(N-2)
 #pragma unroll
                 for (int m = 0; m < 3; m++) {
                     const int q = m == 0 ? 2 : (m == 1 ? 6 : 8);
-                    const int si = k.nx0 - 2 - cxq(q), sj = j - cyq(q);
-                    g[q] = (sj >= 0 && sj < k.ny0) ? IO.ld(fc + q * ns + slot0(k, si, sj), q)
-                                                   : IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
+                    const int sj = j - cyq(q);
+                    const bool yin = sj >= 0 && sj < k.ny0;
+                    const int qs = yin ? q : mirror_y(q), js = yin ? sj : j;
+                    const float g2 = IO.ld(fc + qs * ns + slot0(k, k.nx0 - 1, js), qs);    // source of N-2
+                    g[q] = g2;
+                    if (k.outlet == 0) g[q] = 2.0f * g2 - IO.ld(fc + qs * ns + slot0(k, k.nx0 - 2, js), qs);
                 }
             }
         }

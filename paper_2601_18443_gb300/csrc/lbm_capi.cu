@@ -357,6 +357,7 @@ static bool config_ok(const lbm_config *cfg)
         cfg->layers < 3 || !(cfg->Re > 0) || !(cfg->Ma > 0) || !(cfg->chord > 0) || cfg->store < 0 || cfg->store > 2 ||
         (cfg->periodic && (cfg->nx0 % LBM_TX || cfg->ny0 % LBM_TY)) || (!cfg->periodic && (cfg->nx0 < 8)) ||
         cfg->wall_model < 0 || cfg->wall_model > 3 || cfg->sa_convection < 0 || cfg->sa_convection > 1 ||
+        cfg->outlet < 0 || cfg->outlet > 1 ||
         (!cfg->dev_alloc != !cfg->dev_free));
 }
 
@@ -575,6 +576,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     s->k.level0_edges = !c.periodic;
     s->k.nx0 = c.nx0; s->k.ny0 = c.ny0; s->k.ntx0 = s->g.lv[0].ntx;
     s->k.turbulence = c.turbulence; s->k.wall_model = c.wall_model; s->k.sa_convection = c.sa_convection;
+    s->k.outlet = c.outlet;
     s->k.U = (float)s->U; s->k.chi_inf = (float)c.chi_inf;
     s->k.d_wr = (float)c.d_wr; s->k.d_wv = (float)c.d_wv;
     {
@@ -1214,21 +1216,42 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
 
 // ---------------------------------------------------------------- checkpoint / resume
 struct StateHeader {
-    char magic[8];                 // "LBMSTAT1"
+    char magic[8];                 // "LBMSTAT2"
     int levels, store, turbulence, have_cl;
     long long step, nrec;
     double last_cl;
     long long ns[LBM_MAXL];
-    unsigned long long grid_hash;  // FNV-1a of every level's flag words
+    unsigned long long grid_hash;  // FNV-1a of every level's flag words and wall distances and of the wall records
+    unsigned long long cfg_hash;   // FNV-1a of the configuration's physical and model parameters
 };
 
 static unsigned long long grid_hash(const lbm_solver *s)
 {
-    unsigned long long h = 1469598103934665603ull;
-    for (int l = 0; l < s->L; l++)
-        for (uint32_t w : s->lv[l].flags)
-            for (int b = 0; b < 4; b++) { h ^= (w >> (8 * b)) & 0xFFu; h *= 1099511628211ull; }
-    return h;
+    Fnv f;
+    for (int l = 0; l < s->L; l++) {
+        f.vec(s->lv[l].flags);
+        f.vec(s->g.lv[l].dist);
+    }
+    for (const lbmgrid::Record &r : s->g.recs) {
+        f.val(r.i); f.val(r.j); f.val(r.loop);
+        f.bytes(r.n, sizeof r.n); f.val(r.dwb); f.bytes(r.r, sizeof r.r); f.bytes(r.q, sizeof r.q);
+        f.val(r.ns); f.bytes(r.si, sizeof(int) * r.ns); f.bytes(r.sj, sizeof(int) * r.ns);
+    }
+    return f.h;
+}
+
+// every configuration value that changes the arithmetic of a step (not the stream or the
+// allocator hooks)
+static unsigned long long cfg_hash(const lbm_solver *s)
+{
+    const lbm_config &c = s->cfg;
+    Fnv f;
+    const int iv[14] = {c.levels, c.nx0, c.ny0, c.layers, c.turbulence, c.wall_model, c.periodic, c.solid_walls,
+                        c.store, c.sa_convection, c.outlet, 0, 0, 0};
+    const double dv[9] = {c.x0, c.y0, c.h0, c.chord, c.Re, c.Ma, c.chi_inf, c.d_wr, c.d_wv};
+    f.bytes(iv, sizeof iv);
+    f.bytes(dv, sizeof dv);
+    return f.h;
 }
 
 static size_t state_bytes(const lbm_solver *s)
@@ -1249,11 +1272,12 @@ lbm_status lbm_get_state(lbm_solver *s, void *buf, size_t cap, size_t *size)
     CK(cudaStreamSynchronize(s->stream));
     StateHeader h;
     std::memset(&h, 0, sizeof h);
-    std::memcpy(h.magic, "LBMSTAT1", 8);
+    std::memcpy(h.magic, "LBMSTAT2", 8);
     h.levels = s->L; h.store = s->cfg.store; h.turbulence = s->cfg.turbulence; h.have_cl = s->have_cl;
     h.step = s->step; h.nrec = s->rec.n; h.last_cl = s->last_cl;
     for (int l = 0; l < s->L; l++) h.ns[l] = s->lv[l].v.ns;
     h.grid_hash = grid_hash(s);
+    h.cfg_hash = cfg_hash(s);
     unsigned char *o = (unsigned char *)buf;
     std::memcpy(o, &h, sizeof h);
     o += sizeof h;
@@ -1278,10 +1302,12 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     StateHeader h;
     if (size < sizeof h) return fail(s, LBM_ERR_INVALID_ARG, "state blob too short");
     std::memcpy(&h, buf, sizeof h);
-    if (std::memcmp(h.magic, "LBMSTAT1", 8) != 0) return fail(s, LBM_ERR_INVALID_ARG, "not a state blob");
+    if (std::memcmp(h.magic, "LBMSTAT2", 8) != 0) return fail(s, LBM_ERR_INVALID_ARG, "not a state blob");
     bool same = h.levels == s->L && h.store == s->cfg.store && h.turbulence == s->cfg.turbulence && h.nrec == s->rec.n;
     for (int l = 0; same && l < s->L; l++) same = h.ns[l] == s->lv[l].v.ns;
     if (!same || h.grid_hash != grid_hash(s)) return fail(s, LBM_ERR_INVALID_ARG, "state blob from another configuration or grid");
+    if (h.cfg_hash != cfg_hash(s))
+        return fail(s, LBM_ERR_INVALID_ARG, "state blob from a solve with other physical or model parameters");
     if (size != state_bytes(s)) return fail(s, LBM_ERR_INVALID_ARG, "state blob size differs");
     const unsigned char *o = (const unsigned char *)buf + sizeof h;
     const size_t pb = pop_bytes(s->cfg.store);

@@ -75,7 +75,7 @@ def l_shape(x0, y0, x1, y1, xm, ym) -> np.ndarray:
 def base_config(**kw) -> dict:
     cfg = dict(levels=1, nx0=64, ny0=64, x0=0.0, y0=0.0, h0=1.0, layers=8, chord=1.0, Re=1000.0, Ma=0.1,
                chi_inf=3.0, d_wr=2.0, d_wv=1.0, turbulence=0, wall_model=3, periodic=0, solid_walls=1,
-               sa_convection=0)
+               sa_convection=0, outlet=1)
     cfg.update(kw)
     return cfg
 

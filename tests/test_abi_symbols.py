@@ -45,7 +45,8 @@ def test_create_rejects_invalid_configurations():
     # validation happens on the host before any CUDA call
     from paper_2601_18443_gb300 import workloads as W
     bad = [dict(levels=0), dict(levels=17), dict(nx0=2), dict(h0=0.0), dict(layers=2), dict(Re=0.0),
-           dict(Ma=-1.0), dict(chord=0.0), dict(store=7), dict(periodic=1, nx0=48), dict(wall_model=5)]
+           dict(Ma=-1.0), dict(chord=0.0), dict(store=7), dict(periodic=1, nx0=48), dict(wall_model=5),
+           dict(outlet=2), dict(outlet=-1)]
     for kw in bad:
         cfg = W.base_config(**kw)
         try:

@@ -289,8 +289,32 @@ def test_wall_function_state_matches():
         assert e <= TOL_FIELD, (name, e)
 
 
-def test_smoke_case_turbulent_airfoil():
+@pytest.mark.parametrize("outlet", [0, 1])
+def test_outlet_forms_on_a_linear_density_profile(outlet):
+    # one stream from f_eq(1 + a x, 0): both outlet forms (Sec 3.1.1) element by element against
+    # the oracle, and the last column against the closed form of each (Yu's linear
+    # extrapolation continues rho and j_x = -a/3; the zero-gradient copy gives rho - a/6, -a/6)
+    nx, ny, a = 64, 16, 1e-3
+    cfg = W.base_config(levels=1, nx0=nx, ny0=ny, h0=1.0, Re=1e3, Ma=0.1, turbulence=0, wall_model=3, outlet=outlet)
+    g, r = pair(cfg, [])
+    X = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)[0]
+    rho0 = 1.0 + a * (X - nx / 2)
+    for s in (g, r):
+        s.set_fields(0, rho=rho0, ux=np.zeros_like(X), uy=np.zeros_like(X))
+    g.step(1); r.step(1)
+    assert_fields(g, r, 1, turbulent=False)
+    F = g.get_fields(0)
+    want_rho, want_jx = (rho0[:, -1], -a / 3) if outlet == 0 else (rho0[:, -1] - a / 6, -a / 6)
+    assert np.abs(F["rho"][:, -1] - want_rho).max() < 1e-7
+    assert np.abs(F["rho"][:, -1] * F["ux"][:, -1] - want_jx).max() < 1e-9
+    g.step(49); r.step(49)
+    assert_fields(g, r, 1, turbulent=False)
+
+
+@pytest.mark.parametrize("outlet", [0, 1])
+def test_smoke_case_turbulent_airfoil(outlet):
     cfg, loops = __import__("__graft_entry__").smoke_case()
+    cfg["outlet"] = outlet
     g, r = pair(cfg, loops)
     g.step(50); r.step(50)
     assert_fields(g, r, cfg["levels"])

@@ -18,9 +18,10 @@ def re_for(nu_lat, cells_per_chord=1.0):
     return U_LAT * cells_per_chord / nu_lat
 
 
-def test_uniform_freestream_is_steady():
-    # Zou-He inlet, symmetry planes and the extrapolation outlet reproduce a uniform stream exactly
-    cfg = W.base_config(levels=1, nx0=40, ny0=20, h0=0.1, Re=1e5, Ma=MA, turbulence=1, wall_model=0)
+@pytest.mark.parametrize("outlet", [0, 1])
+def test_uniform_freestream_is_steady(outlet):
+    # Zou-He inlet, symmetry planes and either outlet form reproduce a uniform stream exactly
+    cfg = W.base_config(levels=1, nx0=40, ny0=20, h0=0.1, Re=1e5, Ma=MA, turbulence=1, wall_model=0, outlet=outlet)
     s = oracle.Solver(cfg)
     s.set_geometry([])
     s.step(100)
@@ -144,11 +145,37 @@ def test_taylor_green_decay_rate():
     assert math.log2(errs[0] / errs[1]) > 1.8 and math.log2(errs[1] / errs[2]) > 1.8
 
 
-def _vortex_box(nx=96, ny=48, Re=2000.0):
+@pytest.mark.parametrize("outlet", [0, 1])
+def test_outlet_closes_a_linear_density_profile(outlet):
+    # Sec 3.1.1 outlet on the post-stream populations q = 2, 6, 8 entering from x = N.  From
+    # f = f_eq(rho(x), 0) with rho = 1 + a x, one stream gives f_q(x) = w_q rho(x - c_qx) in
+    # the interior, hence rho(x) and j_x = -a/3 there.  Yu's linear extrapolation continues
+    # this exactly in the last column (rho(N-1), j_x = -a/3); the zero-gradient copy brings
+    # rho(N-1) - a/6 and j_x = -a/6 (its entering populations carry rho(N-1) instead of rho(N)).
+    nx, ny, a = 32, 16, 1e-3
+    cfg = W.base_config(levels=1, nx0=nx, ny0=ny, h0=1.0, Re=1e3, Ma=MA, turbulence=0, wall_model=3, outlet=outlet)
+    s = oracle.Solver(cfg)
+    s.set_geometry([])
+    X = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5)[0]
+    rho0 = 1.0 + a * (X - nx / 2)
+    s.set_fields(0, rho=rho0, ux=np.zeros_like(X), uy=np.zeros_like(X))
+    s.step(1)
+    F = s.get_fields(0)
+    mid = slice(2, nx - 1)
+    assert np.abs(F["rho"][:, mid] - rho0[:, mid]).max() < 1e-15
+    assert np.abs(F["rho"][:, mid] * F["ux"][:, mid] + a / 3).max() < 1e-16
+    last = rho0[:, -1]
+    want_rho, want_jx = (last, -a / 3) if outlet == 0 else (last - a / 6, -a / 6)
+    assert np.abs(F["rho"][:, -1] - want_rho).max() < 1e-15
+    assert np.abs(F["rho"][:, -1] * F["ux"][:, -1] - want_jx).max() < 1e-16
+    assert np.abs(F["uy"]).max() < 1e-16
+
+
+def _vortex_box(nx=96, ny=48, Re=2000.0, outlet=1):
     """Laminar 96 x 48 box (inlet, symmetry planes, outlet) with a Gaussian vortex of core 5
     cells and peak swirl U/2 convected by the free stream; it reaches the outlet after ~300 steps."""
     cfg = W.base_config(levels=1, nx0=nx, ny0=ny, h0=1.0, Re=Re, periodic=0, solid_walls=1, turbulence=0,
-                        wall_model=3, Ma=0.1)
+                        wall_model=3, Ma=0.1, outlet=outlet)
     r = oracle.Solver(cfg)
     r.set_geometry([])
     U = 0.1 * math.sqrt(1.0 / 3.0)
@@ -163,9 +190,8 @@ def _vortex_box(nx=96, ny=48, Re=2000.0):
 
 def test_vortex_leaves_through_the_outlet():
     # The zero-gradient outlet lets the vortex out: after 1200 steps the disturbance keeps
-    # under 0.1% of its energy and the density is back at 1 to 1e-3.  (The linear extrapolation
-    # 2 f(N-2) - f(N-3) grows it instead: 26 times the initial energy by step 500.)
-    r, U = _vortex_box()
+    # under 0.1% of its energy and the density is back at 1 to 1e-3.
+    r, U = _vortex_box(outlet=1)
     f = r.get_fields(0)
     e0 = ((f["ux"] - U) ** 2 + f["uy"] ** 2).sum()
     r.step(1200)
@@ -186,3 +212,16 @@ def test_zou_he_inlet_imposes_the_velocity_exactly():
         assert np.abs(f["uy"][:, 1]).max() > 1e-7          # the next column is disturbed ...
         assert np.abs(f["ux"][:, 0] - U).max() < 1e-14     # ... the inlet column is not
         assert np.abs(f["uy"][:, 0]).max() < 1e-14
+
+
+def test_linear_outlet_amplifies_the_vortex():
+    # Yu's linear extrapolation, the form Sec 3.1.1 names, does not let the same vortex out:
+    # the disturbance grows past its initial energy once the vortex reaches the last columns.
+    # This is why the workloads use the zero-gradient outlet (outlet = 1).
+    r, U = _vortex_box(outlet=0)
+    f = r.get_fields(0)
+    e0 = ((f["ux"] - U) ** 2 + f["uy"] ** 2).sum()
+    r.step(500)
+    f = r.get_fields(0)
+    e = ((f["ux"] - U) ** 2 + f["uy"] ** 2).sum()
+    assert not np.isfinite(e) or e > e0
