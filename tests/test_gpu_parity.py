@@ -5,12 +5,10 @@ Integer work (level boxes, cell masks, cut-link sets, wall-record stencils) must
 bit-exact.  Field work is compared element by element over the active fluid cells
 of every level with the relative L2 bound ``TOL_FIELD`` = 1e-5 on rho, on the
 velocity vector and on chi = nu_tilde / nu, and ``TOL_LOADS`` = 1e-3 on C_L, C_D.
-The density departure rho - 1 is additionally held to ``TOL_DRHO`` relative to its
-own norm wherever its RMS exceeds 1e-5 (a hundred times the FP32 resolution of rho).
-Its error is dominated by a uniform offset: with a velocity inlet and an extrapolated
-outlet nothing restores the mean density, so the FP32 rounding of the population sums
-accumulates there (about 1e-6 in rho after 16000 finest sub-steps, against an RMS of
-rho - 1 near 7e-4 on the airfoil case).
+The density departure rho - 1 is additionally held to ``TOL_DRHO`` = 1e-3 relative to
+its own norm wherever its RMS exceeds 1e-5 (a hundred times the FP32 resolution of rho).
+On the small NACA 0012 case after its 1000-coarse-step horizon (32000 finest sub-steps)
+the FP32 path measured 9e-9 on rho, 5e-7 on u, 4e-6 on chi and 1.3e-5 on rho - 1.
 """
 import math
 
@@ -25,7 +23,7 @@ pytestmark = pytest.mark.gpu
 
 TOL_FIELD = 1e-5
 TOL_LOADS = 1e-3
-TOL_DRHO = 5e-3
+TOL_DRHO = 1e-3
 U_LAT = 0.1 * math.sqrt(1.0 / 3.0)
 
 
@@ -75,7 +73,7 @@ def assert_fields(g, r, levels, turbulent=True, tol=TOL_FIELD):
         assert e["chi"] <= tol, e
     if e["drho_rms"] > 1e-5:
         # rho - 1 well above the FP32 resolution of rho: its own relative error is meaningful
-        assert e["drho"] <= TOL_DRHO * (tol / TOL_FIELD), e
+        assert e["drho"] <= TOL_DRHO, e
     return e
 
 
@@ -337,15 +335,11 @@ def _naca_small_pair(laminar=False):
     return cfg, g, r
 
 
-# Horizons.  FP32 and FP64 trajectories separate slowly on the airfoil cases: lattice
-# viscosities near 1e-5 (tau - 1/2 ~ 5e-5) damp little, and with a velocity inlet and an
-# extrapolated outlet nothing restores the mean density, so rounding differences grow.
-# Builds that differ only in FP32 rounding (division path, momentum taken from the sums
-# or from rho * u) differ from the oracle by 1e-7 at 100 coarse steps, by 1e-6 to 3e-6
-# at 300 and by 1e-6 to 2e-5 at 1000, in an order that changes from build to build.
-# The parity bound TOL_FIELD is therefore checked at 300 coarse steps (9600 finest
-# sub-steps), and the 1000-step horizon checks the loads at TOL_LOADS and the fields at
-# 5 TOL_FIELD.
+# Horizon of the small NACA 0012 case: 1000 coarse steps (32000 finest sub-steps).  The
+# FP64 oracle does not amplify perturbations of the size of FP32 rounding on this case:
+# started from the FP32-rounded copy of the same initial state, its own trajectory stays
+# within 1e-8 (u) of the unrounded one over the whole horizon, so FP32-vs-FP64 differences
+# come from the rounding of every step and stay near 5e-7 (u) and 4e-6 (chi).
 HORIZON_STRICT = 300
 HORIZON_FULL = 1000
 
@@ -358,7 +352,7 @@ def test_naca0012_small_full_horizon():
         g.step(chunk); r.step(chunk)
         assert_fields(g, r, cfg["levels"])
     g.step(HORIZON_FULL - HORIZON_STRICT); r.step(HORIZON_FULL - HORIZON_STRICT)
-    assert_fields(g, r, cfg["levels"], tol=5 * TOL_FIELD)
+    assert_fields(g, r, cfg["levels"])
     lg, lr = g.get_loads(), r.get_loads()
     print("loads gpu", lg["CL"], lg["CD"], "oracle", lr["CL"], lr["CD"])
     assert abs(lg["CD"] - lr["CD"]) <= TOL_LOADS * abs(lr["CD"])
@@ -372,7 +366,7 @@ def test_naca0012_small_laminar_full_horizon():
     g.step(HORIZON_STRICT); r.step(HORIZON_STRICT)
     assert_fields(g, r, cfg["levels"], turbulent=False)
     g.step(HORIZON_FULL - HORIZON_STRICT); r.step(HORIZON_FULL - HORIZON_STRICT)
-    assert_fields(g, r, cfg["levels"], turbulent=False, tol=5 * TOL_FIELD)
+    assert_fields(g, r, cfg["levels"], turbulent=False)
     lg, lr = g.get_loads(), r.get_loads()
     assert abs(lg["CD"] - lr["CD"]) <= TOL_LOADS * abs(lr["CD"])
 
