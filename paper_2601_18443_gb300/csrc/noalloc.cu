@@ -8,6 +8,9 @@
 // held by every GPU that loads the library until the process exits.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "../../include/lbm.h"
 #include "layout.hpp"
 
@@ -25,8 +28,12 @@ struct NaScratch {
 
 static __device__ __align__(256) NaScratch na_scratch;
 
-// Device address of na_scratch per device ordinal, looked up once per device.
-static NaScratch *na_ptr[NA_MAX_DEVICES];
+// Device address of na_scratch per device ordinal, looked up once per device (under
+// na_mu, so that first calls from several host threads look it up once) and read
+// without a lock afterwards.  A cudaDeviceReset destroys the module instance the
+// address belongs to: the cached address is then stale.
+static std::atomic<NaScratch *> na_ptr[NA_MAX_DEVICES];
+static std::mutex na_mu;
 
 __device__ __forceinline__ double na_warp_sum(double v)
 {
@@ -104,11 +111,17 @@ extern "C" lbm_status lbm_level_mass_noalloc(const unsigned int *flags, const fl
         return LBM_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return LBM_ERR_CUDA;
-    if (!na_ptr[dev]) {
+    NaScratch *sc = na_ptr[dev].load(std::memory_order_acquire);
+    if (!sc) {
         // first call on this device: look up the device address of the scratch array
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, na_scratch) != cudaSuccess || !p) return LBM_ERR_CUDA;
-        na_ptr[dev] = (NaScratch *)p;
+        std::lock_guard<std::mutex> lock(na_mu);
+        sc = na_ptr[dev].load(std::memory_order_relaxed);
+        if (!sc) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, na_scratch) != cudaSuccess || !p) return LBM_ERR_CUDA;
+            sc = (NaScratch *)p;
+            na_ptr[dev].store(sc, std::memory_order_release);
+        }
     }
     cudaStream_t st = (cudaStream_t)stream;
     const long long per_block = (long long)NA_THREADS * NA_CELLS_PER_THREAD;
@@ -116,7 +129,7 @@ extern "C" lbm_status lbm_level_mass_noalloc(const unsigned int *flags, const fl
     if (nb < 1) nb = 1;
     const long long chunk = (n_cells + nb - 1) / nb > 0 ? (n_cells + nb - 1) / nb : 1;
     k_mass_partial<<<(unsigned)nb, NA_THREADS, 0, st>>>(flags, (const float *)drho, ux, uy, nu_tilde_ratio, n_cells,
-                                                        chunk, area, na_ptr[dev]);
-    k_mass_final<<<1, NA_THREADS, 0, st>>>(na_ptr[dev], (int)nb, mass_out, nonfinite_out);
+                                                        chunk, area, sc);
+    k_mass_final<<<1, NA_THREADS, 0, st>>>(sc, (int)nb, mass_out, nonfinite_out);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

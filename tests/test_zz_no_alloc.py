@@ -29,11 +29,16 @@ def _level_arrays(solver, level):
     return arr, int(flags.size)
 
 
-def _mass_noalloc(arrays, levels):
+def _outputs():
     import torch
 
-    out_m = torch.zeros(1, dtype=torch.float64, device="cuda")
-    out_f = torch.zeros(1, dtype=torch.int32, device="cuda")
+    return torch.zeros(1, dtype=torch.float64, device="cuda"), torch.zeros(1, dtype=torch.int32, device="cuda")
+
+
+def _mass_noalloc(arrays, levels, outs=None):
+    import torch
+
+    out_m, out_f = outs if outs is not None else _outputs()
     total, bad = 0.0, 0
     stream = torch.cuda.current_stream().cuda_stream
     for level, (a, n) in enumerate(arrays):
@@ -61,8 +66,15 @@ def test_noalloc_mass_matches_get_loads_twice():
     s.step(5)
     ref = s.get_loads()["mass"]
     arrays = [_level_arrays(s, l) for l in range(cfg["levels"])]
-    m1, b1 = _mass_noalloc(arrays, cfg["levels"])
-    m2, b2 = _mass_noalloc(arrays, cfg["levels"])
+    outs = _outputs()
+    m1, b1 = _mass_noalloc(arrays, cfg["levels"], outs)
+    # after that first call (which looks up the scratch address on this device) a call
+    # leaves the device's free memory unchanged: it allocates nothing
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    m2, b2 = _mass_noalloc(arrays, cfg["levels"], outs)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     assert b1 == 0 and b2 == 0
     # same FP64 sum of the same FP32 values, different summation order
     assert abs(m1 - ref) <= 1e-12 * ref, (m1, ref)
