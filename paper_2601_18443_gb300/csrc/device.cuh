@@ -24,9 +24,15 @@ struct LevelView {
     int n_work_tiles;
     const uint32_t *flags;        // per slot
     const float *inv_d2;          // 1 / d^2, d the wall distance in level lattice units (SA-neg)
-    const int *rec;               // wall record of a B node (finest level) or nullptr
-    void *f[2];                   // populations f - w, [q * ns + slot], two lattices (storage type: store)
+    const int *aux;               // per slot: wall record of a B node (finest level), band index of a
+                                  // band cell, 4 * (parent's band index) + child index of a ghost, or -1
+    void *f;                      // populations f - w, [d * ns + slot], one lattice in the AA layout
+                                  // (storage type: store); see the level kernel for the layout
     int store;                    // 0 FP32, 1 FP16, 2 BF16 population storage (arithmetic is FP32)
+    float *ebuf;                  // 9 per band cell: its last post-collision f - w (the explosion)
+    float *gbuf;                  // 36 per band cell: f - w its four ghost children pulled in the
+                                  // fine level's second sub-step (the coalescence)
+    int n_band;                   // band cells
     float *drho[2], *ux[2], *uy[2];  // macroscopic fields (rho - 1, u) at the two time levels
     float *chi[2];                // nu_tilde / nu at the two time levels
     float nu;                     // lattice viscosity of the level
@@ -46,6 +52,7 @@ struct RecView {
     const float *slip;            // prescribed slip per loop (wall model 2), 2 per loop
     float *drhoW, *uWx, *uWy, *utau, *chiB, *tx, *ty, *ut;
     float *utau_start;            // Newton start of the next step (written by the step only)
+    float *fpost;                 // 9 per record: post-collision f - w of the boundary node, last step
 };
 
 struct StepConsts {
@@ -60,6 +67,8 @@ struct StepConsts {
     float d_wr, d_wv;
     int sms;            // streaming multiprocessors of the device
     float pshift[9];    // 16-bit storage holds g_q - pshift_q (pshift = f_eq(1, U, 0) - w); 0 for FP32
+    float *obuf;        // level-0 outlet: [2 parities][2 columns N-1, N-2][directions 2, 6, 8][ny0]
+                        // post-collision f - w; a step at parity p reads [p] and writes [p ^ 1]
 };
 
 // device status word bits (lbm_step maps them to lbm_status codes).  TIMEOUT is reserved
@@ -69,8 +78,8 @@ struct StepConsts {
 
 // What one launch of the fused level kernel does besides the level's own update.
 struct LevelStep {
-    int p;              // time level of this level (reads [p], writes [p ^ 1])
-    int pf;             // time level of level l+1 (coalescence source, explosion target)
+    int p;              // time level of this level (reads [p], writes [p ^ 1]); also the parity of
+                        // the in-place population update (0 even, 1 odd)
     int has_child;      // level l+1 exists
     int is_level0;      // level 0 (box-edge conditions may apply)
     int wall;           // this level holds the wall records (finest level)
@@ -96,8 +105,17 @@ void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const
 void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pdl);
 void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k);
 void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pp, int pf);
-void launch_explode_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pf);
 void launch_init_feq(cudaStream_t st, const LevelView &P, const float *feq9, float U, float chi_inf);
+void launch_fill9(cudaStream_t st, float *buf, long long n, const float *g9);
+// the in-place layout <-> logical post-collision populations (f - w) of the active cells,
+// [q * ns + slot] on the device; p is the parity of the level's next step; C (gather) is
+// the parent level (ghosts report its exploded values)
+void launch_gather_post(cudaStream_t st, const LevelView &P, const LevelView *C, const RecView &R, const StepConsts &k,
+                        int p, int is_level0, float *out);
+void launch_store_post(cudaStream_t st, const LevelView &P, const RecView &R, const StepConsts &k, int p, int is_level0,
+                       const float *in);
+void launch_explode(cudaStream_t st, const LevelView &P, const LevelView &F, const RecView &R, const StepConsts &k,
+                    const float *post);
 
 struct LoadsView {
     int nseg;

@@ -433,69 +433,177 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
 }
 
 // ------------------------------------------------------------------ the fused level step
-// 16-bit storage keeps the populations relative to the free-stream equilibrium, so that
-// in most of the domain the stored values are small and their relative rounding is
-// small in absolute terms; FP32 storage keeps g = f - w itself.
-template <typename T> struct ShiftedIO {
+// Population layout (one lattice per level, updated in place; the "AA pattern").  With
+// d the storage direction of a slot and q the population it holds:
+//   before an even step (p = 0) slot (x, q) holds the population f_q arriving at x,
+//   before an odd step  (p = 1) slot (x, opp q) holds the post-collision f*_q of x.
+// An even step reads its cell's own nine slots and writes f*_q to (x, opp q).  An odd
+// step reads f*_q of the upstream cell from (x - c_q, opp q) and writes its own f*_q to
+// (x + c_q, q), the slot the downstream cell reads in the next even step.  In either
+// step each slot is read and then written by one thread only (its own cell in an even
+// step, the cell x - c_q of slot (x, q) in an odd step), so one lattice suffices.
+// Levels l >= 1 take their two sub-steps of a parent step as an even and an odd step;
+// level 0 alternates from coarse step to coarse step.
+//
+// Values that a step needs but that another thread's slot holds are kept in small side
+// buffers written by the cell that owns them:
+//   - a boundary node's last post-collision populations (R.fpost), for eq 27;
+//   - the outlet columns' post-collision populations entering from x = N (k.obuf);
+//   - a band cell's last post-collision populations (ebuf: the explosion), which its ghost
+//     children keep where their upstream cell is not fluid;
+//   - the populations each ghost child pulled in the fine level's odd sub-step (gbuf), which
+//     the band cell averages (the coalescence).
+// 16-bit storage keeps populations relative to the free-stream equilibrium, so that in
+// most of the domain the stored values are small and their relative rounding is small in
+// absolute terms; FP32 storage keeps g = f - w itself.  The shift belongs to the population
+// (q), not to the slot direction (d).
+template <typename T> struct Lat {
+    T *f;
+    int ns;
     const float *sh;
-    __device__ __forceinline__ float ld(const T *p, int q) const
+    __device__ __forceinline__ float ld(int d, int s, int q) const
     {
-        if constexpr (std::is_same<T, float>::value) return PopIO<T>::ld(p);
-        else return PopIO<T>::ld(p) + sh[q];
+        if constexpr (std::is_same<T, float>::value) return PopIO<T>::ld(f + (size_t)d * ns + s);
+        else return PopIO<T>::ld(f + (size_t)d * ns + s) + sh[q];
     }
-    __device__ __forceinline__ float ldp(const T *p, int q) const
+    __device__ __forceinline__ void st(int d, int s, int q, float v) const
     {
-        if constexpr (std::is_same<T, float>::value) return PopIO<T>::ldp(p);
-        else return PopIO<T>::ldp(p) + sh[q];
-    }
-    __device__ __forceinline__ void st(T *p, int q, float v) const
-    {
-        if constexpr (std::is_same<T, float>::value) PopIO<T>::st(p, v);
-        else PopIO<T>::st(p, v - sh[q]);
+        if constexpr (std::is_same<T, float>::value) PopIO<T>::st(f + (size_t)d * ns + s, v);
+        else PopIO<T>::st(f + (size_t)d * ns + s, v - sh[q]);
     }
 };
+
+// outlet buffer index of direction 2, 6 or 8
+__device__ __forceinline__ int obuf_m(int q) { return q == 2 ? 0 : (q == 6 ? 1 : 2); }
+
+// Post-collision populations o of an active fluid cell into the layout the next step of
+// the level reads: an even step (ODD false) keeps them in the cell's own slots, an odd
+// step sends each to the downstream cell, with the level-0 box edges (specular reflection
+// at the symmetry planes, nothing across the inlet and the outlet).  nbs / present: slots
+// at offsets +c_q and the mask of the present ones.  Boundary nodes, outlet columns and
+// band cells also fill their side buffers (the explosion is done by the caller).
+template <typename T, bool ODD>
+__device__ __forceinline__ void put_post(const Lat<T> &F, const StepConsts &k, int slot, const int nbs[9],
+                                         unsigned present, bool edge, int gi, int gj, const float o[9])
+{
+    if (!ODD) {
+#pragma unroll
+        for (int q = 0; q < 9; q++) F.st(oppq(q), slot, q, o[q]);
+    } else if (!edge) {
+        F.st(0, slot, 0, o[0]);
+#pragma unroll
+        for (int q = 1; q < 9; q++)
+            if (present >> q & 1) F.st(q, nbs[q], q, o[q]);
+    } else {
+        F.st(0, slot, 0, o[0]);
+#pragma unroll
+        for (int q = 1; q < 9; q++) {
+            const int di = gi + cxq(q), dj = gj + cyq(q);
+            if (di < 0 || di >= k.nx0) continue;                       // across the inlet or the outlet
+            if (dj >= 0 && dj < k.ny0) F.st(q, slot0(k, di, dj), q, o[q]);
+            else F.st(mirror_y(q), slot0(k, di, gj), mirror_y(q), o[q]);  // reflected at the plane
+        }
+    }
+}
+
+// Outlet side buffer (parity par): the populations 2, 6, 8 of the outlet columns N-1 and N-2
+// (flags FL_OUTLET, FL_OUTLET2) at row gj.
+__device__ __forceinline__ void put_obuf(const StepConsts &k, int par, uint32_t fl, int gj, const float o[9])
+{
+    float *ob = k.obuf + par * (6 * k.ny0) + ((fl & FL_OUTLET) ? 0 : 3 * k.ny0);
+    ob[gj] = o[2]; ob[k.ny0 + gj] = o[6]; ob[2 * k.ny0 + gj] = o[8];
+}
+
+// Explosion (Rohde, Sec 2.1) of band cell (t, lx, ly) with post-collision populations o: they
+// become those of its four ghost children, written where the fine level's next even sub-step
+// reads them (slot (g + c_q, q) for child g).  Children that are solid or have no tile relay
+// nothing, so their share of the next coalescence is this value too.
+template <typename T>
+__device__ __forceinline__ void explode_band(const LevelView &P, const LevelView &F, const StepConsts &k, int t, int lx,
+                                             int ly, uint32_t fl, int slot, const float o[9])
+{
+    const int b = __ldg(P.aux + slot);
+    float *eb = P.ebuf + b * 9;
+#pragma unroll
+    for (int q = 0; q < 9; q++) eb[q] = o[q];
+    const uint32_t sch = fl >> FL_SCH_SHIFT;
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        if (sch >> m & 1) {
+            float *gb = P.gbuf + (4 * b + m) * 9;
+#pragma unroll
+            for (int q = 0; q < 9; q++) gb[q] = o[q];
+        }
+    }
+    const int ct = P.child[t * 4 + ((2 * ly) >> 3) * 2 + ((2 * lx) >> 5)];
+    if (ct < 0) return;
+    const Lat<T> LF{static_cast<T *>(F.f), F.ns, k.pshift};
+    const int cx0 = (2 * lx) & (LBM_TX - 1), cy0 = (2 * ly) & (LBM_TY - 1);
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        const int ax = cx0 + (m & 1), ay = cy0 + (m >> 1);
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            const int nx = ax + cxq(q), ny = ay + cyq(q);
+            const int sx = nx < 0 ? 0 : (nx >= LBM_TX ? 2 : 1), sy = ny < 0 ? 0 : (ny >= LBM_TY ? 2 : 1);
+            const int tt = (sx == 1 && sy == 1) ? ct : __ldg(F.nbr + ct * 9 + dir_of3(sy * 3 + sx));
+            if (tt >= 0) LF.st(q, tt * LBM_TILE + (ny & (LBM_TY - 1)) * LBM_TX + (nx & (LBM_TX - 1)), q, o[q]);
+        }
+    }
+}
 
 // One tile of the fused level step (the body of k_level): every thread updates its cell
 // of tile t.  nb3 holds the 3 x 3 neighbour tiles of t for this warp.  The cell's flag
 // word is read here, or passed in (FL_GIVEN) when the caller has fetched it ahead.
-template <bool WALL, bool CHILD, typename T, bool FL_GIVEN>
+template <bool WALL, bool CHILD, typename T, bool ODD, bool FL_GIVEN>
 __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &F, const LevelView &C, const RecView &R,
-                                           const StepConsts &k, const LevelStep &ls, const ShiftedIO<T> &IO, int t,
-                                           int lane, int lx, int ly, const int *nb3, uint32_t fl_given)
+                                           const StepConsts &k, const LevelStep &ls, const Lat<T> &L, int t, int lane,
+                                           int lx, int ly, const int *nb3, uint32_t fl_given)
 {
     const int slot = t * LBM_TILE + ly * LBM_TX + lx;
     const uint32_t fl = FL_GIVEN ? fl_given : __ldg(P.flags + slot);
     const uint32_t kind = fl & FL_KIND_MASK;
     const bool fluid = !(fl & FL_SOLID);
-    const int ns = P.ns, p = ls.p;
-    const T *fc = static_cast<const T *>(P.f[p]);
-    T *fn = static_cast<T *>(P.f[p ^ 1]);
+    const int p = ls.p;
     bool valid = false;
     float n_dr = 0.f, n_ux = 0.f, n_uy = 0.f, n_chi = 0.f;
 
     if (kind == KIND_GHOST && fluid) {
-        // ghosts are streamed (relayed), never collided
+        // ghosts are streamed (relayed), never collided.  Even sub-step: the arriving
+        // populations stay in the cell, moved to the slots an odd step reads; odd sub-step:
+        // the pulled populations go to the parent's coalescence buffer.  Where the upstream
+        // cell is not fluid the ghost keeps its own value, the parent's exploded one.
+        const int ax = __ldg(P.aux + slot);
+        const float *eb = C.ebuf + (ax >> 2) * 9;
+        const uint32_t keep = fl >> FL_KEEP_SHIFT;
+        if (!ODD) {
+            float v[9];
+            v[0] = L.ld(0, slot, 0);
 #pragma unroll
-        for (int q = 0; q < 9; q++) {
-            const int s = q == 0 ? slot : nb_slot(nb3, lx, ly, -cxq(q), -cyq(q));
-            bool ok = false;
-            if (s >= 0) {
-                const uint32_t fs = __ldg(P.flags + s);
-                const uint32_t ks = fs & FL_KIND_MASK;
-                ok = (ks == KIND_ACTIVE || ks == KIND_GHOST) && !(fs & FL_SOLID);
+            for (int q = 1; q < 9; q++) v[q] = (keep >> (q - 1) & 1) ? eb[q] : L.ld(q, slot, q);
+#pragma unroll
+            for (int q = 0; q < 9; q++) L.st(oppq(q), slot, q, v[q]);
+        } else {
+            float *gb = C.gbuf + ax * 9;
+            gb[0] = L.ld(0, slot, 0);
+#pragma unroll
+            for (int q = 1; q < 9; q++) {
+                const int s = nb_slot(nb3, lx, ly, -cxq(q), -cyq(q));
+                gb[q] = (keep >> (q - 1) & 1) || s < 0 ? eb[q] : L.ld(oppq(q), s, q);
             }
-            IO.st(fn + q * ns + slot, q, IO.ld(fc + q * ns + (ok ? s : slot), q));
         }
     } else if (kind == KIND_ACTIVE && fluid) {
         const bool edge = ls.is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
         const bool bnode = WALL && (fl & FL_BNODE);
         int nbs[9];
-        neighbours(nb3, lx, ly, slot, nbs);
+        const unsigned present = neighbours(nb3, lx, ly, slot, nbs);
+        int gi = 0, gj = 0;
+        if (edge) { gi = P.tile_x[t] * LBM_TX + lx; gj = P.tile_y[t] * LBM_TY + ly; }
         // ---- wall function of the boundary node (Sec 2.3), fields at time t
         float drW = 0.f, uWx = 0.f, uWy = 0.f, chiB = 0.f;
         int r = -1;
         if (bnode) {
-            r = P.rec[slot];
+            r = __ldg(P.aux + slot);
             wall_record(P, p, R, k, r, true, drW, uWx, uWy, chiB);
         }
         // ---- SA-neg update of chi (Sec 2.2), fields at time t
@@ -504,14 +612,13 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
             if (bnode) {
                 chin = chiB;                                        // Dirichlet nu_t~_B (Sec 2.2)
             } else if (edge) {
-                const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
                 if (fl & FL_INLET) {
                     chin = k.chi_inf;
                 } else {
-                    const int ic = (fl & FL_OUTLET) ? k.nx0 - 2 : i;     // outlet: copy of its neighbour
+                    const int ic = (fl & FL_OUTLET) ? k.nx0 - 2 : gi;     // outlet: copy of its neighbour
                     Stencil S;
-                    gather0(P.chi[p], P.ux[p], P.uy[p], k, ic, j, S);
-                    chin = sa_update(S, P.inv_d2[slot0(k, ic, j)], P.nu, k.sa_convection);
+                    gather0(P.chi[p], P.ux[p], P.uy[p], k, ic, gj, S);
+                    chin = sa_update(S, P.inv_d2[slot0(k, ic, gj)], P.nu, k.sa_convection);
                 }
             } else {
                 Stencil S;
@@ -526,58 +633,62 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         } else {
             chin = __ldg(P.chi[p] + slot);
         }
-        // ---- pull streaming (eq 1) with coalescence, cut links and box edges
+        // ---- streaming (eq 1): the populations arriving at the cell
         float g[9];
-        g[0] = IO.ld(fc + slot, 0);
-        const uint32_t special = fl & (0xFFu << FL_COAL_SHIFT | 0xFFu << FL_CUT_SHIFT);
-        if (!edge && !special) {
-            // plain cell: every direction is pulled from its upstream neighbour
+        g[0] = L.ld(0, slot, 0);
+        if (!ODD) {
 #pragma unroll
-            for (int q = 1; q < 9; q++) g[q] = IO.ld(fc + q * ns + nbs[oppq(q)], q);
+            for (int q = 1; q < 9; q++) g[q] = L.ld(q, slot, q);
         } else if (!edge) {
-            int cb = -1;
-            if (CHILD && (fl & FL_BAND)) cb = child_base(P, t, lx, ly);
 #pragma unroll
-            for (int q = 1; q < 9; q++) {
-                if (CHILD && (fl & (1u << (FL_COAL_SHIFT + q - 1)))) {
-                    // coalescence: mean of the four ghost children after the two fine sub-steps
-                    const T *ff = static_cast<const T *>(F.f[ls.pf]) + q * F.ns;
-                    g[q] = cb >= 0 ? 0.25f * (IO.ldp(ff + cb, q) + IO.ldp(ff + cb + 1, q) + IO.ldp(ff + cb + LBM_TX, q) +
-                                              IO.ldp(ff + cb + LBM_TX + 1, q))
-                                   : IO.ld(fc + q * ns + slot, q);
-                } else if (WALL && (fl & (1u << (FL_CUT_SHIFT + q - 1)))) {
-                    // Yu interpolated bounce-back with the slip velocity of the wall record (eq 27)
-                    const int qo = oppq(q);
-                    const float qf = R.q[r * 9 + q];
-                    const float mom = 6.0f * wq(q) * (1.0f + drW) * (cxq(q) * uWx + cyq(q) * uWy);
-                    const int sf = nbs[q];
-                    bool ok = false;
-                    if (sf != slot) {
-                        const uint32_t ff = __ldg(P.flags + sf);
-                        ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
-                    }
-                    if (ok)
-                        g[q] = ((1.0f - qf) * IO.ld(fc + qo * ns + sf, qo) + qf * IO.ld(fc + qo * ns + slot, qo) + mom) /
-                                   (1.0f + qf) +
-                               qf / (1.0f + qf) * IO.ld(fc + q * ns + slot, q);
-                    else
-                        g[q] = IO.ld(fc + qo * ns + slot, qo) + mom;        // half-way form, eq 24
-                } else {
-                    g[q] = IO.ld(fc + q * ns + nbs[oppq(q)], q);
-                }
-            }
+            for (int q = 1; q < 9; q++) g[q] = L.ld(oppq(q), nbs[oppq(q)], q);
         } else {
-            // level-0 box edge: in-box pulls, symmetry planes, Zou-He inlet, zero-gradient outlet (Sec 3.1.1)
-            const int i = P.tile_x[t] * LBM_TX + lx, j = P.tile_y[t] * LBM_TY + ly;
+            // level-0 box edge: in-box pulls and the symmetry planes' reflections
 #pragma unroll
             for (int q = 1; q < 9; q++) {
-                const int si = i - cxq(q), sj = j - cyq(q);
+                const int si = gi - cxq(q), sj = gj - cyq(q);
                 const bool xin = si >= 0 && si < k.nx0, yin = sj >= 0 && sj < k.ny0;
-                if (xin && yin) g[q] = IO.ld(fc + q * ns + slot0(k, si, sj), q);
-                else if (xin) g[q] = IO.ld(fc + mirror_y(q) * ns + slot0(k, si, j), mirror_y(q));
+                if (xin && yin) g[q] = L.ld(oppq(q), slot0(k, si, sj), q);
+                else if (xin) g[q] = L.ld(oppq(mirror_y(q)), slot0(k, si, gj), mirror_y(q));
                 else g[q] = 0.0f;
             }
-            if (i == 0) {
+        }
+        const uint32_t special = fl & (0xFFu << FL_COAL_SHIFT | 0xFFu << FL_CUT_SHIFT);
+        if (CHILD && (fl & (0xFFu << FL_COAL_SHIFT))) {
+            // coalescence: mean of what the four ghost children pulled in the fine level's odd sub-step
+            const float *gb = P.gbuf + __ldg(P.aux + slot) * 36;
+#pragma unroll
+            for (int q = 1; q < 9; q++)
+                if (fl & (1u << (FL_COAL_SHIFT + q - 1)))
+                    g[q] = 0.25f * (gb[q] + gb[9 + q] + gb[18 + q] + gb[27 + q]);
+        }
+        if (WALL && bnode && special) {
+            // Yu's interpolated bounce-back with the slip velocity of the wall record (eq 27): the
+            // next fluid node's f*_qo arrives at B as its own f_qo; f*_q(B) and f*_qo(B) of the last
+            // step come from the record's buffer
+            const float *fp = R.fpost + r * 9;
+            float gin[9];
+#pragma unroll
+            for (int q = 0; q < 9; q++) gin[q] = g[q];
+#pragma unroll
+            for (int q = 1; q < 9; q++) {
+                if (!(fl & (1u << (FL_CUT_SHIFT + q - 1)))) continue;
+                const int qo = oppq(q);
+                const float qf = R.q[r * 9 + q];
+                const float mom = 6.0f * wq(q) * (1.0f + drW) * (cxq(q) * uWx + cyq(q) * uWy);
+                const int sf = nbs[q];
+                bool ok = false;
+                if (sf != slot) {
+                    const uint32_t ff = __ldg(P.flags + sf);
+                    ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
+                }
+                if (ok) g[q] = ((1.0f - qf) * gin[qo] + qf * fp[qo] + mom) / (1.0f + qf) + qf / (1.0f + qf) * fp[q];
+                else g[q] = fp[qo] + mom;                               // half-way form, eq 24
+            }
+        }
+        if (edge) {
+            if (gi == 0) {
+                // Zou-He velocity inlet (Sec 3.1.1)
                 const float U = k.U;
                 const float S = g[0] + g[3] + g[4] + 2.0f * (g[2] + g[6] + g[8]);   // sum of w over these is 1
                 const float rho = (1.0f + S) / (1.0f - U);
@@ -585,19 +696,20 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
                 g[5] = g[6] - 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
                 g[7] = g[8] + 0.5f * (g[3] - g[4]) + rho * U * (1.0f / 6.0f);
             }
-            if (i == k.nx0 - 1) {
+            if (gi == k.nx0 - 1) {
                 // outlet, for the directions 2, 6, 8 entering from outside, on the post-stream
-                // values of the columns N-2 and N-3 (in-box pull or symmetry reflection):
+                // values of the columns N-2 and N-3 (the post-collision values of the columns
+                // N-1 and N-2 one row up or down, or reflected at a symmetry plane):
                 // Yu's linear extrapolation 2 g_q(N-2) - g_q(N-3), or the zero-gradient copy g_q(N-2)
+                const float *ob = k.obuf + p * (6 * k.ny0);
 #pragma unroll
                 for (int m = 0; m < 3; m++) {
                     const int q = m == 0 ? 2 : (m == 1 ? 6 : 8);
-                    const int sj = j - cyq(q);
+                    const int sj = gj - cyq(q);
                     const bool yin = sj >= 0 && sj < k.ny0;
-                    const int qs = yin ? q : mirror_y(q), js = yin ? sj : j;
-                    const float g2 = IO.ld(fc + qs * ns + slot0(k, k.nx0 - 1, js), qs);    // source of N-2
-                    g[q] = g2;
-                    if (k.outlet == 0) g[q] = 2.0f * g2 - IO.ld(fc + qs * ns + slot0(k, k.nx0 - 2, js), qs);
+                    const int ms = obuf_m(yin ? q : mirror_y(q)), js = yin ? sj : gj;
+                    const float g2 = ob[ms * k.ny0 + js];
+                    g[q] = k.outlet == 0 ? 2.0f * g2 - ob[(3 + ms) * k.ny0 + js] : g2;
                 }
             }
         }
@@ -610,20 +722,15 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         P.drho[p ^ 1][slot] = drho; P.ux[p ^ 1][slot] = ux; P.uy[p ^ 1][slot] = uy;
         float o[9];
         collide_cm(g, drho, jx, jy, ux, uy, delta_of(P.nu, chin, k.turbulence), o);
+        put_post<T, ODD>(L, k, slot, nbs, present, edge, gi, gj, o);
+        if (bnode) {
+            float *fp = R.fpost + r * 9;
 #pragma unroll
-        for (int q = 0; q < 9; q++) IO.st(fn + q * ns + slot, q, o[q]);
-        if (CHILD && (fl & FL_BAND)) {
-            // explosion: post-collision populations copied to the four ghost children
-            const int cb = child_base(P, t, lx, ly);
-            if (cb >= 0) {
-#pragma unroll
-                for (int q = 0; q < 9; q++) {
-                    T *ff = static_cast<T *>(F.f[ls.pf]) + q * F.ns;
-                    IO.st(ff + cb, q, o[q]); IO.st(ff + cb + 1, q, o[q]);
-                    IO.st(ff + cb + LBM_TX, q, o[q]); IO.st(ff + cb + LBM_TX + 1, q, o[q]);
-                }
-            }
+            for (int q = 0; q < 9; q++) fp[q] = o[q];
         }
+        if (ls.is_level0 && k.level0_edges && (fl & (FL_OUTLET | FL_OUTLET2)))
+            put_obuf(k, p ^ 1, fl, P.tile_y[t] * LBM_TY + ly, o);
+        if (CHILD && (fl & FL_BAND)) explode_band<T>(P, F, k, t, lx, ly, fl, slot, o);
         valid = true;
         n_dr = drho; n_ux = ux; n_uy = uy; n_chi = chin;
     }
@@ -663,12 +770,12 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
 // strides over the level's work tiles instead of one block per tile.  Both are picked
 // per level by the autotuner.  Every variant computes bit-identical results (larger
 // budgets, 3 or 4 blocks, were measured to round differently and to run no faster, and
-// are not offered).
-template <bool WALL, bool CHILD, typename T, int MINB, bool PERSIST>
+// are not offered).  ODD: the parity of the in-place population update.
+template <bool WALL, bool CHILD, typename T, int MINB, bool PERSIST, bool ODD>
 __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, LevelView C, RecView R, StepConsts k,
                                                       LevelStep ls)
 {
-    const ShiftedIO<T> IO{k.pshift};
+    const Lat<T> L{static_cast<T *>(P.f), P.ns, k.pshift};
     __shared__ int nb3w[LBM_TILE / 32][9];       // one copy per warp: no block-wide barrier
     const int c = threadIdx.x;
     const int lane = c & 31;
@@ -681,7 +788,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
         __syncwarp();
         griddep_launch();
         griddep_wait();
-        level_tile<WALL, CHILD, T, false>(P, F, C, R, k, ls, IO, t, lane, lx, ly, nb3, 0u);
+        level_tile<WALL, CHILD, T, ODD, false>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, 0u);
     } else {
         // the grid tables are static: the first tile's neighbour table and flag word are
         // read before the wait, and each tile's flag word one tile ahead
@@ -706,7 +813,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
                 if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
                 __syncwarp();
             }
-            level_tile<WALL, CHILD, T, true>(P, F, C, R, k, ls, IO, t, lane, lx, ly, nb3, fl);
+            level_tile<WALL, CHILD, T, ODD, true>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, fl);
         }
     }
 
@@ -781,8 +888,61 @@ __global__ void k_restrict(LevelView P, LevelView F, int pp, int pf)
     P.chi[pp][slot] = sc / n;
 }
 
+// Logical post-collision populations (f - w, unshifted) of the active fluid cells of a level
+// whose next step has parity p, gathered from the in-place layout into out[q * ns + slot]:
+// the inverse of put_post.  Values the layout does not keep (populations leaving across the
+// inlet or the outlet, or towards a cell without a tile; no step reads them) are NaN.
+// Boundary nodes come from their record buffer; ghosts report their parent's exploded values.
 template <typename T>
-__global__ void k_explode_prolong(LevelView P, LevelView F, int p, int pf)
+__global__ void k_gather_post(LevelView P, LevelView C, RecView R, StepConsts k, int p, int is_level0, float *out)
+{
+    __shared__ int nb3[9];
+    const int t = blockIdx.x, c = threadIdx.x;
+    const int lx = c & 31, ly = c >> 5;
+    load_nb3(P, t, nb3);
+    __syncthreads();
+    const int slot = t * LBM_TILE + c;
+    const Lat<T> L{static_cast<T *>(P.f), P.ns, k.pshift};
+    const uint32_t fl = P.flags[slot];
+    const uint32_t kind = fl & FL_KIND_MASK;
+    float o[9];
+    for (int q = 0; q < 9; q++) o[q] = NAN;
+    if (kind == KIND_GHOST && !(fl & FL_SOLID)) {
+        const float *eb = C.ebuf + (P.aux[slot] >> 2) * 9;
+        for (int q = 0; q < 9; q++) o[q] = eb[q];
+    } else if (kind == KIND_ACTIVE && !(fl & FL_SOLID)) {
+        if (R.n > 0 && (fl & FL_BNODE) && P.aux) {
+            const float *fp = R.fpost + P.aux[slot] * 9;
+            for (int q = 0; q < 9; q++) o[q] = fp[q];
+        } else if (p == 1) {
+            for (int q = 0; q < 9; q++) o[q] = L.ld(oppq(q), slot, q);
+        } else {
+            int nbs[9];
+            const unsigned present = neighbours(nb3, lx, ly, slot, nbs);
+            o[0] = L.ld(0, slot, 0);
+            const bool edge = is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
+            const int gi = P.tile_x[t] * LBM_TX + lx, gj = P.tile_y[t] * LBM_TY + ly;
+            for (int q = 1; q < 9; q++) {
+                if (!edge) {
+                    if (present >> q & 1) o[q] = L.ld(q, nbs[q], q);
+                } else {
+                    const int di = gi + cxq(q), dj = gj + cyq(q);
+                    if (di < 0 || di >= k.nx0) continue;
+                    if (dj >= 0 && dj < k.ny0) o[q] = L.ld(q, slot0(k, di, dj), q);
+                    else o[q] = L.ld(mirror_y(q), slot0(k, di, gj), mirror_y(q));
+                }
+            }
+        }
+    }
+    for (int q = 0; q < 9; q++) out[(size_t)q * P.ns + slot] = o[q];
+}
+
+// Store logical post-collision populations in[q * ns + slot] (f - w) of the active fluid
+// cells of a level whose next step has parity p into the in-place layout, the record
+// buffers of boundary nodes and the outlet buffer (put_post's writes).  Ghost slots are left
+// to the explosion.
+template <typename T>
+__global__ void k_store_post(LevelView P, RecView R, StepConsts k, int p, int is_level0, const float *in)
 {
     __shared__ int nb3[9];
     const int t = blockIdx.x, c = threadIdx.x;
@@ -791,29 +951,41 @@ __global__ void k_explode_prolong(LevelView P, LevelView F, int p, int pf)
     __syncthreads();
     const int slot = t * LBM_TILE + c;
     const uint32_t fl = P.flags[slot];
-    if ((fl & FL_KIND_MASK) != KIND_ACTIVE || (fl & FL_SOLID) || !(fl & FL_BAND)) return;
-    const int cb = child_base(P, t, lx, ly);
-    if (cb < 0) return;
-    Stencil S;
-    gather(nb3, P.chi[p], P.ux[p], P.uy[p], lx, ly, slot, S);
-    float gcx, gcy, gux, guy, gvx, gvy;
-    lsq_grad(S.chi, gcx, gcy); lsq_grad(S.ux, gux, guy); lsq_grad(S.uy, gvx, gvy);
-    for (int m = 0; m < 4; m++) {
-        const int a = m & 1, b = m >> 1;
-        const float ox = 0.5f * (a - 0.5f), oy = 0.5f * (b - 0.5f);
-        const int cs = cb + b * LBM_TX + a;
-        const float vc = S.chi[0] + gcx * ox + gcy * oy;
-        const float vu = S.ux[0] + gux * ox + guy * oy;
-        const float vv = S.uy[0] + gvx * ox + gvy * oy;
-        for (int h = 0; h < 2; h++) {
-            F.chi[h][cs] = vc; F.ux[h][cs] = vu; F.uy[h][cs] = vv; F.drho[h][cs] = P.drho[p][slot];
-        }
-        for (int q = 0; q < 9; q++)
-            static_cast<T *>(F.f[pf])[q * F.ns + cs] = static_cast<const T *>(P.f[p])[q * P.ns + slot];
+    if ((fl & FL_KIND_MASK) != KIND_ACTIVE || (fl & FL_SOLID)) return;
+    const Lat<T> L{static_cast<T *>(P.f), P.ns, k.pshift};
+    float o[9];
+    for (int q = 0; q < 9; q++) o[q] = in[(size_t)q * P.ns + slot];
+    int nbs[9];
+    const unsigned present = neighbours(nb3, lx, ly, slot, nbs);
+    const bool edge = is_level0 && k.level0_edges && (fl & (FL_INLET | FL_OUTLET | FL_BOTTOM | FL_TOP));
+    const int gi = P.tile_x[t] * LBM_TX + lx, gj = P.tile_y[t] * LBM_TY + ly;
+    if (p == 0) put_post<T, true>(L, k, slot, nbs, present, edge, gi, gj, o);
+    else put_post<T, false>(L, k, slot, nbs, present, edge, gi, gj, o);
+    if (R.n > 0 && (fl & FL_BNODE) && P.aux) {
+        float *fp = R.fpost + P.aux[slot] * 9;
+        for (int q = 0; q < 9; q++) fp[q] = o[q];
     }
+    if (is_level0 && k.level0_edges && (fl & (FL_OUTLET | FL_OUTLET2))) put_obuf(k, p, fl, gj, o);
 }
 
-struct Feq9 { float g[9]; };   // values to store (already relative to the storage shift)
+// explosion of every band cell of P into the ghosts of F from logical post-collision
+// populations post[q * ns + slot] of P
+template <typename T>
+__global__ void k_explode(LevelView P, LevelView F, StepConsts k, const float *post)
+{
+    const int t = blockIdx.x, c = threadIdx.x;
+    const int lx = c & 31, ly = c >> 5;
+    const int slot = t * LBM_TILE + c;
+    const uint32_t fl = P.flags[slot];
+    if ((fl & FL_KIND_MASK) != KIND_ACTIVE || (fl & FL_SOLID) || !(fl & FL_BAND)) return;
+    float o[9];
+    for (int q = 0; q < 9; q++) o[q] = post[(size_t)q * P.ns + slot];
+    explode_band<T>(P, F, k, t, lx, ly, fl, slot, o);
+}
+
+// rest state: every present cell's populations are e (values to store, relative to the
+// storage shift), its fields rho = 1, u = (U, 0), chi = chi_inf
+struct Feq9 { float g[9]; };
 
 template <typename T>
 __global__ void k_init(LevelView P, Feq9 e, float U, float chi_inf)
@@ -821,17 +993,20 @@ __global__ void k_init(LevelView P, Feq9 e, float U, float chi_inf)
     const int slot = blockIdx.x * LBM_TILE + threadIdx.x;
     const uint32_t fl = P.flags[slot];
     const bool present = (fl & FL_KIND_MASK) != KIND_ABSENT;
-    for (int q = 0; q < 9; q++) {
-        const float v = present ? e.g[q] : 0.0f;
-        PopIO<T>::st(static_cast<T *>(P.f[0]) + q * P.ns + slot, v);
-        PopIO<T>::st(static_cast<T *>(P.f[1]) + q * P.ns + slot, v);
-    }
+    for (int q = 0; q < 9; q++) PopIO<T>::st(static_cast<T *>(P.f) + (size_t)q * P.ns + slot, present ? e.g[q] : 0.0f);
     for (int h = 0; h < 2; h++) {
         P.drho[h][slot] = 0.0f;
         P.ux[h][slot] = present ? U : 0.0f;
         P.uy[h][slot] = 0.0f;
         P.chi[h][slot] = chi_inf;
     }
+}
+
+// n groups of nine values g (side buffers at rest)
+__global__ void k_fill9(float *buf, long long n, Feq9 g)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 9 * n) buf[i] = g.g[i % 9];
 }
 
 // ------------------------------------------------------------------ FP64 reductions
@@ -923,28 +1098,36 @@ static void launch_pdl(void (*kern)(Args...), unsigned grid, cudaStream_t st, in
 }
 
 // the level holding the wall records is the finest one, which has no child level
-template <typename T, int MINB, bool PERSIST>
+template <typename T, int MINB, bool PERSIST, bool ODD>
 static void launch_level_mb(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
                             const RecView &R, const StepConsts &k, const LevelStep &ls, int pdl)
 {
     // persistent: two rounds of the resident blocks stride over the work tiles
     const unsigned grid = PERSIST ? (unsigned)std::min(P.n_work_tiles, 2 * k.sms * MINB) : (unsigned)P.n_work_tiles;
-    if (ls.wall) launch_pdl(k_level<true, false, T, MINB, PERSIST>, grid, st, pdl, P, Fv, Cv, R, k, ls);
-    else if (child) launch_pdl(k_level<false, true, T, MINB, PERSIST>, grid, st, pdl, P, Fv, Cv, R, k, ls);
-    else launch_pdl(k_level<false, false, T, MINB, PERSIST>, grid, st, pdl, P, Fv, Cv, R, k, ls);
+    if (ls.wall) launch_pdl(k_level<true, false, T, MINB, PERSIST, ODD>, grid, st, pdl, P, Fv, Cv, R, k, ls);
+    else if (child) launch_pdl(k_level<false, true, T, MINB, PERSIST, ODD>, grid, st, pdl, P, Fv, Cv, R, k, ls);
+    else launch_pdl(k_level<false, false, T, MINB, PERSIST, ODD>, grid, st, pdl, P, Fv, Cv, R, k, ls);
 }
 
-template <typename T>
+template <typename T, bool ODD>
 static void launch_level_t(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
                            const RecView &R, const StepConsts &k, const LevelStep &ls, const LevelTune &tu)
 {
     if (tu.min_blocks == 6) {
-        if (tu.persistent) launch_level_mb<T, 6, true>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
-        else launch_level_mb<T, 6, false>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        if (tu.persistent) launch_level_mb<T, 6, true, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        else launch_level_mb<T, 6, false, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
     } else {
-        if (tu.persistent) launch_level_mb<T, 5, true>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
-        else launch_level_mb<T, 5, false>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        if (tu.persistent) launch_level_mb<T, 5, true, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        else launch_level_mb<T, 5, false, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
     }
+}
+
+template <typename T>
+static void launch_level_p(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
+                           const RecView &R, const StepConsts &k, const LevelStep &ls, const LevelTune &tu)
+{
+    if (ls.p) launch_level_t<T, true>(st, P, Fv, Cv, child, R, k, ls, tu);
+    else launch_level_t<T, false>(st, P, Fv, Cv, child, R, k, ls, tu);
 }
 
 void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,
@@ -953,9 +1136,9 @@ void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const
     const LevelView Fv = F ? *F : P, Cv = C ? *C : P;
     if (P.n_work_tiles <= 0) return;
     switch (P.store) {
-    case 1: launch_level_t<__half>(st, P, Fv, Cv, F != nullptr, R, k, ls, tu); break;
-    case 2: launch_level_t<__nv_bfloat16>(st, P, Fv, Cv, F != nullptr, R, k, ls, tu); break;
-    default: launch_level_t<float>(st, P, Fv, Cv, F != nullptr, R, k, ls, tu); break;
+    case 1: launch_level_p<__half>(st, P, Fv, Cv, F != nullptr, R, k, ls, tu); break;
+    case 2: launch_level_p<__nv_bfloat16>(st, P, Fv, Cv, F != nullptr, R, k, ls, tu); break;
+    default: launch_level_p<float>(st, P, Fv, Cv, F != nullptr, R, k, ls, tu); break;
     }
 }
 
@@ -975,13 +1158,42 @@ void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, in
     k_restrict<<<P.ntiles, LBM_TILE, 0, st>>>(P, F, pp, pf);
 }
 
-void launch_explode_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pf)
+template <typename T>
+static void launch_aa_util(int what, cudaStream_t st, const LevelView &P, const LevelView &Q, const RecView &R,
+                           const StepConsts &k, int p, int is_level0, float *buf)
 {
+    if (what == 0) k_gather_post<T><<<P.ntiles, LBM_TILE, 0, st>>>(P, Q, R, k, p, is_level0, buf);
+    else if (what == 1) k_store_post<T><<<P.ntiles, LBM_TILE, 0, st>>>(P, R, k, p, is_level0, buf);
+    else k_explode<T><<<P.ntiles, LBM_TILE, 0, st>>>(P, Q, k, buf);
+}
+
+static void launch_aa(int what, cudaStream_t st, const LevelView &P, const LevelView &Q, const RecView &R,
+                      const StepConsts &k, int p, int is_level0, float *buf)
+{
+    if (P.ntiles <= 0) return;
     switch (P.store) {
-    case 1: k_explode_prolong<__half><<<P.ntiles, LBM_TILE, 0, st>>>(P, F, p, pf); break;
-    case 2: k_explode_prolong<__nv_bfloat16><<<P.ntiles, LBM_TILE, 0, st>>>(P, F, p, pf); break;
-    default: k_explode_prolong<float><<<P.ntiles, LBM_TILE, 0, st>>>(P, F, p, pf); break;
+    case 1: launch_aa_util<__half>(what, st, P, Q, R, k, p, is_level0, buf); break;
+    case 2: launch_aa_util<__nv_bfloat16>(what, st, P, Q, R, k, p, is_level0, buf); break;
+    default: launch_aa_util<float>(what, st, P, Q, R, k, p, is_level0, buf); break;
     }
+}
+
+void launch_gather_post(cudaStream_t st, const LevelView &P, const LevelView *C, const RecView &R, const StepConsts &k,
+                        int p, int is_level0, float *out)
+{
+    launch_aa(0, st, P, C ? *C : P, R, k, p, is_level0, out);
+}
+
+void launch_store_post(cudaStream_t st, const LevelView &P, const RecView &R, const StepConsts &k, int p, int is_level0,
+                       const float *in)
+{
+    launch_aa(1, st, P, P, R, k, p, is_level0, const_cast<float *>(in));
+}
+
+void launch_explode(cudaStream_t st, const LevelView &P, const LevelView &F, const RecView &R, const StepConsts &k,
+                    const float *post)
+{
+    launch_aa(2, st, P, F, R, k, 0, 0, const_cast<float *>(post));
 }
 
 void launch_init_feq(cudaStream_t st, const LevelView &P, const float *feq9, float U, float chi_inf)
@@ -993,6 +1205,14 @@ void launch_init_feq(cudaStream_t st, const LevelView &P, const float *feq9, flo
     case 2: k_init<__nv_bfloat16><<<P.ntiles, LBM_TILE, 0, st>>>(P, e, U, chi_inf); break;
     default: k_init<float><<<P.ntiles, LBM_TILE, 0, st>>>(P, e, U, chi_inf); break;
     }
+}
+
+void launch_fill9(cudaStream_t st, float *buf, long long n, const float *g9)
+{
+    if (n <= 0) return;
+    Feq9 e;
+    for (int q = 0; q < 9; q++) e.g[q] = g9[q];
+    k_fill9<<<(unsigned)((9 * n + 255) / 256), 256, 0, st>>>(buf, n, e);
 }
 
 void launch_loads(cudaStream_t st, const LoadsView &S, const RecView &R, float U, double *acc4)

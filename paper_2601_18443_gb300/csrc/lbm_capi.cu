@@ -39,14 +39,6 @@ void feq_shifted(double rho, double ux, double uy, float *g)
 // bytes of one stored population: FP32, FP16 or BF16
 size_t pop_bytes(int store) { return store == 0 ? 4 : 2; }
 
-// store one population value (rounded to nearest) into a host copy of a lattice
-void put_pop(int store, unsigned char *base, size_t idx, float v)
-{
-    if (store == 1) reinterpret_cast<__half *>(base)[idx] = __float2half_rn(v);
-    else if (store == 2) reinterpret_cast<__nv_bfloat16 *>(base)[idx] = __float2bfloat16_rn(v);
-    else reinterpret_cast<float *>(base)[idx] = v;
-}
-
 // Step 1 of Sec 2.3 as fixed linear combinations of the stencil values, from the static
 // geometry of a wall record: rho_R = sum wr_m rho_m with inverse-distance weights 1/d^2
 // (normalised), u_R = sum wu_m u_m with wu the intercept row of the unweighted linear
@@ -173,6 +165,24 @@ static void *dalloc(lbm_solver *s, size_t bytes)
     return p;
 }
 
+// device scratch of a host utility (queries, set_fields): through the caller's allocator
+// when given, freed before the call returns
+static void *tmp_alloc(lbm_solver *s, size_t bytes)
+{
+    void *p = nullptr;
+    if (s->cfg.dev_alloc) p = s->cfg.dev_alloc(bytes, (void *)s->stream, s->cfg.alloc_ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    return p;
+}
+
+static void tmp_free(lbm_solver *s, void *p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(s->stream);
+    if (s->cfg.dev_free) s->cfg.dev_free(p, (void *)s->stream, s->cfg.alloc_ctx);
+    else cudaFree(p);
+}
+
 static void free_all(lbm_solver *s)
 {
     if (s->planning) {
@@ -253,7 +263,6 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     }
     lbmdev::LevelStep ls;
     ls.p = s->parity[l];
-    ls.pf = F ? s->parity[l + 1] : 0;
     ls.has_child = F != nullptr;
     ls.is_level0 = l == 0;
     ls.wall = (l == L - 1) && s->rec.n > 0;
@@ -428,6 +437,29 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     if (rc != 0) return fail(s, (lbm_status)rc, msg);
     const int L = s->L;
     bool ok = true;
+    // band indices (the explosion and coalescence buffers of each level with a finer one):
+    // band cells in row-major order of the level's box
+    std::vector<std::vector<int>> bidx(L);
+    std::vector<int> n_band(L, 0);
+    for (int l = 0; l + 1 < L; l++) {
+        const lbmgrid::Level &G = s->g.lv[l];
+        bidx[l].assign(G.kind.size(), -1);
+        std::vector<int> row(G.bny + 1, 0);
+#pragma omp parallel for schedule(static)
+        for (int r = 0; r < G.bny; r++) {
+            int n = 0;
+            for (int q = 0; q < G.bnx; q++) n += G.band[(size_t)r * G.bnx + q] != 0;
+            row[r + 1] = n;
+        }
+        for (int r = 0; r < G.bny; r++) row[r + 1] += row[r];
+#pragma omp parallel for schedule(static)
+        for (int r = 0; r < G.bny; r++) {
+            int n = row[r];
+            for (int q = 0; q < G.bnx; q++)
+                if (G.band[(size_t)r * G.bnx + q]) bidx[l][(size_t)r * G.bnx + q] = n++;
+        }
+        n_band[l] = row[G.bny];
+    }
     // per-level flag words and device arrays
     for (int l = 0; l < L; l++) {
         lbmgrid::Level &G = s->g.lv[l];
@@ -436,7 +468,9 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         if (9 * ns >= (1LL << 31)) { free_all(s); return fail(s, LBM_ERR_INVALID_ARG, "level too large for 32-bit slot indices"); }
         H.flags.assign(ns, 0);
         std::vector<float> inv_d2(ns, 0.f);
-        std::vector<int> rec(l == L - 1 ? ns : 1, -1);
+        std::vector<int> aux(ns, -1);
+        const lbmgrid::Level *Gc = l > 0 ? &s->g.lv[l - 1] : nullptr;
+        const lbmgrid::Level *Gf = l + 1 < L ? &s->g.lv[l + 1] : nullptr;
         // every slot is written by the thread of its tile
 #pragma omp parallel for schedule(static)
         for (int t = 0; t < G.ntiles; t++)
@@ -444,29 +478,66 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
                 long long i = (long long)G.tile_x[t] * LBM_TX + (c2 & 31), j = (long long)G.tile_y[t] * LBM_TY + (c2 >> 5);
                 long b = G.idx(i, j);
                 if (b < 0 || G.kind[b] == KIND_ABSENT) continue;
+                long long sl = (long long)t * LBM_TILE + c2;
                 uint32_t f = G.kind[b];
                 if (G.solid[b]) f |= FL_SOLID;
                 if (G.band[b]) f |= FL_BAND;
                 if (G.bnode[b]) f |= FL_BNODE;
-                for (int d = 1; d < 9; d++) {
+                for (int d = 1; d < 9; d++)
                     if (G.coal[b] >> d & 1) f |= 1u << (FL_COAL_SHIFT + d - 1);
-                    if (G.cut[b] >> d & 1) f |= 1u << (FL_CUT_SHIFT + d - 1);
+                if (G.kind[b] == KIND_GHOST) {
+                    // the ghost keeps its own value along d where the upstream cell is not an
+                    // active or ghost fluid cell; aux: the parent's band index and the child index
+                    for (int d = 1; d < 9; d++) {
+                        const long u = G.idx(i - CXh[d], j - CYh[d]);
+                        const bool flows = u >= 0 && !G.solid[u] && (G.kind[u] == KIND_ACTIVE || G.kind[u] == KIND_GHOST);
+                        if (!flows) f |= 1u << (FL_KEEP_SHIFT + d - 1);
+                    }
+                    const long pc = Gc->idx(i >> 1, j >> 1);
+                    aux[sl] = 4 * bidx[l - 1][pc] + (int)(((j & 1) << 1) | (i & 1));
+                } else {
+                    for (int d = 1; d < 9; d++)
+                        if (G.cut[b] >> d & 1) f |= 1u << (FL_CUT_SHIFT + d - 1);
                 }
+                if (G.band[b] && Gf) {
+                    // band cell: its index, and which children are solid or have no tile
+                    aux[sl] = bidx[l][b];
+                    for (int m = 0; m < 4; m++) {
+                        const long long fi = 2 * i + (m & 1), fj = 2 * j + (m >> 1);
+                        const long fc = Gf->idx(fi, fj);
+                        if (Gf->slot(fi, fj) < 0 || fc < 0 || Gf->solid[fc]) f |= 1u << (FL_SCH_SHIFT + m);
+                    }
+                }
+                if (l == L - 1 && G.bnode[b]) aux[sl] = G.rec[b];
                 if (l == 0 && !c.periodic) {
                     if (i == 0) f |= FL_INLET;
                     if (i == c.nx0 - 1) f |= FL_OUTLET;
+                    if (i == c.nx0 - 2) f |= FL_OUTLET2;
                     if (j == 0) f |= FL_BOTTOM;
                     if (j == c.ny0 - 1) f |= FL_TOP;
                 }
-                long long sl = (long long)t * LBM_TILE + c2;
                 H.flags[sl] = f;
                 // SA-neg sees d >= 1/2 (level units): a fluid node closer to the wall than that
                 // lies beside a wall sliver thinner than the lattice (a sharp trailing edge
                 // between nodes), where d -> 0 makes the explicit destruction term unstable
                 const double dsa = G.dist[b] > 0.5 ? (double)G.dist[b] : 0.5;
                 inv_d2[sl] = (float)(1.0 / (dsa * dsa));
-                if (l == L - 1) rec[sl] = G.rec[b];
             }
+        // every index the kernels follow from aux stays inside its buffer
+        {
+            const int nr = (int)s->g.recs.size();
+            bool bad = false;
+#pragma omp parallel for schedule(static) reduction(|| : bad)
+            for (long long sl = 0; sl < ns; sl++) {
+                const uint32_t f = H.flags[sl];
+                const uint32_t kd = f & FL_KIND_MASK;
+                const int a = aux[sl];
+                if (kd == KIND_GHOST && !(f & FL_SOLID)) bad = bad || a < 0 || l == 0 || (a >> 2) >= n_band[l - 1];
+                if ((f & FL_BAND) && l + 1 < L) bad = bad || a < 0 || a >= n_band[l];
+                if ((f & FL_BNODE) && l == L - 1) bad = bad || a < 0 || a >= nr;
+            }
+            if (bad) { free_all(s); return fail(s, LBM_ERR_GEOMETRY, "internal: inconsistent band or record index"); }
+        }
         LevelView &v = H.v;
         v.ntiles = G.ntiles;
         v.ns = (int)ns;
@@ -482,15 +553,20 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.n_work_tiles = (int)G.work_tiles.size();
         v.flags = upload(s, H.flags, ok);
         v.inv_d2 = upload(s, inv_d2, ok);
-        v.rec = (l == L - 1) ? upload(s, rec, ok) : nullptr;
+        v.aux = upload(s, aux, ok);
+        v.f = dalloc(s, 9 * ns * pop_bytes(c.store));
+        ok = ok && v.f;
         for (int b = 0; b < 2; b++) {
-            v.f[b] = dalloc(s, 9 * ns * pop_bytes(c.store));
             v.chi[b] = (float *)dalloc(s, ns * sizeof(float));
             v.drho[b] = (float *)dalloc(s, ns * sizeof(float));
             v.ux[b] = (float *)dalloc(s, ns * sizeof(float));
             v.uy[b] = (float *)dalloc(s, ns * sizeof(float));
-            ok = ok && v.f[b] && v.chi[b] && v.drho[b] && v.ux[b] && v.uy[b];
+            ok = ok && v.chi[b] && v.drho[b] && v.ux[b] && v.uy[b];
         }
+        v.n_band = n_band[l];
+        v.ebuf = (float *)dalloc(s, 9 * (size_t)std::max(n_band[l], 1) * sizeof(float));
+        v.gbuf = (float *)dalloc(s, 36 * (size_t)std::max(n_band[l], 1) * sizeof(float));
+        ok = ok && v.ebuf && v.gbuf;
         v.nu = (float)(s->U * (c.chord / c.h0) * (double)(1LL << l) / c.Re);
         v.store = c.store;
         if (!ok) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
@@ -533,7 +609,9 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.slip = s->d_slip;
         float **outs[9] = {&v.drhoW, &v.uWx, &v.uWy, &v.utau, &v.chiB, &v.tx, &v.ty, &v.ut, &v.utau_start};
         for (auto o : outs) { *o = (float *)dalloc(s, (size_t)std::max(nr, 1) * sizeof(float)); ok = ok && *o; }
-        if (!ok || !s->d_slip) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
+        v.fpost = (float *)dalloc(s, 9 * (size_t)std::max(nr, 1) * sizeof(float));
+        s->k.obuf = (float *)dalloc(s, 12 * (size_t)c.ny0 * sizeof(float));
+        if (!ok || !s->d_slip || !v.fpost || !s->k.obuf) { free_all(s); return fail(s, LBM_ERR_OOM, "device allocation failed"); }
         if (!s->planning) {
             CK(cudaMemsetAsync(s->d_slip, 0, 2 * (size_t)std::max(n_loops, 1) * sizeof(float), s->stream));
             for (auto o : outs) CK(cudaMemsetAsync(*o, 0, (size_t)std::max(nr, 1) * sizeof(float), s->stream));
@@ -589,7 +667,21 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
     for (int q = 0; q < 9; q++) s->k.pshift[q] = c.store != 0 ? g9[q] : 0.0f;
     float st9[9];
     for (int q = 0; q < 9; q++) st9[q] = g9[q] - s->k.pshift[q];
-    for (int l = 0; l < L; l++) lbmdev::launch_init_feq(s->stream, s->lv[l].v, st9, (float)s->U, (float)c.chi_inf);
+    for (int l = 0; l < L; l++) {
+        lbmdev::launch_init_feq(s->stream, s->lv[l].v, st9, (float)s->U, (float)c.chi_inf);
+        lbmdev::launch_fill9(s->stream, s->lv[l].v.ebuf, s->lv[l].v.n_band, g9);
+        lbmdev::launch_fill9(s->stream, s->lv[l].v.gbuf, 4LL * s->lv[l].v.n_band, g9);
+    }
+    lbmdev::launch_fill9(s->stream, s->rec.fpost, s->rec.n, g9);
+    {
+        // outlet buffer at rest: [parity][column][direction 2, 6, 8][row]
+        std::vector<float> ob(12 * (size_t)c.ny0);
+        for (int b = 0; b < 4; b++)
+            for (int m = 0; m < 3; m++)
+                for (int j = 0; j < c.ny0; j++) ob[((size_t)b * 3 + m) * c.ny0 + j] = g9[m == 0 ? 2 : (m == 1 ? 6 : 8)];
+        CK(cudaMemcpyAsync(s->k.obuf, ob.data(), ob.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
     for (int l = 0; l < LBM_MAXL; l++) s->parity[l] = 0;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
@@ -777,12 +869,20 @@ lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, dou
     return LBM_OK;
 }
 
-// one stored population of a host copy of a lattice, as f - w (storage shift undone)
-static double get_pop(int store, const unsigned char *base, size_t idx)
+// logical post-collision populations f - w of a level's cells, [q * ns + slot] on the host
+static lbm_status gather_post(lbm_solver *s, int l, std::vector<float> &out)
 {
-    if (store == 1) return (double)__half2float(reinterpret_cast<const __half *>(base)[idx]);
-    if (store == 2) return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(base)[idx]);
-    return (double)reinterpret_cast<const float *>(base)[idx];
+    const LevelView &v = s->lv[l].v;
+    const size_t n = 9 * (size_t)v.ns;
+    float *d = (float *)tmp_alloc(s, n * sizeof(float));
+    if (!d) return fail(s, LBM_ERR_OOM, "device allocation failed (query scratch)");
+    lbmdev::launch_gather_post(s->stream, v, l > 0 ? &s->lv[l - 1].v : nullptr, s->rec, s->k, s->parity[l], l == 0, d);
+    out.resize(n);
+    cudaError_t e = cudaMemcpyAsync(out.data(), d, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    tmp_free(s, d);
+    if (e != cudaSuccess) return cuda_fail(s, e, "gather_post");
+    return LBM_OK;
 }
 
 lbm_status lbm_get_populations(lbm_solver *s, int level, double *pop, long long cap)
@@ -794,10 +894,8 @@ lbm_status lbm_get_populations(lbm_solver *s, int level, double *pop, long long 
     const long long ncell = (long long)nx * ny;
     if (!pop || 9 * ncell > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
     const LevelView &v = s->lv[level].v;
-    const size_t pb = pop_bytes(s->cfg.store);
-    std::vector<unsigned char> f(9 * (size_t)v.ns * pb);
-    CK(cudaMemcpyAsync(f.data(), v.f[s->parity[level]], f.size(), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
+    std::vector<float> f;
+    if ((st = gather_post(s, level, f)) != LBM_OK) return st;
     const lbmgrid::Level &G = s->g.lv[level];
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
@@ -805,10 +903,8 @@ lbm_status lbm_get_populations(lbm_solver *s, int level, double *pop, long long 
             const long sl = G.slot(i0 + i, j0 + j);
             const unsigned char m = mask_of(G, b);
             const bool has = sl >= 0 && (m == 1 || m == 2 || m == 4);
-            for (int q = 0; q < 9; q++) {
-                const double g = has ? get_pop(s->cfg.store, f.data(), (size_t)q * v.ns + sl) + s->k.pshift[q] : NAN;
-                pop[q * ncell + (long long)j * nx + i] = has ? g + WQh[q] : NAN;
-            }
+            for (int q = 0; q < 9; q++)
+                pop[q * ncell + (long long)j * nx + i] = has ? (double)f[(size_t)q * v.ns + sl] + WQh[q] : NAN;
         }
     return LBM_OK;
 }
@@ -854,14 +950,11 @@ lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const dou
     if (st != LBM_OK) return st;
     const LevelView &v = s->lv[level].v;
     const int p = s->parity[level];
-    const size_t pb = pop_bytes(s->cfg.store);
-    std::vector<float> dr, u, w, c2, c3(v.ns);
-    std::vector<unsigned char> f(9 * (size_t)v.ns * pb);
+    std::vector<float> dr, u, w, c2, c3(v.ns), post;
     st = download_level(s, level, dr, u, w, c2);
     if (st != LBM_OK) return st;
     CK(cudaMemcpyAsync(c3.data(), v.chi[p ^ 1], v.ns * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(f.data(), v.f[p], f.size(), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
+    if ((st = gather_post(s, level, post)) != LBM_OK) return st;
     const lbmgrid::Level &G = s->g.lv[level];
     const std::vector<uint32_t> &fl = s->lv[level].flags;
     for (int j = 0; j < ny; j++)
@@ -878,20 +971,34 @@ lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const dou
             if (chi) { c2[sl] = (float)chi[o]; c3[sl] = (float)chi[o]; }
             float g9[9];
             feq_shifted(r, a, b, g9);
-            for (int q = 0; q < 9; q++) put_pop(s->cfg.store, f.data(), (size_t)q * v.ns + sl, g9[q] - s->k.pshift[q]);
+            for (int q = 0; q < 9; q++) post[(size_t)q * v.ns + sl] = g9[q];
         }
     CK(cudaMemcpyAsync(v.drho[p], dr.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.ux[p], u.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.uy[p], w.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.chi[p], c2.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(v.chi[p ^ 1], c3.data(), v.ns * sizeof(float), cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(v.f[p], f.data(), f.size(), cudaMemcpyHostToDevice, s->stream));
-    // re-synchronise the interfaces: restriction bottom-up, then explosion and ghost reconstruction
-    for (int l = s->L - 2; l >= 0; l--)
-        lbmdev::launch_restrict(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], s->parity[l + 1]);
-    for (int l = 0; l < s->L - 1; l++)
-        lbmdev::launch_explode_prolong(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], s->parity[l + 1]);
-    CK(cudaGetLastError());
+    size_t ns_max = 0;
+    for (int l = 0; l < s->L; l++) ns_max = std::max(ns_max, (size_t)s->lv[l].v.ns);
+    float *d = (float *)tmp_alloc(s, 9 * ns_max * sizeof(float));
+    if (!d) return fail(s, LBM_ERR_OOM, "device allocation failed (set_fields scratch)");
+    cudaError_t e = cudaMemcpyAsync(d, post.data(), post.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) {
+        lbmdev::launch_store_post(s->stream, v, s->rec, s->k, p, level == 0, d);
+        // re-synchronise the interfaces: restriction bottom-up, then explosion and ghost
+        // reconstruction top-down
+        for (int l = s->L - 2; l >= 0; l--)
+            lbmdev::launch_restrict(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], s->parity[l + 1]);
+        for (int l = 0; l < s->L - 1; l++) {
+            lbmdev::launch_gather_post(s->stream, s->lv[l].v, l > 0 ? &s->lv[l - 1].v : nullptr, s->rec, s->k, s->parity[l],
+                                       l == 0, d);
+            lbmdev::launch_explode(s->stream, s->lv[l].v, s->lv[l + 1].v, s->rec, s->k, d);
+            lbmdev::launch_prolong(s->stream, s->lv[l].v, s->lv[l + 1].v, s->parity[l], 0);
+        }
+        e = cudaGetLastError();
+    }
+    tmp_free(s, d);
+    if (e != cudaSuccess) return cuda_fail(s, e, "set_fields");
     CK(cudaStreamSynchronize(s->stream));
     return LBM_OK;
 }
@@ -1216,8 +1323,9 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
 
 // ---------------------------------------------------------------- checkpoint / resume
 struct StateHeader {
-    char magic[8];                 // "LBMSTAT2"
+    char magic[8];                 // "LBMSTAT3"
     int levels, store, turbulence, have_cl;
+    int parity0, pad;              // level-0 parity of the in-place layout (finer levels are at 0)
     long long step, nrec;
     double last_cl;
     long long ns[LBM_MAXL];
@@ -1254,12 +1362,33 @@ static unsigned long long cfg_hash(const lbm_solver *s)
     return f.h;
 }
 
-static size_t state_bytes(const lbm_solver *s)
+// the raw device arrays of a checkpoint, in blob order: per level the lattice, the fields of
+// the current time level and the explosion / coalescence buffers; then the wall records'
+// Newton starts and post-collision buffers and the outlet buffer
+static void state_arrays(lbm_solver *s, std::vector<std::pair<void *, size_t>> &a)
 {
-    size_t n = sizeof(StateHeader);
     const size_t pb = pop_bytes(s->cfg.store);
-    for (int l = 0; l < s->L; l++) n += (size_t)s->lv[l].v.ns * (9 * pb + 4 * sizeof(float));
-    return n + (size_t)s->rec.n * sizeof(float);
+    for (int l = 0; l < s->L; l++) {
+        LevelView &v = s->lv[l].v;
+        const int p = s->parity[l];
+        const size_t nm = (size_t)v.ns * sizeof(float);
+        a.push_back({v.f, 9 * (size_t)v.ns * pb});
+        a.push_back({v.drho[p], nm}); a.push_back({v.ux[p], nm}); a.push_back({v.uy[p], nm}); a.push_back({v.chi[p], nm});
+        a.push_back({v.ebuf, 9 * (size_t)v.n_band * sizeof(float)});
+        a.push_back({v.gbuf, 36 * (size_t)v.n_band * sizeof(float)});
+    }
+    a.push_back({s->rec.utau_start, (size_t)s->rec.n * sizeof(float)});
+    a.push_back({s->rec.fpost, 9 * (size_t)s->rec.n * sizeof(float)});
+    a.push_back({s->k.obuf, 12 * (size_t)s->cfg.ny0 * sizeof(float)});
+}
+
+static size_t state_bytes(lbm_solver *s)
+{
+    std::vector<std::pair<void *, size_t>> a;
+    state_arrays(s, a);
+    size_t n = sizeof(StateHeader);
+    for (auto &x : a) n += x.second;
+    return n;
 }
 
 lbm_status lbm_get_state(lbm_solver *s, void *buf, size_t cap, size_t *size)
@@ -1272,8 +1401,9 @@ lbm_status lbm_get_state(lbm_solver *s, void *buf, size_t cap, size_t *size)
     CK(cudaStreamSynchronize(s->stream));
     StateHeader h;
     std::memset(&h, 0, sizeof h);
-    std::memcpy(h.magic, "LBMSTAT2", 8);
+    std::memcpy(h.magic, "LBMSTAT3", 8);
     h.levels = s->L; h.store = s->cfg.store; h.turbulence = s->cfg.turbulence; h.have_cl = s->have_cl;
+    h.parity0 = s->parity[0];
     h.step = s->step; h.nrec = s->rec.n; h.last_cl = s->last_cl;
     for (int l = 0; l < s->L; l++) h.ns[l] = s->lv[l].v.ns;
     h.grid_hash = grid_hash(s);
@@ -1281,16 +1411,12 @@ lbm_status lbm_get_state(lbm_solver *s, void *buf, size_t cap, size_t *size)
     unsigned char *o = (unsigned char *)buf;
     std::memcpy(o, &h, sizeof h);
     o += sizeof h;
-    const size_t pb = pop_bytes(s->cfg.store);
-    for (int l = 0; l < s->L; l++) {
-        const LevelView &v = s->lv[l].v;
-        const int p = s->parity[l];
-        const size_t nf = 9 * (size_t)v.ns * pb, nm = (size_t)v.ns * sizeof(float);
-        CK(cudaMemcpyAsync(o, v.f[p], nf, cudaMemcpyDeviceToHost, s->stream)); o += nf;
-        const float *m[4] = {v.drho[p], v.ux[p], v.uy[p], v.chi[p]};
-        for (const float *a : m) { CK(cudaMemcpyAsync(o, a, nm, cudaMemcpyDeviceToHost, s->stream)); o += nm; }
+    std::vector<std::pair<void *, size_t>> a;
+    state_arrays(s, a);
+    for (auto &x : a) {
+        if (x.second) CK(cudaMemcpyAsync(o, x.first, x.second, cudaMemcpyDeviceToHost, s->stream));
+        o += x.second;
     }
-    if (s->rec.n > 0) CK(cudaMemcpyAsync(o, s->rec.utau_start, (size_t)s->rec.n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return LBM_OK;
 }
@@ -1302,25 +1428,24 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     StateHeader h;
     if (size < sizeof h) return fail(s, LBM_ERR_INVALID_ARG, "state blob too short");
     std::memcpy(&h, buf, sizeof h);
-    if (std::memcmp(h.magic, "LBMSTAT2", 8) != 0) return fail(s, LBM_ERR_INVALID_ARG, "not a state blob");
-    bool same = h.levels == s->L && h.store == s->cfg.store && h.turbulence == s->cfg.turbulence && h.nrec == s->rec.n;
+    if (std::memcmp(h.magic, "LBMSTAT3", 8) != 0) return fail(s, LBM_ERR_INVALID_ARG, "not a state blob");
+    bool same = h.levels == s->L && h.store == s->cfg.store && h.turbulence == s->cfg.turbulence && h.nrec == s->rec.n &&
+                (h.parity0 == 0 || h.parity0 == 1);
     for (int l = 0; same && l < s->L; l++) same = h.ns[l] == s->lv[l].v.ns;
     if (!same || h.grid_hash != grid_hash(s)) return fail(s, LBM_ERR_INVALID_ARG, "state blob from another configuration or grid");
     if (h.cfg_hash != cfg_hash(s))
         return fail(s, LBM_ERR_INVALID_ARG, "state blob from a solve with other physical or model parameters");
     if (size != state_bytes(s)) return fail(s, LBM_ERR_INVALID_ARG, "state blob size differs");
-    const unsigned char *o = (const unsigned char *)buf + sizeof h;
-    const size_t pb = pop_bytes(s->cfg.store);
     CK(cudaStreamSynchronize(s->stream));
-    for (int l = 0; l < s->L; l++) {
-        LevelView &v = s->lv[l].v;
-        const int p = s->parity[l];
-        const size_t nf = 9 * (size_t)v.ns * pb, nm = (size_t)v.ns * sizeof(float);
-        CK(cudaMemcpyAsync(v.f[p], o, nf, cudaMemcpyHostToDevice, s->stream)); o += nf;
-        float *m[4] = {v.drho[p], v.ux[p], v.uy[p], v.chi[p]};
-        for (float *a : m) { CK(cudaMemcpyAsync(a, o, nm, cudaMemcpyHostToDevice, s->stream)); o += nm; }
+    // the blob's level-0 parity becomes the solver's (the step graphs exist for both parities)
+    s->parity[0] = h.parity0;
+    const unsigned char *o = (const unsigned char *)buf + sizeof h;
+    std::vector<std::pair<void *, size_t>> a;
+    state_arrays(s, a);
+    for (auto &x : a) {
+        if (x.second) CK(cudaMemcpyAsync(x.first, o, x.second, cudaMemcpyHostToDevice, s->stream));
+        o += x.second;
     }
-    if (s->rec.n > 0) CK(cudaMemcpyAsync(s->rec.utau_start, o, (size_t)s->rec.n * sizeof(float), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->step = h.step;

@@ -1,7 +1,15 @@
-"""lbm_autotune on the GPU: its choices are valid, and the tuned solve stays bit-identical
-to an untuned one (every launch variant computes the same numbers), both through the
-eager timing steps of all candidates and through the recaptured step graphs; and each
-variant set directly gives the same populations as the default."""
+"""lbm_autotune on the GPU: its choices are valid, and the tuned solve computes the same
+numbers as an untuned one, both through the eager timing steps of all candidates and
+through the recaptured step graphs; and each variant set directly gives the same
+populations as the default.
+
+"The same numbers" is up to FP32 rounding: the variants run the same source, but the
+compiler schedules (and contracts into FMAs) the wall-level arithmetic differently under
+the 40- and 48-register budgets and the persistent loop, which shows as differences near
+1e-8 in the populations.  Programmatic dependent launch changes nothing, and one variant
+run twice is bitwise identical.  The bound POP_TOL is a hundred times that rounding; with
+16-bit storage such a difference can move a stored value by one unit in its last place
+(about 1e-5 at the magnitudes stored), hence POP_TOL_16."""
 import numpy as np
 import pytest
 
@@ -9,6 +17,17 @@ import paper_2601_18443_gb300 as pkg
 from paper_2601_18443_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-6
+POP_TOL_16 = 1e-4
+
+
+def same_populations(a, b, L, tol=POP_TOL):
+    for l in range(L):
+        x, y = a.get_populations(l), b.get_populations(l)
+        assert np.array_equal(np.isnan(x), np.isnan(y)), l
+        d = np.nanmax(np.abs(x - y)) if np.isfinite(x).any() else 0.0
+        assert d <= tol, (l, d)
 
 
 @pytest.mark.parametrize("store", [0, 1])
@@ -30,15 +49,17 @@ def test_autotuned_solve_equals_the_default_one(store):
     assert all(m in (5, 6) for m in rep["min_blocks"]) and rep["pdl"] in (0, 1)
     assert all(t > 0 for ts in rep["level_us"].values() for t in ts)
     assert rep["default_step_us"] > 0 and min(rep["step_us"].values()) > 0
+    tol = POP_TOL if store == 0 else POP_TOL_16
     a.step(rep["steps_taken"])
-    for l in range(L):
-        assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), l
+    same_populations(a, b, L, tol)
     a.step(25)
     b.step(25)
-    for l in range(L):
-        assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), l
+    same_populations(a, b, L, tol)
     la, lb = a.coefficients(), b.coefficients()
-    assert la["step"] == lb["step"] and abs(la["CL"] - lb["CL"]) < 1e-12
+    assert la["step"] == lb["step"]
+    assert abs(la["CD"] - lb["CD"]) <= 1e-5 * abs(la["CD"])
+    # alpha = 0 on a symmetric section: C_L is near zero, compare against the drag scale
+    assert abs(la["CL"] - lb["CL"]) <= 1e-4 * max(abs(la["CL"]), abs(la["CD"]))
 
 
 @pytest.mark.parametrize("mb,pdl,pe", [(6, 1, 0), (5, 0, 0), (6, 0, 1), (5, 1, 1), (6, 1, 1)])
@@ -52,12 +73,24 @@ def test_each_launch_variant_computes_the_same_numbers(mb, pdl, pe):
     b.set_launch_variant([mb] * L, pdl, [pe] * L)
     a.step(6)
     b.step(6)
-    for l in range(L):
-        assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), l
+    same_populations(a, b, L)
     with pytest.raises(pkg.LBMError):
         b.set_launch_variant([4] * L, 1)
     # queries in between leave the trajectory alone
     a.coefficients(); b.coefficients()
     a.step(3); b.step(3)
-    for l in range(L):
-        assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), l
+    same_populations(a, b, L)
+
+
+def test_a_variant_run_twice_is_bitwise_identical():
+    pkg.build()
+    cfg, loops = W.naca0012_small(levels=5)
+    L = cfg["levels"]
+    for mb, pe in ((5, 0), (6, 1)):
+        a, b = pkg.Solver(cfg), pkg.Solver(cfg)
+        for s in (a, b):
+            s.set_geometry(loops)
+            s.set_launch_variant([mb] * L, 1, [pe] * L)
+            s.step(7)
+        for l in range(L):
+            assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), (mb, pe, l)

@@ -1,6 +1,6 @@
 """Checkpoint and resume through the C ABI: a solve restored from lbm_get_state, into a new
-solver or into the same one (rewind), continues bit for bit; blobs from another grid or
-configuration are rejected."""
+solver or into the same one (rewind), continues bit for bit; blobs from another grid,
+storage precision or set of physical parameters are rejected."""
 import numpy as np
 import pytest
 
@@ -61,3 +61,22 @@ def test_state_from_another_grid_is_rejected():
     d.set_geometry(loops)
     with pytest.raises(pkg.LBMError):
         d.set_state(blob)                      # other storage precision
+
+
+@pytest.mark.parametrize("change", [dict(Re=2.0e6), dict(Ma=0.12), dict(chi_inf=4.0), dict(outlet=0),
+                                    dict(sa_convection=1), dict(d_wv=0.9)])
+def test_state_from_other_physical_parameters_is_rejected(change):
+    # the same grid (identical flag words) but another Reynolds or Mach number, inlet
+    # nu_tilde, outlet form, SA convection or virtual-node distance: the blob is refused
+    pkg.build()
+    cfg, loops = W.naca0012_small(levels=4)
+    a = pkg.Solver(cfg)
+    a.set_geometry(loops)
+    a.step(2)
+    blob = a.get_state()
+    b = pkg.Solver(dict(cfg, **change))
+    b.set_geometry(loops)
+    with pytest.raises(pkg.LBMError) as e:
+        b.set_state(blob)
+    assert e.value.code == -1
+    a.set_state(blob)                          # the same configuration still accepts it

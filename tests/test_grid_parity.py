@@ -225,19 +225,40 @@ def test_flag_words_encode_the_tables(name):
             want |= np.where(hit & (band == 1), 1 << (d - 1), 0)
         assert np.array_equal(coal[seen], want[seen]), l
         assert np.all(coal[band == 0] == 0)
-        # cut links: finest level only, as listed by lbm_get_cut_links
-        cut = (f >> 13) & 0xFF
+        # bits 13..20: cut links of boundary nodes (finest level only, as listed by
+        # lbm_get_cut_links); on ghosts, the directions whose upstream cell is not an active or
+        # ghost fluid cell (the ghost keeps its own value there); on band cells, the children
+        # (b * 2 + a) that are solid or have no slot on the next level
+        hi = (f >> 13) & 0xFF
         want = np.zeros((ny, nx), dtype=np.int64)
         if l == L - 1:
             for i, j, d in ijd:
                 want[j - j0, i - i0] |= 1 << (d - 1)
-        assert np.array_equal(cut, want), l
-        # level-0 edges of a box with domain boundaries
-        edges = (f >> 21) & 0xF
+        ghost = kind == 3
+        S = np.ones((ny + 2, nx + 2), dtype=bool)
+        S[1:-1, 1:-1] = solid == 1
+        flows = ((K == 1) | (K == 3)) & ~S
+        for d in range(1, 9):
+            up = flows[1 - CY[d]:1 - CY[d] + ny, 1 - CX[d]:1 - CX[d] + nx]
+            want |= np.where(ghost & ~up, 1 << (d - 1), 0)
+        if l < L - 1:
+            fi0, fj0, fnx, fny = g.level_box(l + 1)
+            ff = g.flags(l + 1).astype(np.int64)
+            fm = g.mask(l + 1)
+            for j, i in zip(*np.nonzero(band == 1)):
+                for m_ in range(4):
+                    ci, cj = 2 * (i + i0) + (m_ & 1) - fi0, 2 * (j + j0) + (m_ >> 1) - fj0
+                    inside = 0 <= ci < fnx and 0 <= cj < fny
+                    if not inside or ff[cj, ci] == 0 or fm[cj, ci] == 5:
+                        want[j, i] |= 1 << m_
+        assert np.array_equal(hi, want), l
+        # level-0 edges of a box with domain boundaries, and the column before the outlet
+        edges = (f >> 21) & 0x1F
         if l == 0 and not cfg.get("periodic"):
             I, J = np.meshgrid(np.arange(i0, i0 + nx), np.arange(j0, j0 + ny))
             pres = kind != 0
-            want = ((I == 0) * 1 + (I == cfg["nx0"] - 1) * 2 + (J == 0) * 4 + (J == cfg["ny0"] - 1) * 8) * pres
+            want = ((I == 0) * 1 + (I == cfg["nx0"] - 1) * 2 + (J == 0) * 4 + (J == cfg["ny0"] - 1) * 8 +
+                    (I == cfg["nx0"] - 2) * 16) * pres
             assert np.array_equal(edges, want)
         else:
             assert np.all(edges == 0)
