@@ -55,11 +55,14 @@ def test_autotuned_solve_equals_the_default_one(store):
     a.step(25)
     b.step(25)
     same_populations(a, b, L, tol)
+    # loads: FP32 rounding differences stay near 1e-6 in C_D; one-ulp differences of 16-bit
+    # storage reach the 16-bit error level itself (C_D within 5e-4 to 4e-3 of the oracle)
+    ltol = 1e-5 if store == 0 else 1e-2
     la, lb = a.coefficients(), b.coefficients()
     assert la["step"] == lb["step"]
-    assert abs(la["CD"] - lb["CD"]) <= 1e-5 * abs(la["CD"])
+    assert abs(la["CD"] - lb["CD"]) <= ltol * abs(la["CD"])
     # alpha = 0 on a symmetric section: C_L is near zero, compare against the drag scale
-    assert abs(la["CL"] - lb["CL"]) <= 1e-4 * max(abs(la["CL"]), abs(la["CD"]))
+    assert abs(la["CL"] - lb["CL"]) <= 10 * ltol * max(abs(la["CL"]), abs(la["CD"]))
 
 
 @pytest.mark.parametrize("mb,pdl,pe", [(6, 1, 0), (5, 0, 0), (6, 0, 1), (5, 1, 1), (6, 1, 1)])
