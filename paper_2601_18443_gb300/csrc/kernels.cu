@@ -322,7 +322,7 @@ __device__ float sa_update(const Stencil &S, float id2, float nu, int conv)
     // the diffusion's diagonal at the new time level (point-implicit): the explicit increment
     // divided by 1 + sum_f D_f / sigma; unconditionally stable diffusion, same steady states
     const float a = nu * (De + Dw + Dn + Ds) * (1.0f / SA_SIGMA);
-    return chi + (cv + src + diff) / (1.0f + a);
+    return chi + __fdividef(cv + src + diff, 1.0f + a);
 }
 
 // ------------------------------------------------------------------ wall function (Sec 2.3 steps 1-5)
@@ -457,19 +457,20 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
 // most of the domain the stored values are small and their relative rounding is small in
 // absolute terms; FP32 storage keeps g = f - w itself.  The shift belongs to the population
 // (q), not to the slot direction (d).
+// Slot (d, s) is element d * ns + s: a 32-bit index, since the host keeps 9 ns below 2^31.
 template <typename T> struct Lat {
     T *f;
     int ns;
     const float *sh;
     __device__ __forceinline__ float ld(int d, int s, int q) const
     {
-        if constexpr (std::is_same<T, float>::value) return PopIO<T>::ld(f + (size_t)d * ns + s);
-        else return PopIO<T>::ld(f + (size_t)d * ns + s) + sh[q];
+        if constexpr (std::is_same<T, float>::value) return PopIO<T>::ld(f + (d * ns + s));
+        else return PopIO<T>::ld(f + (d * ns + s)) + sh[q];
     }
     __device__ __forceinline__ void st(int d, int s, int q, float v) const
     {
-        if constexpr (std::is_same<T, float>::value) PopIO<T>::st(f + (size_t)d * ns + s, v);
-        else PopIO<T>::st(f + (size_t)d * ns + s, v - sh[q]);
+        if constexpr (std::is_same<T, float>::value) PopIO<T>::st(f + (d * ns + s), v);
+        else PopIO<T>::st(f + (d * ns + s), v - sh[q]);
     }
 };
 
@@ -717,7 +718,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         const float drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
         const float jx = g[1] - g[2] + g[5] - g[6] + g[7] - g[8];
         const float jy = g[3] - g[4] + g[5] - g[6] - g[7] + g[8];
-        const float irho = 1.0f / (1.0f + drho);
+        const float irho = __fdividef(1.0f, 1.0f + drho);
         const float ux = jx * irho, uy = jy * irho;
         P.drho[p ^ 1][slot] = drho; P.ux[p ^ 1][slot] = ux; P.uy[p ^ 1][slot] = uy;
         float o[9];
