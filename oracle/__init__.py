@@ -94,6 +94,12 @@ def lib():
             L.oracle_sa_source.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
             L.oracle_sa_update_point.argtypes = [dp, dp, dp, C.c_double, C.c_double, C.c_int]
             L.oracle_sa_convection.argtypes = [dp, C.c_double, C.c_double, C.c_int]
+            L.oracle_wall_point.argtypes = [C.POINTER(Config), C.c_double, C.c_int, dp, dp, dp, dp, dp, dp, C.c_double,
+                                            dp, dp]
+            L.oracle_wall_point.restype = None
+            L.oracle_yu_link.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_double, C.c_int]
+            L.oracle_yu_link.restype = C.c_double
             L.oracle_sa_convection.restype = C.c_double
             L.oracle_sa_update_point.restype = C.c_double
             _lib = L
@@ -150,6 +156,24 @@ def sa_update_point(chi9, ux9, uy9, d, nu, convection=0):
 def sa_convection(nt9, u, v, scheme=0):
     a = np.ascontiguousarray(nt9, dtype=np.float64)
     return lib().oracle_sa_convection(_dp(a), float(u), float(v), int(scheme))
+
+
+def wall_point(cfg, nu, dx, dy, rho, ux, uy, n, dwb, slip=(0.0, 0.0)):
+    """Wall state of one boundary node from its stencil (Sec 2.3 steps 1-5): rho_W, u_W
+    (2), u_tau, chi_B, t (2), |u_Rt|; dx, dy: stencil cell centres relative to R."""
+    c = Config()
+    for name, _ in Config._fields_:
+        setattr(c, name, cfg.get(name, 0))
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (dx, dy, rho, ux, uy, n, slip)]
+    out = np.zeros(8)
+    lib().oracle_wall_point(C.byref(c), float(nu), len(a[0]), *[_dp(x) for x in a[:6]], float(dwb), _dp(a[6]), _dp(out))
+    return out
+
+
+def yu_link(q, qf, rhoW, uWx, uWy, f_qo_next, f_qo_B, f_q_B, next_fluid):
+    """Yu's interpolated slip bounce-back for pulled direction q (eq 27, eq 24 fallback)."""
+    return lib().oracle_yu_link(int(q), float(qf), float(rhoW), float(uWx), float(uWy), float(f_qo_next),
+                                float(f_qo_B), float(f_q_B), int(bool(next_fluid)))
 
 
 # --- solver ------------------------------------------------------------------

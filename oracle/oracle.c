@@ -986,6 +986,82 @@ static void init_state(oracle_solver *s)
  * Wall function per boundary node (Sec 2.3 steps 1-5, eq 28)
  * ========================================================================= */
 
+/* Wall state of one boundary node (Sec 2.3 steps 1-5, eq 28; reading O7-O9): from the
+ * fields rho, u at the ns stencil cells whose centres lie at (dx, dy) from the reference
+ * point R, the unit normal n (wall to fluid), the wall distance dwb of B and the level's
+ * viscosity nu.  out = rho_W, u_W (2), u_tau, chi_B, t (2), |u_Rt|.  slip: the prescribed
+ * wall velocity (wall model 2). */
+void oracle_wall_point(const oracle_config *c, double nu, int ns, const double *dx, const double *dy,
+                       const double *rho, const double *ux, const double *uy, const double *n, double dwb,
+                       const double *slip, double *out)
+{
+    /* step 1: rho_R by inverse-distance weighting, u_R by unweighted linear LSQ */
+    double sw = 0, swr = 0, swu = 0, swv = 0;
+    double A[9] = {0}, bu[3] = {0}, bv[3] = {0};
+    for (int m = 0; m < ns; m++) {
+        double d2 = dx[m] * dx[m] + dy[m] * dy[m];
+        double w = 1.0 / (d2 > 1e-20 ? d2 : 1e-20);
+        sw += w; swr += w * rho[m]; swu += w * ux[m]; swv += w * uy[m];
+        double phi[3] = {1.0, dx[m], dy[m]};
+        for (int a = 0; a < 3; a++) {
+            for (int b = 0; b < 3; b++) A[3 * a + b] += phi[a] * phi[b];
+            bu[a] += phi[a] * ux[m];
+            bv[a] += phi[a] * uy[m];
+        }
+    }
+    double rhoR = ns > 0 ? swr / sw : 1.0;
+    double uR = ns > 0 ? swu / sw : 0.0, vR = ns > 0 ? swv / sw : 0.0;
+    double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                 A[2] * (A[3] * A[7] - A[4] * A[6]);
+    if (ns >= 3 && det > 1e-9 * A[0] * A[4] * A[8]) {
+        double A2[9];
+        memcpy(A2, A, sizeof A2);
+        solve_dense(3, A, bu);
+        solve_dense(3, A2, bv);
+        uR = bu[0]; vR = bv[0];
+    }
+    /* step 2: tangential component */
+    double un = uR * n[0] + vR * n[1];
+    double utx = uR - un * n[0], uty = vR - un * n[1];
+    double ut = sqrt(utx * utx + uty * uty);
+    double t[2];
+    if (ut > 0) { t[0] = utx / ut; t[1] = uty / ut; }
+    else { t[0] = -n[1]; t[1] = n[0]; }
+    double utau = 0, uW[2] = {0, 0}, chiB = 0;
+    if (c->wall_model == 0) {
+        /* step 3: friction velocity from eq 22 at R */
+        utau = oracle_wf_utau(ut, c->d_wr, nu);
+        /* step 4: u_V = u_tau f_SA(y+_V) */
+        double ypv = utau * c->d_wv / nu;
+        double uV = utau * oracle_wf_uplus(ypv);
+        /* step 5 / eq 28 with (nu_t)_V = nu kappa y+_V; direction: reading t = u_Rt/|u_Rt| */
+        double uWm = uV - utau * utau * c->d_wv / (nu * (1.0 + SA_KAPPA * ypv));
+        uW[0] = uWm * t[0];
+        uW[1] = uWm * t[1];
+        /* SA Dirichlet at B: nu_t~_B = nu kappa d+_WB (Sec 2.2) */
+        chiB = SA_KAPPA * utau * dwb / nu;
+    } else if (c->wall_model == 1) {
+        /* Nishimura's slip adapted to RANS (Sec 3.1.5, eq 31).  Readings: u_tau from eq 22 at
+           R (step 3 kept: eq 31 needs it; Sec 2.3 names the VN steps 4-5 as the ones
+           Nishimura's approach lacks, so Sec 3.1.5's 'steps 3 and 4' are read as those);
+           (nu_t)_R is the eddy viscosity of the SA log layer at R, nu kappa y+_R (eq 20; the
+           mixing-length value Nishimura et al. use at R, and the value the VN method takes at
+           V); slip along t = u_Rt/|u_Rt|; the SA Dirichlet value as in the VN method. */
+        utau = oracle_wf_utau(ut, c->d_wr, nu);
+        double ypr = utau * c->d_wr / nu;
+        double uWm = ut - utau * utau * c->d_wr / (nu * (1.0 + SA_KAPPA * ypr));
+        uW[0] = uWm * t[0];
+        uW[1] = uWm * t[1];
+        chiB = SA_KAPPA * utau * dwb / nu;
+    } else if (c->wall_model == 2) {
+        uW[0] = slip[0];
+        uW[1] = slip[1];
+    }
+    out[0] = rhoR;                                          /* step 6: rho_W ~ rho_R */
+    out[1] = uW[0]; out[2] = uW[1]; out[3] = utau; out[4] = chiB;
+    out[5] = t[0]; out[6] = t[1]; out[7] = ut;
+}
+
 static void wall_function(oracle_solver *s)
 {
     const oracle_config *c = &s->cfg;
@@ -994,76 +1070,20 @@ static void wall_function(oracle_solver *s)
 #pragma omp parallel for schedule(dynamic, 16)
     for (int r = 0; r < s->nrec; r++) {
         orec *R0 = &s->rec[r];
-        /* step 1: rho_R by inverse-distance weighting, u_R by unweighted linear LSQ */
-        double sw = 0, swr = 0, swu = 0, swv = 0;
-        double A[9] = {0}, bu[3] = {0}, bv[3] = {0};
+        double dx[16], dy[16], rho[16], ux[16], uy[16], out[8];
         for (int m = 0; m < R0->ns; m++) {
             long k = cidx(F, R0->si[m], R0->sj[m]);
-            double dx = R0->si[m] + 0.5 - R0->r[0], dy = R0->sj[m] + 0.5 - R0->r[1];
-            double d2 = dx * dx + dy * dy;
-            double w = 1.0 / (d2 > 1e-20 ? d2 : 1e-20);
-            sw += w; swr += w * F->rho[k]; swu += w * F->ux[k]; swv += w * F->uy[k];
-            double phi[3] = {1.0, dx, dy};
-            for (int a = 0; a < 3; a++) {
-                for (int b = 0; b < 3; b++) A[3 * a + b] += phi[a] * phi[b];
-                bu[a] += phi[a] * F->ux[k];
-                bv[a] += phi[a] * F->uy[k];
-            }
+            dx[m] = R0->si[m] + 0.5 - R0->r[0];
+            dy[m] = R0->sj[m] + 0.5 - R0->r[1];
+            rho[m] = F->rho[k]; ux[m] = F->ux[k]; uy[m] = F->uy[k];
         }
-        double rhoR = R0->ns > 0 ? swr / sw : 1.0;
-        double uR = R0->ns > 0 ? swu / sw : 0.0, vR = R0->ns > 0 ? swv / sw : 0.0;
-        double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
-                     A[2] * (A[3] * A[7] - A[4] * A[6]);
-        if (R0->ns >= 3 && det > 1e-9 * A[0] * A[4] * A[8]) {
-            double A2[9];
-            memcpy(A2, A, sizeof A2);
-            solve_dense(3, A, bu);
-            solve_dense(3, A2, bv);
-            uR = bu[0]; vR = bv[0];
-        }
-        /* step 2: tangential component */
-        double un = uR * R0->n[0] + vR * R0->n[1];
-        double utx = uR - un * R0->n[0], uty = vR - un * R0->n[1];
-        double ut = sqrt(utx * utx + uty * uty);
-        R0->rhoW = rhoR;                                       /* step 6: rho_W ~ rho_R */
-        R0->ut = ut;
-        if (ut > 0) { R0->t[0] = utx / ut; R0->t[1] = uty / ut; }
-        else { R0->t[0] = -R0->n[1]; R0->t[1] = R0->n[0]; }
-        if (c->wall_model == 0) {
-            /* step 3: friction velocity from eq 22 at R */
-            double utau = oracle_wf_utau(ut, c->d_wr, nu);
-            /* step 4: u_V = u_tau f_SA(y+_V) */
-            double ypv = utau * c->d_wv / nu;
-            double uV = utau * oracle_wf_uplus(ypv);
-            /* step 5 / eq 28 with (nu_t)_V = nu kappa y+_V; direction: reading t = u_Rt/|u_Rt| */
-            double uW = uV - utau * utau * c->d_wv / (nu * (1.0 + SA_KAPPA * ypv));
-            R0->utau = utau;
-            R0->uW[0] = uW * R0->t[0];
-            R0->uW[1] = uW * R0->t[1];
-            /* SA Dirichlet at B: nu_t~_B = nu kappa d+_WB (Sec 2.2) */
-            R0->chiB = SA_KAPPA * utau * R0->dwb / nu;
-        } else if (c->wall_model == 1) {
-            /* Nishimura's slip adapted to RANS (Sec 3.1.5, eq 31).  Readings: u_tau from eq 22 at
-               R (step 3 kept: eq 31 needs it; Sec 2.3 names the VN steps 4-5 as the ones
-               Nishimura's approach lacks, so Sec 3.1.5's 'steps 3 and 4' are read as those);
-               (nu_t)_R is the eddy viscosity of the SA log layer at R, nu kappa y+_R (eq 20; the
-               mixing-length value Nishimura et al. use at R, and the value the VN method takes at
-               V); slip along t = u_Rt/|u_Rt|; the SA Dirichlet value as in the VN method. */
-            double utau = oracle_wf_utau(ut, c->d_wr, nu);
-            double ypr = utau * c->d_wr / nu;
-            double uW = ut - utau * utau * c->d_wr / (nu * (1.0 + SA_KAPPA * ypr));
-            R0->utau = utau;
-            R0->uW[0] = uW * R0->t[0];
-            R0->uW[1] = uW * R0->t[1];
-            R0->chiB = SA_KAPPA * utau * R0->dwb / nu;
-        } else if (c->wall_model == 2) {
-            R0->utau = 0;
-            R0->uW[0] = s->loop_slip[2 * R0->loop];
-            R0->uW[1] = s->loop_slip[2 * R0->loop + 1];
-            R0->chiB = 0;
-        } else {
-            R0->utau = 0; R0->uW[0] = 0; R0->uW[1] = 0; R0->chiB = 0;
-        }
+        oracle_wall_point(c, nu, R0->ns, dx, dy, rho, ux, uy, R0->n, R0->dwb, &s->loop_slip[2 * R0->loop], out);
+        R0->rhoW = out[0];
+        R0->uW[0] = out[1]; R0->uW[1] = out[2];
+        R0->utau = out[3];
+        R0->chiB = out[4];
+        R0->t[0] = out[5]; R0->t[1] = out[6];
+        R0->ut = out[7];
     }
 }
 
@@ -1130,6 +1150,23 @@ static int pull0(const oracle_solver *s, const olevel *P, int i, int j, int q, d
     return 1;
 }
 
+/* Yu's interpolated bounce-back with the wall velocity (eq 27, reading O10) for the pulled
+ * direction q of a boundary node B whose upstream B - c_q is solid: from the post-collision
+ * f*_qo of the next fluid node B + c_q, f*_qo(B) and f*_q(B) (qo = opposite of q), the wall
+ * fraction qf of the cut link and rho_W, u_W of B's wall state; the half-way form (eq 24)
+ * where B + c_q is not an active fluid cell. */
+double oracle_yu_link(int q, double qf, double rhoW, double uWx, double uWy, double f_qo_next, double f_qo_B,
+                      double f_q_B, int next_fluid)
+{
+    double cu = CX[q] * uWx + CY[q] * uWy;
+    double mom = 2.0 * WQ[q] * rhoW * cu / CS2;
+    if (next_fluid) {
+        double fw = (1.0 - qf) * f_qo_next + qf * f_qo_B + mom;
+        return fw / (1.0 + qf) + qf / (1.0 + qf) * f_q_B;
+    }
+    return f_qo_B + mom;                                   /* half-way fallback, eq 24 */
+}
+
 static void stream_collide_level(oracle_solver *s, int l)
 {
     const oracle_config *c = &s->cfg;
@@ -1168,18 +1205,12 @@ static void stream_collide_level(oracle_solver *s, int l)
                     /* Yu interpolated bounce-back with slip velocity (eqs 24, 27; reading O10) */
                     const orec *R0 = &s->rec[P->rec[k]];
                     int qo = OPPD[q];
-                    double qf = R0->q[q];
-                    double cu = CX[q] * R0->uW[0] + CY[q] * R0->uW[1];
-                    double mom = 2.0 * WQ[q] * R0->rhoW * cu / CS2;
                     long long fi = i + CX[q], fj = j + CY[q];
                     if (l == 0 && c->periodic) { fi = (fi + c->nx0) % c->nx0; fj = (fj + c->ny0) % c->ny0; }
                     long kf = cidx(P, fi, fj);
-                    if (kf >= 0 && P->kind[kf] == K_ACTIVE && !P->solid[kf]) {
-                        double fw = (1.0 - qf) * P->f[9 * kf + qo] + qf * own[qo] + mom;
-                        out[q] = fw / (1.0 + qf) + qf / (1.0 + qf) * own[q];
-                    } else {
-                        out[q] = own[qo] + mom;                       /* half-way fallback, eq 24 */
-                    }
+                    const int next_fluid = kf >= 0 && P->kind[kf] == K_ACTIVE && !P->solid[kf];
+                    out[q] = oracle_yu_link(q, R0->q[q], R0->rhoW, R0->uW[0], R0->uW[1], next_fluid ? P->f[9 * kf + qo] : 0.0,
+                                            own[qo], own[q], next_fluid);
                     continue;
                 }
                 long long si = i - CX[q], sj = j - CY[q];

@@ -78,6 +78,15 @@ void   oracle_sa_source(double chi, double nu, double vort, double d, double *P,
 double oracle_sa_update_point(const double *chi9, const double *ux9, const double *uy9,
                               double d, double nu, int convection); /* explicit FD update, eqs 12/16 */
 double oracle_sa_convection(const double *nt9, double u, double v, int scheme); /* convective increment */
+/* wall state of one boundary node from its stencil (Sec 2.3 steps 1-5, eq 28): out = rho_W,
+   u_W (2), u_tau, chi_B, t (2), |u_Rt|; dx, dy: stencil cell centres relative to R */
+void   oracle_wall_point(const oracle_config *cfg, double nu, int ns, const double *dx, const double *dy,
+                         const double *rho, const double *ux, const double *uy, const double *n, double dwb,
+                         const double *slip, double *out);
+/* Yu's interpolated slip bounce-back for pulled direction q of a boundary node (eq 27; eq 24
+   where the next node along the link is not fluid) */
+double oracle_yu_link(int q, double qf, double rhoW, double uWx, double uWy, double f_qo_next, double f_qo_B,
+                      double f_q_B, int next_fluid);
 
 #ifdef __cplusplus
 }
