@@ -188,8 +188,33 @@ lbm_status lbm_get_fields(lbm_solver *s, int level, double *rho, double *ux, dou
 /* Copy a level's populations f_i (eq 1, index i = 0..8 in the order of eq 2) to the host:
  * pop[i * nx * ny + (j - j0) * nx + (i - i0)] over the box of lbm_get_level_box, the
  * post-collision values the next step streams.  Cells without populations of their own
- * (absent, solid, covered) hold NaN.  cap: element capacity (>= 9 nx ny). */
+ * (absent, solid, covered) hold NaN, and so do the values the in-place layout does not
+ * keep because no step reads them (populations leaving across the inlet or the outlet, or
+ * towards a cell without a tile).  Ghost cells report the values they relay next: their
+ * parent's exploded populations at a coarse-step boundary.  cap: element capacity
+ * (>= 9 nx ny).  The device scratch of the query goes through dev_alloc when given. */
 lbm_status lbm_get_populations(lbm_solver *s, int level, double *pop, long long cap);
+
+/* One launch of the level schedule of Sec 2.1, for element-wise checks of single launches
+ * against an independent implementation: kind 0 the fused step of `level` (wall function on
+ * the finest level, SA-neg, stream with coalescence and cut links, collide, explode), kind 1
+ * the same with the restriction of its new fields into the covered cells of level - 1 (the
+ * second of two sub-steps), kind 2 the prolongation of level's fields into the ghosts of
+ * level + 1.  Synchronous; the status word is checked as in lbm_step.  Afterwards the levels
+ * are out of the recursive schedule: lbm_step and lbm_step_async return
+ * LBM_ERR_INVALID_ARG until lbm_set_state restores a checkpoint.  No paper counterpart.
+ * Errors: LBM_ERR_INVALID_ARG (bad level or kind: kind 2 on the finest level),
+ * LBM_ERR_NO_GEOMETRY, LBM_ERR_CUDA, LBM_ERR_DIVERGED. */
+lbm_status lbm_step_launch(lbm_solver *s, int level, int kind);
+
+/* The coalescence inputs of a level's band cells (Rohde, Sec 2.1): for band cell b (the
+ * active cells of `level` beside a covered one, in row-major order of the level's box) its
+ * global cell indices ij[2 b], ij[2 b + 1] and, for each child m = 2 by + bx and direction i,
+ * vals[36 b + 9 m + i]: the population f_i its ghost child pulled in the fine level's last
+ * odd sub-step (the parent's exploded value where the child keeps its own).  With ij NULL
+ * only *n is set.  Errors: LBM_ERR_INVALID_ARG (level without a finer level, capacity),
+ * LBM_ERR_NO_GEOMETRY, LBM_ERR_CUDA. */
+lbm_status lbm_get_ghost_relay(lbm_solver *s, int level, int *ij, double *vals, int cap, int *n);
 
 /* Set the macroscopic fields of the active fluid cells of a level (NULL = keep) and
  * reset their populations to the equilibrium of eq 4; the interfaces are re-synchronised

@@ -106,6 +106,8 @@ def library():
         "lbm_get_fields": ([vp, C.c_int, dp, dp, dp, dp, vp, C.c_int], C.c_int),
         "lbm_set_fields": ([vp, C.c_int, dp, dp, dp, dp], C.c_int),
         "lbm_get_populations": ([vp, C.c_int, dp, C.c_longlong], C.c_int),
+        "lbm_step_launch": ([vp, C.c_int, C.c_int], C.c_int),
+        "lbm_get_ghost_relay": ([vp, C.c_int, ip, dp, C.c_int, ip], C.c_int),
         "lbm_get_loads": ([vp, C.POINTER(lbm_loads), dp, dp, C.c_int, ip], C.c_int),
         "lbm_get_cut_links": ([vp, ip, dp, C.c_int, ip], C.c_int),
         "lbm_get_wall_records": ([vp, ip, dp, ip, C.c_int, ip], C.c_int),
@@ -292,6 +294,21 @@ class Solver:
         pop = np.zeros((9, ny, nx))
         self._check(self._lib.lbm_get_populations(self._h, level, _dp(pop), pop.size))
         return pop
+
+    def step_launch(self, level, kind):
+        """lbm_step_launch: one launch of the level schedule (0 level step, 1 level step with
+        restriction, 2 prolongation); the solver then refuses step() until set_state()."""
+        self._check(self._lib.lbm_step_launch(self._h, int(level), int(kind)))
+
+    def ghost_relay(self, level):
+        """lbm_get_ghost_relay: band cells (n, 2) of a level and, per child m and direction i,
+        the population its ghost child pulled in the fine level's last odd sub-step (n, 4, 9)."""
+        n = C.c_int(0)
+        self._check(self._lib.lbm_get_ghost_relay(self._h, level, None, None, 0, C.byref(n)))
+        ij = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+        vals = np.zeros((max(n.value, 1), 4, 9))
+        self._check(self._lib.lbm_get_ghost_relay(self._h, level, _ip(ij), _dp(vals), n.value, C.byref(n)))
+        return ij[:n.value], vals[:n.value]
 
     def set_fields(self, level, rho=None, ux=None, uy=None, chi=None):
         i0, j0, nx, ny = self.level_box(level)

@@ -893,7 +893,8 @@ __global__ void k_restrict(LevelView P, LevelView F, int pp, int pf)
 // whose next step has parity p, gathered from the in-place layout into out[q * ns + slot]:
 // the inverse of put_post.  Values the layout does not keep (populations leaving across the
 // inlet or the outlet, or towards a cell without a tile; no step reads them) are NaN.
-// Boundary nodes come from their record buffer; ghosts report their parent's exploded values.
+// Boundary nodes come from their record buffer.  Ghosts report their parent's exploded
+// values before an even sub-step and what they relay before an odd one.
 template <typename T>
 __global__ void k_gather_post(LevelView P, LevelView C, RecView R, StepConsts k, int p, int is_level0, float *out)
 {
@@ -909,8 +910,10 @@ __global__ void k_gather_post(LevelView P, LevelView C, RecView R, StepConsts k,
     float o[9];
     for (int q = 0; q < 9; q++) o[q] = NAN;
     if (kind == KIND_GHOST && !(fl & FL_SOLID)) {
+        // before an odd sub-step a ghost holds what it relays next (its even sub-step's
+        // pulls); before an even one, its parent's exploded values
         const float *eb = C.ebuf + (P.aux[slot] >> 2) * 9;
-        for (int q = 0; q < 9; q++) o[q] = eb[q];
+        for (int q = 0; q < 9; q++) o[q] = p == 1 ? L.ld(oppq(q), slot, q) : eb[q];
     } else if (kind == KIND_ACTIVE && !(fl & FL_SOLID)) {
         if (R.n > 0 && (fl & FL_BNODE) && P.aux) {
             const float *fp = R.fpost + P.aux[slot] * 9;

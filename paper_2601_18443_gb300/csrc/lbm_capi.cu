@@ -73,6 +73,7 @@ void stencil_weights(const lbmgrid::Record &R, double wr[16], double wu[16])
 struct HostLevelDev {
     LevelView v;
     std::vector<uint32_t> flags;   // host copy
+    std::vector<int> band_ij;      // global cell indices of the band cells, in band-index order
 };
 
 }  // namespace
@@ -97,6 +98,7 @@ struct lbm_solver {
     int min_blocks[LBM_MAXL];     // register budget of each level's kernel (lbm_autotune)
     int persistent[LBM_MAXL];     // persistent grid for each level's kernel (lbm_autotune)
     int pdl = 1;                  // programmatic dependent launch (lbm_autotune)
+    bool off_schedule = false;    // single launches (lbm_step_launch) left the level schedule
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<void *> allocs;
     double device_bytes = 0;
@@ -459,7 +461,16 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
                 if (G.band[(size_t)r * G.bnx + q]) bidx[l][(size_t)r * G.bnx + q] = n++;
         }
         n_band[l] = row[G.bny];
+        std::vector<int> &bij = s->lv[l].band_ij;
+        bij.assign(2 * (size_t)n_band[l], 0);
+#pragma omp parallel for schedule(static)
+        for (int r = 0; r < G.bny; r++)
+            for (int q = 0; q < G.bnx; q++) {
+                const int b = bidx[l][(size_t)r * G.bnx + q];
+                if (b >= 0) { bij[2 * (size_t)b] = G.bi0 + q; bij[2 * (size_t)b + 1] = G.bj0 + r; }
+            }
     }
+    s->lv[L - 1].band_ij.clear();
     // per-level flag words and device arrays
     for (int l = 0; l < L; l++) {
         lbmgrid::Level &G = s->g.lv[l];
@@ -783,6 +794,8 @@ lbm_status lbm_step_async(lbm_solver *s, int n)
 {
     if (!s) return LBM_ERR_INVALID_ARG;
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (s->off_schedule)
+        return fail(s, LBM_ERR_INVALID_ARG, "single launches left the level schedule (restore a checkpoint first)");
     if (n < 0) return fail(s, LBM_ERR_INVALID_ARG, "negative step count");
     return enqueue_steps(s, n);
 }
@@ -795,6 +808,58 @@ lbm_status lbm_synchronize(lbm_solver *s)
     if (st != LBM_OK) return st;
     CK(cudaGetLastError());
     return check_status(s);
+}
+
+lbm_status lbm_step_launch(lbm_solver *s, int level, int kind)
+{
+    if (!s) return LBM_ERR_INVALID_ARG;
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (level < 0 || level >= s->L || kind < 0 || kind > 2 || (kind == 2 && level == s->L - 1))
+        return fail(s, LBM_ERR_INVALID_ARG, "bad level or launch kind");
+    const int L = s->L, l = level;
+    LevelView &P = s->lv[l].v;
+    if (kind == 2) {
+        lbmdev::launch_prolong(s->stream, P, s->lv[l + 1].v, s->parity[l], 0);
+    } else {
+        const LevelView *F = (l < L - 1) ? &s->lv[l + 1].v : nullptr;
+        const LevelView *C = (l > 0) ? &s->lv[l - 1].v : nullptr;
+        lbmdev::LevelStep ls;
+        ls.p = s->parity[l];
+        ls.has_child = F != nullptr;
+        ls.is_level0 = l == 0;
+        ls.wall = (l == L - 1) && s->rec.n > 0;
+        ls.restrict_up = kind == 1 && C != nullptr;
+        ls.pp = C ? s->parity[l - 1] : 0;
+        ls.status = s->d_status;
+        const lbmdev::LevelTune tu{s->min_blocks[l], 0, s->persistent[l]};
+        lbmdev::launch_level(s->stream, P, F, C, s->rec, s->k, ls, tu);
+        s->parity[l] ^= 1;
+    }
+    s->off_schedule = true;
+    CK(cudaGetLastError());
+    return check_status(s);
+}
+
+lbm_status lbm_get_ghost_relay(lbm_solver *s, int level, int *ij, double *vals, int cap, int *n)
+{
+    if (!s || !n) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (level < 0 || level >= s->L - 1) return fail(s, LBM_ERR_INVALID_ARG, "level has no finer level");
+    const LevelView &v = s->lv[level].v;
+    *n = v.n_band;
+    if (!ij) return LBM_OK;
+    if (v.n_band > cap || !vals) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    std::vector<float> h(36 * (size_t)v.n_band);
+    if (!h.empty()) {
+        CK(cudaMemcpyAsync(h.data(), v.gbuf, h.size() * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    for (int b = 0; b < v.n_band; b++) {
+        ij[2 * b] = s->lv[level].band_ij[2 * (size_t)b];
+        ij[2 * b + 1] = s->lv[level].band_ij[2 * (size_t)b + 1];
+        for (int m = 0; m < 36; m++) vals[36 * (size_t)b + m] = (double)h[36 * (size_t)b + m] + WQh[m % 9];
+    }
+    return LBM_OK;
 }
 
 lbm_status lbm_step(lbm_solver *s, int n)
@@ -1437,8 +1502,11 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
         return fail(s, LBM_ERR_INVALID_ARG, "state blob from a solve with other physical or model parameters");
     if (size != state_bytes(s)) return fail(s, LBM_ERR_INVALID_ARG, "state blob size differs");
     CK(cudaStreamSynchronize(s->stream));
-    // the blob's level-0 parity becomes the solver's (the step graphs exist for both parities)
+    // the blob's level-0 parity becomes the solver's (the step graphs exist for both parities);
+    // finer levels are at parity 0 at every coarse step
     s->parity[0] = h.parity0;
+    for (int l = 1; l < s->L; l++) s->parity[l] = 0;
+    s->off_schedule = false;
     const unsigned char *o = (const unsigned char *)buf + sizeof h;
     std::vector<std::pair<void *, size_t>> a;
     state_arrays(s, a);

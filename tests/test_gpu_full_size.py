@@ -10,11 +10,9 @@ oracle computes one by one (its full grid build is brute force and too slow here
 
 Workloads: NACA 0012 at alpha 10 deg, 6 levels to c/4096 (1.52M nodes), and the
 synthetic three-element high-lift section, 8 levels to c/8192 (7.46M nodes).  The
-high-lift case is checked on its grid only: started impulsively from the uniform
-stream at Ma 0.2 it diverges within its first coarse step (128 finest sub-steps), the
-flow around the sharp slat and flap trailing edges reaching lattice speeds beyond the
-stability of the D2Q9 model at c/8192; its stepping is checked at oracle size in
-test_gpu_parity.py.
+high-lift case is checked on its grid only here; its stepping is checked at oracle size
+in test_gpu_parity.py.  Single launches of the NACA workload's finest levels are checked
+against the oracle's building blocks in test_gpu_full_size_steps.py.
 """
 import math
 import time
