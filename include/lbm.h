@@ -356,6 +356,33 @@ lbm_status lbm_level_mass_noalloc(const unsigned int *flags, const float *drho, 
                                   const float *nu_tilde_ratio, long long n_cells, double area, double *mass_out,
                                   int *nonfinite_out, void *stream);
 
+/* ---- Batched solves (serving) -------------------------------------------------------
+ * A batch steps up to LBM_BATCH_MAX_SOLVES resident solves in lockstep, one launch per node
+ * of the recursive level schedule of Sec 2.1 covering the same level of every member that
+ * has it (level l takes 2^l sub-steps per coarse step in every solve, so members with
+ * different level counts share the schedule of the deepest one).  Each block of a launch
+ * carries its solve's views, so one graph node advances one level of all members.  No paper
+ * counterpart: the paper steps one solve at a time.
+ *
+ * lbm_batch_create: the members (distinct handles with geometry, on the current device,
+ * all with the same population storage, none left off the schedule by lbm_step_launch)
+ * stay owned by the caller and must outlive the batch.  The batch owns a stream and two
+ * captured step graphs.  Errors: LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_CUDA.
+ * lbm_batch_step: enqueue n coarse steps of every member on the batch's stream, ordered
+ * after the work already on the members' streams and before later work on them (events),
+ * so a member's queries (lbm_synchronize, lbm_get_loads, ...) see the stepped state.  A
+ * member must not be stepped on its own while in a batch (LBM_ERR_INVALID_ARG: make a new
+ * batch).  Each member's results equal its results stepped alone up to FP32 rounding.
+ * lbm_batch_info: members, levels of the deepest member, launches per coarse step.
+ * lbm_batch_destroy: NULL-safe; waits for the batch's work. */
+#define LBM_BATCH_MAX_SOLVES 24
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(lbm_solver *const *solvers, int n, lbm_batch **out);
+lbm_status lbm_batch_step(lbm_batch *b, int n_coarse_steps);
+lbm_status lbm_batch_info(const lbm_batch *b, int *members, int *levels, long long *kernels_per_step);
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Per-handle message of the last error. */
 const char *lbm_last_error(const lbm_solver *s);
 

@@ -107,6 +107,11 @@ def library():
         "lbm_set_fields": ([vp, C.c_int, dp, dp, dp, dp], C.c_int),
         "lbm_get_populations": ([vp, C.c_int, dp, C.c_longlong], C.c_int),
         "lbm_step_launch": ([vp, C.c_int, C.c_int], C.c_int),
+        "lbm_batch_create": ([C.POINTER(vp), C.c_int, C.POINTER(vp)], C.c_int),
+        "lbm_batch_step": ([vp, C.c_int], C.c_int),
+        "lbm_batch_info": ([vp, ip, ip, C.POINTER(C.c_longlong)], C.c_int),
+        "lbm_batch_last_error": ([vp], C.c_char_p),
+        "lbm_batch_destroy": ([vp], None),
         "lbm_get_ghost_relay": ([vp, C.c_int, ip, dp, C.c_int, ip], C.c_int),
         "lbm_get_loads": ([vp, C.POINTER(lbm_loads), dp, dp, C.c_int, ip], C.c_int),
         "lbm_get_cut_links": ([vp, ip, dp, C.c_int, ip], C.c_int),
@@ -450,3 +455,40 @@ def level_mass_noalloc(flags, drho, ux, uy, chi, n_cells, area, mass_out, nonfin
     (for example ``tensor.data_ptr()``); returns the status code.  Only enqueues work."""
     return library().lbm_level_mass_noalloc(flags, drho, ux, uy, chi, int(n_cells), float(area), mass_out,
                                             nonfinite_out, stream)
+
+
+class Batch:
+    """lbm_batch: steps several resident solves in lockstep, one launch per level-schedule
+    node covering every member (see include/lbm.h).  The solvers stay owned by the caller
+    and must outlive the batch; queries go to the solvers themselves."""
+
+    def __init__(self, solvers):
+        self._lib = library()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s._h for s in self.solvers])
+        h = C.c_void_p()
+        rc = self._lib.lbm_batch_create(arr, len(self.solvers), C.byref(h))
+        if rc != 0:
+            raise LBMError(rc, "lbm_batch_create")
+        self._h = h
+
+    def step(self, n=1):
+        rc = self._lib.lbm_batch_step(self._h, int(n))
+        if rc != 0:
+            raise LBMError(rc, "lbm_batch_step: " + self._lib.lbm_batch_last_error(self._h).decode())
+
+    def info(self):
+        m, lv, nk = C.c_int(), C.c_int(), C.c_longlong()
+        self._lib.lbm_batch_info(self._h, C.byref(m), C.byref(lv), C.byref(nk))
+        return dict(members=m.value, levels=lv.value, kernels_per_step=nk.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

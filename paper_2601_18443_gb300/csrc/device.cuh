@@ -117,6 +117,33 @@ void launch_store_post(cudaStream_t st, const LevelView &P, const RecView &R, co
 void launch_explode(cudaStream_t st, const LevelView &P, const LevelView &F, const RecView &R, const StepConsts &k,
                     const float *post);
 
+// Batched launches: one launch advances the same level of up to LBM_BATCH_MAX resident
+// solves.  Each solve's views travel in the kernel's parameter block; a block finds its
+// solve from its index (the solve's blocks are consecutive from first_block).
+#define LBM_BATCH_MAX 24
+struct SolveDesc {
+    LevelView P, F, C;   // the level, its finer level (or P) and its coarser level (or P)
+    RecView R;
+    StepConsts k;
+    LevelStep ls;
+    int kind;            // 0 no finer level, 1 with a finer level, 2 finest level with wall records
+    int first_block;
+};
+struct BatchArgs {
+    int n;               // solves in this launch
+    SolveDesc d[LBM_BATCH_MAX];
+};
+struct ProlongDesc {
+    LevelView P, F;
+    int p, first_block;
+};
+struct ProlongBatchArgs {
+    int n;
+    ProlongDesc d[LBM_BATCH_MAX];
+};
+void launch_level_batch(cudaStream_t st, const BatchArgs &a, int store, unsigned grid, int pdl);
+void launch_prolong_batch(cudaStream_t st, const ProlongBatchArgs &a, unsigned grid, int pdl);
+
 struct LoadsView {
     int nseg;
     const int *b1, *b2;

@@ -820,18 +820,48 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
 
 }
 
+// The batched form of k_level (one block per work tile, register budget of 5 blocks per SM):
+// block b belongs to the last solve whose first block is at most b; its kind and the
+// parity of its level select the body.  Per cell it runs the same code as k_level.
+template <typename T>
+__global__ void __launch_bounds__(256, 5) k_level_batch(const __grid_constant__ BatchArgs a)
+{
+    int i = 0;
+    for (int m = 1; m < a.n; m++)
+        if (a.d[m].first_block <= (int)blockIdx.x) i = m;
+    const SolveDesc &d = a.d[i];
+    __shared__ int nb3w[LBM_TILE / 32][9];
+    const int c = threadIdx.x;
+    const int lane = c & 31;
+    int lx, ly;
+    cell_of_thread(c, lx, ly);
+    int *nb3 = nb3w[c >> 5];
+    const int t = d.P.work_tiles[blockIdx.x - d.first_block];
+    if (lane < 9) nb3[lane] = d.P.nbr[t * 9 + dir_of3(lane)];
+    __syncwarp();
+    griddep_launch();
+    griddep_wait();
+    const Lat<T> L{static_cast<T *>(d.P.f), d.P.ns, d.k.pshift};
+    const bool odd = d.ls.p != 0;
+    if (d.kind == 2) {
+        if (odd) level_tile<true, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
+        else level_tile<true, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
+    } else if (d.kind == 1) {
+        if (odd) level_tile<false, true, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
+        else level_tile<false, true, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
+    } else {
+        if (odd) level_tile<false, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
+        else level_tile<false, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
+    }
+}
+
 // ------------------------------------------------------------------ prolongation (Sec 2.2)
 // ghost children of the band cells of level l: linear LSQ reconstruction of chi and u
 // about the parent (fields at time t), rho copied; written to both time levels of l+1
-__global__ void __launch_bounds__(256) k_prolong(LevelView P, LevelView F, int p)
+__device__ __forceinline__ void prolong_tile(const LevelView &P, const LevelView &F, int p, int t, int *nb3)
 {
-    __shared__ int nb3[9];
-    const int t = P.band_tiles[blockIdx.x], c = threadIdx.x;
+    const int c = threadIdx.x;
     const int lx = c & 31, ly = c >> 5;
-    load_nb3(P, t, nb3);
-    __syncthreads();
-    griddep_launch();
-    griddep_wait();
     const int slot = t * LBM_TILE + c;
     const uint32_t fl = P.flags[slot];
     if ((fl & FL_KIND_MASK) != KIND_ACTIVE || (fl & FL_SOLID) || !(fl & FL_BAND)) return;
@@ -855,6 +885,33 @@ __global__ void __launch_bounds__(256) k_prolong(LevelView P, LevelView F, int p
             F.chi[h][cs] = vc; F.ux[h][cs] = vu; F.uy[h][cs] = vv; F.drho[h][cs] = dr;
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_prolong(LevelView P, LevelView F, int p)
+{
+    __shared__ int nb3[9];
+    const int t = P.band_tiles[blockIdx.x];
+    load_nb3(P, t, nb3);
+    __syncthreads();
+    griddep_launch();
+    griddep_wait();
+    prolong_tile(P, F, p, t, nb3);
+}
+
+// batched form of k_prolong (same solve lookup as k_level_batch, over band tiles)
+__global__ void __launch_bounds__(256) k_prolong_batch(const __grid_constant__ ProlongBatchArgs a)
+{
+    int i = 0;
+    for (int m = 1; m < a.n; m++)
+        if (a.d[m].first_block <= (int)blockIdx.x) i = m;
+    const ProlongDesc &d = a.d[i];
+    __shared__ int nb3[9];
+    const int t = d.P.band_tiles[blockIdx.x - d.first_block];
+    load_nb3(d.P, t, nb3);
+    __syncthreads();
+    griddep_launch();
+    griddep_wait();
+    prolong_tile(d.P, d.F, d.p, t, nb3);
 }
 
 // ------------------------------------------------------------------ wall-state query
@@ -1144,6 +1201,21 @@ void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const
     case 2: launch_level_p<__nv_bfloat16>(st, P, Fv, Cv, F != nullptr, R, k, ls, tu); break;
     default: launch_level_p<float>(st, P, Fv, Cv, F != nullptr, R, k, ls, tu); break;
     }
+}
+
+void launch_level_batch(cudaStream_t st, const BatchArgs &a, int store, unsigned grid, int pdl)
+{
+    if (grid == 0) return;
+    switch (store) {
+    case 1: launch_pdl(k_level_batch<__half>, grid, st, pdl, a); break;
+    case 2: launch_pdl(k_level_batch<__nv_bfloat16>, grid, st, pdl, a); break;
+    default: launch_pdl(k_level_batch<float>, grid, st, pdl, a); break;
+    }
+}
+
+void launch_prolong_batch(cudaStream_t st, const ProlongBatchArgs &a, unsigned grid, int pdl)
+{
+    if (grid > 0) launch_pdl(k_prolong_batch, grid, st, pdl, a);
 }
 
 void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pdl)

@@ -1386,6 +1386,181 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     return check_status(s);
 }
 
+// ---------------------------------------------------------------- batched solves
+// One batch steps several resident solves in lockstep: every node of the recursive level
+// schedule (Sec 2.1) is one launch over all member solves that have that level.  Level l
+// takes 2^l sub-steps per coarse step in every solve, so the recursion of the deepest member
+// drives all of them; a member without level l has no blocks in that node's launch.
+struct lbm_batch {
+    std::vector<lbm_solver *> m;
+    std::vector<int> parity0;          // each member's level-0 parity the next graph expects
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int phase = 0;
+    int Lmax = 0, store = 0;
+    cudaEvent_t done = nullptr;
+    std::vector<cudaEvent_t> ready;
+    long long kernels_per_step = 0;
+    std::string err;
+};
+
+static lbm_status bfail(lbm_batch *b, lbm_status code, const std::string &msg)
+{
+    if (b) b->err = msg;
+    return code;
+}
+
+static void batch_advance(lbm_batch *b, cudaStream_t st, int l, int restrict_up, long long &nk)
+{
+    // prolongation of level l into the ghosts of l + 1, for the members that have l + 1
+    {
+        lbmdev::ProlongBatchArgs a;
+        a.n = 0;
+        unsigned grid = 0;
+        for (lbm_solver *s : b->m) {
+            if (l + 1 >= s->L || s->lv[l].v.n_band_tiles <= 0) continue;
+            lbmdev::ProlongDesc &d = a.d[a.n++];
+            d.P = s->lv[l].v; d.F = s->lv[l + 1].v; d.p = s->parity[l]; d.first_block = (int)grid;
+            grid += (unsigned)s->lv[l].v.n_band_tiles;
+        }
+        if (grid) { lbmdev::launch_prolong_batch(st, a, grid, 1); nk++; }
+    }
+    if (l + 1 < b->Lmax) {
+        batch_advance(b, st, l + 1, 0, nk);
+        batch_advance(b, st, l + 1, 1, nk);
+    }
+    lbmdev::BatchArgs a;
+    a.n = 0;
+    unsigned grid = 0;
+    for (lbm_solver *s : b->m) {
+        if (l >= s->L) continue;
+        const int L = s->L;
+        lbmdev::SolveDesc &d = a.d[a.n++];
+        d.P = s->lv[l].v;
+        d.F = l + 1 < L ? s->lv[l + 1].v : d.P;
+        d.C = l > 0 ? s->lv[l - 1].v : d.P;
+        d.R = s->rec;
+        d.k = s->k;
+        d.ls.p = s->parity[l];
+        d.ls.has_child = l + 1 < L;
+        d.ls.is_level0 = l == 0;
+        d.ls.wall = (l == L - 1) && s->rec.n > 0;
+        d.ls.restrict_up = restrict_up && l > 0;
+        d.ls.pp = l > 0 ? s->parity[l - 1] : 0;
+        d.ls.status = s->d_status;
+        d.kind = d.ls.wall ? 2 : (d.ls.has_child ? 1 : 0);
+        d.first_block = (int)grid;
+        grid += (unsigned)std::max(d.P.n_work_tiles, 0);
+        s->parity[l] ^= 1;
+    }
+    if (grid) { lbmdev::launch_level_batch(st, a, b->store, grid, 1); nk++; }
+}
+
+static lbm_status batch_capture(lbm_batch *b)
+{
+    for (int g = 0; g < 2; g++) {
+        cudaGraph_t gr;
+        long long nk = 0;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return bfail(b, LBM_ERR_CUDA, "batch capture begin");
+        batch_advance(b, b->stream, 0, 0, nk);
+        if (cudaStreamEndCapture(b->stream, &gr) != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "batch capture end");
+        const cudaError_t e = cudaGraphInstantiate(&b->graph[g], gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+        b->kernels_per_step = nk;
+    }
+    // the two captures advanced every member's parities by two coarse steps: as they were
+    return LBM_OK;
+}
+
+extern "C" {
+
+void lbm_batch_destroy(lbm_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (int g = 0; g < 2; g++)
+        if (b->graph[g]) cudaGraphExecDestroy(b->graph[g]);
+    for (cudaEvent_t e : b->ready) cudaEventDestroy(e);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+lbm_status lbm_batch_create(lbm_solver *const *solvers, int n, lbm_batch **out)
+{
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    static_assert(LBM_BATCH_MAX == LBM_BATCH_MAX_SOLVES, "batch sizes of the ABI and the kernels");
+    if (!solvers || n < 1 || n > LBM_BATCH_MAX) return LBM_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
+    for (int i = 0; i < n; i++) {
+        const lbm_solver *s = solvers[i];
+        if (!s || !s->geometry || s->off_schedule || s->device != dev || s->cfg.store != solvers[0]->cfg.store)
+            return LBM_ERR_INVALID_ARG;
+        for (int j = 0; j < i; j++)
+            if (solvers[j] == s) return LBM_ERR_INVALID_ARG;
+    }
+    lbm_batch *b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ERR_OOM;
+    b->m.assign(solvers, solvers + n);
+    b->store = solvers[0]->cfg.store;
+    for (lbm_solver *s : b->m) {
+        b->Lmax = std::max(b->Lmax, s->L);
+        b->parity0.push_back(s->parity[0]);
+    }
+    bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < n; i++) {
+        cudaEvent_t e;
+        ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (ok) b->ready.push_back(e);
+    }
+    if (!ok) { lbm_batch_destroy(b); return LBM_ERR_CUDA; }
+    if (batch_capture(b) != LBM_OK) { lbm_batch_destroy(b); return LBM_ERR_CUDA; }
+    *out = b;
+    return LBM_OK;
+}
+
+const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->err.c_str() : "null handle"; }
+
+lbm_status lbm_batch_step(lbm_batch *b, int n)
+{
+    if (!b || n < 0) return bfail(b, LBM_ERR_INVALID_ARG, "bad argument");
+    for (size_t i = 0; i < b->m.size(); i++)
+        if (b->m[i]->off_schedule || b->m[i]->parity[0] != (b->parity0[i] ^ b->phase))
+            return bfail(b, LBM_ERR_INVALID_ARG, "a member stepped outside the batch (create a new batch)");
+    // the batch stream follows everything enqueued on the members' own streams ...
+    for (size_t i = 0; i < b->m.size(); i++) {
+        if (cudaEventRecord(b->ready[i], b->m[i]->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(b->stream, b->ready[i], 0) != cudaSuccess)
+            return bfail(b, LBM_ERR_CUDA, "batch stream ordering");
+    }
+    for (int it = 0; it < n; it++) {
+        if (cudaGraphLaunch(b->graph[b->phase], b->stream) != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "batch graph launch");
+        b->phase ^= 1;
+        for (lbm_solver *s : b->m) { s->parity[0] ^= 1; s->step++; }
+    }
+    // ... and the members' streams follow the batch (queries see the stepped state)
+    if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "batch event");
+    for (lbm_solver *s : b->m)
+        if (cudaStreamWaitEvent(s->stream, b->done, 0) != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "batch stream ordering");
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_info(const lbm_batch *b, int *members, int *levels, long long *kernels_per_step)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (members) *members = (int)b->m.size();
+    if (levels) *levels = b->Lmax;
+    if (kernels_per_step) *kernels_per_step = b->kernels_per_step;
+    return LBM_OK;
+}
+
+}  // extern "C"
+
 // ---------------------------------------------------------------- checkpoint / resume
 struct StateHeader {
     char magic[8];                 // "LBMSTAT3"

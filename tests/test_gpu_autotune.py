@@ -9,7 +9,7 @@ the 40- and 48-register budgets and the persistent loop, which shows as differen
 1e-8 in the populations.  Programmatic dependent launch changes nothing, and one variant
 run twice is bitwise identical.  The bound POP_TOL is a hundred times that rounding; with
 16-bit storage such a difference can move a stored value by one unit in its last place
-(about 1e-5 at the magnitudes stored), hence POP_TOL_16."""
+(up to 1.2e-4 at the largest magnitudes stored, 0.1 .. 0.25), hence POP_TOL_16."""
 import numpy as np
 import pytest
 
@@ -19,7 +19,7 @@ from paper_2601_18443_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 POP_TOL = 1e-6
-POP_TOL_16 = 1e-4
+POP_TOL_16 = 5e-4
 
 
 def same_populations(a, b, L, tol=POP_TOL):

@@ -1,0 +1,98 @@
+"""Batched solves (lbm_batch): one launch per node of the level schedule advances the same
+level of every member.  Each member's result equals that solve stepped alone, up to FP32
+rounding (the batched kernel runs the same per-cell code under another instantiation; with
+16-bit storage a rounding difference can move a stored value by one unit in its last place),
+for members of different level counts and level-0 parities; a member stepped on its own
+invalidates the batch."""
+import numpy as np
+import pytest
+
+import paper_2601_18443_gb300 as pkg
+from paper_2601_18443_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases(store, n=5):
+    out = []
+    want_levels = [4, 5, 6, 4, 7, 5]
+    for q in W.polar_requests(256):
+        if want_levels and q["levels"] == want_levels[0]:
+            cfg, loops = W.polar_case(q)
+            out.append((dict(cfg, store=store), loops))
+            want_levels.pop(0)
+        if len(out) == n:
+            break
+    return out
+
+
+def _solvers(cases, pre):
+    ss = []
+    for (cfg, loops), k in zip(cases, pre):
+        s = pkg.Solver(cfg)
+        s.set_geometry(loops)
+        if k:
+            s.step(k)                  # members start at different steps and level-0 parities
+        ss.append(s)
+    return ss
+
+
+@pytest.mark.parametrize("store", [0, 1])
+def test_batched_members_equal_solves_alone(store):
+    import torch
+
+    pkg.build()
+    torch.cuda.set_device(0)
+    cases = _cases(store)
+    pre = [0, 1, 2, 3, 0]
+    alone = _solvers(cases, pre)
+    for s in alone:
+        s.step(60)
+    batched = _solvers(cases, pre)
+    b = pkg.Batch(batched)
+    info = b.info()
+    assert info["members"] == len(cases) and info["levels"] == max(c["levels"] for c, _ in cases)
+    # one launch per schedule node instead of one per node and solve
+    assert info["kernels_per_step"] < sum(s.info()["kernels_per_step"] for s in batched)
+    b.step(20)
+    b.step(40)
+    # 16-bit: a few units in the last place at the largest stored magnitudes (0.1 .. 0.25, unit 2^-13)
+    tol, ltol = (1e-6, 1e-5) if store == 0 else (5e-4, 1e-2)
+    for a, s, k in zip(alone, batched, pre):
+        la, ls = a.get_loads(), s.get_loads()
+        assert la["step"] == ls["step"] == k + 60
+        for lvl in (0, a.cfg["levels"] - 1):
+            x, y = a.get_populations(lvl), s.get_populations(lvl)
+            assert np.array_equal(np.isnan(x), np.isnan(y)), lvl
+            d = np.nanmax(np.abs(x - y))
+            assert d <= tol, (lvl, d)
+        assert abs(la["CD"] - ls["CD"]) <= ltol * abs(la["CD"])
+        assert abs(la["CL"] - ls["CL"]) <= ltol * max(abs(la["CL"]), abs(la["CD"]))
+        assert abs(la["mass"] - ls["mass"]) <= 1e-6 * la["mass"]
+    # a member stepped on its own leaves the batch's schedule
+    batched[2].step(1)
+    with pytest.raises(pkg.LBMError):
+        b.step(1)
+    b.close()
+    for s in alone + batched:
+        s.close()
+
+
+def test_batch_rejects_invalid_members():
+    import torch
+
+    pkg.build()
+    torch.cuda.set_device(0)
+    cases = _cases(0, 2)
+    ss = _solvers(cases, [0, 0])
+    with pytest.raises(pkg.LBMError):
+        pkg.Batch([ss[0], ss[0]])                      # the same solve twice
+    other = pkg.Solver(dict(cases[1][0], store=1))
+    other.set_geometry(cases[1][1])
+    with pytest.raises(pkg.LBMError):
+        pkg.Batch([ss[0], other])                      # mixed population storage
+    ss[1].step_launch(0, 0)
+    with pytest.raises(pkg.LBMError):
+        pkg.Batch(ss)                                  # off the level schedule
+    for s in ss + [other]:
+        s.close()
