@@ -464,12 +464,19 @@ def serving_arm(args):
     except Exception:
         pass
     out = {}
-    arms = [("batched", args.serving_slots)] + ([] if args.serving_no_baseline else [("one_at_a_time", 1)])
+    # batched: resident solves stepped together, one launch per level-schedule node for all of
+    # them (lbm_batch); streams: the same slots, each solve on its own stream with its own
+    # launches; one_at_a_time: one slot
+    arms = [("batched", args.serving_slots, True)]
+    if not args.serving_no_baseline:
+        arms += [("streams", args.serving_slots, False), ("one_at_a_time", 1, False)]
+    if args.serving_arms:
+        arms = [a for a in arms if a[0] in args.serving_arms.split(",")]
     clk = None
-    for name, slots in arms:
+    for name, slots, batched in arms:
         clocks = ClockSampler(uuid)
         clocks.start()
-        svc = Service(max_slots=slots, backend=GpuBackend())
+        svc = Service(max_slots=slots, backend=GpuBackend(), batched=batched)
         res = svc.run(reqs)
         c = clocks.stop()
         if name == "batched":
@@ -489,7 +496,7 @@ def serving_arm(args):
         sm["by_levels"] = {L: dict(n=len(v), steps_mean=float(np.mean([r.steps for r in v])),
                                    latency_p50_s=float(np.median([r.latency for r in v])))
                            for L, v in sorted(by_levels.items())}
-    b = out["batched"]
+    b = out[arms[0][0]]
     line = {"metric": "solves_per_hour", "value": b.get("solves_per_hour"), "unit": "solves/h", "n_gpus": 1,
             "higher_is_better": True, "impl": "ours", "dtype": "f16-store/f32",
             "data": "synthetic", "config": {"workload": f"polar_stream_{args.serving}req_seed2026",
@@ -525,6 +532,7 @@ def main():
     ap.add_argument("--serving-window", type=int, default=8, help="chunks of 100 level-0 steps per CL window")
     ap.add_argument("--serving-tol", type=float, default=5e-3, help="|change of the window-mean CL|")
     ap.add_argument("--serving-no-baseline", action="store_true")
+    ap.add_argument("--serving-arms", default="", help="comma list of arms to run: batched,streams,one_at_a_time")
     ap.add_argument("--serving-dump", default=None, help="write per-request results to <path>.<arm>.json")
     args = ap.parse_args()
     if args.profile_case:

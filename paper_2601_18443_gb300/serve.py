@@ -76,15 +76,20 @@ class SolveResult:
 
 
 class _GpuHandle:
-    def __init__(self, solver, stream):
+    def __init__(self, solver, stream, backend=None):
         import torch
 
         self.solver = solver
         self.stream = stream
+        self.backend = backend
         self.event = torch.cuda.Event()
 
     def enqueue(self, n):
         self.solver.step_async(n)
+        self.event.record(self.stream)
+
+    def mark(self):
+        """After a batched chunk: the chunk is done when this solve's stream reaches here."""
         self.event.record(self.stream)
 
     def ready(self):
@@ -96,12 +101,53 @@ class _GpuHandle:
         return self.solver.coefficients()
 
     def close(self):
+        if self.backend is not None:
+            self.backend.drop_batches(self)
         self.solver.close()
 
 
 class GpuBackend:
     """Solves on the current CUDA device through the C ABI (one stream per solve, device
-    memory from PyTorch's caching allocator through the allocation hooks)."""
+    memory from PyTorch's caching allocator through the allocation hooks).  step_batch
+    advances several solves as lbm_batch batches (one launch per level-schedule node for
+    all of them), regrouped whenever the set of solves changes."""
+
+    def __init__(self):
+        self._batches = {}           # group key -> [(member handles, Batch)]
+
+    def step_batch(self, handles, n, key=0):
+        """Advance the handles of one group by n level-0 steps as lbm_batch batches (one
+        storage type per batch, at most 24 solves each), rebuilt when the group changes."""
+        from . import Batch
+
+        ids = [id(h) for h in handles]
+        cur = self._batches.get(key, [])
+        if [id(h) for grp, _ in cur for h in grp] != ids:
+            self._drop(key)
+            groups = {}
+            for h in handles:
+                groups.setdefault(h.solver.cfg.get("store", 0), []).append(h)
+            cur = []
+            for grp in groups.values():
+                for i in range(0, len(grp), 24):
+                    part = grp[i:i + 24]
+                    cur.append((part, Batch([h.solver for h in part])))
+            self._batches[key] = cur
+            handles[:] = [h for grp, _ in cur for h in grp]
+        for _, b in cur:
+            b.step(n)
+        for h in handles:
+            h.mark()
+
+    def _drop(self, key):
+        for _, b in self._batches.pop(key, []):
+            b.close()
+
+    def drop_batches(self, handle=None):
+        """Close the batches holding handle (every batch with handle None)."""
+        for key in list(self._batches):
+            if handle is None or any(handle is h for grp, _ in self._batches[key] for h in grp):
+                self._drop(key)
 
     def plan(self, cfg, loops):
         from . import plan
@@ -120,7 +166,7 @@ class GpuBackend:
         except Exception:
             s.close()
             raise
-        return _GpuHandle(s, stream)
+        return _GpuHandle(s, stream, self)
 
     def free_bytes(self):
         import torch
@@ -134,12 +180,13 @@ class GpuBackend:
 
 
 class _Slot:
-    __slots__ = ("req", "res", "handle", "need", "calm", "enqueued", "released")
+    __slots__ = ("req", "res", "handle", "need", "calm", "enqueued", "done", "released")
 
     def __init__(self, req, res, handle, need):
         self.req, self.res, self.handle, self.need = req, res, handle, need
         self.calm = 0
-        self.enqueued = 0
+        self.enqueued = 0            # level-0 steps enqueued
+        self.done = 0                # level-0 steps whose chunk has been read (batched mode)
         self.released = False
 
 
@@ -152,9 +199,17 @@ class Service:
     builders      worker threads for planning and grid building; each build uses an equal
                   share of the host processors (concurrent builds that each took all of
                   them would oversubscribe the cores)
+    batched       step the resident solves of the same level count together, in lockstep
+                  chunks through the backend's step_batch (one launch per level-schedule node
+                  for the group); groups advance independently, and a solve whose build
+                  finishes during its group's chunk joins at the group's next chunk.  (One
+                  lockstep group for all solves would hold the shallow solves to the pace
+                  of the deepest one.)
     """
 
-    def __init__(self, max_slots=8, mem_budget=None, overhead=16 << 20, builders=4, poll_s=2e-4, backend=None):
+    def __init__(self, max_slots=8, mem_budget=None, overhead=16 << 20, builders=4, poll_s=2e-4, backend=None,
+                 batched=False):
+        self.batched = bool(batched)
         self.max_slots = int(max_slots)
         self.backend = backend or GpuBackend()
         self.mem_budget = mem_budget
@@ -252,6 +307,10 @@ class Service:
                             continue
                         slot = _Slot(r, res, h, need)
                         res.started = now()
+                        if self.batched:         # joins the next lockstep chunk
+                            active.append(slot)
+                            note("start", r.rid)
+                            continue
                         try:
                             self._enqueue(slot)
                         except Exception as e:   # the solve could not be stepped: release it
@@ -264,6 +323,51 @@ class Service:
                         active.append(slot)
                         note("start", r.rid)
                     building = still
+
+                    # batched: per level-count group, when the lockstep chunk of every member is
+                    # done, every member reads CL; the continuing ones and the newcomers of the
+                    # group step its next chunk together
+                    if self.batched:
+                        groups = {}
+                        for slot in active:
+                            groups.setdefault(self._group(slot), []).append(slot)
+                        active = []
+                        for key, grp in groups.items():
+                            if not all(sl.handle.ready() for sl in grp if sl.enqueued > sl.done):
+                                active += grp
+                                continue
+                            moved = True
+                            keep = []
+                            for slot in grp:
+                                if slot.enqueued > slot.done:
+                                    slot.done = slot.enqueued
+                                    if not self._advance(slot, enqueue=False):
+                                        self._finish(slot, now, on_finish, note)
+                                        used -= slot.need
+                                        resident -= 1
+                                        continue
+                                keep.append(slot)
+                            if keep:
+                                n = min(min(sl.req.check_every, sl.req.max_steps - sl.enqueued) for sl in keep)
+                                handles = [sl.handle for sl in keep]
+                                try:
+                                    self.backend.step_batch(handles, n, key)
+                                except Exception as e:
+                                    for slot in keep:
+                                        slot.res.status, slot.res.message = "error", str(e)
+                                        self._finish(slot, now, on_finish, note)
+                                        used -= slot.need
+                                        resident -= 1
+                                    keep = []
+                                else:
+                                    pos = {id(h): k for k, h in enumerate(handles)}
+                                    keep.sort(key=lambda sl: pos[id(sl.handle)])
+                                    for slot in keep:
+                                        slot.enqueued += n
+                            active += keep
+                        if not moved:
+                            time.sleep(self.poll_s)
+                        continue
 
                     # chunks that completed: read CL, test convergence, continue or finish
                     keep = []
@@ -301,13 +405,28 @@ class Service:
                         pass
         return [results[r.rid] for r in requests]
 
+    @staticmethod
+    def _group(slot):
+        """Lockstep group of a solve in batched mode: its level count."""
+        return slot.req.cfg.get("levels", 1)
+
+    def _finish(self, slot, now, on_finish, note):
+        slot.res.finished = now()
+        try:
+            if on_finish is not None:
+                on_finish(slot.res, slot.handle)
+        finally:
+            slot.handle.close()
+            slot.released = True
+            note("finish", slot.req.rid)
+
     def _enqueue(self, slot):
         r = slot.req
         n = min(r.check_every, r.max_steps - slot.enqueued)
         slot.handle.enqueue(n)
         slot.enqueued += n
 
-    def _advance(self, slot):
+    def _advance(self, slot, enqueue=True):
         """Handle a completed chunk; True while the solve continues."""
         r, res = slot.req, slot.res
         try:
@@ -336,7 +455,8 @@ class Service:
         if slot.enqueued >= r.max_steps:
             res.status = "max_steps"
             return False
-        self._enqueue(slot)
+        if enqueue:
+            self._enqueue(slot)
         return True
 
 

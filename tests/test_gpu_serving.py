@@ -25,7 +25,7 @@ def _requests(n=5, steps=300, levels=(4, 5), stagger=0.02):
     return out
 
 
-def _serve(reqs, slots, budget=8 << 30):
+def _serve(reqs, slots, budget=8 << 30, batched=False):
     snaps = {}
 
     def keep(res, h):
@@ -33,7 +33,7 @@ def _serve(reqs, slots, budget=8 << 30):
         L = s.cfg["levels"]
         snaps[res.rid] = (s.get_populations(0), s.get_populations(L - 1))
 
-    svc = Service(max_slots=slots, mem_budget=budget, backend=GpuBackend())
+    svc = Service(max_slots=slots, mem_budget=budget, backend=GpuBackend(), batched=batched)
     res = svc.run(reqs, on_finish=keep)
     return svc, res, snaps
 
@@ -70,6 +70,27 @@ def test_results_alone_equal_results_in_the_mix():
         ha, hb = np.array(a.history), np.array(b.history)
         assert ha.shape == hb.shape
         np.testing.assert_allclose(ha, hb, rtol=0, atol=1e-12)
+
+
+def test_batched_service_results_equal_results_alone():
+    # resident solves stepped together by batched launches (lbm_batch) give each solve's own
+    # result: FP16 storage, so up to a few 16-bit units in the last place in the populations
+    # and the 16-bit error level in the loads
+    pkg.build()
+    reqs = _requests(5, levels=(4, 5, 6))
+    _, alone, snaps_alone = _serve(reqs, slots=1)
+    svc, mixed, snaps_mixed = _serve(reqs, slots=5, batched=True)
+    assert all(r.status == "max_steps" and r.steps == 300 for r in alone + mixed), \
+        [(r.rid, r.status, r.steps, r.message) for r in alone + mixed]
+    assert max(res for _, _, _, _, res in svc.trace) >= 2
+    for a, b in zip(alone, mixed):
+        for pa, pb in zip(snaps_alone[a.rid], snaps_mixed[b.rid]):
+            assert np.array_equal(np.isnan(pa), np.isnan(pb))
+            assert np.nanmax(np.abs(pa - pb)) <= 5e-4
+        ha, hb = np.array(a.history), np.array(b.history)
+        assert ha.shape == hb.shape and np.array_equal(ha[:, 0], hb[:, 0])
+        scale = np.maximum(np.abs(ha[:, 1]), np.abs(ha[:, 2]))
+        assert np.all(np.abs(ha[:, 1:] - hb[:, 1:]) <= 1e-2 * scale[:, None])
 
 
 def test_memory_budget_limits_the_resident_solves():

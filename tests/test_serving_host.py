@@ -243,3 +243,50 @@ def test_host_thread_count_leaves_the_grid_unchanged():
         assert pkg.grid_digest(cfg, loops) == ref
     finally:
         pkg.set_host_threads(0)
+
+
+class BatchingBackend(FakeBackend):
+    """Steps all handles of a batch together (the cost of the batch's slowest member) and
+    records the chunks it was given."""
+
+    def __init__(self, **kw):
+        super().__init__(**kw)
+        self.chunks = []               # (member rids, steps)
+
+    def step_batch(self, handles, n, key=0):
+        self.chunks.append(([h.req.rid for h in handles], n, key))
+        cost = max(h.req.cfg["cost"] for h in handles)
+        t = time.perf_counter() + n * cost
+        for h in handles:
+            h.steps += n
+            h.ready_at = t
+
+
+def test_batched_mode_steps_members_in_lockstep_with_the_same_results():
+    reqs = [make(k, 0.002 * k, 1 << 20, cost=2e-5, tau=100.0 + 30 * k) for k in range(6)]
+    reqs[4].cfg["diverge_at"] = 400
+    for k, r in enumerate(reqs):
+        r.cfg["levels"] = 4 + k % 2          # two lockstep groups
+    be = BatchingBackend()
+    svc = Service(max_slots=3, mem_budget=64 << 20, overhead=0, backend=be, batched=True)
+    res = svc.run(reqs)
+    alone = Service(max_slots=3, mem_budget=64 << 20, overhead=0, backend=FakeBackend()).run(reqs)
+    # same statuses, step counts and CL histories as the unbatched service
+    for a, b in zip(alone, res):
+        assert (a.status, a.steps) == (b.status, b.steps)
+        assert a.history == b.history
+    assert res[4].status == "diverged" and res[4].steps == 400
+    # every chunk steps each member by the same count; no chunk holds more than the slots;
+    # a chunk holds solves of one level count only
+    assert all(n == 100 for _, n, _ in be.chunks)
+    assert all(len(m) <= 3 for m, _, _ in be.chunks)
+    assert all({reqs[rid].cfg["levels"] for rid in m} == {key} for m, _, key in be.chunks)
+    # a member appears in consecutive chunks of its group from its first to its last
+    for r in res:
+        key = reqs[r.rid].cfg["levels"]
+        mine = [m for m, _, k in be.chunks if k == key]
+        seen = [k for k, m in enumerate(mine) if r.rid in m]
+        assert seen == list(range(seen[0], seen[-1] + 1))
+        assert len(seen) * 100 == r.steps
+    check_trace(svc, 64 << 20, 3)
+    assert be.live == 0 and all(h.closed for h in be.handles)
