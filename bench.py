@@ -371,6 +371,7 @@ def gpu_arm(args, rank, world, dist):
             "e2e": e2e,
             "autotune": None if tune is None else {
                 "min_blocks_per_level": tune["min_blocks"], "persistent_per_level": tune["persistent"],
+                "shape_per_level": tune["shape"],
                 "pdl": tune["pdl"],
                 "step_us_default": round(tune["default_step_us"], 2),
                 "step_us_tuned": round(min(tune["step_us"].values()), 2)},

@@ -66,14 +66,14 @@ class lbm_kernel_times(C.Structure):
                 ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
 
 
-TUNE_CANDIDATES = 4
+TUNE_CANDIDATES = 8
 
 
 class lbm_tune_report(C.Structure):
     _fields_ = [("levels", C.c_int), ("candidate_min_blocks", C.c_int * TUNE_CANDIDATES),
-                ("candidate_persistent", C.c_int * TUNE_CANDIDATES),
+                ("candidate_persistent", C.c_int * TUNE_CANDIDATES), ("candidate_shape", C.c_int * TUNE_CANDIDATES),
                 ("level_us", (C.c_double * 16) * TUNE_CANDIDATES), ("min_blocks", C.c_int * 16),
-                ("persistent", C.c_int * 16), ("step_us_confirm", C.c_double * 3),
+                ("persistent", C.c_int * 16), ("shape", C.c_int * 16), ("step_us_confirm", C.c_double * 3),
                 ("default_step_us", C.c_double), ("step_us", C.c_double * 2),
                 ("pdl", C.c_int), ("steps_taken", C.c_longlong)]
 
@@ -124,7 +124,7 @@ def library():
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
-        "lbm_set_launch_variant": ([vp, ip, ip, C.c_int], C.c_int),
+        "lbm_set_launch_variant": ([vp, ip, ip, ip, C.c_int], C.c_int),
         "lbm_get_state": ([vp, vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
         "lbm_set_state": ([vp, vp, C.c_size_t], C.c_int),
         "lbm_level_mass_noalloc": ([vp, vp, vp, vp, vp, C.c_longlong, C.c_double, vp, vp, vp], C.c_int),
@@ -423,12 +423,14 @@ class Solver:
         b = np.ascontiguousarray(blob, dtype=np.uint8)
         self._check(self._lib.lbm_set_state(self._h, b.ctypes.data_as(C.c_void_p), b.size))
 
-    def set_launch_variant(self, min_blocks, pdl=1, persistent=None):
+    def set_launch_variant(self, min_blocks, pdl=1, persistent=None, shape=None):
         """lbm_set_launch_variant: per-level register budget (5 or 6 blocks per SM), grid
-        schedule (persistent 0/1) and PDL."""
+        schedule (persistent 0/1), work shape of a warp (0 a 16 x 2 block, 1 a 32-cell row)
+        and PDL."""
         mb = np.ascontiguousarray(min_blocks, dtype=np.int32)
         pe = np.ascontiguousarray(persistent if persistent is not None else [0] * len(mb), dtype=np.int32)
-        self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), _ip(pe), int(pdl)))
+        sh = np.ascontiguousarray(shape if shape is not None else [0] * len(mb), dtype=np.int32)
+        self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), _ip(pe), _ip(sh), int(pdl)))
 
     def time_kernels(self, n=1):
         out = lbm_kernel_times()
@@ -439,10 +441,11 @@ class Solver:
 
 def _tune_dict(out):
     L = out.levels
-    cand = list(zip(out.candidate_min_blocks, out.candidate_persistent))
+    cand = list(zip(out.candidate_min_blocks, out.candidate_persistent, out.candidate_shape))
     return dict(levels=L, candidates=cand,
                 level_us={c: list(out.level_us[i][:L]) for i, c in enumerate(cand)},
                 min_blocks=list(out.min_blocks[:L]), persistent=list(out.persistent[:L]),
+                shape=list(out.shape[:L]),
                 step_us_confirm={"pick": out.step_us_confirm[0], "pick_no_persistent": out.step_us_confirm[1],
                                  "before": out.step_us_confirm[2]},
                 default_step_us=out.default_step_us,

@@ -85,17 +85,20 @@ struct LevelStep {
     int wall;           // this level holds the wall records (finest level)
     int restrict_up;    // write the restriction of this level's new fields into level l-1
     int pp;             // time level of level l-1 (restriction writes [pp ^ 1])
+    int shape;          // cells of a warp: 0 a 16 x 2 block, 1 a 32 x 1 row of the tile
     int *status;        // device status word (LBM_STATUS_* bits)
 };
 
 // Launch variant of a level's kernels (chosen by lbm_autotune): the register budget of the
 // fused level kernel, as the minimum resident blocks per SM (5 or 6), whether its blocks
-// persist over several tiles, and whether launches use programmatic dependent launch.
-// Every variant computes the same numbers.
+// persist over several tiles, the cells a warp covers within the tile, and whether
+// launches use programmatic dependent launch.  Every variant computes the same numbers
+// up to FP32 rounding.
 struct LevelTune {
     int min_blocks;
     int pdl;
     int persistent;     // grid of 2 x SMs x min_blocks blocks striding over the work tiles
+    int shape;          // work shape of a warp (LevelStep::shape)
 };
 
 

@@ -49,15 +49,22 @@ __device__ __forceinline__ void load_nb3(const LevelView &P, int t, int *nb3)
     if (threadIdx.x < 9) nb3[threadIdx.x] = P.nbr[t * 9 + dir_of3(threadIdx.x)];
 }
 
-// Thread -> cell map of the level kernel: warp w covers the 16 x 2 cells
-// x in [16 (w & 1), +16), y in {2 (w >> 1), +1}, so that every 2 x 2 group of children
-// (restriction) lies inside one warp.  A warp still reads two 64-byte row segments per
-// plane, i.e. whole 32-byte sectors.
-__device__ __forceinline__ void cell_of_thread(int c, int &lx, int &ly)
+// Thread -> cell map of the level kernel (the work shape of a warp).  Shape 0: warp w
+// covers the 16 x 2 cells x in [16 (w & 1), +16), y in {2 (w >> 1), +1}, so that every 2 x 2
+// group of children lies inside one warp (the restriction is a warp shuffle) and a warp
+// reads two 64-byte row segments per plane.  Shape 1: warp w covers row w, one 128-byte
+// segment per plane, so that an access shifted by one cell touches 5 sectors instead of 6;
+// its 2 x 2 groups span two warps and the restriction goes through shared memory.
+__device__ __forceinline__ void cell_of_thread(int c, int &lx, int &ly, int shape)
 {
     const int w = c >> 5, lane = c & 31;
-    lx = (w & 1) * 16 + (lane & 15);
-    ly = (w >> 1) * 2 + (lane >> 4);
+    if (shape) {
+        lx = lane;
+        ly = w;
+    } else {
+        lx = (w & 1) * 16 + (lane & 15);
+        ly = (w >> 1) * 2 + (lane >> 4);
+    }
 }
 
 // slot of the cell at offset (dx, dy) from (lx, ly), or -1 if its tile is absent
@@ -559,7 +566,7 @@ __device__ __forceinline__ void explode_band(const LevelView &P, const LevelView
 template <bool WALL, bool CHILD, typename T, bool ODD, bool FL_GIVEN>
 __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &F, const LevelView &C, const RecView &R,
                                            const StepConsts &k, const LevelStep &ls, const Lat<T> &L, int t, int lane,
-                                           int lx, int ly, const int *nb3, uint32_t fl_given)
+                                           int lx, int ly, const int *nb3, uint32_t fl_given, float *red)
 {
     const int slot = t * LBM_TILE + ly * LBM_TX + lx;
     const uint32_t fl = FL_GIVEN ? fl_given : __ldg(P.flags + slot);
@@ -738,20 +745,38 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
 
     if (ls.restrict_up) {
         // restriction into the covered parents (their children are this level's active
-        // cells; a 2 x 2 group of children lies inside one warp, lanes l, l+1, l+16, l+17):
-        // rho and chi are the means over the fluid children, u is mass-weighted (Rohde
-        // transfers, Sec 2.1)
+        // cells): rho and chi are the means over the fluid children, u is mass-weighted
+        // (Rohde transfers, Sec 2.1).  Sums in the order ((x, y) + (x+1, y)) + ((x, y+1) +
+        // (x+1, y+1)) in both work shapes.
         const float rr = valid ? 1.0f + n_dr : 0.0f;
         float a0 = valid ? n_dr : 0.0f, a1 = rr, a2 = rr * n_ux, a3 = rr * n_uy, a4 = valid ? n_chi : 0.0f;
         float a5 = valid ? 1.0f : 0.0f;
-        // sum over (l, l+1) then over (l, l+16)
+        bool head;
+        if (ls.shape == 0) {
+            // a 2 x 2 group lies inside the warp, lanes l, l+1, l+16, l+17: sum over (l, l+1)
+            // then over (l, l+16)
 #pragma unroll
-        for (int d = 1; d <= 16; d <<= 4) {
-            a0 += __shfl_down_sync(0xffffffffu, a0, d); a1 += __shfl_down_sync(0xffffffffu, a1, d);
-            a2 += __shfl_down_sync(0xffffffffu, a2, d); a3 += __shfl_down_sync(0xffffffffu, a3, d);
-            a4 += __shfl_down_sync(0xffffffffu, a4, d); a5 += __shfl_down_sync(0xffffffffu, a5, d);
+            for (int d = 1; d <= 16; d <<= 4) {
+                a0 += __shfl_down_sync(0xffffffffu, a0, d); a1 += __shfl_down_sync(0xffffffffu, a1, d);
+                a2 += __shfl_down_sync(0xffffffffu, a2, d); a3 += __shfl_down_sync(0xffffffffu, a3, d);
+                a4 += __shfl_down_sync(0xffffffffu, a4, d); a5 += __shfl_down_sync(0xffffffffu, a5, d);
+            }
+            head = !(lane & 1) && lane < 16;
+        } else {
+            // rows ly and ly + 1 are two warps: pairs along x by shuffle, then the two rows
+            // through shared memory behind a block barrier (this branch is block-uniform)
+            a0 += __shfl_down_sync(0xffffffffu, a0, 1); a1 += __shfl_down_sync(0xffffffffu, a1, 1);
+            a2 += __shfl_down_sync(0xffffffffu, a2, 1); a3 += __shfl_down_sync(0xffffffffu, a3, 1);
+            a4 += __shfl_down_sync(0xffffffffu, a4, 1); a5 += __shfl_down_sync(0xffffffffu, a5, 1);
+            float *rs = red + 6 * (ly * LBM_TX + lx);
+            rs[0] = a0; rs[1] = a1; rs[2] = a2; rs[3] = a3; rs[4] = a4; rs[5] = a5;
+            __syncthreads();
+            const float *rn = red + 6 * (((ly + 1) & (LBM_TY - 1)) * LBM_TX + lx);
+            a0 += rn[0]; a1 += rn[1]; a2 += rn[2]; a3 += rn[3]; a4 += rn[4]; a5 += rn[5];
+            __syncthreads();
+            head = !(lx & 1) && !(ly & 1);
         }
-        if (!(lane & 1) && lane < 16 && kind == KIND_ACTIVE) {
+        if (head && kind == KIND_ACTIVE) {
             const int pt = P.parent[t];
             const int n = (int)a5;
             if (pt >= 0 && n > 0) {
@@ -778,10 +803,12 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
 {
     const Lat<T> L{static_cast<T *>(P.f), P.ns, k.pshift};
     __shared__ int nb3w[LBM_TILE / 32][9];       // one copy per warp: no block-wide barrier
+    extern __shared__ float red[];               // restriction sums of work shape 1 (dynamic:
+                                                 // 6 floats a thread, launched with shape 1 only)
     const int c = threadIdx.x;
     const int lane = c & 31;
     int lx, ly;
-    cell_of_thread(c, lx, ly);
+    cell_of_thread(c, lx, ly, ls.shape);
     int *nb3 = nb3w[c >> 5];
     if constexpr (!PERSIST) {
         const int t = P.work_tiles[blockIdx.x];
@@ -789,7 +816,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
         __syncwarp();
         griddep_launch();
         griddep_wait();
-        level_tile<WALL, CHILD, T, ODD, false>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, 0u);
+        level_tile<WALL, CHILD, T, ODD, false>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, 0u, red);
     } else {
         // the grid tables are static: the first tile's neighbour table and flag word are
         // read before the wait, and each tile's flag word one tile ahead
@@ -814,7 +841,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
                 if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
                 __syncwarp();
             }
-            level_tile<WALL, CHILD, T, ODD, true>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, fl);
+            level_tile<WALL, CHILD, T, ODD, true>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, fl, red);
         }
     }
 
@@ -831,10 +858,11 @@ __global__ void __launch_bounds__(256, 5) k_level_batch(const __grid_constant__ 
         if (a.d[m].first_block <= (int)blockIdx.x) i = m;
     const SolveDesc &d = a.d[i];
     __shared__ int nb3w[LBM_TILE / 32][9];
+    float *red = nullptr;                        // batched launches use work shape 0
     const int c = threadIdx.x;
     const int lane = c & 31;
     int lx, ly;
-    cell_of_thread(c, lx, ly);
+    cell_of_thread(c, lx, ly, 0);
     int *nb3 = nb3w[c >> 5];
     const int t = d.P.work_tiles[blockIdx.x - d.first_block];
     if (lane < 9) nb3[lane] = d.P.nbr[t * 9 + dir_of3(lane)];
@@ -844,14 +872,14 @@ __global__ void __launch_bounds__(256, 5) k_level_batch(const __grid_constant__ 
     const Lat<T> L{static_cast<T *>(d.P.f), d.P.ns, d.k.pshift};
     const bool odd = d.ls.p != 0;
     if (d.kind == 2) {
-        if (odd) level_tile<true, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
-        else level_tile<true, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
+        if (odd) level_tile<true, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
+        else level_tile<true, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
     } else if (d.kind == 1) {
-        if (odd) level_tile<false, true, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
-        else level_tile<false, true, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
+        if (odd) level_tile<false, true, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
+        else level_tile<false, true, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
     } else {
-        if (odd) level_tile<false, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
-        else level_tile<false, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u);
+        if (odd) level_tile<false, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
+        else level_tile<false, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
     }
 }
 
@@ -1143,12 +1171,12 @@ __global__ void __launch_bounds__(256) k_mass(LevelView P, int p, double area, d
 // ------------------------------------------------------------------ launchers
 // launch, with programmatic stream serialization when pdl is set (see griddep_wait)
 template <typename... Args>
-static void launch_pdl(void (*kern)(Args...), unsigned grid, cudaStream_t st, int pdl, Args... args)
+static void launch_pdl_smem(void (*kern)(Args...), unsigned grid, cudaStream_t st, int pdl, size_t smem, Args... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(LBM_TILE);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1158,6 +1186,12 @@ static void launch_pdl(void (*kern)(Args...), unsigned grid, cudaStream_t st, in
     cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+template <typename... Args>
+static void launch_pdl(void (*kern)(Args...), unsigned grid, cudaStream_t st, int pdl, Args... args)
+{
+    launch_pdl_smem(kern, grid, st, pdl, 0, args...);
+}
+
 // the level holding the wall records is the finest one, which has no child level
 template <typename T, int MINB, bool PERSIST, bool ODD>
 static void launch_level_mb(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
@@ -1165,9 +1199,10 @@ static void launch_level_mb(cudaStream_t st, const LevelView &P, const LevelView
 {
     // persistent: two rounds of the resident blocks stride over the work tiles
     const unsigned grid = PERSIST ? (unsigned)std::min(P.n_work_tiles, 2 * k.sms * MINB) : (unsigned)P.n_work_tiles;
-    if (ls.wall) launch_pdl(k_level<true, false, T, MINB, PERSIST, ODD>, grid, st, pdl, P, Fv, Cv, R, k, ls);
-    else if (child) launch_pdl(k_level<false, true, T, MINB, PERSIST, ODD>, grid, st, pdl, P, Fv, Cv, R, k, ls);
-    else launch_pdl(k_level<false, false, T, MINB, PERSIST, ODD>, grid, st, pdl, P, Fv, Cv, R, k, ls);
+    const size_t smem = ls.shape ? 6 * LBM_TILE * sizeof(float) : 0;
+    if (ls.wall) launch_pdl_smem(k_level<true, false, T, MINB, PERSIST, ODD>, grid, st, pdl, smem, P, Fv, Cv, R, k, ls);
+    else if (child) launch_pdl_smem(k_level<false, true, T, MINB, PERSIST, ODD>, grid, st, pdl, smem, P, Fv, Cv, R, k, ls);
+    else launch_pdl_smem(k_level<false, false, T, MINB, PERSIST, ODD>, grid, st, pdl, smem, P, Fv, Cv, R, k, ls);
 }
 
 template <typename T, bool ODD>

@@ -97,6 +97,7 @@ struct lbm_solver {
     int parity[LBM_MAXL];
     int min_blocks[LBM_MAXL];     // register budget of each level's kernel (lbm_autotune)
     int persistent[LBM_MAXL];     // persistent grid for each level's kernel (lbm_autotune)
+    int shape[LBM_MAXL];          // work shape of a warp for each level's kernel (lbm_autotune)
     int pdl = 1;                  // programmatic dependent launch (lbm_autotune)
     bool off_schedule = false;    // single launches (lbm_step_launch) left the level schedule
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -270,9 +271,10 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     ls.wall = (l == L - 1) && s->rec.n > 0;
     ls.restrict_up = restrict_up && C != nullptr;
     ls.pp = C ? s->parity[l - 1] : 0;
+    ls.shape = s->shape[l];
     ls.status = s->d_status;
     mark_begin(s);
-    const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl, s->persistent[l]};
+    const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl, s->persistent[l], s->shape[l]};
     lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls, tu);
     mark_end(s, l == L - 1 ? KC_LEVEL_FINEST : KC_LEVEL_COARSE, P.ns, l);
     nk++;
@@ -382,7 +384,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
     s->cfg = *cfg;
     s->L = cfg->levels;
     s->U = cfg->Ma * std::sqrt(1.0 / 3.0);
-    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; s->persistent[l] = 0; }
+    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; s->persistent[l] = 0; s->shape[l] = 0; }
     if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LBM_ERR_CUDA; }
     if (cfg->cuda_stream) {
         s->stream = (cudaStream_t)cfg->cuda_stream;
@@ -830,8 +832,9 @@ lbm_status lbm_step_launch(lbm_solver *s, int level, int kind)
         ls.wall = (l == L - 1) && s->rec.n > 0;
         ls.restrict_up = kind == 1 && C != nullptr;
         ls.pp = C ? s->parity[l - 1] : 0;
+        ls.shape = s->shape[l];
         ls.status = s->d_status;
-        const lbmdev::LevelTune tu{s->min_blocks[l], 0, s->persistent[l]};
+        const lbmdev::LevelTune tu{s->min_blocks[l], 0, s->persistent[l], s->shape[l]};
         lbmdev::launch_level(s->stream, P, F, C, s->rec, s->k, ls, tu);
         s->parity[l] ^= 1;
     }
@@ -1317,23 +1320,25 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
 {
     if (!s || !out || steps < 1) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
-    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6, 5, 6};
-    static const int CAND_PE[LBM_TUNE_CANDIDATES] = {0, 0, 1, 1};
+    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6, 5, 6, 5, 6, 5, 6};
+    static const int CAND_PE[LBM_TUNE_CANDIDATES] = {0, 0, 1, 1, 0, 0, 1, 1};
+    static const int CAND_SH[LBM_TUNE_CANDIDATES] = {0, 0, 0, 0, 1, 1, 1, 1};
     std::memset(out, 0, sizeof *out);
     const int L = s->L;
     out->levels = L;
     lbm_status st;
     if ((st = graph_step_time(s, steps, &out->default_step_us)) != LBM_OK) return st;
-    int keep_mb[LBM_MAXL], keep_pe[LBM_MAXL];
-    for (int l = 0; l < L; l++) { keep_mb[l] = s->min_blocks[l]; keep_pe[l] = s->persistent[l]; }
+    int keep_mb[LBM_MAXL], keep_pe[LBM_MAXL], keep_sh[LBM_MAXL];
+    for (int l = 0; l < L; l++) { keep_mb[l] = s->min_blocks[l]; keep_pe[l] = s->persistent[l]; keep_sh[l] = s->shape[l]; }
     // 1: register budget and grid schedule per level, from per-launch event timings of
     //    every candidate
     for (int c = 0; c < LBM_TUNE_CANDIDATES; c++) {
-        for (int l = 0; l < L; l++) { s->min_blocks[l] = CAND_MB[c]; s->persistent[l] = CAND_PE[c]; }
+        for (int l = 0; l < L; l++) { s->min_blocks[l] = CAND_MB[c]; s->persistent[l] = CAND_PE[c]; s->shape[l] = CAND_SH[c]; }
         out->candidate_min_blocks[c] = CAND_MB[c];
         out->candidate_persistent[c] = CAND_PE[c];
+        out->candidate_shape[c] = CAND_SH[c];
         if ((st = level_launch_times(s, steps, out->level_us[c])) != LBM_OK) {
-            for (int l = 0; l < L; l++) { s->min_blocks[l] = keep_mb[l]; s->persistent[l] = keep_pe[l]; }
+            for (int l = 0; l < L; l++) { s->min_blocks[l] = keep_mb[l]; s->persistent[l] = keep_pe[l]; s->shape[l] = keep_sh[l]; }
             return st;
         }
     }
@@ -1343,22 +1348,25 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
             if (out->level_us[c][l] < out->level_us[best][l]) best = c;
         s->min_blocks[l] = CAND_MB[best];
         s->persistent[l] = CAND_PE[best];
+        s->shape[l] = CAND_SH[best];
         out->min_blocks[l] = CAND_MB[best];
         out->persistent[l] = CAND_PE[best];
+        out->shape[l] = CAND_SH[best];
     }
     // 1b: per-launch timings miss how launches overlap inside the graph (a persistent grid
     //     occupies every SM while the next launch would start): keep the per-level choice
     //     only if whole graph steps confirm it, against the same choice without persistent
     //     grids and against the default form
     {
-        int pick_mb[LBM_MAXL], pick_pe[LBM_MAXL];
-        for (int l = 0; l < L; l++) { pick_mb[l] = s->min_blocks[l]; pick_pe[l] = s->persistent[l]; }
+        int pick_mb[LBM_MAXL], pick_pe[LBM_MAXL], pick_sh[LBM_MAXL];
+        for (int l = 0; l < L; l++) { pick_mb[l] = s->min_blocks[l]; pick_pe[l] = s->persistent[l]; pick_sh[l] = s->shape[l]; }
         double best_us = 0.0;
         int best = 0;
         for (int v = 0; v < 3; v++) {
             for (int l = 0; l < L; l++) {
                 s->min_blocks[l] = v == 2 ? keep_mb[l] : pick_mb[l];
                 s->persistent[l] = v == 0 ? pick_pe[l] : (v == 1 ? 0 : keep_pe[l]);
+                s->shape[l] = v == 2 ? keep_sh[l] : pick_sh[l];
             }
             double us = 0.0;
             if ((st = capture_graphs(s)) != LBM_OK) return st;
@@ -1369,8 +1377,10 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
         for (int l = 0; l < L; l++) {
             s->min_blocks[l] = best == 2 ? keep_mb[l] : pick_mb[l];
             s->persistent[l] = best == 0 ? pick_pe[l] : (best == 1 ? 0 : keep_pe[l]);
+            s->shape[l] = best == 2 ? keep_sh[l] : pick_sh[l];
             out->min_blocks[l] = s->min_blocks[l];
             out->persistent[l] = s->persistent[l];
+            out->shape[l] = s->shape[l];
         }
     }
     // 2: programmatic dependent launch on or off, from whole graph steps
@@ -1447,6 +1457,7 @@ static void batch_advance(lbm_batch *b, cudaStream_t st, int l, int restrict_up,
         d.ls.wall = (l == L - 1) && s->rec.n > 0;
         d.ls.restrict_up = restrict_up && l > 0;
         d.ls.pp = l > 0 ? s->parity[l - 1] : 0;
+        d.ls.shape = 0;
         d.ls.status = s->d_status;
         d.kind = d.ls.wall ? 2 : (d.ls.has_child ? 1 : 0);
         d.first_block = (int)grid;
@@ -1697,14 +1708,20 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, int pdl)
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, const int *shape,
+                                  int pdl)
 {
     if (!s || !min_blocks || !persistent || (pdl != 0 && pdl != 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     for (int l = 0; l < s->L; l++)
-        if ((min_blocks[l] != 5 && min_blocks[l] != 6) || (persistent[l] != 0 && persistent[l] != 1))
-            return fail(s, LBM_ERR_INVALID_ARG, "launch variant: min_blocks must be 5 or 6, persistent 0 or 1");
-    for (int l = 0; l < s->L; l++) { s->min_blocks[l] = min_blocks[l]; s->persistent[l] = persistent[l]; }
+        if ((min_blocks[l] != 5 && min_blocks[l] != 6) || (persistent[l] != 0 && persistent[l] != 1) ||
+            (shape && shape[l] != 0 && shape[l] != 1))
+            return fail(s, LBM_ERR_INVALID_ARG, "launch variant: min_blocks must be 5 or 6, persistent and shape 0 or 1");
+    for (int l = 0; l < s->L; l++) {
+        s->min_blocks[l] = min_blocks[l];
+        s->persistent[l] = persistent[l];
+        s->shape[l] = shape ? shape[l] : 0;
+    }
     s->pdl = pdl;
     return capture_graphs(s);
 }

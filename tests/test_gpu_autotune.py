@@ -42,10 +42,10 @@ def test_autotuned_solve_equals_the_default_one(store):
     b.step(3)                      # odd level-0 parity: the recapture starts from graph 1
     rep = b.autotune(steps=2)
     L = cfg["levels"]
-    assert rep["steps_taken"] == 2 * 10 and rep["levels"] == L
+    assert rep["steps_taken"] == 2 * 14 and rep["levels"] == L
     assert min(rep["step_us_confirm"].values()) > 0
-    assert rep["candidates"] == [(5, 0), (6, 0), (5, 1), (6, 1)]
-    assert all(pe in (0, 1) for pe in rep["persistent"])
+    assert rep["candidates"] == [(5, 0, 0), (6, 0, 0), (5, 1, 0), (6, 1, 0), (5, 0, 1), (6, 0, 1), (5, 1, 1), (6, 1, 1)]
+    assert all(pe in (0, 1) for pe in rep["persistent"]) and all(sh in (0, 1) for sh in rep["shape"])
     assert all(m in (5, 6) for m in rep["min_blocks"]) and rep["pdl"] in (0, 1)
     assert all(t > 0 for ts in rep["level_us"].values() for t in ts)
     assert rep["default_step_us"] > 0 and min(rep["step_us"].values()) > 0
@@ -65,15 +65,16 @@ def test_autotuned_solve_equals_the_default_one(store):
     assert abs(la["CL"] - lb["CL"]) <= 10 * ltol * max(abs(la["CL"]), abs(la["CD"]))
 
 
-@pytest.mark.parametrize("mb,pdl,pe", [(6, 1, 0), (5, 0, 0), (6, 0, 1), (5, 1, 1), (6, 1, 1)])
-def test_each_launch_variant_computes_the_same_numbers(mb, pdl, pe):
+@pytest.mark.parametrize("mb,pdl,pe,sh", [(6, 1, 0, 0), (5, 0, 0, 0), (6, 0, 1, 0), (5, 1, 1, 0), (6, 1, 1, 0),
+                                         (5, 1, 0, 1), (6, 1, 1, 1), (5, 0, 1, 1)])
+def test_each_launch_variant_computes_the_same_numbers(mb, pdl, pe, sh):
     pkg.build()
     cfg, loops = W.naca0012_small(levels=5)
     L = cfg["levels"]
     a, b = pkg.Solver(cfg), pkg.Solver(cfg)
     a.set_geometry(loops)
     b.set_geometry(loops)
-    b.set_launch_variant([mb] * L, pdl, [pe] * L)
+    b.set_launch_variant([mb] * L, pdl, [pe] * L, [sh] * L)
     a.step(6)
     b.step(6)
     same_populations(a, b, L)
@@ -89,11 +90,11 @@ def test_a_variant_run_twice_is_bitwise_identical():
     pkg.build()
     cfg, loops = W.naca0012_small(levels=5)
     L = cfg["levels"]
-    for mb, pe in ((5, 0), (6, 1)):
+    for mb, pe, sh in ((5, 0, 0), (6, 1, 0), (5, 0, 1)):
         a, b = pkg.Solver(cfg), pkg.Solver(cfg)
         for s in (a, b):
             s.set_geometry(loops)
-            s.set_launch_variant([mb] * L, 1, [pe] * L)
+            s.set_launch_variant([mb] * L, 1, [pe] * L, [sh] * L)
             s.step(7)
         for l in range(L):
-            assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), (mb, pe, l)
+            assert np.array_equal(a.get_populations(l), b.get_populations(l), equal_nan=True), (mb, pe, sh, l)
