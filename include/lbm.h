@@ -88,7 +88,8 @@ typedef struct {
     long long node_updates_per_step; /* sum_l active_l * 2^l per coarse step                         */
     long long wall_records, cut_links, surface_segments;
     long long kernels_per_step;   /* kernel launches issued per coarse step                          */
-    double bytes_per_node_update; /* algorithmic bytes of the stream-collide per node update         */
+    double bytes_per_node_update; /* bytes the fused level step moves per node update (populations, flag
+                                     word, chi, rho and u; with SA-neg also chi written, u and 1/d^2 read) */
     double device_bytes;          /* device memory held by the handle                                */
 } lbm_info;
 

@@ -1228,9 +1228,11 @@ lbm_status lbm_get_info(lbm_solver *s, lbm_info *out)
     out->cut_links = s->g.n_cut;
     out->surface_segments = s->segs.nseg;
     out->kernels_per_step = s->kernels_per_step;
-    // fused level step: 9 populations read + 9 written (FP32), rho and u written; with
-    // SA-neg also nu_tilde read and written, u read for the stencil, wall distance read
-    out->bytes_per_node_update = 18.0 * (double)pop_bytes(s->cfg.store) + 12.0 + (s->cfg.turbulence ? 8.0 + 8.0 + 4.0 : 0.0);
+    // fused level step, per node update: 9 populations read and 9 written, the flag word and
+    // chi read, rho - 1 and u written; with SA-neg also chi written, u read for the stencil
+    // (its neighbours' values come through the caches) and 1/d^2 read
+    out->bytes_per_node_update = 18.0 * (double)pop_bytes(s->cfg.store) + 12.0 + 4.0 + 4.0 +
+                                 (s->cfg.turbulence ? 4.0 + 8.0 + 4.0 : 0.0);
     out->device_bytes = s->device_bytes;
     return LBM_OK;
 }
