@@ -424,7 +424,7 @@ def gpu_arm(args, rank, world, dist):
             "loads": {"CL": loads["CL"], "CD": loads["CD"], "step": loads["step"]},
             "e2e": e2e,
             "autotune": None if tune is None else {
-                "min_blocks_per_level": tune["min_blocks"], "persistent_per_level": tune["persistent"],
+                "min_blocks_per_level": tune["min_blocks"], "sched_per_level": tune["sched"],
                 "shape_per_level": tune["shape"],
                 "pdl": tune["pdl"],
                 "step_us_default": round(tune["default_step_us"], 2),
@@ -488,8 +488,10 @@ def profile_case(args):
         cfg, loops = W.naca0012_large()
     s = pkg.Solver(cfg)
     s.set_geometry(loops)
-    if args.profile_persistent:
-        s.set_launch_variant([6] * cfg["levels"], 1, [1] * cfg["levels"])
+    if args.profile_variant:
+        mb, sc, sh = (int(v) for v in args.profile_variant.split(","))
+        L = cfg["levels"]
+        s.set_launch_variant([mb] * L, 1, [sc] * L, [sh] * L)
     elif not args.no_autotune:
         s.autotune(2)
     # the steps to profile sit in an NVTX range ("steps"): ncu --nvtx --nvtx-include steps/
@@ -580,8 +582,9 @@ def main():
     ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--profile-case", choices=["hbm_grid", "hbm_grid_laminar", "workload"], default=None)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch variant")
-    ap.add_argument("--profile-persistent", action="store_true",
-                    help="profile case: persistent grid, 6 blocks/SM on every level instead of autotuning")
+    ap.add_argument("--profile-variant", default="",
+                    help="profile case: launch variant 'min_blocks,sched,shape' on every level (sched 0 tile "
+                         "blocks, 1 persistent grid, 2 warp list) instead of autotuning")
     ap.add_argument("--workload", choices=["naca0012", "highlift"], default="naca0012",
                     help="highlift: the three-element 8-level case (10 timed steps, no extra measurements)")
     ap.add_argument("--serving", type=int, default=0, help="serve this many requests of the polar stream")

@@ -91,6 +91,8 @@ typedef struct {
     double bytes_per_node_update; /* bytes the fused level step moves per node update (populations, flag
                                      word, chi, rho and u; with SA-neg also chi written, u and 1/d^2 read) */
     double device_bytes;          /* device memory held by the handle                                */
+    long long work_tiles[16];     /* tiles per level holding an active or ghost fluid cell           */
+    long long work_warps[16];     /* 16 x 2-cell warps of those tiles that hold one (LBM_SCHED_WARPS) */
 } lbm_info;
 
 /* Per-kernel-class timing of eagerly launched steps (CUDA events on the solver stream). */
@@ -278,36 +280,41 @@ lbm_status lbm_get_info(lbm_solver *s, lbm_info *out);
  * the solver stream; accumulate device time per kernel class.  Same results as lbm_step. */
 lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times *out);
 
+/* Grid schedules of the fused level kernel (lbm_autotune, lbm_set_launch_variant). */
+#define LBM_SCHED_TILE 0      /* one 256-thread block per work tile                              */
+#define LBM_SCHED_PERSIST 1   /* a grid of 2 x SMs x budget blocks striding over the work tiles  */
+#define LBM_SCHED_WARPS 2     /* two-warp blocks over the list of work warps (16 x 2 cells each
+                                 of a work tile that hold an active or ghost fluid cell; shape 0) */
+
 /* Launch autotuner.  Not part of the paper's method (Sec 2.1 gives the level schedule, not
  * its mapping to a GPU).  For each level it picks one of LBM_TUNE_CANDIDATES launch forms
- * of the fused level kernel: a register budget of at least 5 or 6 resident 256-thread
- * blocks per SM (at most 48 or 40 registers a thread), each either with one block per
- * tile or with a persistent grid (2 x SMs x that budget) whose blocks stride over the
- * level's tiles, and each with one of two work shapes of a warp within the 32 x 8 cell
- * tile (shape 0: a 16 x 2 block of cells; shape 1: a 32-cell row, whose accesses shifted
- * by one cell touch fewer sectors and whose restriction goes through shared memory).
- * The choice comes from per-launch CUDA-event timings of `steps` eager
+ * of the fused level kernel: a register budget of at most 48 or 40 registers a thread (at
+ * least 5 or 6 resident 256-thread blocks per SM), each with one of the grid schedules
+ * LBM_SCHED_* and, for the tile schedules, one of two work shapes of a warp within the
+ * 32 x 8 cell tile (shape 0: a 16 x 2 block of cells; shape 1: a 32-cell row, whose
+ * accesses shifted by one cell touch fewer sectors and whose restriction goes through
+ * shared memory).  The choice comes from per-launch CUDA-event timings of `steps` eager
  * coarse steps per candidate, and is kept only if `steps` coarse steps through the step
- * graphs confirm it (against the same choice without persistent grids, and against the
- * form before tuning), since launches overlap inside the graphs.  Then it picks whether launches use
- * programmatic dependent launch, from the time of `steps` coarse steps through the step
- * graphs each way, and recaptures the graphs with the choice.  The variants compute the
- * same numbers up to FP32 rounding (the compiler schedules and contracts the arithmetic
- * differently per variant); the timed steps are real steps of the solve (steps_taken of
- * them).
+ * graphs confirm it (against the same choice with one block per tile where it picked a
+ * persistent grid, and against the form before tuning), since launches overlap inside the
+ * graphs.  Then it picks whether launches use programmatic dependent launch, from the time
+ * of `steps` coarse steps through the step graphs each way, and recaptures the graphs with
+ * the choice.  The variants compute the same numbers up to FP32 rounding (the compiler
+ * schedules and contracts the arithmetic differently per variant); the timed steps are real
+ * steps of the solve (steps_taken of them).
  * Synchronous.  Errors as lbm_step. */
-#define LBM_TUNE_CANDIDATES 8
+#define LBM_TUNE_CANDIDATES 10
 typedef struct {
     int levels;
     int candidate_min_blocks[LBM_TUNE_CANDIDATES];
-    int candidate_persistent[LBM_TUNE_CANDIDATES];
+    int candidate_sched[LBM_TUNE_CANDIDATES];
     int candidate_shape[LBM_TUNE_CANDIDATES];
     double level_us[LBM_TUNE_CANDIDATES][16]; /* mean launch time of level l's kernel per candidate */
     int min_blocks[16];                       /* chosen register budget per level                  */
-    int persistent[16];                       /* chosen grid schedule per level (1 persistent)     */
+    int sched[16];                            /* chosen grid schedule per level (LBM_SCHED_*)      */
     int shape[16];                            /* chosen work shape per level                       */
-    double step_us_confirm[3];                /* coarse step: per-level pick, pick without
-                                                 persistent grids, form before tuning            */
+    double step_us_confirm[3];                /* coarse step: per-level pick, pick with tile
+                                                 blocks for persistent grids, form before tuning */
     double default_step_us;                   /* coarse step through the graphs before tuning      */
     double step_us[2];                        /* coarse step, chosen kernels, PDL off / on         */
     int pdl;                                  /* chosen: 1 programmatic dependent launch on        */
@@ -331,11 +338,11 @@ lbm_status lbm_get_state(lbm_solver *s, void *buf, size_t cap, size_t *size);
 lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size);
 
 /* Set the launch variant directly (for instance one lbm_autotune found on a solve of the
- * same shape): min_blocks[l] in {5, 6}, persistent[l] in {0, 1} and shape[l] in {0, 1}
- * (NULL: shape 0 on every level) for each of the solver's levels, pdl 0 or 1; the step
- * graphs are recaptured.  No device work.  Errors: LBM_ERR_INVALID_ARG for a value
- * outside those sets, LBM_ERR_NO_GEOMETRY. */
-lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, const int *shape,
+ * same shape): min_blocks[l] in {5, 6}, sched[l] one of LBM_SCHED_* and shape[l] in {0, 1}
+ * (NULL: shape 0 on every level; LBM_SCHED_WARPS requires shape 0) for each of the solver's
+ * levels, pdl 0 or 1; the step graphs are recaptured.  No device work.  Errors:
+ * LBM_ERR_INVALID_ARG for a value outside those sets, LBM_ERR_NO_GEOMETRY. */
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *sched, const int *shape,
                                   int pdl);
 
 /* Largest n_cells that lbm_level_mass_noalloc accepts (its fixed scratch holds 4096

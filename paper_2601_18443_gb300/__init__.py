@@ -53,7 +53,7 @@ class lbm_info(C.Structure):
                 ("slots", C.c_longlong * 16), ("node_updates_per_step", C.c_longlong),
                 ("wall_records", C.c_longlong), ("cut_links", C.c_longlong), ("surface_segments", C.c_longlong),
                 ("kernels_per_step", C.c_longlong), ("bytes_per_node_update", C.c_double),
-                ("device_bytes", C.c_double)]
+                ("device_bytes", C.c_double), ("work_tiles", C.c_longlong * 16), ("work_warps", C.c_longlong * 16)]
 
 
 class lbm_plan(C.Structure):
@@ -66,14 +66,15 @@ class lbm_kernel_times(C.Structure):
                 ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
 
 
-TUNE_CANDIDATES = 8
+TUNE_CANDIDATES = 10
+SCHED_TILE, SCHED_PERSIST, SCHED_WARPS = 0, 1, 2     # LBM_SCHED_* of include/lbm.h
 
 
 class lbm_tune_report(C.Structure):
     _fields_ = [("levels", C.c_int), ("candidate_min_blocks", C.c_int * TUNE_CANDIDATES),
-                ("candidate_persistent", C.c_int * TUNE_CANDIDATES), ("candidate_shape", C.c_int * TUNE_CANDIDATES),
+                ("candidate_sched", C.c_int * TUNE_CANDIDATES), ("candidate_shape", C.c_int * TUNE_CANDIDATES),
                 ("level_us", (C.c_double * 16) * TUNE_CANDIDATES), ("min_blocks", C.c_int * 16),
-                ("persistent", C.c_int * 16), ("shape", C.c_int * 16), ("step_us_confirm", C.c_double * 3),
+                ("sched", C.c_int * 16), ("shape", C.c_int * 16), ("step_us_confirm", C.c_double * 3),
                 ("default_step_us", C.c_double), ("step_us", C.c_double * 2),
                 ("pdl", C.c_int), ("steps_taken", C.c_longlong)]
 
@@ -401,7 +402,8 @@ class Solver:
                     slots=list(out.slots[:L]), node_updates_per_step=out.node_updates_per_step,
                     wall_records=out.wall_records, cut_links=out.cut_links,
                     surface_segments=out.surface_segments, kernels_per_step=out.kernels_per_step,
-                    bytes_per_node_update=out.bytes_per_node_update, device_bytes=out.device_bytes)
+                    bytes_per_node_update=out.bytes_per_node_update, device_bytes=out.device_bytes,
+                    work_tiles=list(out.work_tiles[:L]), work_warps=list(out.work_warps[:L]))
 
     def autotune(self, steps=10):
         """lbm_autotune: per-level register budget and PDL choice by timing; advances the
@@ -423,12 +425,12 @@ class Solver:
         b = np.ascontiguousarray(blob, dtype=np.uint8)
         self._check(self._lib.lbm_set_state(self._h, b.ctypes.data_as(C.c_void_p), b.size))
 
-    def set_launch_variant(self, min_blocks, pdl=1, persistent=None, shape=None):
+    def set_launch_variant(self, min_blocks, pdl=1, sched=None, shape=None):
         """lbm_set_launch_variant: per-level register budget (5 or 6 blocks per SM), grid
-        schedule (persistent 0/1), work shape of a warp (0 a 16 x 2 block, 1 a 32-cell row)
-        and PDL."""
+        schedule (SCHED_TILE, SCHED_PERSIST or SCHED_WARPS), work shape of a warp (0 a 16 x 2
+        block, 1 a 32-cell row; 0 with SCHED_WARPS) and PDL."""
         mb = np.ascontiguousarray(min_blocks, dtype=np.int32)
-        pe = np.ascontiguousarray(persistent if persistent is not None else [0] * len(mb), dtype=np.int32)
+        pe = np.ascontiguousarray(sched if sched is not None else [SCHED_TILE] * len(mb), dtype=np.int32)
         sh = np.ascontiguousarray(shape if shape is not None else [0] * len(mb), dtype=np.int32)
         self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), _ip(pe), _ip(sh), int(pdl)))
 
@@ -441,12 +443,12 @@ class Solver:
 
 def _tune_dict(out):
     L = out.levels
-    cand = list(zip(out.candidate_min_blocks, out.candidate_persistent, out.candidate_shape))
+    cand = list(zip(out.candidate_min_blocks, out.candidate_sched, out.candidate_shape))
     return dict(levels=L, candidates=cand,
                 level_us={c: list(out.level_us[i][:L]) for i, c in enumerate(cand)},
-                min_blocks=list(out.min_blocks[:L]), persistent=list(out.persistent[:L]),
+                min_blocks=list(out.min_blocks[:L]), sched=list(out.sched[:L]),
                 shape=list(out.shape[:L]),
-                step_us_confirm={"pick": out.step_us_confirm[0], "pick_no_persistent": out.step_us_confirm[1],
+                step_us_confirm={"pick": out.step_us_confirm[0], "pick_tile_for_persistent": out.step_us_confirm[1],
                                  "before": out.step_us_confirm[2]},
                 default_step_us=out.default_step_us,
                 step_us={"pdl_off": out.step_us[0], "pdl_on": out.step_us[1]}, pdl=out.pdl,

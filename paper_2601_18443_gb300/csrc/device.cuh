@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "layout.hpp"
+#include "../../include/lbm.h"
 
 namespace lbmdev {
 
@@ -22,6 +23,8 @@ struct LevelView {
     int n_band_tiles;
     const int *work_tiles;        // tiles with active or ghost fluid cells (the level kernel's grid)
     int n_work_tiles;
+    const int *work_warps;        // tile * 8 + w for each warp w (work shape 0) of a work tile that
+    int n_work_warps;             // holds an active or ghost fluid cell (the warp-list schedule)
     const uint32_t *flags;        // per slot
     const float *inv_d2;          // 1 / d^2, d the wall distance in level lattice units (SA-neg)
     const int *aux;               // per slot: wall record of a B node (finest level), band index of a
@@ -53,6 +56,10 @@ struct RecView {
     float *drhoW, *uWx, *uWy, *utau, *chiB, *tx, *ty, *ut;
     float *utau_start;            // Newton start of the next step (written by the step only)
     float *fpost;                 // 9 per record: post-collision f - w of the boundary node, last step
+    const uint32_t *nfluid;       // per record: bit q set where the node B + c_q is active fluid
+                                  // (present and not solid), for eq 27's interpolation
+    const float *yc;              // 18 per record: 1 / (1 + q_c) and q_c / (1 + q_c) per direction
+                                  // (eq 27's interpolation weights)
 };
 
 struct StepConsts {
@@ -97,7 +104,9 @@ struct LevelStep {
 struct LevelTune {
     int min_blocks;
     int pdl;
-    int persistent;     // grid of 2 x SMs x min_blocks blocks striding over the work tiles
+    int sched;          // LBM_SCHED_TILE: one block per work tile; LBM_SCHED_PERSIST: a grid of
+                        // 2 x SMs x min_blocks blocks striding over the work tiles;
+                        // LBM_SCHED_WARPS: two-warp blocks over the work-warp list (shape 0)
     int shape;          // work shape of a warp (LevelStep::shape)
 };
 

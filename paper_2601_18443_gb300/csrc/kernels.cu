@@ -356,28 +356,33 @@ __device__ __forceinline__ float wf_dudy(float y)
 {   // eq 21
     float k3 = SA_KAPPA * y;
     k3 = k3 * k3 * k3;
-    return (SA_CV1_3 + k3) / (SA_CV1_3 + k3 * (1.0f + SA_KAPPA * y));
+    return __fdividef(SA_CV1_3 + k3, SA_CV1_3 + k3 * (1.0f + SA_KAPPA * y));
 }
 
 // Friction velocity from u_t at distance y (step 3): Newton on g(u) = u u+(u y / nu) - u_t,
 // g' = u+ + y+ du+/dy+ > 0, started from the previous sub-step's value when there is one,
 // else from the viscous-sublayer value (which lies left of the root, since u+ <= y+).
-// Every evaluation narrows a sign bracket; steps leaving it are replaced by bisection
-// (or doubling while no right end is known).  At most 24 evaluations.
-__device__ float wf_utau(float ut, float y, float nu, float guess)
+// y_nu = y / nu.  Every evaluation narrows a sign bracket; steps leaving it are replaced by
+// bisection (or doubling while no right end is known).  The iteration stops after a Newton
+// step (not a bisection) shorter than 3e-4 u: Newton's error after a step of relative size
+// e is about (g'' u / 2 g') e^2, at most e^2 / 2 (the viscous sublayer; about 0.05 e^2 in
+// the log layer), so the result is within 4.5e-8 relative of the root, below FP32
+// resolution.  At most 24 evaluations.
+__device__ float wf_utau(float ut, float y_nu, float guess)
 {
     if (!(ut > 0.0f)) return 0.0f;
     float lo = 0.0f, hi = INFINITY;
-    float u = guess > 0.0f ? guess : sqrtf(ut * nu / y);
+    float u = guess > 0.0f ? guess : sqrtf(ut / y_nu);
     for (int it = 0; it < 24; it++) {
-        const float yp = u * y / nu;
+        const float yp = u * y_nu;
         const float up = wf_uplus(yp);
         const float gv = u * up - ut;
         if (gv > 0.0f) hi = u; else lo = u;
         const float gp = up + yp * wf_dudy(yp);
-        float un = gp > 0.0f ? u - gv / gp : -1.0f;
-        if (!(un > lo && un < hi)) un = isinf(hi) ? 2.0f * fmaxf(u, lo) : 0.5f * (lo + hi);
-        const bool done = fabsf(un - u) <= 1e-6f * un;
+        float un = gp > 0.0f ? u - __fdividef(gv, gp) : -1.0f;
+        const bool newton = un > lo && un < hi;
+        if (!newton) un = isinf(hi) ? 2.0f * fmaxf(u, lo) : 0.5f * (lo + hi);
+        const bool done = newton && fabsf(un - u) <= 3e-4f * un;
         u = un;
         if (done) break;
     }
@@ -397,40 +402,49 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
     // step 1: rho_R and u_R as fixed weighted sums over the 16-entry stencil (unused
     // entries carry zero weight); all 48 loads are independent
     float drR = 0.f, uR = 0.f, vR = 0.f;
+    const int4 *sl4 = reinterpret_cast<const int4 *>(R.st_slot + r * 16);      // 64-byte records
+    const float4 *wr4 = reinterpret_cast<const float4 *>(R.st_wr + r * 16);
+    const float4 *wu4 = reinterpret_cast<const float4 *>(R.st_wu + r * 16);
 #pragma unroll
-    for (int m = 0; m < 16; m++) {
-        const int s = R.st_slot[r * 16 + m];
-        const float wr = R.st_wr[r * 16 + m], wu = R.st_wu[r * 16 + m];
-        drR += wr * dr[s]; uR += wu * ux[s]; vR += wu * uy[s];
+    for (int m4 = 0; m4 < 4; m4++) {
+        const int4 sv = __ldg(sl4 + m4);
+        const float4 wrv = __ldg(wr4 + m4), wuv = __ldg(wu4 + m4);
+        const int sa[4] = {sv.x, sv.y, sv.z, sv.w};
+        const float ra[4] = {wrv.x, wrv.y, wrv.z, wrv.w}, ua[4] = {wuv.x, wuv.y, wuv.z, wuv.w};
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            const int s = sa[m];
+            drR += ra[m] * dr[s]; uR += ua[m] * ux[s]; vR += ua[m] * uy[s];
+        }
     }
     const float nx = R.nx[r], ny = R.ny[r];
     const float un = uR * nx + vR * ny;
     const float utx = uR - un * nx, uty = vR - un * ny;
     const float ut = sqrtf(utx * utx + uty * uty);
     float tx = -ny, ty = nx;
-    if (ut > 0.0f) { tx = utx / ut; ty = uty / ut; }
+    if (ut > 0.0f) { const float iut = 1.0f / ut; tx = utx * iut; ty = uty * iut; }
     float utau = 0.f;
     uWx = 0.f; uWy = 0.f; chiB = 0.f;
     if (k.wall_model == 0) {
-        const float nu = P.nu;
-        utau = wf_utau(ut, k.d_wr, nu, R.utau_start[r]);                    // step 3
+        const float inu = 1.0f / P.nu;
+        utau = wf_utau(ut, k.d_wr * inu, R.utau_start[r]);                  // step 3
         if (keep_start) R.utau_start[r] = utau;
-        const float ypv = utau * k.d_wv / nu;
+        const float ypv = utau * k.d_wv * inu;
         const float uV = utau * wf_uplus(ypv);                              // step 4
-        const float uW = uV - utau * utau * k.d_wv / (nu * (1.0f + SA_KAPPA * ypv));   // eq 28
+        const float uW = uV - __fdividef(utau * utau * k.d_wv * inu, 1.0f + SA_KAPPA * ypv);   // eq 28
         uWx = uW * tx; uWy = uW * ty;                                       // step 5
-        chiB = SA_KAPPA * utau * R.dwb[r] / nu;
+        chiB = SA_KAPPA * utau * R.dwb[r] * inu;
     } else if (k.wall_model == 1) {
         // Nishimura's slip adapted to RANS (Sec 3.1.5, eq 31): u_tau from eq 22 at R and the
         // slip extrapolated linearly from R with the SA log-layer eddy viscosity
         // (nu_t)_R = nu kappa y+_R (eq 20)
-        const float nu = P.nu;
-        utau = wf_utau(ut, k.d_wr, nu, R.utau_start[r]);
+        const float inu = 1.0f / P.nu;
+        utau = wf_utau(ut, k.d_wr * inu, R.utau_start[r]);
         if (keep_start) R.utau_start[r] = utau;
-        const float ypr = utau * k.d_wr / nu;
-        const float uW = ut - utau * utau * k.d_wr / (nu * (1.0f + SA_KAPPA * ypr));
+        const float ypr = utau * k.d_wr * inu;
+        const float uW = ut - __fdividef(utau * utau * k.d_wr * inu, 1.0f + SA_KAPPA * ypr);
         uWx = uW * tx; uWy = uW * ty;
-        chiB = SA_KAPPA * utau * R.dwb[r] / nu;
+        chiB = SA_KAPPA * utau * R.dwb[r] * inu;
     } else if (k.wall_model == 2) {
         uWx = R.slip[2 * R.loop[r]]; uWy = R.slip[2 * R.loop[r] + 1];
     }
@@ -528,9 +542,8 @@ __device__ __forceinline__ void put_obuf(const StepConsts &k, int par, uint32_t 
 // nothing, so their share of the next coalescence is this value too.
 template <typename T>
 __device__ __forceinline__ void explode_band(const LevelView &P, const LevelView &F, const StepConsts &k, int t, int lx,
-                                             int ly, uint32_t fl, int slot, const float o[9])
+                                             int ly, uint32_t fl, int b, const float o[9])
 {
-    const int b = __ldg(P.aux + slot);
     float *eb = P.ebuf + b * 9;
 #pragma unroll
     for (int q = 0; q < 9; q++) eb[q] = o[q];
@@ -560,16 +573,25 @@ __device__ __forceinline__ void explode_band(const LevelView &P, const LevelView
     }
 }
 
+// Whether a cell's aux word is used by the level step: ghosts, boundary nodes, band cells
+// and coalescing cells.
+__device__ __forceinline__ bool uses_aux(uint32_t fl)
+{
+    return (fl & FL_KIND_MASK) == KIND_GHOST || (fl & (FL_BNODE | FL_BAND | (0xFFu << FL_COAL_SHIFT)));
+}
+
 // One tile of the fused level step (the body of k_level): every thread updates its cell
 // of tile t.  nb3 holds the 3 x 3 neighbour tiles of t for this warp.  The cell's flag
-// word is read here, or passed in (FL_GIVEN) when the caller has fetched it ahead.
+// word and aux word are read here, or passed in (FL_GIVEN) when the caller has fetched
+// them ahead (the aux word only where uses_aux holds).
 template <bool WALL, bool CHILD, typename T, bool ODD, bool FL_GIVEN>
 __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &F, const LevelView &C, const RecView &R,
                                            const StepConsts &k, const LevelStep &ls, const Lat<T> &L, int t, int lane,
-                                           int lx, int ly, const int *nb3, uint32_t fl_given, float *red)
+                                           int lx, int ly, const int *nb3, uint32_t fl_given, int ax_given, float *red)
 {
     const int slot = t * LBM_TILE + ly * LBM_TX + lx;
     const uint32_t fl = FL_GIVEN ? fl_given : __ldg(P.flags + slot);
+    auto aux_of = [&]() { return FL_GIVEN ? ax_given : __ldg(P.aux + slot); };
     const uint32_t kind = fl & FL_KIND_MASK;
     const bool fluid = !(fl & FL_SOLID);
     const int p = ls.p;
@@ -581,7 +603,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         // populations stay in the cell, moved to the slots an odd step reads; odd sub-step:
         // the pulled populations go to the parent's coalescence buffer.  Where the upstream
         // cell is not fluid the ghost keeps its own value, the parent's exploded one.
-        const int ax = __ldg(P.aux + slot);
+        const int ax = aux_of();
         const float *eb = C.ebuf + (ax >> 2) * 9;
         const uint32_t keep = fl >> FL_KEEP_SHIFT;
         if (!ODD) {
@@ -611,7 +633,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         float drW = 0.f, uWx = 0.f, uWy = 0.f, chiB = 0.f;
         int r = -1;
         if (bnode) {
-            r = __ldg(P.aux + slot);
+            r = aux_of();
             wall_record(P, p, R, k, r, true, drW, uWx, uWy, chiB);
         }
         // ---- SA-neg update of chi (Sec 2.2), fields at time t
@@ -664,7 +686,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         const uint32_t special = fl & (0xFFu << FL_COAL_SHIFT | 0xFFu << FL_CUT_SHIFT);
         if (CHILD && (fl & (0xFFu << FL_COAL_SHIFT))) {
             // coalescence: mean of what the four ghost children pulled in the fine level's odd sub-step
-            const float *gb = P.gbuf + __ldg(P.aux + slot) * 36;
+            const float *gb = P.gbuf + aux_of() * 36;
 #pragma unroll
             for (int q = 1; q < 9; q++)
                 if (fl & (1u << (FL_COAL_SHIFT + q - 1)))
@@ -675,6 +697,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
             // next fluid node's f*_qo arrives at B as its own f_qo; f*_q(B) and f*_qo(B) of the last
             // step come from the record's buffer
             const float *fp = R.fpost + r * 9;
+            const uint32_t nf = __ldg(R.nfluid + r);      // bit q: the node B + c_q is active fluid
             float gin[9];
 #pragma unroll
             for (int q = 0; q < 9; q++) gin[q] = g[q];
@@ -684,13 +707,10 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
                 const int qo = oppq(q);
                 const float qf = R.q[r * 9 + q];
                 const float mom = 6.0f * wq(q) * (1.0f + drW) * (cxq(q) * uWx + cyq(q) * uWy);
-                const int sf = nbs[q];
-                bool ok = false;
-                if (sf != slot) {
-                    const uint32_t ff = __ldg(P.flags + sf);
-                    ok = (ff & FL_KIND_MASK) == KIND_ACTIVE && !(ff & FL_SOLID);
+                if (nf >> q & 1) {
+                    const float2 c = __ldg(reinterpret_cast<const float2 *>(R.yc) + r * 9 + q);   // 1/(1+q), q/(1+q)
+                    g[q] = ((1.0f - qf) * gin[qo] + qf * fp[qo] + mom) * c.x + c.y * fp[q];
                 }
-                if (ok) g[q] = ((1.0f - qf) * gin[qo] + qf * fp[qo] + mom) / (1.0f + qf) + qf / (1.0f + qf) * fp[q];
                 else g[q] = fp[qo] + mom;                               // half-way form, eq 24
             }
         }
@@ -738,7 +758,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         }
         if (ls.is_level0 && k.level0_edges && (fl & (FL_OUTLET | FL_OUTLET2)))
             put_obuf(k, p ^ 1, fl, P.tile_y[t] * LBM_TY + ly, o);
-        if (CHILD && (fl & FL_BAND)) explode_band<T>(P, F, k, t, lx, ly, fl, slot, o);
+        if (CHILD && (fl & FL_BAND)) explode_band<T>(P, F, k, t, lx, ly, fl, aux_of(), o);
         valid = true;
         n_dr = drho; n_ux = ux; n_uy = uy; n_chi = chin;
     }
@@ -816,7 +836,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
         __syncwarp();
         griddep_launch();
         griddep_wait();
-        level_tile<WALL, CHILD, T, ODD, false>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, 0u, red);
+        level_tile<WALL, CHILD, T, ODD, false>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, 0u, 0, red);
     } else {
         // the grid tables are static: the first tile's neighbour table and flag word are
         // read before the wait, and each tile's flag word one tile ahead
@@ -841,10 +861,45 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
                 if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
                 __syncwarp();
             }
-            level_tile<WALL, CHILD, T, ODD, true>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, fl, red);
+            const int ax = uses_aux(fl) ? __ldg(P.aux + t * LBM_TILE + cell) : -1;
+            level_tile<WALL, CHILD, T, ODD, true>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, fl, ax, red);
         }
     }
 
+}
+
+// Warp-list schedule of k_level: blocks of LBM_WL_WARPS warps, each warp taking one entry of
+// the level's work-warp list (tile * 8 + its warp in work shape 0), so that the warps of a
+// work tile holding no active or ghost fluid cell are not launched, and a block is retired
+// (and replaced) as soon as its two warps are done rather than its tile's eight.  MINB keeps
+// the register budget of k_level<.., MINB, ..>: 20 two-warp blocks (40 warps) fit 48
+// registers a thread, 24 fit 40 (a sub-partition's 16384 registers hold 10 warps of 48 or
+// 12 of 40, whatever the block size).  Per cell it runs the same code as k_level with work
+// shape 0.
+#define LBM_WL_WARPS 2
+template <bool WALL, bool CHILD, typename T, int MINB, bool ODD>
+__global__ void __launch_bounds__(LBM_WL_WARPS * 32, MINB == 6 ? 24 : 20)
+    k_level_wl(LevelView P, LevelView F, LevelView C, RecView R, StepConsts k, LevelStep ls)
+{
+    const Lat<T> L{static_cast<T *>(P.f), P.ns, k.pshift};
+    __shared__ int nb3w[LBM_WL_WARPS][9];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int w = blockIdx.x * LBM_WL_WARPS + wb;
+    const bool have = w < P.n_work_warps;
+    int *nb3 = nb3w[wb];
+    int t = 0, lx = 0, ly = 0;
+    if (have) {
+        const int e = __ldg(P.work_warps + w);
+        t = e >> 3;
+        cell_of_thread((e & 7) * 32 + lane, lx, ly, 0);
+        if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
+    }
+    __syncwarp();
+    griddep_launch();
+    griddep_wait();
+    LevelStep l0 = ls;
+    l0.shape = 0;
+    if (have) level_tile<WALL, CHILD, T, ODD, false>(P, F, C, R, k, l0, L, t, lane, lx, ly, nb3, 0u, 0, nullptr);
 }
 
 // The batched form of k_level (one block per work tile, register budget of 5 blocks per SM):
@@ -872,14 +927,14 @@ __global__ void __launch_bounds__(256, 5) k_level_batch(const __grid_constant__ 
     const Lat<T> L{static_cast<T *>(d.P.f), d.P.ns, d.k.pshift};
     const bool odd = d.ls.p != 0;
     if (d.kind == 2) {
-        if (odd) level_tile<true, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
-        else level_tile<true, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
+        if (odd) level_tile<true, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, 0, red);
+        else level_tile<true, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, 0, red);
     } else if (d.kind == 1) {
-        if (odd) level_tile<false, true, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
-        else level_tile<false, true, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
+        if (odd) level_tile<false, true, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, 0, red);
+        else level_tile<false, true, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, 0, red);
     } else {
-        if (odd) level_tile<false, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
-        else level_tile<false, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, red);
+        if (odd) level_tile<false, false, T, true, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, 0, red);
+        else level_tile<false, false, T, false, false>(d.P, d.F, d.C, d.R, d.k, d.ls, L, t, lane, lx, ly, nb3, 0u, 0, red);
     }
 }
 
@@ -1069,7 +1124,7 @@ __global__ void k_explode(LevelView P, LevelView F, StepConsts k, const float *p
     if ((fl & FL_KIND_MASK) != KIND_ACTIVE || (fl & FL_SOLID) || !(fl & FL_BAND)) return;
     float o[9];
     for (int q = 0; q < 9; q++) o[q] = post[(size_t)q * P.ns + slot];
-    explode_band<T>(P, F, k, t, lx, ly, fl, slot, o);
+    explode_band<T>(P, F, k, t, lx, ly, fl, __ldg(P.aux + slot), o);
 }
 
 // rest state: every present cell's populations are e (values to store, relative to the
@@ -1171,11 +1226,12 @@ __global__ void __launch_bounds__(256) k_mass(LevelView P, int p, double area, d
 // ------------------------------------------------------------------ launchers
 // launch, with programmatic stream serialization when pdl is set (see griddep_wait)
 template <typename... Args>
-static void launch_pdl_smem(void (*kern)(Args...), unsigned grid, cudaStream_t st, int pdl, size_t smem, Args... args)
+static void launch_pdl_bs(void (*kern)(Args...), unsigned grid, unsigned block, cudaStream_t st, int pdl, size_t smem,
+                          Args... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(LBM_TILE);
+    cfg.blockDim = dim3(block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1184,6 +1240,12 @@ static void launch_pdl_smem(void (*kern)(Args...), unsigned grid, cudaStream_t s
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename... Args>
+static void launch_pdl_smem(void (*kern)(Args...), unsigned grid, cudaStream_t st, int pdl, size_t smem, Args... args)
+{
+    launch_pdl_bs(kern, grid, LBM_TILE, st, pdl, smem, args...);
 }
 
 template <typename... Args>
@@ -1205,15 +1267,29 @@ static void launch_level_mb(cudaStream_t st, const LevelView &P, const LevelView
     else launch_pdl_smem(k_level<false, false, T, MINB, PERSIST, ODD>, grid, st, pdl, smem, P, Fv, Cv, R, k, ls);
 }
 
+template <typename T, int MINB, bool ODD>
+static void launch_level_wl(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
+                            const RecView &R, const StepConsts &k, const LevelStep &ls, int pdl)
+{
+    const unsigned grid = (unsigned)((P.n_work_warps + LBM_WL_WARPS - 1) / LBM_WL_WARPS);
+    if (grid == 0) return;
+    const unsigned bs = LBM_WL_WARPS * 32;
+    if (ls.wall) launch_pdl_bs(k_level_wl<true, false, T, MINB, ODD>, grid, bs, st, pdl, 0, P, Fv, Cv, R, k, ls);
+    else if (child) launch_pdl_bs(k_level_wl<false, true, T, MINB, ODD>, grid, bs, st, pdl, 0, P, Fv, Cv, R, k, ls);
+    else launch_pdl_bs(k_level_wl<false, false, T, MINB, ODD>, grid, bs, st, pdl, 0, P, Fv, Cv, R, k, ls);
+}
+
 template <typename T, bool ODD>
 static void launch_level_t(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
                            const RecView &R, const StepConsts &k, const LevelStep &ls, const LevelTune &tu)
 {
     if (tu.min_blocks == 6) {
-        if (tu.persistent) launch_level_mb<T, 6, true, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        if (tu.sched == LBM_SCHED_WARPS) launch_level_wl<T, 6, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        else if (tu.sched == LBM_SCHED_PERSIST) launch_level_mb<T, 6, true, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
         else launch_level_mb<T, 6, false, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
     } else {
-        if (tu.persistent) launch_level_mb<T, 5, true, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        if (tu.sched == LBM_SCHED_WARPS) launch_level_wl<T, 5, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        else if (tu.sched == LBM_SCHED_PERSIST) launch_level_mb<T, 5, true, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
         else launch_level_mb<T, 5, false, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
     }
 }

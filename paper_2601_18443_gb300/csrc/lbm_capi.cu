@@ -96,7 +96,7 @@ struct lbm_solver {
     StepConsts k;
     int parity[LBM_MAXL];
     int min_blocks[LBM_MAXL];     // register budget of each level's kernel (lbm_autotune)
-    int persistent[LBM_MAXL];     // persistent grid for each level's kernel (lbm_autotune)
+    int sched[LBM_MAXL];          // grid schedule (LBM_SCHED_*) of each level's kernel (lbm_autotune)
     int shape[LBM_MAXL];          // work shape of a warp for each level's kernel (lbm_autotune)
     int pdl = 1;                  // programmatic dependent launch (lbm_autotune)
     bool off_schedule = false;    // single launches (lbm_step_launch) left the level schedule
@@ -274,7 +274,7 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     ls.shape = s->shape[l];
     ls.status = s->d_status;
     mark_begin(s);
-    const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl, s->persistent[l], s->shape[l]};
+    const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl, s->sched[l], s->shape[l]};
     lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls, tu);
     mark_end(s, l == L - 1 ? KC_LEVEL_FINEST : KC_LEVEL_COARSE, P.ns, l);
     nk++;
@@ -384,7 +384,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
     s->cfg = *cfg;
     s->L = cfg->levels;
     s->U = cfg->Ma * std::sqrt(1.0 / 3.0);
-    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; s->persistent[l] = 0; s->shape[l] = 0; }
+    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; s->sched[l] = LBM_SCHED_TILE; s->shape[l] = 0; }
     if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LBM_ERR_CUDA; }
     if (cfg->cuda_stream) {
         s->stream = (cudaStream_t)cfg->cuda_stream;
@@ -564,6 +564,24 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.n_band_tiles = (int)G.band_tiles.size();
         v.work_tiles = upload(s, G.work_tiles, ok);
         v.n_work_tiles = (int)G.work_tiles.size();
+        {
+            // warps (work shape 0: 16 x 2 cells) of the work tiles that hold an active or ghost fluid cell
+            std::vector<int> ww;
+            ww.reserve(G.work_tiles.size() * 8);
+            for (const int t : G.work_tiles)
+                for (int w = 0; w < 8; w++) {
+                    bool any = false;
+                    for (int c = 0; c < 32 && !any; c++) {
+                        const int lx = (w & 1) * 16 + (c & 15), ly = (w >> 1) * 2 + (c >> 4);
+                        const uint32_t f = H.flags[(size_t)t * LBM_TILE + ly * LBM_TX + lx];
+                        const uint32_t kd = f & FL_KIND_MASK;
+                        any = (kd == KIND_ACTIVE || kd == KIND_GHOST) && !(f & FL_SOLID);
+                    }
+                    if (any) ww.push_back(t * 8 + w);
+                }
+            v.work_warps = upload(s, ww, ok);
+            v.n_work_warps = (int)ww.size();
+        }
         v.flags = upload(s, H.flags, ok);
         v.inv_d2 = upload(s, inv_d2, ok);
         v.aux = upload(s, aux, ok);
@@ -590,6 +608,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         const lbmgrid::Level &G = s->g.lv[L - 1];
         std::vector<int> bslot(nr), nsv(nr), st_slot((size_t)nr * 16, -1), loop(nr);
         std::vector<float> st_wr((size_t)nr * 16, 0.f), st_wu((size_t)nr * 16, 0.f), nx(nr), ny(nr), dwb(nr), q((size_t)nr * 9, 0.f);
+        std::vector<float> yc((size_t)nr * 18, 0.f);
         for (int r = 0; r < nr; r++) {
             const lbmgrid::Record &R = s->g.recs[r];
             bslot[r] = (int)G.slot(R.i, R.j);
@@ -603,8 +622,36 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
                 st_wu[(size_t)r * 16 + m] = m < R.ns ? (float)wu[m] : 0.f;
             }
             nx[r] = (float)R.n[0]; ny[r] = (float)R.n[1]; dwb[r] = (float)R.dwb;
-            for (int d = 0; d < 9; d++) q[(size_t)r * 9 + d] = (float)R.q[d];
+            for (int d = 0; d < 9; d++) {
+                q[(size_t)r * 9 + d] = (float)R.q[d];
+                yc[(size_t)r * 18 + 2 * d] = (float)(1.0 / (1.0 + R.q[d]));
+                yc[(size_t)r * 18 + 2 * d + 1] = (float)(R.q[d] / (1.0 + R.q[d]));
+            }
             loop[r] = R.loop;
+        }
+        // per record, the directions q whose node B + c_q is active fluid: its tile is present
+        // (through the tile neighbour table, as the level kernel finds it) and the cell is
+        // active and not solid
+        std::vector<uint32_t> nfluid(nr, 0u);
+        {
+            static const int CX[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1}, CY[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+            auto dir_of = [](int dx, int dy) {
+                for (int d = 0; d < 9; d++)
+                    if (CX[d] == dx && CY[d] == dy) return d;
+                return 0;
+            };
+            const std::vector<uint32_t> &fl = s->lv[L - 1].flags;
+            for (int r = 0; r < nr; r++) {
+                const int t = bslot[r] / LBM_TILE, lx = bslot[r] % LBM_TX, ly = (bslot[r] % LBM_TILE) / LBM_TX;
+                for (int d = 1; d < 9; d++) {
+                    const int ax = lx + CX[d], ay = ly + CY[d];
+                    const int sx = ax < 0 ? -1 : (ax >= LBM_TX ? 1 : 0), sy = ay < 0 ? -1 : (ay >= LBM_TY ? 1 : 0);
+                    const int tt = (sx == 0 && sy == 0) ? t : G.nbr[(size_t)t * 9 + dir_of(sx, sy)];
+                    if (tt < 0) continue;
+                    const uint32_t f = fl[(size_t)tt * LBM_TILE + (ay & (LBM_TY - 1)) * LBM_TX + (ax & (LBM_TX - 1))];
+                    if ((f & FL_KIND_MASK) == KIND_ACTIVE && !(f & FL_SOLID)) nfluid[r] |= 1u << d;
+                }
+            }
         }
         RecView &v = s->rec;
         v.n = nr;
@@ -618,6 +665,8 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.dwb = upload(s, dwb, ok);
         v.q = upload(s, q, ok);
         v.loop = upload(s, loop, ok);
+        v.nfluid = upload(s, nfluid, ok);
+        v.yc = upload(s, yc, ok);
         s->d_slip = (float *)dalloc(s, 2 * (size_t)std::max(n_loops, 1) * sizeof(float));
         v.slip = s->d_slip;
         float **outs[9] = {&v.drhoW, &v.uWx, &v.uWy, &v.utau, &v.chiB, &v.tx, &v.ty, &v.ut, &v.utau_start};
@@ -834,7 +883,7 @@ lbm_status lbm_step_launch(lbm_solver *s, int level, int kind)
         ls.pp = C ? s->parity[l - 1] : 0;
         ls.shape = s->shape[l];
         ls.status = s->d_status;
-        const lbmdev::LevelTune tu{s->min_blocks[l], 0, s->persistent[l], s->shape[l]};
+        const lbmdev::LevelTune tu{s->min_blocks[l], 0, s->sched[l], s->shape[l]};
         lbmdev::launch_level(s->stream, P, F, C, s->rec, s->k, ls, tu);
         s->parity[l] ^= 1;
     }
@@ -1221,6 +1270,8 @@ lbm_status lbm_get_info(lbm_solver *s, lbm_info *out)
         out->cells_active[l] = act;
         out->cells_present[l] = pres;
         out->slots[l] = (long long)G.ntiles * LBM_TILE;
+        out->work_tiles[l] = s->lv[l].v.n_work_tiles;
+        out->work_warps[l] = s->lv[l].v.n_work_warps;
         nu += act << l;
     }
     out->node_updates_per_step = nu;
@@ -1318,29 +1369,31 @@ static lbm_status graph_step_time(lbm_solver *s, int n, double *us)
     return LBM_OK;
 }
 
+static int no_persist(int sched) { return sched == LBM_SCHED_PERSIST ? LBM_SCHED_TILE : sched; }
+
 lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
 {
     if (!s || !out || steps < 1) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
-    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6, 5, 6, 5, 6, 5, 6};
-    static const int CAND_PE[LBM_TUNE_CANDIDATES] = {0, 0, 1, 1, 0, 0, 1, 1};
-    static const int CAND_SH[LBM_TUNE_CANDIDATES] = {0, 0, 0, 0, 1, 1, 1, 1};
+    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6, 5, 6, 5, 6, 5, 6, 5, 6};
+    static const int CAND_PE[LBM_TUNE_CANDIDATES] = {0, 0, 1, 1, 0, 0, 1, 1, 2, 2};
+    static const int CAND_SH[LBM_TUNE_CANDIDATES] = {0, 0, 0, 0, 1, 1, 1, 1, 0, 0};
     std::memset(out, 0, sizeof *out);
     const int L = s->L;
     out->levels = L;
     lbm_status st;
     if ((st = graph_step_time(s, steps, &out->default_step_us)) != LBM_OK) return st;
     int keep_mb[LBM_MAXL], keep_pe[LBM_MAXL], keep_sh[LBM_MAXL];
-    for (int l = 0; l < L; l++) { keep_mb[l] = s->min_blocks[l]; keep_pe[l] = s->persistent[l]; keep_sh[l] = s->shape[l]; }
+    for (int l = 0; l < L; l++) { keep_mb[l] = s->min_blocks[l]; keep_pe[l] = s->sched[l]; keep_sh[l] = s->shape[l]; }
     // 1: register budget and grid schedule per level, from per-launch event timings of
     //    every candidate
     for (int c = 0; c < LBM_TUNE_CANDIDATES; c++) {
-        for (int l = 0; l < L; l++) { s->min_blocks[l] = CAND_MB[c]; s->persistent[l] = CAND_PE[c]; s->shape[l] = CAND_SH[c]; }
+        for (int l = 0; l < L; l++) { s->min_blocks[l] = CAND_MB[c]; s->sched[l] = CAND_PE[c]; s->shape[l] = CAND_SH[c]; }
         out->candidate_min_blocks[c] = CAND_MB[c];
-        out->candidate_persistent[c] = CAND_PE[c];
+        out->candidate_sched[c] = CAND_PE[c];
         out->candidate_shape[c] = CAND_SH[c];
         if ((st = level_launch_times(s, steps, out->level_us[c])) != LBM_OK) {
-            for (int l = 0; l < L; l++) { s->min_blocks[l] = keep_mb[l]; s->persistent[l] = keep_pe[l]; s->shape[l] = keep_sh[l]; }
+            for (int l = 0; l < L; l++) { s->min_blocks[l] = keep_mb[l]; s->sched[l] = keep_pe[l]; s->shape[l] = keep_sh[l]; }
             return st;
         }
     }
@@ -1349,25 +1402,25 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
         for (int c = 1; c < LBM_TUNE_CANDIDATES; c++)
             if (out->level_us[c][l] < out->level_us[best][l]) best = c;
         s->min_blocks[l] = CAND_MB[best];
-        s->persistent[l] = CAND_PE[best];
+        s->sched[l] = CAND_PE[best];
         s->shape[l] = CAND_SH[best];
         out->min_blocks[l] = CAND_MB[best];
-        out->persistent[l] = CAND_PE[best];
+        out->sched[l] = CAND_PE[best];
         out->shape[l] = CAND_SH[best];
     }
     // 1b: per-launch timings miss how launches overlap inside the graph (a persistent grid
     //     occupies every SM while the next launch would start): keep the per-level choice
-    //     only if whole graph steps confirm it, against the same choice without persistent
-    //     grids and against the default form
+    //     only if whole graph steps confirm it, against the same choice with one block per
+    //     tile where it took a persistent grid, and against the default form
     {
         int pick_mb[LBM_MAXL], pick_pe[LBM_MAXL], pick_sh[LBM_MAXL];
-        for (int l = 0; l < L; l++) { pick_mb[l] = s->min_blocks[l]; pick_pe[l] = s->persistent[l]; pick_sh[l] = s->shape[l]; }
+        for (int l = 0; l < L; l++) { pick_mb[l] = s->min_blocks[l]; pick_pe[l] = s->sched[l]; pick_sh[l] = s->shape[l]; }
         double best_us = 0.0;
         int best = 0;
         for (int v = 0; v < 3; v++) {
             for (int l = 0; l < L; l++) {
                 s->min_blocks[l] = v == 2 ? keep_mb[l] : pick_mb[l];
-                s->persistent[l] = v == 0 ? pick_pe[l] : (v == 1 ? 0 : keep_pe[l]);
+                s->sched[l] = v == 0 ? pick_pe[l] : (v == 1 ? no_persist(pick_pe[l]) : keep_pe[l]);
                 s->shape[l] = v == 2 ? keep_sh[l] : pick_sh[l];
             }
             double us = 0.0;
@@ -1378,10 +1431,10 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
         }
         for (int l = 0; l < L; l++) {
             s->min_blocks[l] = best == 2 ? keep_mb[l] : pick_mb[l];
-            s->persistent[l] = best == 0 ? pick_pe[l] : (best == 1 ? 0 : keep_pe[l]);
+            s->sched[l] = best == 0 ? pick_pe[l] : (best == 1 ? no_persist(pick_pe[l]) : keep_pe[l]);
             s->shape[l] = best == 2 ? keep_sh[l] : pick_sh[l];
             out->min_blocks[l] = s->min_blocks[l];
-            out->persistent[l] = s->persistent[l];
+            out->sched[l] = s->sched[l];
             out->shape[l] = s->shape[l];
         }
     }
@@ -1710,18 +1763,22 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *persistent, const int *shape,
+lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *sched, const int *shape,
                                   int pdl)
 {
-    if (!s || !min_blocks || !persistent || (pdl != 0 && pdl != 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s || !min_blocks || !sched || (pdl != 0 && pdl != 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
-    for (int l = 0; l < s->L; l++)
-        if ((min_blocks[l] != 5 && min_blocks[l] != 6) || (persistent[l] != 0 && persistent[l] != 1) ||
-            (shape && shape[l] != 0 && shape[l] != 1))
-            return fail(s, LBM_ERR_INVALID_ARG, "launch variant: min_blocks must be 5 or 6, persistent and shape 0 or 1");
+    for (int l = 0; l < s->L; l++) {
+        const int sh = shape ? shape[l] : 0;
+        if ((min_blocks[l] != 5 && min_blocks[l] != 6) || sched[l] < LBM_SCHED_TILE || sched[l] > LBM_SCHED_WARPS ||
+            (sh != 0 && sh != 1) || (sched[l] == LBM_SCHED_WARPS && sh != 0))
+            return fail(s, LBM_ERR_INVALID_ARG,
+                        "launch variant: min_blocks must be 5 or 6, sched one of LBM_SCHED_*, shape 0 or 1 (0 with "
+                        "LBM_SCHED_WARPS)");
+    }
     for (int l = 0; l < s->L; l++) {
         s->min_blocks[l] = min_blocks[l];
-        s->persistent[l] = persistent[l];
+        s->sched[l] = sched[l];
         s->shape[l] = shape ? shape[l] : 0;
     }
     s->pdl = pdl;
