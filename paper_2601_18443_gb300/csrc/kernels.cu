@@ -392,9 +392,10 @@ __device__ float wf_utau(float ut, float y_nu, float guess)
 // Wall state of one boundary node from the macroscopic fields at time level p:
 // steps 1-5 of Sec 2.3 (IDW density and LSQ velocity at R, tangential part, u_tau from
 // eq 22, u_V, slip velocity of eq 28 along t) and the SA Dirichlet value (Sec 2.2).
-// Writes the record's state arrays; returns rho_W - 1, u_W and chi_B.  The Newton
-// iteration starts from the u_tau of the previous step; only the step (keep_start)
-// stores its result as the next start, so that queries leave the trajectory unchanged.
+// Returns rho_W - 1, u_W and chi_B.  The Newton iteration starts from the u_tau of the
+// previous step; only the step (keep_start) stores its result as the next start, so that
+// queries leave the trajectory unchanged, and only queries (!keep_start) write the
+// record's state arrays.
 __device__ void wall_record(const LevelView &P, int p, const RecView &R, const StepConsts &k, int r, bool keep_start,
                             float &drW, float &uWx, float &uWy, float &chiB)
 {
@@ -449,8 +450,12 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
         uWx = R.slip[2 * R.loop[r]]; uWy = R.slip[2 * R.loop[r] + 1];
     }
     drW = drR;
-    R.drhoW[r] = drR; R.uWx[r] = uWx; R.uWy[r] = uWy; R.utau[r] = utau; R.chiB[r] = chiB;
-    R.tx[r] = tx; R.ty[r] = ty; R.ut[r] = ut;
+    if (!keep_start) {
+        // the query form fills the record's state arrays (lbm_get_loads, lbm_get_wall_state
+        // run it first); the step only needs the returned values
+        R.drhoW[r] = drR; R.uWx[r] = uWx; R.uWy[r] = uWy; R.utau[r] = utau; R.chiB[r] = chiB;
+        R.tx[r] = tx; R.ty[r] = ty; R.ut[r] = ut;
+    }
 }
 
 // ------------------------------------------------------------------ the fused level step
@@ -875,7 +880,9 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
 // the register budget of k_level<.., MINB, ..>: 20 two-warp blocks (40 warps) fit 48
 // registers a thread, 24 fit 40 (a sub-partition's 16384 registers hold 10 warps of 48 or
 // 12 of 40, whatever the block size).  Per cell it runs the same code as k_level with work
-// shape 0.
+// shape 0.  (A persistent form, the resident blocks walking the list, measured 30 % slower
+// on the finest level of the c/4096 workload: with every resident warp busy all the time
+// each entry takes longer, so the throughput falls; it is not offered.)
 #define LBM_WL_WARPS 2
 template <bool WALL, bool CHILD, typename T, int MINB, bool ODD>
 __global__ void __launch_bounds__(LBM_WL_WARPS * 32, MINB == 6 ? 24 : 20)
