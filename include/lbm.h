@@ -285,6 +285,7 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times 
 #define LBM_SCHED_PERSIST 1   /* a grid of 2 x SMs x budget blocks striding over the work tiles  */
 #define LBM_SCHED_WARPS 2     /* two-warp blocks over the list of work warps (16 x 2 cells each
                                  of a work tile that hold an active or ghost fluid cell; shape 0) */
+#define LBM_SCHED_WARPS4 3    /* four-warp blocks over the same list (shape 0)                    */
 
 /* Launch autotuner.  Not part of the paper's method (Sec 2.1 gives the level schedule, not
  * its mapping to a GPU).  For each level it picks one of LBM_TUNE_CANDIDATES launch forms
@@ -303,7 +304,7 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times 
  * schedules and contracts the arithmetic differently per variant); the timed steps are real
  * steps of the solve (steps_taken of them).
  * Synchronous.  Errors as lbm_step. */
-#define LBM_TUNE_CANDIDATES 10
+#define LBM_TUNE_CANDIDATES 12
 typedef struct {
     int levels;
     int candidate_min_blocks[LBM_TUNE_CANDIDATES];
@@ -339,11 +340,20 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size);
 
 /* Set the launch variant directly (for instance one lbm_autotune found on a solve of the
  * same shape): min_blocks[l] in {5, 6}, sched[l] one of LBM_SCHED_* and shape[l] in {0, 1}
- * (NULL: shape 0 on every level; LBM_SCHED_WARPS requires shape 0) for each of the solver's
+ * (NULL: shape 0 on every level; the warp-list schedules require shape 0) for each of the solver's
  * levels, pdl 0 or 1; the step graphs are recaptured.  No device work.  Errors:
  * LBM_ERR_INVALID_ARG for a value outside those sets, LBM_ERR_NO_GEOMETRY. */
 lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *sched, const int *shape,
                                   int pdl);
+
+/* Launch grouping of the prolongations (Sec 2.1): in each descent of the recursive schedule
+ * the prolongations of consecutive levels l - 1, l go out as one launch (on by default)
+ * where level l's band cells have no ghost cell of level l in their 3 x 3 neighbourhood, so
+ * that neither reads what the other writes.  on 0 launches each on its own.  merged_levels
+ * (may be NULL) returns the number of levels l whose prolongation can join the one of
+ * l - 1.  The step graphs are recaptured.  No device work.  Errors: LBM_ERR_INVALID_ARG,
+ * LBM_ERR_NO_GEOMETRY. */
+lbm_status lbm_set_prolong_merge(lbm_solver *s, int on, int *merged_levels);
 
 /* Largest n_cells that lbm_level_mass_noalloc accepts (its fixed scratch holds 4096
  * per-block partial sums of at most 16384 cells each). */

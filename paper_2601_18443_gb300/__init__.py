@@ -66,8 +66,8 @@ class lbm_kernel_times(C.Structure):
                 ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
 
 
-TUNE_CANDIDATES = 10
-SCHED_TILE, SCHED_PERSIST, SCHED_WARPS = 0, 1, 2     # LBM_SCHED_* of include/lbm.h
+TUNE_CANDIDATES = 12
+SCHED_TILE, SCHED_PERSIST, SCHED_WARPS, SCHED_WARPS4 = 0, 1, 2, 3   # LBM_SCHED_* of include/lbm.h
 
 
 class lbm_tune_report(C.Structure):
@@ -126,6 +126,7 @@ def library():
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
         "lbm_set_launch_variant": ([vp, ip, ip, ip, C.c_int], C.c_int),
+        "lbm_set_prolong_merge": ([vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "lbm_get_state": ([vp, vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
         "lbm_set_state": ([vp, vp, C.c_size_t], C.c_int),
         "lbm_level_mass_noalloc": ([vp, vp, vp, vp, vp, C.c_longlong, C.c_double, vp, vp, vp], C.c_int),
@@ -427,12 +428,19 @@ class Solver:
 
     def set_launch_variant(self, min_blocks, pdl=1, sched=None, shape=None):
         """lbm_set_launch_variant: per-level register budget (5 or 6 blocks per SM), grid
-        schedule (SCHED_TILE, SCHED_PERSIST or SCHED_WARPS), work shape of a warp (0 a 16 x 2
-        block, 1 a 32-cell row; 0 with SCHED_WARPS) and PDL."""
+        schedule (SCHED_TILE, SCHED_PERSIST, SCHED_WARPS or SCHED_WARPS4), work shape of a warp
+        (0 a 16 x 2 block, 1 a 32-cell row; 0 with the warp-list schedules) and PDL."""
         mb = np.ascontiguousarray(min_blocks, dtype=np.int32)
         pe = np.ascontiguousarray(sched if sched is not None else [SCHED_TILE] * len(mb), dtype=np.int32)
         sh = np.ascontiguousarray(shape if shape is not None else [0] * len(mb), dtype=np.int32)
         self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), _ip(pe), _ip(sh), int(pdl)))
+
+    def set_prolong_merge(self, on=True):
+        """lbm_set_prolong_merge: one launch for the prolongations of consecutive levels where
+        they are independent; returns the number of levels whose prolongation can join."""
+        n = C.c_int()
+        self._check(self._lib.lbm_set_prolong_merge(self._h, int(bool(on)), C.byref(n)))
+        return n.value
 
     def time_kernels(self, n=1):
         out = lbm_kernel_times()

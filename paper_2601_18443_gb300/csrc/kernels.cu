@@ -873,25 +873,25 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
 
 }
 
-// Warp-list schedule of k_level: blocks of LBM_WL_WARPS warps, each warp taking one entry of
-// the level's work-warp list (tile * 8 + its warp in work shape 0), so that the warps of a
-// work tile holding no active or ghost fluid cell are not launched, and a block is retired
-// (and replaced) as soon as its two warps are done rather than its tile's eight.  MINB keeps
-// the register budget of k_level<.., MINB, ..>: 20 two-warp blocks (40 warps) fit 48
-// registers a thread, 24 fit 40 (a sub-partition's 16384 registers hold 10 warps of 48 or
-// 12 of 40, whatever the block size).  Per cell it runs the same code as k_level with work
-// shape 0.  (A persistent form, the resident blocks walking the list, measured 30 % slower
-// on the finest level of the c/4096 workload: with every resident warp busy all the time
-// each entry takes longer, so the throughput falls; it is not offered.)
-#define LBM_WL_WARPS 2
-template <bool WALL, bool CHILD, typename T, int MINB, bool ODD>
-__global__ void __launch_bounds__(LBM_WL_WARPS * 32, MINB == 6 ? 24 : 20)
+// Warp-list schedules of k_level: blocks of WPB warps (2 or 4), each warp taking one entry
+// of the level's work-warp list (tile * 8 + its warp in work shape 0), so that the warps of
+// a work tile holding no active or ghost fluid cell are not launched, and a block is retired
+// (and replaced) as soon as its WPB warps are done rather than its tile's eight.  Smaller
+// blocks balance better; larger ones ask less of the block dispatcher, which refills an SM
+// at a bounded rate.  MINB keeps the register budget of k_level<.., MINB, ..>: 40 warps a
+// SM fit 48 registers a thread, 48 fit 40 (a sub-partition's 16384 registers hold 10 warps
+// of 48 or 12 of 40, whatever the block size).  Per cell it runs the same code as k_level
+// with work shape 0.  (A persistent form, the resident blocks walking the list, measured
+// 30 % slower on the finest level of the c/4096 workload: with every resident warp busy all
+// the time each entry takes longer, so the throughput falls; it is not offered.)
+template <bool WALL, bool CHILD, typename T, int MINB, int WPB, bool ODD>
+__global__ void __launch_bounds__(WPB * 32, (MINB == 6 ? 48 : 40) / WPB)
     k_level_wl(LevelView P, LevelView F, LevelView C, RecView R, StepConsts k, LevelStep ls)
 {
     const Lat<T> L{static_cast<T *>(P.f), P.ns, k.pshift};
-    __shared__ int nb3w[LBM_WL_WARPS][9];
+    __shared__ int nb3w[WPB][9];
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-    const int w = blockIdx.x * LBM_WL_WARPS + wb;
+    const int w = blockIdx.x * WPB + wb;
     const bool have = w < P.n_work_warps;
     int *nb3 = nb3w[wb];
     int t = 0, lx = 0, ly = 0;
@@ -1274,16 +1274,16 @@ static void launch_level_mb(cudaStream_t st, const LevelView &P, const LevelView
     else launch_pdl_smem(k_level<false, false, T, MINB, PERSIST, ODD>, grid, st, pdl, smem, P, Fv, Cv, R, k, ls);
 }
 
-template <typename T, int MINB, bool ODD>
+template <typename T, int MINB, int WPB, bool ODD>
 static void launch_level_wl(cudaStream_t st, const LevelView &P, const LevelView &Fv, const LevelView &Cv, bool child,
                             const RecView &R, const StepConsts &k, const LevelStep &ls, int pdl)
 {
-    const unsigned grid = (unsigned)((P.n_work_warps + LBM_WL_WARPS - 1) / LBM_WL_WARPS);
+    const unsigned grid = (unsigned)((P.n_work_warps + WPB - 1) / WPB);
     if (grid == 0) return;
-    const unsigned bs = LBM_WL_WARPS * 32;
-    if (ls.wall) launch_pdl_bs(k_level_wl<true, false, T, MINB, ODD>, grid, bs, st, pdl, 0, P, Fv, Cv, R, k, ls);
-    else if (child) launch_pdl_bs(k_level_wl<false, true, T, MINB, ODD>, grid, bs, st, pdl, 0, P, Fv, Cv, R, k, ls);
-    else launch_pdl_bs(k_level_wl<false, false, T, MINB, ODD>, grid, bs, st, pdl, 0, P, Fv, Cv, R, k, ls);
+    const unsigned bs = WPB * 32;
+    if (ls.wall) launch_pdl_bs(k_level_wl<true, false, T, MINB, WPB, ODD>, grid, bs, st, pdl, 0, P, Fv, Cv, R, k, ls);
+    else if (child) launch_pdl_bs(k_level_wl<false, true, T, MINB, WPB, ODD>, grid, bs, st, pdl, 0, P, Fv, Cv, R, k, ls);
+    else launch_pdl_bs(k_level_wl<false, false, T, MINB, WPB, ODD>, grid, bs, st, pdl, 0, P, Fv, Cv, R, k, ls);
 }
 
 template <typename T, bool ODD>
@@ -1291,11 +1291,13 @@ static void launch_level_t(cudaStream_t st, const LevelView &P, const LevelView 
                            const RecView &R, const StepConsts &k, const LevelStep &ls, const LevelTune &tu)
 {
     if (tu.min_blocks == 6) {
-        if (tu.sched == LBM_SCHED_WARPS) launch_level_wl<T, 6, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        if (tu.sched == LBM_SCHED_WARPS) launch_level_wl<T, 6, 2, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        else if (tu.sched == LBM_SCHED_WARPS4) launch_level_wl<T, 6, 4, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
         else if (tu.sched == LBM_SCHED_PERSIST) launch_level_mb<T, 6, true, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
         else launch_level_mb<T, 6, false, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
     } else {
-        if (tu.sched == LBM_SCHED_WARPS) launch_level_wl<T, 5, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        if (tu.sched == LBM_SCHED_WARPS) launch_level_wl<T, 5, 2, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
+        else if (tu.sched == LBM_SCHED_WARPS4) launch_level_wl<T, 5, 4, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
         else if (tu.sched == LBM_SCHED_PERSIST) launch_level_mb<T, 5, true, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
         else launch_level_mb<T, 5, false, ODD>(st, P, Fv, Cv, child, R, k, ls, tu.pdl);
     }

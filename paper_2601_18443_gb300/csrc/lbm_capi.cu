@@ -96,6 +96,15 @@ struct lbm_solver {
     StepConsts k;
     int parity[LBM_MAXL];
     int min_blocks[LBM_MAXL];     // register budget of each level's kernel (lbm_autotune)
+    // prolongations of consecutive levels that read nothing the other writes go out as one
+    // launch: prolong_indep[l] holds when no band cell of level l has a ghost of level l in
+    // its 3 x 3 neighbourhood (prolongation l - 1 writes those ghosts, prolongation l reads
+    // the band cells' neighbourhoods)
+    bool prolong_indep[LBM_MAXL];
+    int prolong_merge = 1;          // lbm_set_prolong_merge
+    lbmdev::ProlongBatchArgs pend;  // prolongations waiting for the next level-step launch
+    unsigned pend_grid = 0;
+    int pend_level = 0;
     int sched[LBM_MAXL];          // grid schedule (LBM_SCHED_*) of each level's kernel (lbm_autotune)
     int shape[LBM_MAXL];          // work shape of a warp for each level's kernel (lbm_autotune)
     int pdl = 1;                  // programmatic dependent launch (lbm_autotune)
@@ -245,6 +254,19 @@ static void mark_end(lbm_solver *s, int cls, long long cells, int level)
     s->ev_used += 2;
 }
 
+// Launch the pending prolongations (one kernel for all of them).
+static void flush_prolong(lbm_solver *s, cudaStream_t st, long long &nk)
+{
+    if (s->pend.n == 0) return;
+    mark_begin(s);
+    if (s->pend.n == 1) lbmdev::launch_prolong(st, s->pend.d[0].P, s->pend.d[0].F, s->pend.d[0].p, s->pdl);
+    else lbmdev::launch_prolong_batch(st, s->pend, s->pend_grid, s->pdl);
+    mark_end(s, KC_PROLONG, (long long)s->pend_grid * LBM_TILE, s->pend_level);
+    nk++;
+    s->pend.n = 0;
+    s->pend_grid = 0;
+}
+
 // One level-l step (Sec 2.1 recursive sub-cycling): the ghost fields of level l+1 are
 // reconstructed from level l at time t, level l+1 takes two sub-steps (the second one
 // restricts its new fields into the covered cells of level l), then one fused launch
@@ -257,13 +279,21 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     const LevelView *F = (l < L - 1) ? &s->lv[l + 1].v : nullptr;
     const LevelView *C = (l > 0) ? &s->lv[l - 1].v : nullptr;
     if (F) {
-        mark_begin(s);
-        lbmdev::launch_prolong(st, P, *F, s->parity[l], s->pdl);
-        mark_end(s, KC_PROLONG, (long long)P.n_band_tiles * LBM_TILE, l);
-        nk += P.n_band_tiles > 0;
+        // the prolongation joins the pending ones when it reads nothing they write (it
+        // follows the prolongation of level l - 1 in the descent); the next level step
+        // launches them
+        if (P.n_band_tiles > 0) {
+            if (s->pend.n > 0 && !(s->prolong_merge && s->prolong_indep[l] && s->pend_level + s->pend.n == l))
+                flush_prolong(s, st, nk);
+            if (s->pend.n == 0) s->pend_level = l;
+            lbmdev::ProlongDesc &d = s->pend.d[s->pend.n++];
+            d.P = P; d.F = *F; d.p = s->parity[l]; d.first_block = (int)s->pend_grid;
+            s->pend_grid += (unsigned)P.n_band_tiles;
+        }
         advance(s, st, l + 1, 0, nk);
         advance(s, st, l + 1, 1, nk);
     }
+    flush_prolong(s, st, nk);
     lbmdev::LevelStep ls;
     ls.p = s->parity[l];
     ls.has_child = F != nullptr;
@@ -384,7 +414,11 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_solver **out)
     s->cfg = *cfg;
     s->L = cfg->levels;
     s->U = cfg->Ma * std::sqrt(1.0 / 3.0);
-    for (int l = 0; l < LBM_MAXL; l++) { s->parity[l] = 0; s->min_blocks[l] = 5; s->sched[l] = LBM_SCHED_TILE; s->shape[l] = 0; }
+    for (int l = 0; l < LBM_MAXL; l++) {
+        s->parity[l] = 0; s->min_blocks[l] = 5; s->sched[l] = LBM_SCHED_TILE; s->shape[l] = 0;
+        s->prolong_indep[l] = false;
+    }
+    s->pend.n = 0;
     if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LBM_ERR_CUDA; }
     if (cfg->cuda_stream) {
         s->stream = (cudaStream_t)cfg->cuda_stream;
@@ -678,6 +712,30 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
             CK(cudaMemsetAsync(s->d_slip, 0, 2 * (size_t)std::max(n_loops, 1) * sizeof(float), s->stream));
             for (auto o : outs) CK(cudaMemsetAsync(*o, 0, (size_t)std::max(nr, 1) * sizeof(float), s->stream));
         }
+    }
+    // which prolongations may share a launch with the one of the level above
+    for (int l = 0; l < L; l++) {
+        bool indep = l >= 1 && l + 1 < L;
+        const lbmgrid::Level &G = s->g.lv[l];
+        const std::vector<uint32_t> &fl = s->lv[l].flags;
+        static const int CX[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1}, CY[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+        for (int t = 0; indep && t < G.ntiles; t++)
+            for (int c = 0; indep && c < LBM_TILE; c++) {
+                if (!(fl[(size_t)t * LBM_TILE + c] & FL_BAND)) continue;
+                const int lx = c % LBM_TX, ly = c / LBM_TX;
+                for (int d = 1; d < 9 && indep; d++) {
+                    const int ax = lx + CX[d], ay = ly + CY[d];
+                    const int sx = ax < 0 ? -1 : (ax >= LBM_TX ? 1 : 0), sy = ay < 0 ? -1 : (ay >= LBM_TY ? 1 : 0);
+                    int dd = 0;
+                    for (int e = 0; e < 9; e++)
+                        if (CX[e] == sx && CY[e] == sy) dd = e;
+                    const int tt = dd == 0 ? t : G.nbr[(size_t)t * 9 + dd];
+                    if (tt < 0) continue;
+                    const uint32_t f = fl[(size_t)tt * LBM_TILE + (ay & (LBM_TY - 1)) * LBM_TX + (ax & (LBM_TX - 1))];
+                    if ((f & FL_KIND_MASK) == KIND_GHOST) indep = false;
+                }
+            }
+        s->prolong_indep[l] = indep;
     }
     // surface segments for the loads
     {
@@ -1375,9 +1433,9 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
 {
     if (!s || !out || steps < 1) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
-    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6, 5, 6, 5, 6, 5, 6, 5, 6};
-    static const int CAND_PE[LBM_TUNE_CANDIDATES] = {0, 0, 1, 1, 0, 0, 1, 1, 2, 2};
-    static const int CAND_SH[LBM_TUNE_CANDIDATES] = {0, 0, 0, 0, 1, 1, 1, 1, 0, 0};
+    static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6, 5, 6, 5, 6, 5, 6, 5, 6, 5, 6};
+    static const int CAND_PE[LBM_TUNE_CANDIDATES] = {0, 0, 1, 1, 0, 0, 1, 1, 2, 2, 3, 3};
+    static const int CAND_SH[LBM_TUNE_CANDIDATES] = {0, 0, 0, 0, 1, 1, 1, 1, 0, 0, 0, 0};
     std::memset(out, 0, sizeof *out);
     const int L = s->L;
     out->levels = L;
@@ -1763,6 +1821,19 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     return LBM_OK;
 }
 
+lbm_status lbm_set_prolong_merge(lbm_solver *s, int on, int *merged_levels)
+{
+    if (!s || (on != 0 && on != 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    s->prolong_merge = on;
+    if (merged_levels) {
+        int n = 0;
+        for (int l = 0; l < s->L; l++) n += s->prolong_indep[l] ? 1 : 0;
+        *merged_levels = n;
+    }
+    return capture_graphs(s);
+}
+
 lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *sched, const int *shape,
                                   int pdl)
 {
@@ -1770,11 +1841,11 @@ lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const in
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     for (int l = 0; l < s->L; l++) {
         const int sh = shape ? shape[l] : 0;
-        if ((min_blocks[l] != 5 && min_blocks[l] != 6) || sched[l] < LBM_SCHED_TILE || sched[l] > LBM_SCHED_WARPS ||
-            (sh != 0 && sh != 1) || (sched[l] == LBM_SCHED_WARPS && sh != 0))
+        if ((min_blocks[l] != 5 && min_blocks[l] != 6) || sched[l] < LBM_SCHED_TILE || sched[l] > LBM_SCHED_WARPS4 ||
+            (sh != 0 && sh != 1) || (sched[l] >= LBM_SCHED_WARPS && sh != 0))
             return fail(s, LBM_ERR_INVALID_ARG,
                         "launch variant: min_blocks must be 5 or 6, sched one of LBM_SCHED_*, shape 0 or 1 (0 with "
-                        "LBM_SCHED_WARPS)");
+                        "the warp-list schedules)");
     }
     for (int l = 0; l < s->L; l++) {
         s->min_blocks[l] = min_blocks[l];

@@ -42,12 +42,12 @@ def test_autotuned_solve_equals_the_default_one(store):
     b.step(3)                      # odd level-0 parity: the recapture starts from graph 1
     rep = b.autotune(steps=2)
     L = cfg["levels"]
-    assert rep["steps_taken"] == 2 * 16 and rep["levels"] == L
+    assert rep["steps_taken"] == 2 * 18 and rep["levels"] == L
     assert min(rep["step_us_confirm"].values()) > 0
     assert rep["candidates"] == [(5, 0, 0), (6, 0, 0), (5, 1, 0), (6, 1, 0), (5, 0, 1), (6, 0, 1), (5, 1, 1), (6, 1, 1),
-                                 (5, 2, 0), (6, 2, 0)]
-    assert all(sc in (0, 1, 2) for sc in rep["sched"]) and all(sh in (0, 1) for sh in rep["shape"])
-    assert all(sh == 0 for sc, sh in zip(rep["sched"], rep["shape"]) if sc == pkg.SCHED_WARPS)
+                                 (5, 2, 0), (6, 2, 0), (5, 3, 0), (6, 3, 0)]
+    assert all(sc in (0, 1, 2, 3) for sc in rep["sched"]) and all(sh in (0, 1) for sh in rep["shape"])
+    assert all(sh == 0 for sc, sh in zip(rep["sched"], rep["shape"]) if sc >= pkg.SCHED_WARPS)
     assert all(m in (5, 6) for m in rep["min_blocks"]) and rep["pdl"] in (0, 1)
     assert all(t > 0 for ts in rep["level_us"].values() for t in ts)
     assert rep["default_step_us"] > 0 and min(rep["step_us"].values()) > 0
@@ -68,7 +68,8 @@ def test_autotuned_solve_equals_the_default_one(store):
 
 
 @pytest.mark.parametrize("mb,pdl,pe,sh", [(6, 1, 0, 0), (5, 0, 0, 0), (6, 0, 1, 0), (5, 1, 1, 0), (6, 1, 1, 0),
-                                         (5, 1, 0, 1), (6, 1, 1, 1), (5, 0, 1, 1), (5, 1, 2, 0), (6, 0, 2, 0)])
+                                         (5, 1, 0, 1), (6, 1, 1, 1), (5, 0, 1, 1), (5, 1, 2, 0), (6, 0, 2, 0),
+                                         (5, 1, 3, 0), (6, 0, 3, 0)])
 def test_each_launch_variant_computes_the_same_numbers(mb, pdl, pe, sh):
     pkg.build()
     cfg, loops = W.naca0012_small(levels=5)
@@ -85,9 +86,11 @@ def test_each_launch_variant_computes_the_same_numbers(mb, pdl, pe, sh):
     with pytest.raises(pkg.LBMError):
         b.set_launch_variant([4] * L, 1)
     with pytest.raises(pkg.LBMError):
-        b.set_launch_variant([5] * L, 1, [3] * L)
+        b.set_launch_variant([5] * L, 1, [4] * L)
     with pytest.raises(pkg.LBMError):
-        b.set_launch_variant([5] * L, 1, [pkg.SCHED_WARPS] * L, [1] * L)     # the warp list has shape 0 only
+        b.set_launch_variant([5] * L, 1, [pkg.SCHED_WARPS] * L, [1] * L)     # the warp lists have shape 0 only
+    with pytest.raises(pkg.LBMError):
+        b.set_launch_variant([5] * L, 1, [pkg.SCHED_WARPS4] * L, [1] * L)
     # queries in between leave the trajectory alone
     a.coefficients(); b.coefficients()
     a.step(3); b.step(3)
@@ -98,7 +101,7 @@ def test_a_variant_run_twice_is_bitwise_identical():
     pkg.build()
     cfg, loops = W.naca0012_small(levels=5)
     L = cfg["levels"]
-    for mb, pe, sh in ((5, 0, 0), (6, 1, 0), (5, 0, 1), (5, 2, 0)):
+    for mb, pe, sh in ((5, 0, 0), (6, 1, 0), (5, 0, 1), (5, 2, 0), (5, 3, 0)):
         a, b = pkg.Solver(cfg), pkg.Solver(cfg)
         for s in (a, b):
             s.set_geometry(loops)

@@ -66,8 +66,12 @@ def test_batched_members_equal_solves_alone(store):
             assert np.array_equal(np.isnan(x), np.isnan(y)), lvl
             d = np.nanmax(np.abs(x - y))
             assert d <= tol, (lvl, d)
-        assert abs(la["CD"] - ls["CD"]) <= ltol * abs(la["CD"])
-        assert abs(la["CL"] - ls["CL"]) <= ltol * max(abs(la["CL"]), abs(la["CD"]))
+        # the loads are surface integrals of C_p = (2/3)(rho - 1)/U^2: an FP32 rounding difference
+        # of rho (6e-8) is 1e-5 of C_p at Ma 0.15, so C_D (a small difference of pressure and
+        # friction terms) is compared against the scale of both coefficients
+        scale = abs(la["CD"]) + abs(la["CL"])
+        assert abs(la["CD"] - ls["CD"]) <= ltol * scale
+        assert abs(la["CL"] - ls["CL"]) <= ltol * scale
         assert abs(la["mass"] - ls["mass"]) <= 1e-6 * la["mass"]
     # a member stepped on its own leaves the batch's schedule
     batched[2].step(1)
