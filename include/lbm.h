@@ -284,7 +284,9 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times 
 #define LBM_SCHED_TILE 0      /* one 256-thread block per work tile                              */
 #define LBM_SCHED_PERSIST 1   /* a grid of 2 x SMs x budget blocks striding over the work tiles  */
 #define LBM_SCHED_WARPS 2     /* two-warp blocks over the list of work warps (16 x 2 cells each
-                                 of a work tile that hold an active or ghost fluid cell; shape 0) */
+                                 of a work tile that hold an active or ghost fluid cell; shape 0),
+                                 ordered warps with boundary nodes, with band or coalescing cells,
+                                 with other active cells, with ghosts only                      */
 #define LBM_SCHED_WARPS4 3    /* four-warp blocks over the same list (shape 0)                    */
 
 /* Launch autotuner.  Not part of the paper's method (Sec 2.1 gives the level schedule, not

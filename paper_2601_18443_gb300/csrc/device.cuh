@@ -21,7 +21,9 @@ struct LevelView {
     const int *parent;            // tile of level l-1 holding the parents, or -1
     const int *band_tiles;        // tiles with band cells
     int n_band_tiles;
-    const int *work_tiles;        // tiles with active or ghost fluid cells (the level kernel's grid)
+    const int *work_tiles;        // tiles with active or ghost fluid cells (the level kernel's grid),
+                                  // those with boundary nodes first, then with band or coalescing
+                                  // cells, then other active cells, then ghosts only
     int n_work_tiles;
     const int *work_warps;        // tile * 8 + w for each warp w (work shape 0) of a work tile that
     int n_work_warps;             // holds an active or ghost fluid cell (the warp-list schedule)

@@ -596,23 +596,53 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         v.parent = upload(s, G.parent, ok);
         v.band_tiles = upload(s, G.band_tiles, ok);
         v.n_band_tiles = (int)G.band_tiles.size();
-        v.work_tiles = upload(s, G.work_tiles, ok);
-        v.n_work_tiles = (int)G.work_tiles.size();
         {
-            // warps (work shape 0: 16 x 2 cells) of the work tiles that hold an active or ghost fluid cell
-            std::vector<int> ww;
-            ww.reserve(G.work_tiles.size() * 8);
+            // work tiles in the same cost order as the warps below (a block's warps start
+            // together, so the expensive tiles go first and the last blocks are cheap)
+            std::vector<int> cls_t[4];
+            for (const int t : G.work_tiles) {
+                int cls = 0;
+                for (int c = 0; c < LBM_TILE; c++) {
+                    const uint32_t f = H.flags[(size_t)t * LBM_TILE + c];
+                    if ((f & FL_SOLID) || (f & FL_KIND_MASK) != KIND_ACTIVE) continue;
+                    int k = 1;
+                    if (f & (FL_BAND | (0xFFu << FL_COAL_SHIFT))) k = 2;
+                    if ((f & FL_BNODE) && l == L - 1) k = 3;
+                    cls = std::max(cls, k);
+                }
+                cls_t[cls].push_back(t);
+            }
+            std::vector<int> wt;
+            for (int k = 3; k >= 0; k--) wt.insert(wt.end(), cls_t[k].begin(), cls_t[k].end());
+            v.work_tiles = upload(s, wt, ok);
+            v.n_work_tiles = (int)wt.size();
+        }
+        {
+            // warps (work shape 0: 16 x 2 cells) of the work tiles that hold an active or ghost
+            // fluid cell, the expensive ones first so that the last blocks to start are cheap:
+            // warps with a boundary node (wall function), then with a band or coalescing cell
+            // (explosion, coalescence), then with another active cell, then ghosts only (a
+            // relay); tile order within each class
+            std::vector<int> cls_w[4];
             for (const int t : G.work_tiles)
                 for (int w = 0; w < 8; w++) {
-                    bool any = false;
-                    for (int c = 0; c < 32 && !any; c++) {
+                    int cls = -1;
+                    for (int c = 0; c < 32; c++) {
                         const int lx = (w & 1) * 16 + (c & 15), ly = (w >> 1) * 2 + (c >> 4);
                         const uint32_t f = H.flags[(size_t)t * LBM_TILE + ly * LBM_TX + lx];
                         const uint32_t kd = f & FL_KIND_MASK;
-                        any = (kd == KIND_ACTIVE || kd == KIND_GHOST) && !(f & FL_SOLID);
+                        if (f & FL_SOLID) continue;
+                        if (kd == KIND_GHOST) cls = std::max(cls, 0);
+                        if (kd != KIND_ACTIVE) continue;
+                        int k = 1;
+                        if (f & (FL_BAND | (0xFFu << FL_COAL_SHIFT))) k = 2;
+                        if ((f & FL_BNODE) && l == L - 1) k = 3;
+                        cls = std::max(cls, k);
                     }
-                    if (any) ww.push_back(t * 8 + w);
+                    if (cls >= 0) cls_w[cls].push_back(t * 8 + w);
                 }
+            std::vector<int> ww;
+            for (int k = 3; k >= 0; k--) ww.insert(ww.end(), cls_w[k].begin(), cls_w[k].end());
             v.work_warps = upload(s, ww, ok);
             v.n_work_warps = (int)ww.size();
         }
