@@ -299,7 +299,8 @@ lbm_status lbm_time_kernels(lbm_solver *s, int n_coarse_steps, lbm_kernel_times 
  * shared memory).  The choice comes from per-launch CUDA-event timings of `steps` eager
  * coarse steps per candidate, and is kept only if `steps` coarse steps through the step
  * graphs confirm it (against the same choice with one block per tile where it picked a
- * persistent grid, and against the form before tuning), since launches overlap inside the
+ * persistent grid, against the form before tuning, and against each candidate on every
+ * level; the fastest of these is kept), since launches overlap inside the
  * graphs.  Then it picks whether launches use programmatic dependent launch, from the time
  * of `steps` coarse steps through the step graphs each way, and recaptures the graphs with
  * the choice.  The variants compute the same numbers up to FP32 rounding (the compiler
@@ -316,8 +317,10 @@ typedef struct {
     int min_blocks[16];                       /* chosen register budget per level                  */
     int sched[16];                            /* chosen grid schedule per level (LBM_SCHED_*)      */
     int shape[16];                            /* chosen work shape per level                       */
-    double step_us_confirm[3];                /* coarse step: per-level pick, pick with tile
-                                                 blocks for persistent grids, form before tuning */
+    double step_us_confirm[3 + LBM_TUNE_CANDIDATES]; /* coarse step: per-level pick, pick with
+                                                 tile blocks for persistent grids, form before
+                                                 tuning, then each candidate on every level    */
+    int confirm_choice;                       /* index into step_us_confirm of the form kept    */
     double default_step_us;                   /* coarse step through the graphs before tuning      */
     double step_us[2];                        /* coarse step, chosen kernels, PDL off / on         */
     int pdl;                                  /* chosen: 1 programmatic dependent launch on        */

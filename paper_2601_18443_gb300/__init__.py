@@ -74,7 +74,8 @@ class lbm_tune_report(C.Structure):
     _fields_ = [("levels", C.c_int), ("candidate_min_blocks", C.c_int * TUNE_CANDIDATES),
                 ("candidate_sched", C.c_int * TUNE_CANDIDATES), ("candidate_shape", C.c_int * TUNE_CANDIDATES),
                 ("level_us", (C.c_double * 16) * TUNE_CANDIDATES), ("min_blocks", C.c_int * 16),
-                ("sched", C.c_int * 16), ("shape", C.c_int * 16), ("step_us_confirm", C.c_double * 3),
+                ("sched", C.c_int * 16), ("shape", C.c_int * 16),
+                ("step_us_confirm", C.c_double * (3 + TUNE_CANDIDATES)), ("confirm_choice", C.c_int),
                 ("default_step_us", C.c_double), ("step_us", C.c_double * 2),
                 ("pdl", C.c_int), ("steps_taken", C.c_longlong)]
 
@@ -457,7 +458,9 @@ def _tune_dict(out):
                 min_blocks=list(out.min_blocks[:L]), sched=list(out.sched[:L]),
                 shape=list(out.shape[:L]),
                 step_us_confirm={"pick": out.step_us_confirm[0], "pick_tile_for_persistent": out.step_us_confirm[1],
-                                 "before": out.step_us_confirm[2]},
+                                 "before": out.step_us_confirm[2],
+                                 **{("uniform",) + c: out.step_us_confirm[3 + i] for i, c in enumerate(cand)}},
+                confirm_choice=out.confirm_choice,
                 default_step_us=out.default_step_us,
                 step_us={"pdl_off": out.step_us[0], "pdl_on": out.step_us[1]}, pdl=out.pdl,
                 steps_taken=out.steps_taken)

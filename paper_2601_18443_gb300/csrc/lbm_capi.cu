@@ -1499,18 +1499,21 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     // 1b: per-launch timings miss how launches overlap inside the graph (a persistent grid
     //     occupies every SM while the next launch would start): keep the per-level choice
     //     only if whole graph steps confirm it, against the same choice with one block per
-    //     tile where it took a persistent grid, and against the default form
+    //     tile where it took a persistent grid, against the default form, and against each
+    //     candidate on every level
     {
         int pick_mb[LBM_MAXL], pick_pe[LBM_MAXL], pick_sh[LBM_MAXL];
         for (int l = 0; l < L; l++) { pick_mb[l] = s->min_blocks[l]; pick_pe[l] = s->sched[l]; pick_sh[l] = s->shape[l]; }
+        auto form = [&](int v, int l, int &mb, int &pe, int &sh) {
+            if (v >= 3) { mb = CAND_MB[v - 3]; pe = CAND_PE[v - 3]; sh = CAND_SH[v - 3]; return; }
+            mb = v == 2 ? keep_mb[l] : pick_mb[l];
+            pe = v == 0 ? pick_pe[l] : (v == 1 ? no_persist(pick_pe[l]) : keep_pe[l]);
+            sh = v == 2 ? keep_sh[l] : pick_sh[l];
+        };
         double best_us = 0.0;
         int best = 0;
-        for (int v = 0; v < 3; v++) {
-            for (int l = 0; l < L; l++) {
-                s->min_blocks[l] = v == 2 ? keep_mb[l] : pick_mb[l];
-                s->sched[l] = v == 0 ? pick_pe[l] : (v == 1 ? no_persist(pick_pe[l]) : keep_pe[l]);
-                s->shape[l] = v == 2 ? keep_sh[l] : pick_sh[l];
-            }
+        for (int v = 0; v < 3 + LBM_TUNE_CANDIDATES; v++) {
+            for (int l = 0; l < L; l++) form(v, l, s->min_blocks[l], s->sched[l], s->shape[l]);
             double us = 0.0;
             if ((st = capture_graphs(s)) != LBM_OK) return st;
             if ((st = graph_step_time(s, steps, &us)) != LBM_OK) return st;
@@ -1518,13 +1521,12 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
             if (v == 0 || us < best_us) { best_us = us; best = v; }
         }
         for (int l = 0; l < L; l++) {
-            s->min_blocks[l] = best == 2 ? keep_mb[l] : pick_mb[l];
-            s->sched[l] = best == 0 ? pick_pe[l] : (best == 1 ? no_persist(pick_pe[l]) : keep_pe[l]);
-            s->shape[l] = best == 2 ? keep_sh[l] : pick_sh[l];
+            form(best, l, s->min_blocks[l], s->sched[l], s->shape[l]);
             out->min_blocks[l] = s->min_blocks[l];
             out->sched[l] = s->sched[l];
             out->shape[l] = s->shape[l];
         }
+        out->confirm_choice = best;
     }
     // 2: programmatic dependent launch on or off, from whole graph steps
     for (int pdl = 0; pdl < 2; pdl++) {
@@ -1535,7 +1537,7 @@ lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
     s->pdl = out->step_us[1] <= out->step_us[0] ? 1 : 0;
     out->pdl = s->pdl;
     if ((st = capture_graphs(s)) != LBM_OK) return st;
-    out->steps_taken = (long long)steps * (6 + LBM_TUNE_CANDIDATES);
+    out->steps_taken = (long long)steps * (6 + 2 * LBM_TUNE_CANDIDATES);
     return check_status(s);
 }
 

@@ -42,8 +42,9 @@ def test_autotuned_solve_equals_the_default_one(store):
     b.step(3)                      # odd level-0 parity: the recapture starts from graph 1
     rep = b.autotune(steps=2)
     L = cfg["levels"]
-    assert rep["steps_taken"] == 2 * 18 and rep["levels"] == L
-    assert min(rep["step_us_confirm"].values()) > 0
+    assert rep["steps_taken"] == 2 * (6 + 2 * pkg.TUNE_CANDIDATES) and rep["levels"] == L
+    assert min(rep["step_us_confirm"].values()) > 0 and len(rep["step_us_confirm"]) == 3 + pkg.TUNE_CANDIDATES
+    assert 0 <= rep["confirm_choice"] < 3 + pkg.TUNE_CANDIDATES
     assert rep["candidates"] == [(5, 0, 0), (6, 0, 0), (5, 1, 0), (6, 1, 0), (5, 0, 1), (6, 0, 1), (5, 1, 1), (6, 1, 1),
                                  (5, 2, 0), (6, 2, 0), (5, 3, 0), (6, 3, 0)]
     assert all(sc in (0, 1, 2, 3) for sc in rep["sched"]) and all(sh in (0, 1) for sh in rep["shape"])
