@@ -310,6 +310,29 @@ def gpu_arm(args, rank, world, dist):
     peak, peak_kind = peaks()
     l2_peak = l2_copy_gbs(dev) if rank == 0 else None
     total_kt = sum(v["ms"] for v in kt.values())
+    # the same launches inside the step graphs (per-block global-timer records, after the
+    # timed region): first block past its wait to last block done, per launch
+    s.set_timeline(True)
+    s.step(4)
+    tl = s.timeline()
+    s.set_timeline(False)
+    L_ = info["levels"]
+    fin_tl = [e["t_end_us"] - e["t_wait_us"] for e in tl if e["level"] == L_ - 1 and e["kind"] in (0, 1)]
+    in_graph_us = float(np.mean(fin_tl)) if fin_tl else None
+    breakdown = {}
+    for g in (0, 1):
+        evg = [e for e in tl if e["graph"] == g]
+        if not evg:
+            continue
+        span = max(e["t_end_us"] for e in evg)
+        cls = {"finest": 0.0, "coarser": 0.0, "prolong": 0.0}
+        for e in evg:
+            key = "prolong" if e["kind"] == 2 else ("finest" if e["level"] == L_ - 1 else "coarser")
+            cls[key] += e["t_end_us"] - e["t_wait_us"]
+        cls["between_launches"] = span - sum(cls.values())
+        cls["graph_span"] = span
+        for key, v in cls.items():
+            breakdown[key] = breakdown.get(key, 0.0) + v / 2
     loads = s.get_loads()
 
     # end to end through the public API: host polyline -> grid build + upload -> K steps -> loads to host
@@ -409,7 +432,15 @@ def gpu_arm(args, rank, world, dist):
                          "avg_launch_ms": round(avg_ms, 5),
                          "share_of_step": round(fin["ms"] / total_kt, 3) if total_kt > 0 else None,
                          "kernel_bytes_per_node_update": bpn_kernel,
-                         "frac_kernel_bytes": round(act_fin * bpn_kernel / (avg_ms * 1e-3) / 1e9 / peak, 4)},
+                         "frac_kernel_bytes": round(act_fin * bpn_kernel / (avg_ms * 1e-3) / 1e9 / peak, 4),
+                         "in_graph": None if in_graph_us is None else {
+                             "avg_launch_us": round(in_graph_us, 2),
+                             "achieved": round(act_fin * bpn / (in_graph_us * 1e-6) / 1e9, 1),
+                             "frac": round(act_fin * bpn / (in_graph_us * 1e-6) / 1e9 / peak, 4),
+                             "how": "the same launches inside the step graphs: first block past its wait for the "
+                                    "preceding kernel to last block done (lbm_get_timeline, global timer); "
+                                    "avg_launch_ms above brackets each launch with CUDA events outside the graphs"}},
+            "step_breakdown_us": {k: round(v, 1) for k, v in breakdown.items()} or None,
             "roofline_l2": None if l2_peak is None else {
                 "bound": "l2", "achieved": round(achieved, 1), "peak": round(l2_peak, 1), "unit": "GB/s",
                 "frac": round(achieved / l2_peak, 4),

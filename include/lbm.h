@@ -351,6 +351,26 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size);
 lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *sched, const int *shape,
                                   int pdl);
 
+/* Launch timeline.  Not in the paper.  With the timeline on, every block of every launch of
+ * the step graphs records the GPU's global timer when it has passed its wait for the
+ * preceding kernel and when all its threads are done (one thread's clock reads and stores
+ * per block, a block barrier at its end); lbm_get_timeline reduces them per launch for the
+ * most recent run of each of the two step graphs (level-0 parities), in launch order, times
+ * from the first launch of that graph.  lbm_set_timeline recaptures the step graphs (on 1
+ * allocates the records, 24 bytes a block of each launch; off 0 keeps them).  Results are
+ * those of the steps without it.  Errors: LBM_ERR_INVALID_ARG (cap below the launch count:
+ * call with cap 0 for the count), LBM_ERR_NO_GEOMETRY, LBM_ERR_OOM, LBM_ERR_CUDA. */
+typedef struct {
+    int graph;          /* step graph: the level-0 parity it starts from                         */
+    int level;          /* level of the step, or the first level of a prolongation launch        */
+    int kind;           /* 0 even sub-step, 1 odd sub-step, 2 prolongation                        */
+    int blocks;         /* blocks that recorded                                                   */
+    double t_wait_us;   /* first block past its wait for the preceding kernel                    */
+    double t_end_us;    /* last block done                                                        */
+} lbm_launch_time;
+lbm_status lbm_set_timeline(lbm_solver *s, int on);
+lbm_status lbm_get_timeline(lbm_solver *s, lbm_launch_time *out, int cap, int *n);
+
 /* Launch grouping of the prolongations (Sec 2.1): in each descent of the recursive schedule
  * the prolongations of consecutive levels l - 1, l go out as one launch (on by default)
  * where level l's band cells have no ghost cell of level l in their 3 x 3 neighbourhood, so

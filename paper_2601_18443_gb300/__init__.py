@@ -66,6 +66,11 @@ class lbm_kernel_times(C.Structure):
                 ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
 
 
+class lbm_launch_time(C.Structure):
+    _fields_ = [("graph", C.c_int), ("level", C.c_int), ("kind", C.c_int), ("blocks", C.c_int),
+                ("t_wait_us", C.c_double), ("t_end_us", C.c_double)]
+
+
 TUNE_CANDIDATES = 12
 SCHED_TILE, SCHED_PERSIST, SCHED_WARPS, SCHED_WARPS4 = 0, 1, 2, 3   # LBM_SCHED_* of include/lbm.h
 
@@ -128,6 +133,8 @@ def library():
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
         "lbm_set_launch_variant": ([vp, ip, ip, ip, C.c_int], C.c_int),
         "lbm_set_prolong_merge": ([vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
+        "lbm_set_timeline": ([vp, C.c_int], C.c_int),
+        "lbm_get_timeline": ([vp, C.c_void_p, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "lbm_get_state": ([vp, vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
         "lbm_set_state": ([vp, vp, C.c_size_t], C.c_int),
         "lbm_level_mass_noalloc": ([vp, vp, vp, vp, vp, C.c_longlong, C.c_double, vp, vp, vp], C.c_int),
@@ -435,6 +442,19 @@ class Solver:
         pe = np.ascontiguousarray(sched if sched is not None else [SCHED_TILE] * len(mb), dtype=np.int32)
         sh = np.ascontiguousarray(shape if shape is not None else [0] * len(mb), dtype=np.int32)
         self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), _ip(pe), _ip(sh), int(pdl)))
+
+    def set_timeline(self, on=True):
+        """lbm_set_timeline: per-block clock records in every launch of the step graphs."""
+        self._check(self._lib.lbm_set_timeline(self._h, int(bool(on))))
+
+    def timeline(self):
+        """lbm_get_timeline: per launch of the last run of each step graph: graph, level, kind
+        (0 even, 1 odd, 2 prolongation), blocks, t_wait_us, t_end_us."""
+        n = C.c_int()
+        self._check(self._lib.lbm_get_timeline(self._h, None, 0, C.byref(n)))
+        arr = (lbm_launch_time * max(n.value, 1))()
+        self._check(self._lib.lbm_get_timeline(self._h, C.cast(arr, C.c_void_p), n.value, C.byref(n)))
+        return [{k: getattr(arr[i], k) for k, _ in lbm_launch_time._fields_} for i in range(n.value)]
 
     def set_prolong_merge(self, on=True):
         """lbm_set_prolong_merge: one launch for the prolongations of consecutive levels where

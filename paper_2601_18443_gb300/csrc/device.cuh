@@ -96,6 +96,8 @@ struct LevelStep {
     int pp;             // time level of level l-1 (restriction writes [pp ^ 1])
     int shape;          // cells of a warp: 0 a 16 x 2 block, 1 a 32 x 1 row of the tile
     int *status;        // device status word (LBM_STATUS_* bits)
+    unsigned long long *tl;  // launch timeline (lbm_set_timeline): 3 clock readings a block from
+    int tl_base;             // record tl_base + blockIdx.x, or null
 };
 
 // Launch variant of a level's kernels (chosen by lbm_autotune): the register budget of the
@@ -116,7 +118,8 @@ struct LevelTune {
 // launchers (kernels.cu); all enqueue on the given stream
 void launch_level(cudaStream_t st, const LevelView &P, const LevelView *F, const LevelView *C, const RecView &R,
                   const StepConsts &k, const LevelStep &ls, const LevelTune &tu);
-void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pdl);
+void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pdl,
+                    unsigned long long *tl = nullptr, int tl_base = 0);
 void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k);
 void launch_restrict(cudaStream_t st, const LevelView &P, const LevelView &F, int pp, int pf);
 void launch_init_feq(cudaStream_t st, const LevelView &P, const float *feq9, float U, float chi_inf);
@@ -153,6 +156,8 @@ struct ProlongDesc {
 };
 struct ProlongBatchArgs {
     int n;
+    unsigned long long *tl;   // launch timeline (as LevelStep::tl), or null
+    int tl_base;
     ProlongDesc d[LBM_BATCH_MAX];
 };
 void launch_level_batch(cudaStream_t st, const BatchArgs &a, int store, unsigned grid, int pdl);

@@ -152,6 +152,27 @@ __device__ __forceinline__ void griddep_launch()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// ------------------------------------------------------------------ launch timeline
+// With a timeline buffer (lbm_set_timeline), thread 0 of each block records the global
+// timer (ns) at the block's entry, once its wait for the preceding kernel has returned, and
+// once all its threads are done, at tl[3 (base + block) + 0, 1, 2].  Without one (tl null,
+// a kernel parameter, so every branch here is uniform) nothing is read or written.
+__device__ __forceinline__ void tl_mark(unsigned long long *tl, int base, int m)
+{
+    if (tl != nullptr && threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        tl[3ull * (unsigned)(base + (int)blockIdx.x) + (unsigned)m] = t;
+    }
+}
+
+__device__ __forceinline__ void tl_end(unsigned long long *tl, int base)
+{
+    if (tl == nullptr) return;
+    __syncthreads();
+    tl_mark(tl, base, 2);
+}
+
 // ------------------------------------------------------------------ SA-neg constants (Sec 2.2)
 #define SA_CB1 0.1355f
 #define SA_CB2 0.622f
@@ -835,12 +856,14 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
     int lx, ly;
     cell_of_thread(c, lx, ly, ls.shape);
     int *nb3 = nb3w[c >> 5];
+    tl_mark(ls.tl, ls.tl_base, 0);
     if constexpr (!PERSIST) {
         const int t = P.work_tiles[blockIdx.x];
         if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
         __syncwarp();
         griddep_launch();
         griddep_wait();
+        tl_mark(ls.tl, ls.tl_base, 1);
         level_tile<WALL, CHILD, T, ODD, false>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, 0u, 0, red);
     } else {
         // the grid tables are static: the first tile's neighbour table and flag word are
@@ -856,6 +879,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
         __syncwarp();
         griddep_launch();
         griddep_wait();
+        tl_mark(ls.tl, ls.tl_base, 1);
         for (; wt < P.n_work_tiles; wt += gridDim.x) {
             const int t = P.work_tiles[wt];
             const uint32_t fl = fl_next;
@@ -870,6 +894,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
             level_tile<WALL, CHILD, T, ODD, true>(P, F, C, R, k, ls, L, t, lane, lx, ly, nb3, fl, ax, red);
         }
     }
+    tl_end(ls.tl, ls.tl_base);
 
 }
 
@@ -895,6 +920,7 @@ __global__ void __launch_bounds__(WPB * 32, (MINB == 6 ? 48 : 40) / WPB)
     const bool have = w < P.n_work_warps;
     int *nb3 = nb3w[wb];
     int t = 0, lx = 0, ly = 0;
+    tl_mark(ls.tl, ls.tl_base, 0);
     if (have) {
         const int e = __ldg(P.work_warps + w);
         t = e >> 3;
@@ -904,9 +930,11 @@ __global__ void __launch_bounds__(WPB * 32, (MINB == 6 ? 48 : 40) / WPB)
     __syncwarp();
     griddep_launch();
     griddep_wait();
+    tl_mark(ls.tl, ls.tl_base, 1);
     LevelStep l0 = ls;
     l0.shape = 0;
     if (have) level_tile<WALL, CHILD, T, ODD, false>(P, F, C, R, k, l0, L, t, lane, lx, ly, nb3, 0u, 0, nullptr);
+    tl_end(ls.tl, ls.tl_base);
 }
 
 // The batched form of k_level (one block per work tile, register budget of 5 blocks per SM):
@@ -977,15 +1005,18 @@ __device__ __forceinline__ void prolong_tile(const LevelView &P, const LevelView
     }
 }
 
-__global__ void __launch_bounds__(256) k_prolong(LevelView P, LevelView F, int p)
+__global__ void __launch_bounds__(256) k_prolong(LevelView P, LevelView F, int p, unsigned long long *tl, int tl_base)
 {
+    tl_mark(tl, tl_base, 0);
     __shared__ int nb3[9];
     const int t = P.band_tiles[blockIdx.x];
     load_nb3(P, t, nb3);
     __syncthreads();
     griddep_launch();
     griddep_wait();
+    tl_mark(tl, tl_base, 1);
     prolong_tile(P, F, p, t, nb3);
+    tl_end(tl, tl_base);
 }
 
 // batched form of k_prolong (same solve lookup as k_level_batch, over band tiles)
@@ -995,13 +1026,16 @@ __global__ void __launch_bounds__(256) k_prolong_batch(const __grid_constant__ P
     for (int m = 1; m < a.n; m++)
         if (a.d[m].first_block <= (int)blockIdx.x) i = m;
     const ProlongDesc &d = a.d[i];
+    tl_mark(a.tl, a.tl_base, 0);
     __shared__ int nb3[9];
     const int t = d.P.band_tiles[blockIdx.x - d.first_block];
     load_nb3(d.P, t, nb3);
     __syncthreads();
     griddep_launch();
     griddep_wait();
+    tl_mark(a.tl, a.tl_base, 1);
     prolong_tile(d.P, d.F, d.p, t, nb3);
+    tl_end(a.tl, a.tl_base);
 }
 
 // ------------------------------------------------------------------ wall-state query
@@ -1338,9 +1372,10 @@ void launch_prolong_batch(cudaStream_t st, const ProlongBatchArgs &a, unsigned g
     if (grid > 0) launch_pdl(k_prolong_batch, grid, st, pdl, a);
 }
 
-void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pdl)
+void launch_prolong(cudaStream_t st, const LevelView &P, const LevelView &F, int p, int pdl, unsigned long long *tl,
+                    int tl_base)
 {
-    if (P.n_band_tiles > 0) launch_pdl(k_prolong, (unsigned)P.n_band_tiles, st, pdl, P, F, p);
+    if (P.n_band_tiles > 0) launch_pdl(k_prolong, (unsigned)P.n_band_tiles, st, pdl, P, F, p, tl, tl_base);
 }
 
 void launch_wallfn(cudaStream_t st, const LevelView &P, int p, const RecView &R, const StepConsts &k)

@@ -103,6 +103,12 @@ struct lbm_solver {
     bool prolong_indep[LBM_MAXL];
     int prolong_merge = 1;          // lbm_set_prolong_merge
     lbmdev::ProlongBatchArgs pend;  // prolongations waiting for the next level-step launch
+    // launch timeline (lbm_set_timeline): 3 clock readings per block of every launch of the
+    // step graphs, records [tl_meta base, base + blocks) of a launch; meta 5 ints per launch
+    unsigned long long *d_tl = nullptr;
+    long long tl_cap = 0, tl_next = 0;
+    int tl_on = 0, tl_graph = -1;
+    std::vector<int> tl_meta;         // graph, level, kind (0 even, 1 odd, 2 prolongation), base, blocks
     unsigned pend_grid = 0;
     int pend_level = 0;
     int sched[LBM_MAXL];          // grid schedule (LBM_SCHED_*) of each level's kernel (lbm_autotune)
@@ -212,6 +218,10 @@ static void free_all(lbm_solver *s)
     s->allocs.clear();
     s->device_bytes = 0;
     s->geometry = false;
+    s->d_tl = nullptr;
+    s->tl_cap = s->tl_next = 0;
+    s->tl_on = 0;
+    s->tl_meta.clear();
     for (auto &e : s->ev_pool) cudaEventDestroy(e);
     s->ev_pool.clear();
 }
@@ -254,13 +264,31 @@ static void mark_end(lbm_solver *s, int cls, long long cells, int level)
     s->ev_used += 2;
 }
 
+// Records for one launch of the graph being captured, when the timeline is on: the first
+// record, or -1 (no timeline, or no room; the launch then records nothing).
+static int tl_reserve(lbm_solver *s, int level, int kind, int blocks)
+{
+    if (!s->tl_on || s->tl_graph < 0 || !s->d_tl || s->tl_next + blocks > s->tl_cap) return -1;
+    const int base = (int)s->tl_next;
+    s->tl_meta.insert(s->tl_meta.end(), {s->tl_graph, level, kind, base, blocks});
+    s->tl_next += blocks;
+    return base;
+}
+
 // Launch the pending prolongations (one kernel for all of them).
 static void flush_prolong(lbm_solver *s, cudaStream_t st, long long &nk)
 {
     if (s->pend.n == 0) return;
     mark_begin(s);
-    if (s->pend.n == 1) lbmdev::launch_prolong(st, s->pend.d[0].P, s->pend.d[0].F, s->pend.d[0].p, s->pdl);
-    else lbmdev::launch_prolong_batch(st, s->pend, s->pend_grid, s->pdl);
+    const int base = tl_reserve(s, s->pend_level, 2, (int)s->pend_grid);
+    unsigned long long *tl = base >= 0 ? s->d_tl : nullptr;
+    if (s->pend.n == 1) {
+        lbmdev::launch_prolong(st, s->pend.d[0].P, s->pend.d[0].F, s->pend.d[0].p, s->pdl, tl, base);
+    } else {
+        s->pend.tl = tl;
+        s->pend.tl_base = base;
+        lbmdev::launch_prolong_batch(st, s->pend, s->pend_grid, s->pdl);
+    }
     mark_end(s, KC_PROLONG, (long long)s->pend_grid * LBM_TILE, s->pend_level);
     nk++;
     s->pend.n = 0;
@@ -294,7 +322,7 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
         advance(s, st, l + 1, 1, nk);
     }
     flush_prolong(s, st, nk);
-    lbmdev::LevelStep ls;
+    lbmdev::LevelStep ls{};
     ls.p = s->parity[l];
     ls.has_child = F != nullptr;
     ls.is_level0 = l == 0;
@@ -303,6 +331,11 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     ls.pp = C ? s->parity[l - 1] : 0;
     ls.shape = s->shape[l];
     ls.status = s->d_status;
+    {
+        const int base = tl_reserve(s, l, ls.p, std::max(P.n_work_tiles, (P.n_work_warps + 1) / 2));
+        ls.tl = base >= 0 ? s->d_tl : nullptr;
+        ls.tl_base = base;
+    }
     mark_begin(s);
     const lbmdev::LevelTune tu{s->min_blocks[l], s->pdl, s->sched[l], s->shape[l]};
     lbmdev::launch_level(st, P, F, C, s->rec, s->k, ls, tu);
@@ -315,6 +348,8 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
 // the two captures leave every level's parity as it was
 static lbm_status capture_graphs(lbm_solver *s)
 {
+    s->tl_next = 0;
+    s->tl_meta.clear();
     for (int b = 0; b < 2; b++)
         if (s->graph[b]) { cudaGraphExecDestroy(s->graph[b]); s->graph[b] = nullptr; }
     const int b0 = s->parity[0];
@@ -324,7 +359,9 @@ static lbm_status capture_graphs(lbm_solver *s)
         cudaGraph_t gr;
         long long nk = 0;
         CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+        s->tl_graph = b;
         advance(s, s->cap_stream, 0, 0, nk);
+        s->tl_graph = -1;
         CK(cudaStreamEndCapture(s->cap_stream, &gr));
         CK(cudaGraphInstantiate(&s->graph[b], gr, 0));
         cudaGraphDestroy(gr);
@@ -962,7 +999,7 @@ lbm_status lbm_step_launch(lbm_solver *s, int level, int kind)
     } else {
         const LevelView *F = (l < L - 1) ? &s->lv[l + 1].v : nullptr;
         const LevelView *C = (l > 0) ? &s->lv[l - 1].v : nullptr;
-        lbmdev::LevelStep ls;
+        lbmdev::LevelStep ls{};
         ls.p = s->parity[l];
         ls.has_child = F != nullptr;
         ls.is_level0 = l == 0;
@@ -1571,6 +1608,8 @@ static void batch_advance(lbm_batch *b, cudaStream_t st, int l, int restrict_up,
     {
         lbmdev::ProlongBatchArgs a;
         a.n = 0;
+        a.tl = nullptr;
+        a.tl_base = 0;
         unsigned grid = 0;
         for (lbm_solver *s : b->m) {
             if (l + 1 >= s->L || s->lv[l].v.n_band_tiles <= 0) continue;
@@ -1604,6 +1643,8 @@ static void batch_advance(lbm_batch *b, cudaStream_t st, int l, int restrict_up,
         d.ls.pp = l > 0 ? s->parity[l - 1] : 0;
         d.ls.shape = 0;
         d.ls.status = s->d_status;
+        d.ls.tl = nullptr;
+        d.ls.tl_base = 0;
         d.kind = d.ls.wall ? 2 : (d.ls.has_child ? 1 : 0);
         d.first_block = (int)grid;
         grid += (unsigned)std::max(d.P.n_work_tiles, 0);
@@ -1850,6 +1891,68 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     s->step = h.step;
     s->have_cl = h.have_cl != 0;
     s->last_cl = h.last_cl;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_timeline(lbm_solver *s, int on)
+{
+    if (!s || (on != 0 && on != 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (s->planning) return fail(s, LBM_ERR_NO_GEOMETRY, "host-only handle");
+    if (on && !s->d_tl) {
+        // every launch of both step graphs: level l takes 2^l steps, each at most its tile
+        // count or half its work warps in blocks, and a prolongation launch its band tiles
+        long long need = 0;
+        for (int l = 0; l < s->L; l++) {
+            const lbmdev::LevelView &v = s->lv[l].v;
+            need += (1LL << l) * (std::max(v.n_work_tiles, (v.n_work_warps + 1) / 2) + v.n_band_tiles);
+        }
+        need *= 2;
+        s->d_tl = (unsigned long long *)dalloc(s, (size_t)need * 3 * sizeof(unsigned long long));
+        if (!s->d_tl) return fail(s, LBM_ERR_OOM, "timeline buffer");
+        s->tl_cap = need;
+        CK(cudaMemsetAsync(s->d_tl, 0, (size_t)need * 3 * sizeof(unsigned long long), s->stream));
+    }
+    s->tl_on = on;
+    return capture_graphs(s);
+}
+
+lbm_status lbm_get_timeline(lbm_solver *s, lbm_launch_time *out, int cap, int *n)
+{
+    if (!s || !n || (cap > 0 && !out)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    const int nl = (int)s->tl_meta.size() / 5;
+    *n = s->tl_on ? nl : 0;
+    if (!s->tl_on || nl == 0 || cap <= 0) return LBM_OK;
+    if (nl > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    std::vector<unsigned long long> h((size_t)s->tl_next * 3);
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(h.data(), s->d_tl, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    unsigned long long t0[2] = {~0ull, ~0ull};
+    std::vector<unsigned long long> wmin(nl, ~0ull), emax(nl, 0ull);
+    std::vector<int> ran(nl, 0);
+    for (int i = 0; i < nl; i++) {
+        const int *m = &s->tl_meta[(size_t)i * 5];
+        for (int b = 0; b < m[4]; b++) {
+            const unsigned long long *r = &h[3 * ((size_t)m[3] + b)];
+            if (r[2] == 0) continue;                      // block not run since the capture
+            ran[i]++;
+            wmin[i] = std::min(wmin[i], r[1]);
+            emax[i] = std::max(emax[i], r[2]);
+        }
+        if (ran[i]) t0[m[0] & 1] = std::min(t0[m[0] & 1], wmin[i]);
+    }
+    for (int i = 0; i < nl; i++) {
+        const int *m = &s->tl_meta[(size_t)i * 5];
+        lbm_launch_time &o = out[i];
+        o.graph = m[0];
+        o.level = m[1];
+        o.kind = m[2];
+        o.blocks = ran[i];
+        const unsigned long long g0 = t0[m[0] & 1];
+        o.t_wait_us = ran[i] ? 1e-3 * (double)(wmin[i] - g0) : 0.0;
+        o.t_end_us = ran[i] ? 1e-3 * (double)(emax[i] - g0) : 0.0;
+    }
     return LBM_OK;
 }
 
