@@ -351,6 +351,24 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size);
 lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *sched, const int *shape,
                                   int pdl);
 
+/* Load history.  With every > 0, lbm_step and lbm_step_async enqueue, after each coarse step
+ * whose count is a multiple of every, what lbm_get_loads computes (the wall state query,
+ * eq 29-30 with their FP64 sums, the FP64 mass) into the next slot of a device ring of
+ * capacity records, without a host synchronisation; the trajectory is unchanged (the query
+ * leaves the next step's Newton start alone).  lbm_get_load_history returns the kept records
+ * (the last capacity ones) oldest first, after synchronising the stream; the coefficients
+ * equal what lbm_get_loads gives at the same step up to the order of the FP64 sums.  every
+ * 0 stops recording; a new call clears the ring.  lbm_batch_step records nothing.  Errors:
+ * LBM_ERR_INVALID_ARG (capacity < 1 with every > 0; cap below the record count: call with
+ * cap 0 for it), LBM_ERR_NO_GEOMETRY, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_CUDA. */
+typedef struct {
+    long long step;          /* coarse steps taken since lbm_set_geometry                      */
+    double CL, CD, CDp, CDf; /* eq 30                                                           */
+    double mass;             /* as lbm_loads.mass                                              */
+} lbm_load_record;
+lbm_status lbm_set_load_history(lbm_solver *s, int every, int capacity);
+lbm_status lbm_get_load_history(lbm_solver *s, lbm_load_record *out, int cap, int *n);
+
 /* Launch timeline.  Not in the paper.  With the timeline on, every block of every launch of
  * the step graphs records the GPU's global timer when it has passed its wait for the
  * preceding kernel and when all its threads are done (one thread's clock reads and stores

@@ -66,6 +66,11 @@ class lbm_kernel_times(C.Structure):
                 ("launches", C.c_longlong * 8), ("cells", C.c_longlong * 8)]
 
 
+class lbm_load_record(C.Structure):
+    _fields_ = [("step", C.c_longlong), ("CL", C.c_double), ("CD", C.c_double), ("CDp", C.c_double),
+                ("CDf", C.c_double), ("mass", C.c_double)]
+
+
 class lbm_launch_time(C.Structure):
     _fields_ = [("graph", C.c_int), ("level", C.c_int), ("kind", C.c_int), ("blocks", C.c_int),
                 ("t_wait_us", C.c_double), ("t_end_us", C.c_double)]
@@ -134,6 +139,8 @@ def library():
         "lbm_set_launch_variant": ([vp, ip, ip, ip, C.c_int], C.c_int),
         "lbm_set_prolong_merge": ([vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "lbm_set_timeline": ([vp, C.c_int], C.c_int),
+        "lbm_set_load_history": ([vp, C.c_int, C.c_int], C.c_int),
+        "lbm_get_load_history": ([vp, C.c_void_p, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "lbm_get_timeline": ([vp, C.c_void_p, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "lbm_get_state": ([vp, vp, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
         "lbm_set_state": ([vp, vp, C.c_size_t], C.c_int),
@@ -442,6 +449,19 @@ class Solver:
         pe = np.ascontiguousarray(sched if sched is not None else [SCHED_TILE] * len(mb), dtype=np.int32)
         sh = np.ascontiguousarray(shape if shape is not None else [0] * len(mb), dtype=np.int32)
         self._check(self._lib.lbm_set_launch_variant(self._h, _ip(mb), _ip(pe), _ip(sh), int(pdl)))
+
+    def set_load_history(self, every, capacity=1024):
+        """lbm_set_load_history: eq 30's coefficients and the mass into a device ring every
+        `every` coarse steps (0 stops)."""
+        self._check(self._lib.lbm_set_load_history(self._h, int(every), int(capacity)))
+
+    def load_history(self):
+        """lbm_get_load_history: the kept records, oldest first, as dicts."""
+        n = C.c_int()
+        self._check(self._lib.lbm_get_load_history(self._h, None, 0, C.byref(n)))
+        arr = (lbm_load_record * max(n.value, 1))()
+        self._check(self._lib.lbm_get_load_history(self._h, C.cast(arr, C.c_void_p), n.value, C.byref(n)))
+        return [{k: getattr(arr[i], k) for k, _ in lbm_load_record._fields_} for i in range(n.value)]
 
     def set_timeline(self, on=True):
         """lbm_set_timeline: per-block clock records in every launch of the step graphs."""

@@ -171,5 +171,6 @@ struct LoadsView {
 };
 void launch_loads(cudaStream_t st, const LoadsView &S, const RecView &R, float U, double *acc4);
 void launch_mass(cudaStream_t st, const LevelView &P, int p, double area, double *acc, int *status);
+void launch_hist_push(cudaStream_t st, const double *acc, double *ring, int slot, long long step, double chord);
 
 }  // namespace lbmdev

@@ -1264,6 +1264,27 @@ __global__ void __launch_bounds__(256) k_mass(LevelView P, int p, double area, d
     }
 }
 
+// one record of the load history (lbm_set_load_history): the step and eq 30's coefficients
+// from the loads' FP64 sums, formed as lbm_get_loads forms them, and the FP64 mass
+__global__ void k_hist_push(const double *acc, double *ring, int slot, long long step, double chord)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double *r = ring + 6 * (size_t)slot;
+        const double cdf = acc[0] / chord, cdp = acc[2] / chord;
+        r[0] = (double)step;
+        r[1] = acc[3] / chord;
+        r[2] = cdf + cdp;
+        r[3] = cdp;
+        r[4] = cdf;
+        r[5] = acc[4];
+    }
+}
+
+void launch_hist_push(cudaStream_t st, const double *acc, double *ring, int slot, long long step, double chord)
+{
+    k_hist_push<<<1, 32, 0, st>>>(acc, ring, slot, step, chord);
+}
+
 // ------------------------------------------------------------------ launchers
 // launch, with programmatic stream serialization when pdl is set (see griddep_wait)
 template <typename... Args>

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include <nvtx3/nvToolsExt.h>
 #include "device.cuh"
 #include "grid.hpp"
 
@@ -105,6 +106,11 @@ struct lbm_solver {
     lbmdev::ProlongBatchArgs pend;  // prolongations waiting for the next level-step launch
     // launch timeline (lbm_set_timeline): 3 clock readings per block of every launch of the
     // step graphs, records [tl_meta base, base + blocks) of a launch; meta 5 ints per launch
+    // load history (lbm_set_load_history): ring of hist_cap records of 6 doubles, one every
+    // hist_every coarse steps of lbm_step / lbm_step_async; hist_count records taken
+    double *d_hist = nullptr;
+    int hist_every = 0, hist_cap = 0, hist_alloc = 0;
+    long long hist_count = 0;
     unsigned long long *d_tl = nullptr;
     long long tl_cap = 0, tl_next = 0;
     int tl_on = 0, tl_graph = -1;
@@ -154,6 +160,15 @@ static lbm_status cuda_fail(lbm_solver *s, cudaError_t e, const char *where)
         cudaError_t _e = (call);                                     \
         if (_e != cudaSuccess) return cuda_fail(s, _e, #call);       \
     } while (0)
+
+// NVTX range over a scope: the library's calls and, outside graph capture, each launch of
+// the level schedule show up by name in a profiler's timeline (no-ops without a tool)
+struct NvtxRange {
+    explicit NvtxRange(const char *m) { nvtxRangePushA(m); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 static void *dalloc(lbm_solver *s, size_t bytes)
 {
@@ -219,6 +234,9 @@ static void free_all(lbm_solver *s)
     s->device_bytes = 0;
     s->geometry = false;
     s->d_tl = nullptr;
+    s->d_hist = nullptr;
+    s->hist_every = s->hist_cap = s->hist_alloc = 0;
+    s->hist_count = 0;
     s->tl_cap = s->tl_next = 0;
     s->tl_on = 0;
     s->tl_meta.clear();
@@ -279,6 +297,9 @@ static int tl_reserve(lbm_solver *s, int level, int kind, int blocks)
 static void flush_prolong(lbm_solver *s, cudaStream_t st, long long &nk)
 {
     if (s->pend.n == 0) return;
+    char nm[48];
+    snprintf(nm, sizeof nm, "prolong level %d (+%d)", s->pend_level, s->pend.n - 1);
+    NvtxRange range(s->tl_graph < 0 ? nm : "capture");
     mark_begin(s);
     const int base = tl_reserve(s, s->pend_level, 2, (int)s->pend_grid);
     unsigned long long *tl = base >= 0 ? s->d_tl : nullptr;
@@ -331,6 +352,9 @@ static void advance(lbm_solver *s, cudaStream_t st, int l, int restrict_up, long
     ls.pp = C ? s->parity[l - 1] : 0;
     ls.shape = s->shape[l];
     ls.status = s->d_status;
+    char nm[48];
+    snprintf(nm, sizeof nm, "level %d %s step", l, ls.p ? "odd" : "even");
+    NvtxRange range(s->tl_graph < 0 ? nm : "capture");
     {
         const int base = tl_reserve(s, l, ls.p, std::max(P.n_work_tiles, (P.n_work_warps + 1) / 2));
         ls.tl = base >= 0 ? s->d_tl : nullptr;
@@ -370,12 +394,16 @@ static lbm_status capture_graphs(lbm_solver *s)
     return LBM_OK;
 }
 
+static lbm_status enqueue_mass(lbm_solver *s);
+static void enqueue_history(lbm_solver *s);
+
 static lbm_status enqueue_steps(lbm_solver *s, int n)
 {
     for (int it = 0; it < n; it++) {
         CK(cudaGraphLaunch(s->graph[s->parity[0]], s->stream));
         s->parity[0] ^= 1;
         s->step++;
+        if (s->hist_every > 0 && s->step % s->hist_every == 0) enqueue_history(s);
     }
     return LBM_OK;
 }
@@ -389,6 +417,19 @@ static lbm_status enqueue_mass(lbm_solver *s)
         lbmdev::launch_mass(s->stream, s->lv[l].v, s->parity[l], area * area, s->d_acc + 4, s->d_status);
     }
     return LBM_OK;
+}
+
+// the loads of lbm_get_loads (wall state query, eq 29-30 sums, FP64 mass) into the next
+// slot of the load history, on the solver stream
+static void enqueue_history(lbm_solver *s)
+{
+    lbmdev::launch_wallfn(s->stream, s->lv[s->L - 1].v, s->parity[s->L - 1], s->rec, s->k);
+    cudaMemsetAsync(s->d_acc, 0, 4 * sizeof(double), s->stream);
+    lbmdev::launch_loads(s->stream, s->segs, s->rec, (float)s->U, s->d_acc);
+    enqueue_mass(s);
+    const double chord = s->cfg.chord / (s->cfg.h0 / (double)(1LL << (s->L - 1)));
+    lbmdev::launch_hist_push(s->stream, s->d_acc, s->d_hist, (int)(s->hist_count % s->hist_cap), s->step, chord);
+    s->hist_count++;
 }
 
 static lbm_status check_status(lbm_solver *s)
@@ -503,6 +544,7 @@ const char *lbm_last_error(const lbm_solver *s) { return s ? s->err.c_str() : "n
 
 lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off, int n_loops)
 {
+    NvtxRange range("lbm_set_geometry");
     if (!s || n_loops < 0 || (n_loops > 0 && (!xy || !loop_off))) return fail(s, LBM_ERR_INVALID_ARG, "bad geometry arguments");
     free_all(s);
     s->grid_ready = false;
@@ -968,6 +1010,7 @@ lbm_status lbm_set_wall_slip(lbm_solver *s, const double *uw, int n_loops)
 
 lbm_status lbm_step_async(lbm_solver *s, int n)
 {
+    NvtxRange range("lbm_step_async");
     if (!s) return LBM_ERR_INVALID_ARG;
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     if (s->off_schedule)
@@ -1041,6 +1084,7 @@ lbm_status lbm_get_ghost_relay(lbm_solver *s, int level, int *ij, double *vals, 
 
 lbm_status lbm_step(lbm_solver *s, int n)
 {
+    NvtxRange range("lbm_step");
     lbm_status st = lbm_step_async(s, n);
     if (st != LBM_OK) return st;
     return lbm_synchronize(s);
@@ -1247,6 +1291,7 @@ lbm_status lbm_set_fields(lbm_solver *s, int level, const double *rho, const dou
 
 lbm_status lbm_get_loads(lbm_solver *s, lbm_loads *out, double *cp_seg, double *cf_seg, int cap, int *n_seg)
 {
+    NvtxRange range("lbm_get_loads");
     if (!s || !out) return fail(s, LBM_ERR_INVALID_ARG, "null argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     const int nseg = s->segs.nseg;
@@ -1415,6 +1460,7 @@ lbm_status lbm_get_info(lbm_solver *s, lbm_info *out)
 
 lbm_status lbm_time_kernels(lbm_solver *s, int n, lbm_kernel_times *out)
 {
+    NvtxRange range("lbm_time_kernels");
     if (!s || !out || n < 0) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     std::memset(out, 0, sizeof *out);
@@ -1498,6 +1544,7 @@ static int no_persist(int sched) { return sched == LBM_SCHED_PERSIST ? LBM_SCHED
 
 lbm_status lbm_autotune(lbm_solver *s, int steps, lbm_tune_report *out)
 {
+    NvtxRange range("lbm_autotune");
     if (!s || !out || steps < 1) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
     if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
     static const int CAND_MB[LBM_TUNE_CANDIDATES] = {5, 6, 5, 6, 5, 6, 5, 6, 5, 6, 5, 6};
@@ -1892,6 +1939,43 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size)
     s->have_cl = h.have_cl != 0;
     s->last_cl = h.last_cl;
     return LBM_OK;
+}
+
+lbm_status lbm_set_load_history(lbm_solver *s, int every, int capacity)
+{
+    if (!s || every < 0 || (every > 0 && capacity < 1)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (s->planning) return fail(s, LBM_ERR_NO_GEOMETRY, "host-only handle");
+    if (every > 0 && capacity > s->hist_alloc) {
+        s->d_hist = (double *)dalloc(s, (size_t)capacity * 6 * sizeof(double));
+        if (!s->d_hist) { s->hist_alloc = 0; s->hist_every = 0; return fail(s, LBM_ERR_OOM, "load history"); }
+        s->hist_alloc = capacity;
+    }
+    if (every > 0) s->hist_cap = capacity;
+    s->hist_every = every;
+    s->hist_count = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_load_history(lbm_solver *s, lbm_load_record *out, int cap, int *n)
+{
+    if (!s || !n || (cap > 0 && !out)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->geometry) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    const long long kept = s->d_hist ? std::min<long long>(s->hist_count, s->hist_cap) : 0;
+    *n = (int)kept;
+    if (kept == 0 || cap <= 0) return LBM_OK;
+    if (kept > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    std::vector<double> h((size_t)s->hist_cap * 6);
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaMemcpy(h.data(), s->d_hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    const long long first = s->hist_count - kept;                    // oldest kept record
+    for (long long i = 0; i < kept; i++) {
+        const double *r = &h[(size_t)((first + i) % s->hist_cap) * 6];
+        lbm_load_record &o = out[i];
+        o.step = (long long)r[0];
+        o.CL = r[1]; o.CD = r[2]; o.CDp = r[3]; o.CDf = r[4]; o.mass = r[5];
+    }
+    return check_status(s);
 }
 
 lbm_status lbm_set_timeline(lbm_solver *s, int on)
