@@ -529,6 +529,28 @@ def profile_case(args):
     torch.cuda.nvtx.range_push("steps")
     s.step(args.steps)
     torch.cuda.nvtx.range_pop()
+    if args.timeline:
+        # in-graph launch times of the last run of each step graph (lbm_get_timeline)
+        s.set_timeline(True)
+        s.step(max(args.steps, 2))
+        tl = s.timeline()
+        L = cfg["levels"]
+        for g in (0, 1):
+            ev = [e for e in tl if e["graph"] == g]
+            if not ev:
+                continue
+            span = max(e["t_end_us"] for e in ev)
+            rows = {}
+            for e in ev:
+                key = f"prolong from level {e['level']}" if e["kind"] == 2 else f"level {e['level']} {'odd' if e['kind'] else 'even'}"
+                r = rows.setdefault(key, [0, 0.0])
+                r[0] += 1
+                r[1] += e["t_end_us"] - e["t_wait_us"]
+            busy = sum(r[1] for r in rows.values())
+            print(f"timeline graph {g}: span {span:.1f} us, launches {len(ev)}, between launches {span - busy:.1f} us")
+            for key in sorted(rows):
+                n, t = rows[key]
+                print(f"  {key:26s} launches {n:3d}  total {t:8.1f} us  mean {t / n:6.2f} us")
     print("profile case", args.profile_case, "ok", flush=True)
     s.close()
     return 0
@@ -613,6 +635,8 @@ def main():
     ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--profile-case", choices=["hbm_grid", "hbm_grid_laminar", "workload"], default=None)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch variant")
+    ap.add_argument("--timeline", action="store_true",
+                    help="profile case: also print the in-graph launch times (lbm_get_timeline) per level")
     ap.add_argument("--profile-variant", default="",
                     help="profile case: launch variant 'min_blocks,sched,shape' on every level (sched 0 tile "
                          "blocks, 1 persistent grid, 2 warp list) instead of autotuning")
