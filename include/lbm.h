@@ -351,6 +351,16 @@ lbm_status lbm_set_state(lbm_solver *s, const void *buf, size_t size);
 lbm_status lbm_set_launch_variant(lbm_solver *s, const int *min_blocks, const int *sched, const int *shape,
                                   int pdl);
 
+/* The level kernel's work lists of a level, in launch order (also on host-only handles):
+ * warps 0 gives the work tiles (tiles holding an active or ghost fluid cell), warps 1 the
+ * work warps (the 16 x 2-cell warps w of those tiles, cells x in [16 (w & 1), +16), y in
+ * {2 (w >> 1), +1} of the tile, that hold one); both ordered by cost class (a boundary node
+ * of the finest level 3, a band or coalescing cell 2, another active cell 1, ghosts only 0;
+ * non-increasing), tile order within a class.  out holds 3 ints per entry: the global cell
+ * indices i, j of the tile's first cell and the warp (-1 for tiles); with cap 0 only the
+ * count.  Errors: LBM_ERR_INVALID_ARG, LBM_ERR_NO_GEOMETRY. */
+lbm_status lbm_get_work_list(lbm_solver *s, int level, int warps, int *out, int cap, int *n);
+
 /* Load history.  With every > 0, lbm_step and lbm_step_async enqueue, after each coarse step
  * whose count is a multiple of every, what lbm_get_loads computes (the wall state query,
  * eq 29-30 with their FP64 sums, the FP64 mass) into the next slot of a device ring of

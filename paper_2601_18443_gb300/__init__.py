@@ -133,6 +133,7 @@ def library():
         "lbm_get_segment_map": ([vp, dp, ip, dp, C.c_int, ip], C.c_int),
         "lbm_get_wall_distance": ([vp, C.c_int, dp, C.c_int], C.c_int),
         "lbm_get_flags": ([vp, C.c_int, C.POINTER(C.c_uint), C.c_int], C.c_int),
+        "lbm_get_work_list": ([vp, C.c_int, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
@@ -396,6 +397,16 @@ class Solver:
         st = np.zeros((max(n.value, 1), 8))
         self._check(self._lib.lbm_get_wall_state(self._h, _dp(st), n.value, C.byref(n)))
         return st[:n.value]
+
+    def work_list(self, level, warps=False):
+        """lbm_get_work_list: (n, 3) int array of the level kernel's work tiles or warps in
+        launch order: global i, j of the tile's first cell, warp (-1 for tiles)."""
+        n = C.c_int()
+        w = int(bool(warps))
+        self._check(self._lib.lbm_get_work_list(self._h, level, w, None, 0, C.byref(n)))
+        out = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+        self._check(self._lib.lbm_get_work_list(self._h, level, w, out.ctypes.data_as(C.c_void_p), n.value, C.byref(n)))
+        return out[:n.value]
 
     def flags(self, level):
         """The level kernel's 32-bit flag word per cell of the level box."""

@@ -75,6 +75,8 @@ struct HostLevelDev {
     LevelView v;
     std::vector<uint32_t> flags;   // host copy
     std::vector<int> band_ij;      // global cell indices of the band cells, in band-index order
+    std::vector<int> work_tiles;   // host copies of the level kernel's work lists (cost order)
+    std::vector<int> work_warps;
 };
 
 }  // namespace
@@ -695,6 +697,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
             for (int k = 3; k >= 0; k--) wt.insert(wt.end(), cls_t[k].begin(), cls_t[k].end());
             v.work_tiles = upload(s, wt, ok);
             v.n_work_tiles = (int)wt.size();
+            H.work_tiles = wt;
         }
         {
             // warps (work shape 0: 16 x 2 cells) of the work tiles that hold an active or ghost
@@ -724,6 +727,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
             for (int k = 3; k >= 0; k--) ww.insert(ww.end(), cls_w[k].begin(), cls_w[k].end());
             v.work_warps = upload(s, ww, ok);
             v.n_work_warps = (int)ww.size();
+            H.work_warps = ww;
         }
         v.flags = upload(s, H.flags, ok);
         v.inv_d2 = upload(s, inv_d2, ok);
@@ -1208,6 +1212,25 @@ lbm_status lbm_get_flags(lbm_solver *s, int level, unsigned int *flags, int cap)
             const long sl = G.slot(i0 + i, j0 + j);
             flags[(long long)j * nx + i] = sl >= 0 ? fl[sl] : 0u;
         }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_work_list(lbm_solver *s, int level, int warps, int *out, int cap, int *n)
+{
+    if (!s || !n || (warps != 0 && warps != 1) || (cap > 0 && !out)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->grid_ready) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    if (level < 0 || level >= s->L) return fail(s, LBM_ERR_INVALID_ARG, "level out of range");
+    const lbmgrid::Level &G = s->g.lv[level];
+    const std::vector<int> &w = warps ? s->lv[level].work_warps : s->lv[level].work_tiles;
+    *n = (int)w.size();
+    if (cap <= 0) return LBM_OK;
+    if ((int)w.size() > cap) return fail(s, LBM_ERR_INVALID_ARG, "capacity too small");
+    for (size_t k = 0; k < w.size(); k++) {
+        const int t = warps ? w[k] >> 3 : w[k];
+        out[3 * k] = G.tile_x[t] * LBM_TX;
+        out[3 * k + 1] = G.tile_y[t] * LBM_TY;
+        out[3 * k + 2] = warps ? (w[k] & 7) : -1;
+    }
     return LBM_OK;
 }
 
