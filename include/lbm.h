@@ -408,6 +408,12 @@ lbm_status lbm_get_timeline(lbm_solver *s, lbm_launch_time *out, int cap, int *n
  * LBM_ERR_NO_GEOMETRY. */
 lbm_status lbm_set_prolong_merge(lbm_solver *s, int on, int *merged_levels);
 
+/* Per level l (indep[0 .. levels - 1]), 1 where the prolongation of level l may share a
+ * launch with that of level l - 1: 1 <= l <= levels - 2 and no band cell of level l has a
+ * ghost cell of level l among its eight neighbours.  Also on host-only handles.  Errors:
+ * LBM_ERR_INVALID_ARG (cap below the level count), LBM_ERR_NO_GEOMETRY. */
+lbm_status lbm_get_prolong_independence(lbm_solver *s, int *indep, int cap);
+
 /* Largest n_cells that lbm_level_mass_noalloc accepts (its fixed scratch holds 4096
  * per-block partial sums of at most 16384 cells each). */
 #define LBM_NOALLOC_MAX_CELLS 67108864LL

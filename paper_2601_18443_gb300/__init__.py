@@ -134,6 +134,7 @@ def library():
         "lbm_get_wall_distance": ([vp, C.c_int, dp, C.c_int], C.c_int),
         "lbm_get_flags": ([vp, C.c_int, C.POINTER(C.c_uint), C.c_int], C.c_int),
         "lbm_get_work_list": ([vp, C.c_int, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)], C.c_int),
+        "lbm_get_prolong_independence": ([vp, C.POINTER(C.c_int), C.c_int], C.c_int),
         "lbm_get_info": ([vp, C.POINTER(lbm_info)], C.c_int),
         "lbm_time_kernels": ([vp, C.c_int, C.POINTER(lbm_kernel_times)], C.c_int),
         "lbm_autotune": ([vp, C.c_int, C.POINTER(lbm_tune_report)], C.c_int),
@@ -397,6 +398,13 @@ class Solver:
         st = np.zeros((max(n.value, 1), 8))
         self._check(self._lib.lbm_get_wall_state(self._h, _dp(st), n.value, C.byref(n)))
         return st[:n.value]
+
+    def prolong_independence(self):
+        """lbm_get_prolong_independence: per level, whether its prolongation may share a launch
+        with that of the level above."""
+        out = (C.c_int * 16)()
+        self._check(self._lib.lbm_get_prolong_independence(self._h, out, 16))
+        return [bool(out[l]) for l in range(self.cfg["levels"])]
 
     def work_list(self, level, warps=False):
         """lbm_get_work_list: (n, 3) int array of the level kernel's work tiles or warps in

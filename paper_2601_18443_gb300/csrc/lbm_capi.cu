@@ -1215,6 +1215,14 @@ lbm_status lbm_get_flags(lbm_solver *s, int level, unsigned int *flags, int cap)
     return LBM_OK;
 }
 
+lbm_status lbm_get_prolong_independence(lbm_solver *s, int *indep, int cap)
+{
+    if (!s || !indep || cap < s->L) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");
+    if (!s->grid_ready) return fail(s, LBM_ERR_NO_GEOMETRY, "no geometry");
+    for (int l = 0; l < s->L; l++) indep[l] = s->prolong_indep[l] ? 1 : 0;
+    return LBM_OK;
+}
+
 lbm_status lbm_get_work_list(lbm_solver *s, int level, int warps, int *out, int cap, int *n)
 {
     if (!s || !n || (warps != 0 && warps != 1) || (cap > 0 && !out)) return fail(s, LBM_ERR_INVALID_ARG, "bad argument");

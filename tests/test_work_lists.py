@@ -76,3 +76,42 @@ def test_work_lists_cover_the_work_once_in_cost_order(name, warps):
         if l == L - 1:
             assert classes[0] == 3                              # boundary-node work comes first
     g.close()
+
+
+def _independent_levels(g, L):
+    """Recomputed from the flag words: level l (1 <= l <= L - 2) is independent of the level
+    above when no band cell has a ghost among its eight neighbours."""
+    out = []
+    for l in range(L):
+        if not 1 <= l <= L - 2:
+            out.append(False)
+            continue
+        i0, j0, nx, ny = g.level_box(l)
+        fl = g.flags(l).reshape(ny, nx).astype(np.int64)
+        ghost = np.pad((fl & KIND_MASK) == KIND_GHOST, 1)
+        band = (fl & FL_BAND) != 0
+        near = np.zeros((ny, nx), dtype=bool)
+        for dj in (-1, 0, 1):
+            for di in (-1, 0, 1):
+                if di or dj:
+                    near |= ghost[1 + dj:1 + dj + ny, 1 + di:1 + di + nx]
+        out.append(not np.any(band & near))
+    return out
+
+
+def test_prolongation_grouping_follows_the_band_and_ghost_layout():
+    # With exact distance bands a level's band cells lie `layers` of its cells inside its
+    # ghost layer, so every level with a parent and a child is independent here, down to the
+    # thinnest bands the wall-function stencil allows (6 layers); the host check guards the
+    # grouping against layouts where that does not hold
+    cases = [_case(n) for n in ("naca0012-5lvl", "polar-4lvl", "polar-5lvl")]
+    cfg, loops = W.naca0012_small(levels=5)
+    cases.append((dict(cfg, layers=6), loops))
+    for cfg, loops in cases:
+        g = pkg.Solver(cfg, host_only=True)
+        g.set_geometry(loops)
+        L = cfg["levels"]
+        got = g.prolong_independence()
+        assert got == _independent_levels(g, L)
+        assert got == [False] + [True] * (L - 2) + [False]
+        g.close()
