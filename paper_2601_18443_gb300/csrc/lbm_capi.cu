@@ -680,8 +680,11 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         {
             // work tiles in the same cost order as the warps below (a block's warps start
             // together, so the expensive tiles go first and the last blocks are cheap)
-            std::vector<int> cls_t[4];
-            for (const int t : G.work_tiles) {
+            const long nwt = (long)G.work_tiles.size();
+            std::vector<uint8_t> tcls(nwt, 0);
+#pragma omp parallel for schedule(static)
+            for (long m = 0; m < nwt; m++) {
+                const int t = G.work_tiles[m];
                 int cls = 0;
                 for (int c = 0; c < LBM_TILE; c++) {
                     const uint32_t f = H.flags[(size_t)t * LBM_TILE + c];
@@ -691,10 +694,13 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
                     if ((f & FL_BNODE) && l == L - 1) k = 3;
                     cls = std::max(cls, k);
                 }
-                cls_t[cls].push_back(t);
+                tcls[m] = (uint8_t)cls;
             }
             std::vector<int> wt;
-            for (int k = 3; k >= 0; k--) wt.insert(wt.end(), cls_t[k].begin(), cls_t[k].end());
+            wt.reserve(nwt);
+            for (int k = 3; k >= 0; k--)
+                for (long m = 0; m < nwt; m++)
+                    if (tcls[m] == k) wt.push_back(G.work_tiles[m]);
             v.work_tiles = upload(s, wt, ok);
             v.n_work_tiles = (int)wt.size();
             H.work_tiles = wt;
@@ -705,26 +711,30 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
             // warps with a boundary node (wall function), then with a band or coalescing cell
             // (explosion, coalescence), then with another active cell, then ghosts only (a
             // relay); tile order within each class
-            std::vector<int> cls_w[4];
-            for (const int t : G.work_tiles)
-                for (int w = 0; w < 8; w++) {
-                    int cls = -1;
-                    for (int c = 0; c < 32; c++) {
-                        const int lx = (w & 1) * 16 + (c & 15), ly = (w >> 1) * 2 + (c >> 4);
-                        const uint32_t f = H.flags[(size_t)t * LBM_TILE + ly * LBM_TX + lx];
-                        const uint32_t kd = f & FL_KIND_MASK;
-                        if (f & FL_SOLID) continue;
-                        if (kd == KIND_GHOST) cls = std::max(cls, 0);
-                        if (kd != KIND_ACTIVE) continue;
-                        int k = 1;
-                        if (f & (FL_BAND | (0xFFu << FL_COAL_SHIFT))) k = 2;
-                        if ((f & FL_BNODE) && l == L - 1) k = 3;
-                        cls = std::max(cls, k);
-                    }
-                    if (cls >= 0) cls_w[cls].push_back(t * 8 + w);
+            const long nwt8 = 8 * (long)G.work_tiles.size();
+            std::vector<int8_t> wcls(nwt8, -1);
+#pragma omp parallel for schedule(static)
+            for (long mw = 0; mw < nwt8; mw++) {
+                const int t = G.work_tiles[mw >> 3], w = (int)(mw & 7);
+                int cls = -1;
+                for (int c = 0; c < 32; c++) {
+                    const int lx = (w & 1) * 16 + (c & 15), ly = (w >> 1) * 2 + (c >> 4);
+                    const uint32_t f = H.flags[(size_t)t * LBM_TILE + ly * LBM_TX + lx];
+                    const uint32_t kd = f & FL_KIND_MASK;
+                    if (f & FL_SOLID) continue;
+                    if (kd == KIND_GHOST) cls = std::max(cls, 0);
+                    if (kd != KIND_ACTIVE) continue;
+                    int k = 1;
+                    if (f & (FL_BAND | (0xFFu << FL_COAL_SHIFT))) k = 2;
+                    if ((f & FL_BNODE) && l == L - 1) k = 3;
+                    cls = std::max(cls, k);
                 }
+                wcls[mw] = (int8_t)cls;
+            }
             std::vector<int> ww;
-            for (int k = 3; k >= 0; k--) ww.insert(ww.end(), cls_w[k].begin(), cls_w[k].end());
+            for (int k = 3; k >= 0; k--)
+                for (long mw = 0; mw < nwt8; mw++)
+                    if (wcls[mw] == k) ww.push_back(G.work_tiles[mw >> 3] * 8 + (int)(mw & 7));
             v.work_warps = upload(s, ww, ok);
             v.n_work_warps = (int)ww.size();
             H.work_warps = ww;
@@ -788,6 +798,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
                 return 0;
             };
             const std::vector<uint32_t> &fl = s->lv[L - 1].flags;
+#pragma omp parallel for schedule(static)
             for (int r = 0; r < nr; r++) {
                 const int t = bslot[r] / LBM_TILE, lx = bslot[r] % LBM_TX, ly = (bslot[r] % LBM_TILE) / LBM_TX;
                 for (int d = 1; d < 9; d++) {
@@ -832,7 +843,11 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
         const lbmgrid::Level &G = s->g.lv[l];
         const std::vector<uint32_t> &fl = s->lv[l].flags;
         static const int CX[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1}, CY[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
-        for (int t = 0; indep && t < G.ntiles; t++)
+        // (levels without a parent or a child are never grouped: no scan; each thread's copy
+        // of indep starts true and the reduction ands them into the outer value)
+        if (indep) {
+#pragma omp parallel for schedule(static) reduction(&& : indep)
+        for (int t = 0; t < G.ntiles; t++)
             for (int c = 0; indep && c < LBM_TILE; c++) {
                 if (!(fl[(size_t)t * LBM_TILE + c] & FL_BAND)) continue;
                 const int lx = c % LBM_TX, ly = c / LBM_TX;
@@ -848,6 +863,7 @@ lbm_status lbm_set_geometry(lbm_solver *s, const double *xy, const int *loop_off
                     if ((f & FL_KIND_MASK) == KIND_GHOST) indep = false;
                 }
             }
+        }
         s->prolong_indep[l] = indep;
     }
     // surface segments for the loads
