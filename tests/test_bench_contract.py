@@ -1,6 +1,6 @@
 """bench.py's JSON contract, checked on the CPU through the reference arm (the FP64 oracle
 on the host cores): one JSON line with the metric, the configuration, the CPU baseline and
-the end-to-end block the driver reads."""
+the end-to-end block."""
 import json
 import os
 import subprocess
