@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import platform
 import os
 import subprocess
 import sys
@@ -195,6 +196,63 @@ def run_oracle_sample(steps, warmup):
               f"{nu} node updates per coarse step, {steps} coarse steps after {warmup} warm-up, FP64 oracle, "
               f"{dt:.2f} s")
     return mlups, oracle.threads(), sample, dt
+
+
+def _host_cpu():
+    """The host's CPU model as /proc/cpuinfo names it (x86 'model name', else Arm part)."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+        for key in ("model name", "Model", "CPU part"):
+            for ln in txt.splitlines():
+                if ln.split(":")[0].strip() == key:
+                    return f"{key}: {ln.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_timing(args):
+    """The FP64 oracle's node-update rate on this host's cores: config[0] (6 levels to c/256)
+    over --oracle-steps0 coarse steps with all threads and with one, and with --oracle-full
+    the bench workload (6 levels to c/4096) over --oracle-steps1 coarse steps with all threads
+    (its grid build timed apart).  One JSON line; no GPU."""
+    import oracle
+
+    oracle.build()
+    allt = oracle.threads()
+    out = {"metric": "oracle_MLUPS", "unit": "MLUPS", "dtype": "f64", "host": _host_cpu(),
+           "machine": platform.machine(), "nproc": os.cpu_count(), "runs": []}
+
+    def run(cfg, loops, name, steps, threads):
+        oracle.set_threads(allt)
+        t0 = time.perf_counter()
+        s = oracle.Solver(cfg)
+        s.set_geometry(loops)
+        tg = time.perf_counter() - t0
+        nu = 0
+        for l in range(cfg["levels"]):
+            m = s.get_fields(l)["mask"]
+            nu += int(((m == 1) | (m == 2)).sum()) << l
+        oracle.set_threads(threads)
+        s.step(1)
+        t0 = time.perf_counter()
+        s.step(steps)
+        dt = time.perf_counter() - t0
+        s.close()
+        oracle.set_threads(allt)
+        out["runs"].append({"workload": name, "threads": threads, "coarse_steps": steps,
+                            "node_updates_per_step": nu, "seconds": round(dt, 2),
+                            "mlups": round(nu * steps / dt / 1e6, 3), "geometry_s": round(tg, 1)})
+        print(json.dumps(out["runs"][-1]), file=sys.stderr, flush=True)
+
+    cfg0, loops0 = W.naca0012_small()
+    run(cfg0, loops0, CPU_SAMPLE, args.oracle_steps0, allt)
+    run(cfg0, loops0, CPU_SAMPLE, args.oracle_steps0, 1)
+    if args.oracle_full:
+        cfg1, loops1 = W.naca0012_large()
+        run(cfg1, loops1, WORKLOAD, args.oracle_steps1, allt)
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def reference_arm(args, rank, world):
@@ -635,6 +693,12 @@ def main():
     ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--profile-case", choices=["hbm_grid", "hbm_grid_laminar", "workload"], default=None)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch variant")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="time the FP64 oracle on this host's cores (config[0] all threads and one thread; "
+                         "with --oracle-full also the bench workload); no GPU")
+    ap.add_argument("--oracle-steps0", type=int, default=1000)
+    ap.add_argument("--oracle-full", action="store_true")
+    ap.add_argument("--oracle-steps1", type=int, default=50)
     ap.add_argument("--timeline", action="store_true",
                     help="profile case: also print the in-graph launch times (lbm_get_timeline) per level")
     ap.add_argument("--profile-variant", default="",
@@ -653,6 +717,8 @@ def main():
     ap.add_argument("--serving-arms", default="", help="comma list of arms to run: batched,streams,one_at_a_time")
     ap.add_argument("--serving-dump", default=None, help="write per-request results to <path>.<arm>.json")
     args = ap.parse_args()
+    if args.oracle_timing:
+        return oracle_timing(args)
     if args.profile_case:
         return profile_case(args)
     if args.serving:

@@ -65,6 +65,8 @@ def lib():
             ip = C.POINTER(C.c_int)
             L.oracle_create.argtypes = [C.POINTER(Config), C.POINTER(C.c_void_p)]
             L.oracle_destroy.argtypes = [C.c_void_p]
+            L.oracle_set_threads.argtypes = [C.c_int]
+            L.oracle_set_threads.restype = None
             L.oracle_last_error.argtypes = [C.c_void_p]
             L.oracle_last_error.restype = C.c_char_p
             L.oracle_set_geometry.argtypes = [C.c_void_p, dp, ip, C.c_int]
@@ -322,3 +324,8 @@ class Solver:
 
 def threads() -> int:
     return lib().oracle_threads()
+
+
+def set_threads(n: int) -> None:
+    """OpenMP team size of the oracle's parallel regions started from this thread."""
+    lib().oracle_set_threads(int(n))

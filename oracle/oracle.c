@@ -554,6 +554,17 @@ int oracle_threads(void)
 #endif
 }
 
+/* OpenMP team size of the oracle's later parallel regions in the calling thread (n >= 1);
+ * for timing it on one core and on all of them */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 const char *oracle_last_error(const oracle_solver *s) { return s ? s->err : "null handle"; }
 
 int oracle_create(const oracle_config *cfg, oracle_solver **out)

@@ -67,6 +67,7 @@ int  oracle_probe_cells(const oracle_solver *s, int level, const int *ij, int n,
                         unsigned char *near, double *dist);
 int  oracle_probe_links(const oracle_solver *s, const int *ijd, int n, double *q);
 int  oracle_threads(void);
+void oracle_set_threads(int n);
 
 /* building blocks exported for the closed-form pins */
 double oracle_wf_uplus(double yplus);                      /* eq 22 */

@@ -24,3 +24,17 @@ def test_reference_arm_prints_one_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_oracle_timing_reports_all_threads_and_one():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-timing", "--oracle-steps0", "2"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["metric"] == "oracle_MLUPS" and d["dtype"] == "f64" and d["nproc"] >= 1 and d["host"]
+    runs = d["runs"]
+    assert [x["threads"] for x in runs][1:] == [1] and runs[0]["threads"] >= 1
+    for x in runs:
+        assert x["coarse_steps"] == 2 and x["node_updates_per_step"] == 207262 and x["mlups"] > 0
