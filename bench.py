@@ -312,7 +312,8 @@ def gpu_arm(args, rank, world, dist):
         # three-element high-lift case, 8 levels to c/8192 (555M node updates per coarse
         # step, 22 ms each): a few timed steps; the extra measurements are skipped.  Started
         # impulsively it diverges after about 35 coarse steps, so the autotuner times one
-        # coarse step per candidate (14 steps) and 10 steps are timed after 3 warm-up steps.
+        # coarse step per candidate on a checkpoint of the initial state, the solve is
+        # rewound to it, and 10 steps are timed after 3 warm-up steps.
         cfg, loops = W.highlift_3element()
         args.steps, args.warmup, tune_steps = min(args.steps, 10), 3, 1
         args.no_cpu_baseline = args.no_hbm_grid = args.no_precision_forms = True
@@ -323,7 +324,14 @@ def gpu_arm(args, rank, world, dist):
     s.set_geometry(loops)
     # launch autotuner (per-level register budget, grid schedule, work shape, PDL on/off);
     # its steps are untimed
-    tune = None if args.no_autotune else s.autotune(tune_steps)
+    if args.no_autotune:
+        tune = None
+    elif hl:
+        blob = s.get_state()
+        tune = s.autotune(tune_steps)
+        s.set_state(blob)        # the tuned launch form stays; the steps start again from 0
+    else:
+        tune = s.autotune(tune_steps)
     info = s.info()
     nu_step = info["node_updates_per_step"]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
