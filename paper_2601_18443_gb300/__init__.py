@@ -101,7 +101,25 @@ def library():
         return _lib
     if not os.path.exists(_build_ext.SO):
         raise RuntimeError("liblbm.so is not built: run __graft_entry__.build() (the CUDA library is required)")
-    L = C.CDLL(_build_ext.SO)
+    _lib = _load(_build_ext.SO)
+    return _lib
+
+
+_lib_check = None
+
+
+def checked_library():
+    """liblbm_check.so, the bounds-checked build (built on first use): every index the level
+    step follows from a table is checked on the device, and one outside its buffer makes the
+    next synchronising call fail.  Pass it as Solver(..., library=checked_library())."""
+    global _lib_check
+    if _lib_check is None:
+        _lib_check = _load(_build_ext.build(bounds_check=True))
+    return _lib_check
+
+
+def _load(path):
+    L = C.CDLL(path)
     vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
     sig = {
         "lbm_create": ([C.POINTER(lbm_config), C.POINTER(vp)], C.c_int),
@@ -154,7 +172,6 @@ def library():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = res
-    _lib = L
     return L
 
 
@@ -219,8 +236,9 @@ class Solver:
     grid tables on the host and answers the table queries (level_box, mask,
     wall_distance, cut_links, wall_records) on machines without a GPU."""
 
-    def __init__(self, cfg: dict, stream=None, torch_allocator: bool = False, host_only: bool = False):
-        self._lib = library()
+    def __init__(self, cfg: dict, stream=None, torch_allocator: bool = False, host_only: bool = False,
+                 library=None):
+        self._lib = library if library is not None else globals()["library"]()
         c = lbm_config()
         for name, _ in lbm_config._fields_:
             if name in ("cuda_stream", "dev_alloc", "dev_free", "alloc_ctx"):

@@ -84,6 +84,7 @@ struct StepConsts {
 // for a kernel that waits on a flag with an iteration limit; no kernel here waits.
 #define LBM_STATUS_NONFINITE 1
 #define LBM_STATUS_TIMEOUT 2
+#define LBM_STATUS_BOUNDS 4     // a table-derived index left its buffer (LBM_BOUNDS_CHECK builds)
 
 // What one launch of the fused level kernel does besides the level's own update.
 struct LevelStep {

@@ -173,6 +173,27 @@ __device__ __forceinline__ void tl_end(unsigned long long *tl, int base)
     tl_mark(tl, base, 2);
 }
 
+// ------------------------------------------------------------------ bounds-checked builds
+// With LBM_BOUNDS_CHECK every index the level step follows from a table (the work lists,
+// tile neighbours, children and parents, the aux word, the wall stencils) is checked
+// against its buffer: one outside it sets LBM_STATUS_BOUNDS in the status word (when the
+// caller has one) and is replaced by 0, so that the access stays inside the buffer and no
+// lane leaves its warp early; the host then fails the next synchronising call.  The default
+// build compiles none of it.
+__device__ __forceinline__ int checked_index(int i, int n, int *status)
+{
+#ifdef LBM_BOUNDS_CHECK
+    if (i < 0 || i >= n) {
+        if (status) atomicOr(status, LBM_STATUS_BOUNDS);
+        return 0;
+    }
+#else
+    (void)n;
+    (void)status;
+#endif
+    return i;
+}
+
 // ------------------------------------------------------------------ SA-neg constants (Sec 2.2)
 #define SA_CB1 0.1355f
 #define SA_CB2 0.622f
@@ -418,7 +439,7 @@ __device__ float wf_utau(float ut, float y_nu, float guess)
 // queries leave the trajectory unchanged, and only queries (!keep_start) write the
 // record's state arrays.
 __device__ void wall_record(const LevelView &P, int p, const RecView &R, const StepConsts &k, int r, bool keep_start,
-                            float &drW, float &uWx, float &uWy, float &chiB)
+                            float &drW, float &uWx, float &uWy, float &chiB, int *status = nullptr)
 {
     const float *dr = P.drho[p], *ux = P.ux[p], *uy = P.uy[p];
     // step 1: rho_R and u_R as fixed weighted sums over the 16-entry stencil (unused
@@ -435,7 +456,7 @@ __device__ void wall_record(const LevelView &P, int p, const RecView &R, const S
         const float ra[4] = {wrv.x, wrv.y, wrv.z, wrv.w}, ua[4] = {wuv.x, wuv.y, wuv.z, wuv.w};
 #pragma unroll
         for (int m = 0; m < 4; m++) {
-            const int s = sa[m];
+            const int s = checked_index(sa[m], P.ns, status);
             drR += ra[m] * dr[s]; uR += ua[m] * ux[s]; vR += ua[m] * uy[s];
         }
     }
@@ -568,8 +589,9 @@ __device__ __forceinline__ void put_obuf(const StepConsts &k, int par, uint32_t 
 // nothing, so their share of the next coalescence is this value too.
 template <typename T>
 __device__ __forceinline__ void explode_band(const LevelView &P, const LevelView &F, const StepConsts &k, int t, int lx,
-                                             int ly, uint32_t fl, int b, const float o[9])
+                                             int ly, uint32_t fl, int b, const float o[9], int *ls_status = nullptr)
 {
+    b = checked_index(b, P.n_band, ls_status);
     float *eb = P.ebuf + b * 9;
 #pragma unroll
     for (int q = 0; q < 9; q++) eb[q] = o[q];
@@ -582,8 +604,9 @@ __device__ __forceinline__ void explode_band(const LevelView &P, const LevelView
             for (int q = 0; q < 9; q++) gb[q] = o[q];
         }
     }
-    const int ct = P.child[t * 4 + ((2 * ly) >> 3) * 2 + ((2 * lx) >> 5)];
+    int ct = P.child[t * 4 + ((2 * ly) >> 3) * 2 + ((2 * lx) >> 5)];
     if (ct < 0) return;
+    ct = checked_index(ct, F.ntiles, ls_status);
     const Lat<T> LF{static_cast<T *>(F.f), F.ns, k.pshift};
     const int cx0 = (2 * lx) & (LBM_TX - 1), cy0 = (2 * ly) & (LBM_TY - 1);
 #pragma unroll
@@ -594,7 +617,9 @@ __device__ __forceinline__ void explode_band(const LevelView &P, const LevelView
             const int nx = ax + cxq(q), ny = ay + cyq(q);
             const int sx = nx < 0 ? 0 : (nx >= LBM_TX ? 2 : 1), sy = ny < 0 ? 0 : (ny >= LBM_TY ? 2 : 1);
             const int tt = (sx == 1 && sy == 1) ? ct : __ldg(F.nbr + ct * 9 + dir_of3(sy * 3 + sx));
-            if (tt >= 0) LF.st(q, tt * LBM_TILE + (ny & (LBM_TY - 1)) * LBM_TX + (nx & (LBM_TX - 1)), q, o[q]);
+            if (tt >= 0)
+                LF.st(q, checked_index(tt, F.ntiles, ls_status) * LBM_TILE + (ny & (LBM_TY - 1)) * LBM_TX + (nx & (LBM_TX - 1)),
+                      q, o[q]);
         }
     }
 }
@@ -629,7 +654,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         // populations stay in the cell, moved to the slots an odd step reads; odd sub-step:
         // the pulled populations go to the parent's coalescence buffer.  Where the upstream
         // cell is not fluid the ghost keeps its own value, the parent's exploded one.
-        const int ax = aux_of();
+        const int ax = checked_index(aux_of(), 4 * C.n_band, ls.status);
         const float *eb = C.ebuf + (ax >> 2) * 9;
         const uint32_t keep = fl >> FL_KEEP_SHIFT;
         if (!ODD) {
@@ -644,7 +669,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
             gb[0] = L.ld(0, slot, 0);
 #pragma unroll
             for (int q = 1; q < 9; q++) {
-                const int s = nb_slot(nb3, lx, ly, -cxq(q), -cyq(q));
+                const int s = checked_index(nb_slot(nb3, lx, ly, -cxq(q), -cyq(q)), P.ns, ls.status);
                 gb[q] = (keep >> (q - 1) & 1) || s < 0 ? eb[q] : L.ld(oppq(q), s, q);
             }
         }
@@ -653,14 +678,18 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         const bool bnode = WALL && (fl & FL_BNODE);
         int nbs[9];
         const unsigned present = neighbours(nb3, lx, ly, slot, nbs);
+#ifdef LBM_BOUNDS_CHECK
+#pragma unroll
+        for (int q = 1; q < 9; q++) nbs[q] = checked_index(nbs[q], P.ns, ls.status);
+#endif
         int gi = 0, gj = 0;
         if (edge) { gi = P.tile_x[t] * LBM_TX + lx; gj = P.tile_y[t] * LBM_TY + ly; }
         // ---- wall function of the boundary node (Sec 2.3), fields at time t
         float drW = 0.f, uWx = 0.f, uWy = 0.f, chiB = 0.f;
         int r = -1;
         if (bnode) {
-            r = aux_of();
-            wall_record(P, p, R, k, r, true, drW, uWx, uWy, chiB);
+            r = checked_index(aux_of(), R.n, ls.status);
+            wall_record(P, p, R, k, r, true, drW, uWx, uWy, chiB, ls.status);
         }
         // ---- SA-neg update of chi (Sec 2.2), fields at time t
         float chin;
@@ -712,7 +741,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         const uint32_t special = fl & (0xFFu << FL_COAL_SHIFT | 0xFFu << FL_CUT_SHIFT);
         if (CHILD && (fl & (0xFFu << FL_COAL_SHIFT))) {
             // coalescence: mean of what the four ghost children pulled in the fine level's odd sub-step
-            const float *gb = P.gbuf + aux_of() * 36;
+            const float *gb = P.gbuf + checked_index(aux_of(), P.n_band, ls.status) * 36;
 #pragma unroll
             for (int q = 1; q < 9; q++)
                 if (fl & (1u << (FL_COAL_SHIFT + q - 1)))
@@ -784,7 +813,7 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
         }
         if (ls.is_level0 && k.level0_edges && (fl & (FL_OUTLET | FL_OUTLET2)))
             put_obuf(k, p ^ 1, fl, P.tile_y[t] * LBM_TY + ly, o);
-        if (CHILD && (fl & FL_BAND)) explode_band<T>(P, F, k, t, lx, ly, fl, aux_of(), o);
+        if (CHILD && (fl & FL_BAND)) explode_band<T>(P, F, k, t, lx, ly, fl, aux_of(), o, ls.status);
         valid = true;
         n_dr = drho; n_ux = ux; n_uy = uy; n_chi = chin;
     }
@@ -823,7 +852,11 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
             head = !(lx & 1) && !(ly & 1);
         }
         if (head && kind == KIND_ACTIVE) {
+#ifdef LBM_BOUNDS_CHECK
+            const int pt = P.parent[t] < 0 ? -1 : checked_index(P.parent[t], C.ntiles, ls.status);
+#else
             const int pt = P.parent[t];
+#endif
             const int n = (int)a5;
             if (pt >= 0 && n > 0) {
                 const int px = (P.tile_x[t] & 1) * (LBM_TX / 2) + (lx >> 1);
@@ -858,7 +891,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
     int *nb3 = nb3w[c >> 5];
     tl_mark(ls.tl, ls.tl_base, 0);
     if constexpr (!PERSIST) {
-        const int t = P.work_tiles[blockIdx.x];
+        const int t = checked_index(P.work_tiles[blockIdx.x], P.ntiles, ls.status);
         if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
         __syncwarp();
         griddep_launch();
@@ -872,7 +905,7 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
         int wt = blockIdx.x;
         uint32_t fl_next = 0;
         if (wt < P.n_work_tiles) {
-            const int t0 = P.work_tiles[wt];
+            const int t0 = checked_index(P.work_tiles[wt], P.ntiles, ls.status);
             if (lane < 9) nb3[lane] = P.nbr[t0 * 9 + dir_of3(lane)];
             fl_next = __ldg(P.flags + t0 * LBM_TILE + cell);
         }
@@ -881,10 +914,10 @@ __global__ void __launch_bounds__(256, MINB) k_level(LevelView P, LevelView F, L
         griddep_wait();
         tl_mark(ls.tl, ls.tl_base, 1);
         for (; wt < P.n_work_tiles; wt += gridDim.x) {
-            const int t = P.work_tiles[wt];
+            const int t = checked_index(P.work_tiles[wt], P.ntiles, ls.status);
             const uint32_t fl = fl_next;
             if (wt + (int)gridDim.x < P.n_work_tiles)
-                fl_next = __ldg(P.flags + P.work_tiles[wt + gridDim.x] * LBM_TILE + cell);
+                fl_next = __ldg(P.flags + checked_index(P.work_tiles[wt + gridDim.x], P.ntiles, ls.status) * LBM_TILE + cell);
             if (wt != (int)blockIdx.x) {
                 __syncwarp();
                 if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
@@ -923,7 +956,7 @@ __global__ void __launch_bounds__(WPB * 32, (MINB == 6 ? 48 : 40) / WPB)
     tl_mark(ls.tl, ls.tl_base, 0);
     if (have) {
         const int e = __ldg(P.work_warps + w);
-        t = e >> 3;
+        t = checked_index(e >> 3, P.ntiles, ls.status);
         cell_of_thread((e & 7) * 32 + lane, lx, ly, 0);
         if (lane < 9) nb3[lane] = P.nbr[t * 9 + dir_of3(lane)];
     }
@@ -954,7 +987,7 @@ __global__ void __launch_bounds__(256, 5) k_level_batch(const __grid_constant__ 
     int lx, ly;
     cell_of_thread(c, lx, ly, 0);
     int *nb3 = nb3w[c >> 5];
-    const int t = d.P.work_tiles[blockIdx.x - d.first_block];
+    const int t = checked_index(d.P.work_tiles[blockIdx.x - d.first_block], d.P.ntiles, d.ls.status);
     if (lane < 9) nb3[lane] = d.P.nbr[t * 9 + dir_of3(lane)];
     __syncwarp();
     griddep_launch();

@@ -440,6 +440,8 @@ static lbm_status check_status(lbm_solver *s)
     CK(cudaMemcpyAsync(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     if (st & LBM_STATUS_TIMEOUT) return fail(s, LBM_ERR_TIMEOUT, "a device wait reached its limit");
+    if (st & LBM_STATUS_BOUNDS)
+        return fail(s, LBM_ERR_CUDA, "a device index left its buffer (caught by the bounds-checked build)");
     if (st & LBM_STATUS_NONFINITE) return fail(s, LBM_ERR_DIVERGED, "diverged (non-finite field)");
     if (st) return fail(s, LBM_ERR_CUDA, "device status word set");
     return LBM_OK;
