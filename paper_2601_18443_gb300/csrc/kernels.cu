@@ -669,7 +669,8 @@ __device__ __forceinline__ void level_tile(const LevelView &P, const LevelView &
             gb[0] = L.ld(0, slot, 0);
 #pragma unroll
             for (int q = 1; q < 9; q++) {
-                const int s = checked_index(nb_slot(nb3, lx, ly, -cxq(q), -cyq(q)), P.ns, ls.status);
+                int s = nb_slot(nb3, lx, ly, -cxq(q), -cyq(q));          // -1: no upstream tile
+                if (s >= 0) s = checked_index(s, P.ns, ls.status);
                 gb[q] = (keep >> (q - 1) & 1) || s < 0 ? eb[q] : L.ld(oppq(q), s, q);
             }
         }
