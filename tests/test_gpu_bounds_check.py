@@ -11,6 +11,7 @@ from paper_2601_18443_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 POP_TOL = 1e-6          # the two builds may schedule the FP32 arithmetic differently
+POP_TOL_16 = 5e-4       # with 16-bit storage such a difference can move a stored value by one unit
 
 
 def _case(name):
@@ -41,7 +42,7 @@ def test_checked_build_reports_nothing_and_matches(name, sched):
     for l in range(L):
         x, y = a.get_populations(l), b.get_populations(l)
         assert np.array_equal(np.isnan(x), np.isnan(y)), l
-        assert np.nanmax(np.abs(x - y)) <= POP_TOL, l
+        assert np.nanmax(np.abs(x - y)) <= (POP_TOL if cfg.get("store", 0) == 0 else POP_TOL_16), l
     blob = b.get_state()                    # the checkpoint path through the checked build
     b.set_state(blob)
     b.step(2)
