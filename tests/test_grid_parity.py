@@ -76,7 +76,9 @@ def test_host_only_handle_refuses_device_work():
     assert e.value.code == -4
     g.set_geometry(loops)
     for call in (lambda: g.step(1), lambda: g.get_fields(0), lambda: g.get_loads(), lambda: g.get_state(),
-                 lambda: g.get_populations(0), lambda: g.wall_state(), lambda: g.info(), lambda: g.autotune(1)):
+                 lambda: g.get_populations(0), lambda: g.wall_state(), lambda: g.info(), lambda: g.autotune(1),
+                 lambda: g.set_timeline(True), lambda: g.set_load_history(5, 8),
+                 lambda: g.set_prolong_merge(False), lambda: g.set_launch_variant([5] * 6, 1, [3] * 6)):
         with pytest.raises(pkg.LBMError) as e:
             call()
         assert e.value.code == -4
